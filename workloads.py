@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs shaped like the paper's test problems.
+
+This module is shared by the CUDA path's tests/bench and by the CPU oracle.  It
+holds none of the method's arithmetic: it only draws meshes, cross sections,
+sources and Legendre moment shapes from seeded generators (NumPy PCG64, base
+seed 20104559, one stream per workload) and returns them as plain arrays.
+
+A problem is a dict with keys
+  dim            2 or 3
+  ncell          (nx, ny[, nz])
+  lo, hi         box corners (3 floats each; z ignored in 2D)
+  sigma_t        float64[C]  total cross section per cell
+  sigma_s        float64[C]  scatter cross section sigma_{s,0} per cell
+  N              Legendre order of the scatter expansion
+  fmom           float64[N+1] moment shape f_n (sigma_{s,n} = sigma_s * f_n), f_0 = 1
+  q              float64[C]  isotropic volumetric source (scalar emission density)
+  boundary       list of 2*dim (kind, value): kind 0 vacuum, 1 isotropic inflow
+                 of angular flux `value`; face f = 2*axis + side (side 1 = high)
+  basis          "lin" or "const"
+  level          uniform angular level of the finest mesh
+  mg             dict(nlevels, Nr (per level, finest first), nu_pre, nu_post,
+                 coarse_sweeps)
+  tol, restart   GMRES stop tolerance on ||r||/||b|| and restart length
+Cells are numbered c = ix + nx*(iy + ny*iz).
+"""
+import numpy as np
+
+BASE_SEED = 20104559
+
+
+def _rng(k):
+    return np.random.Generator(np.random.PCG64([BASE_SEED, k]))
+
+
+def hg_moments(g, N):
+    """Henyey-Greenstein Legendre moment shape f_n = g^n, n = 0..N."""
+    return np.array([g ** n for n in range(N + 1)], dtype=np.float64)
+
+
+def _central_source(dim, ncell, lo, hi, width, strength=1.0):
+    """Unit isotropic source in the centred box of side `width` (cell-aligned
+    when the mesh is)."""
+    nx, ny = ncell[0], ncell[1]
+    nz = ncell[2] if dim == 3 else 1
+    q = np.zeros(nx * ny * nz)
+    c_lo = [0.5 * (lo[e] + hi[e]) - 0.5 * width for e in range(dim)]
+    c_hi = [0.5 * (lo[e] + hi[e]) + 0.5 * width for e in range(dim)]
+    for iz in range(nz):
+        for iy in range(ny):
+            for ix in range(nx):
+                idx = (ix, iy, iz)
+                inside = True
+                for e in range(dim):
+                    h = (hi[e] - lo[e]) / ncell[e]
+                    mid = lo[e] + (idx[e] + 0.5) * h
+                    inside &= c_lo[e] < mid < c_hi[e]
+                if inside:
+                    q[ix + nx * (iy + ny * iz)] = strength
+    return q
+
+
+def problem(dim, ncell, sigma_t, sigma_s, N, fmom, q, level, basis="lin",
+            boundary=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), mg=None,
+            tol=1e-8, restart=20):
+    if boundary is None:
+        boundary = [(0, 0.0)] * (2 * dim)
+    return dict(dim=dim, ncell=tuple(int(n) for n in ncell), lo=tuple(lo),
+                hi=tuple(hi), sigma_t=np.asarray(sigma_t, dtype=np.float64),
+                sigma_s=np.asarray(sigma_s, dtype=np.float64), N=int(N),
+                fmom=np.asarray(fmom, dtype=np.float64),
+                q=np.asarray(q, dtype=np.float64), boundary=list(boundary),
+                basis=basis, level=int(level), mg=mg, tol=tol, restart=restart)
+
+
+def config1_square16(level=1):
+    """2D unit square, 16x16 cells, level-1 angular mesh (32 patches), HG
+    g = 0.8 at order 8, sigma_t = 1, sigma_s = 0.9, unit source in the centred
+    0.25 x 0.25 square, vacuum, tol 1e-8, GMRES(20)."""
+    nc = (16, 16)
+    C = 256
+    q = _central_source(2, nc, (0, 0, 0), (1, 1, 1), 0.25)
+    mg = dict(nlevels=2, Nr=[8, 4], nu_pre=1, nu_post=1, coarse_sweeps=10)
+    return problem(2, nc, np.ones(C), np.full(C, 0.9), 8, hg_moments(0.8, 8), q,
+                   level, mg=mg)
+
+
+def checkerboard(n, block, seed_k):
+    """Material index per cell: Bernoulli(0.5) per block x block tile."""
+    rng = _rng(seed_k)
+    nb = (n + block - 1) // block
+    tiles = rng.integers(0, 2, size=(nb, nb))
+    mat = np.empty(n * n, dtype=np.int64)
+    for iy in range(n):
+        for ix in range(n):
+            mat[ix + n * iy] = tiles[iy // block, ix // block]
+    return mat
+
+
+def config2_checkerboard(n=128, level=3, N=16, block=16, nlevels=3, Nr=4):
+    """2D unit square, n x n cells, two-material checkerboard of block x block
+    tiles (seeded), materials (sigma_t, c) = (1, 0.5) and (10, 0.99), HG
+    g = 0.9 at order N, centred unit source of side 0.25, vacuum, angular
+    level `level`, `nlevels`-level multigrid with coarse order Nr."""
+    mat = checkerboard(n, block, 2)
+    st = np.where(mat == 0, 1.0, 10.0)
+    ss = np.where(mat == 0, 0.5, 9.9)
+    q = _central_source(2, (n, n), (0, 0, 0), (1, 1, 1), 0.25)
+    mg = dict(nlevels=nlevels, Nr=[N] + [Nr] * (nlevels - 1), nu_pre=1, nu_post=1,
+              coarse_sweeps=10)
+    return problem(2, (n, n), st, ss, N, hg_moments(0.9, N), q, level, mg=mg)
+
+
+def config3_cube(n=32, level=2, N=32):
+    """3D unit cube, n^3 cells, per-cell sigma_t ~ lognormal(0, 0.5) (seeded),
+    sigma_s = 0.9 sigma_t, HG g = 0.95 at order N, centred unit source of
+    side 0.25, vacuum, angular level `level`."""
+    rng = _rng(3)
+    C = n ** 3
+    st = np.exp(rng.normal(0.0, 0.5, size=C))
+    ss = 0.9 * st
+    q = _central_source(3, (n, n, n), (0, 0, 0), (1, 1, 1), 0.25)
+    mg = dict(nlevels=min(3, level + 1), Nr=[N] + [9] * 2, nu_pre=1, nu_post=1,
+              coarse_sweeps=10)
+    mg["Nr"] = mg["Nr"][:mg["nlevels"]]
+    return problem(3, (n, n, n), st, ss, N, hg_moments(0.95, N), q, level, mg=mg)
+
+
+def random_problem(dim, ncell, level, N, seed_k, basis="lin", g=0.8,
+                   inflow=None):
+    """Small random problem for parity tests: lognormal sigma_t, scatter ratio
+    U[0.3, 0.95], random non-negative source; optional isotropic inflow on
+    every face."""
+    rng = _rng(1000 + seed_k)
+    C = int(np.prod(ncell))
+    st = np.exp(rng.normal(0.0, 0.7, size=C))
+    ss = st * rng.uniform(0.3, 0.95, size=C)
+    q = rng.uniform(0.0, 1.0, size=C)
+    bnd = None
+    if inflow is not None:
+        bnd = [(1, inflow)] * (2 * dim)
+    return problem(dim, ncell, st, ss, N, hg_moments(g, N), q, level, basis=basis,
+                   boundary=bnd)
+
+
+def random_vector(shape, seed_k, dtype=np.float64):
+    """Seeded standard-normal test vector."""
+    return _rng(5000 + seed_k).standard_normal(shape).astype(dtype)
