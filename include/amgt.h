@@ -1,0 +1,184 @@
+/*
+ * amgt.h -- C ABI of the GB300 (sm_103a) angular-multigrid DG transport library.
+ *
+ * The library solves the steady mono-energetic linear Boltzmann equation
+ *     Omega . grad phi + sigma_t phi = Q,  phi = phi_in on inflow boundaries
+ * (Lathouwers & Perko, arXiv 2010.04559, Sec. 2, Eq. LBE) discretised by
+ * discontinuous Galerkin in space (Q1 on axis-aligned quads/hexes) and in
+ * angle (spherical patches, Const or Lin basis; Sec. 2.1-2.3), with the
+ * Legendre-expanded scatter source of Sec. 4.2 and the angular multigrid
+ * preconditioner of Sec. 4 (Fig. lmg) inside restarted GMRES.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Cells: c = ix + nx*(iy + ny*iz).  Spatial nodes of a cell: i = a + 2b + 4c
+ * for the corner (a, b, c) in {0,1}^dim, x fastest; s = 2^dim nodes.
+ * Angular mesh: octant o = 4*bx + 2*by + bz (bit 1 = negative axis sign),
+ * vertices (sx e_x, sy e_y, sz e_z); a patch (a, b, c) splits into
+ * (a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca) with ab = (a+b)/|a+b|;
+ * patches are numbered depth first.  Lin function m of a patch is the nodal
+ * function of its vertex m; Const has one function.  a = 3 (Lin) or 1.
+ * Vectors: psi[Nsdof][Nadof] row major, sdof = c*s + i, adof = q*a + m
+ * (Eq. Expansion).  Multigrid level k = 0 is the finest angular mesh T_L,
+ * level k is T_{L-k}.
+ *
+ * Ownership: set_* calls copy their inputs; the context owns every table and
+ * workspace; the caller owns every buffer it passes.  Device pointers passed
+ * to amgt_op_* are read/written on the context's stream, asynchronously.
+ * Errors: every call returns an amgt_status and never throws across the
+ * ABI; amgt_last_error() gives the message of the last failing call.  A
+ * context is not thread safe; use one per host thread / stream.
+ */
+#ifndef AMGT_H
+#define AMGT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amgt_ctx amgt_ctx;
+
+typedef enum {
+  AMGT_OK = 0,
+  AMGT_ERR_ARG = -1,            /* invalid argument or call order            */
+  AMGT_ERR_CUDA = -2,           /* a CUDA runtime call failed                */
+  AMGT_ERR_NOMEM = -3,          /* device allocation failed                  */
+  AMGT_ERR_NOT_CONVERGED = -4,  /* GMRES reached maxit above tol             */
+  AMGT_ERR_BREAKDOWN = -5,      /* Krylov breakdown without convergence      */
+  AMGT_ERR_NAN = -6,            /* NaN/Inf met in a residual                 */
+  AMGT_ERR_DEVICE_TIMEOUT = -7, /* a bounded device-side wait gave up        */
+  AMGT_ERR_STATE = -8,          /* problem not fully specified               */
+  AMGT_ERR_UNSUPPORTED = -9     /* configuration outside the kernels' scope  */
+} amgt_status;
+
+/* element types of device buffers passed to amgt_op_* */
+#define AMGT_F64 0      /* double                                              */
+#define AMGT_F32 1      /* float                                               */
+#define AMGT_F32_BF16TC 2 /* float in/out, scatter contraction on BF16 tensor
+                             cores with FP32 accumulation (amgt_op_scatter)   */
+
+/* preconditioners and precision modes of amgt_solve */
+#define AMGT_PREC_NONE 0
+#define AMGT_PREC_SWEEP 1     /* M^-1 = L^-1, Krylov-accelerated source iteration (Sec. 3) */
+#define AMGT_PREC_MG 2        /* linear V-cycle of Fig. lmg (Sec. 4)              */
+#define AMGT_MODE_F64 0       /* everything in FP64                               */
+#define AMGT_MODE_MIXED 1     /* FP64 GMRES as iterative refinement around an FP32
+                                 flexible GMRES with FP32 sweeps/transfers and a
+                                 BF16 tensor-core scatter (FP32 accumulation)     */
+
+typedef struct amgt_options {
+  double tol;          /* stop when ||b - A x||_2 / ||b||_2 < tol (Sec. 5.1)   */
+  int restart;         /* GMRES restart length m (20)                          */
+  int maxit;           /* cap on Krylov iterations (all cycles)                */
+  int precond;         /* AMGT_PREC_*                                          */
+  int mode;            /* AMGT_MODE_*                                          */
+  int device_ptrs;     /* 1: x0/psi/phi of amgt_solve are device pointers      */
+  double inner_tol;    /* mixed mode: relative tol of each inner FP32 solve    */
+  int inner_maxit;     /* mixed mode: cap per inner solve                      */
+} amgt_options;
+
+#define AMGT_MAX_HIST 1024
+typedef struct amgt_stats {
+  int iterations;          /* Krylov iterations (inner ones in mixed mode)     */
+  int outer_iterations;    /* refinement steps (mixed) / restarts (FP64)       */
+  double relres;           /* final true ||b - A x|| / ||b||, FP64             */
+  double seconds;          /* wall time of the solve                           */
+  int nhist;               /* entries of hist                                  */
+  double hist[AMGT_MAX_HIST]; /* estimated relative residual per iteration     */
+} amgt_stats;
+
+/* ---- context -------------------------------------------------------------- */
+/* Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL for the legacy default stream); every call issues its work on
+ * it.  Returns AMGT_OK and *out, or an error. */
+int amgt_create(amgt_ctx** out, int device, void* cuda_stream);
+void amgt_destroy(amgt_ctx* ctx);
+/* Message of the last failing call on this context (never NULL). */
+const char* amgt_last_error(const amgt_ctx* ctx);
+int amgt_set_stream(amgt_ctx* ctx, void* cuda_stream);
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all contexts).  Host-side counter; no device work. */
+int amgt_query_launches(int64_t* count);
+/* Blocks until all work issued on the context's stream has finished; returns
+ * AMGT_ERR_DEVICE_TIMEOUT if a device-side bounded wait gave up since the
+ * last check. */
+int amgt_sync(amgt_ctx* ctx);
+
+/* ---- problem statement (Sec. 2, Eq. LBE; Sec. 2.1; Sec. 4.2; Sec. 5) ----- */
+/* Axis-aligned box [lo, hi] cut into ncell[0] x ncell[1] (x ncell[2]) equal
+ * cells; dim = 2 (slab infinite and uniform in z) or 3. */
+int amgt_set_mesh_cartesian(amgt_ctx* ctx, int dim, const int64_t ncell[3],
+                            const double lo[3], const double hi[3]);
+/* Per-cell sigma_t[C] and sigma_s[C] (= sigma_{s,0}) on host memory, and the
+ * Legendre moment shape fmom[N+1] with sigma_{s,n} = sigma_s * fmom[n]
+ * (fmom[0] = 1; Sec. 4.2, Eq. for Q).  The scatter kernel is
+ * sum_n (2n+1)/(4 pi) sigma_{s,n} P_n(Omega.Omega').  Requires the mesh. */
+int amgt_set_materials(amgt_ctx* ctx, const double* sigma_t, const double* sigma_s,
+                       int N, const double* fmom);
+/* Uniform angular mesh of the given level (8*4^level patches; Sec. 2.1).
+ * basis: 0 Const, 1 Lin (Sec. 2.2). */
+int amgt_set_angular_uniform(amgt_ctx* ctx, int basis, int level);
+/* Mesh refined about `axis` by the bands 0.97/0.9/0.8/0.6 of Sec. 5.4: an
+ * element is split while its level is below the band of the largest
+ * Omega.axis over its vertices (lmax, lmax-1, ..., floored at 0). */
+int amgt_set_angular_aniso(amgt_ctx* ctx, int basis, const double axis[3], int lmax);
+/* k-level V(nu_pre, nu_post) cycle on T_L..T_{L-k+1} (Fig. lmg).  Nr[j] is
+ * the scatter order used on level j (Sec. 4.3; Nr[0] normally N).  The
+ * coarsest level is solved by coarse_sweeps block Gauss-Seidel sweeps
+ * (Sec. 4.2).  nlevels = 1 keeps only the finest mesh. */
+int amgt_set_multigrid(amgt_ctx* ctx, int nlevels, const int* Nr, int nu_pre,
+                       int nu_post, int coarse_sweeps);
+/* Isotropic volumetric source: q[C] scalar emission density, Q = q/(4 pi). */
+int amgt_set_source_iso(amgt_ctx* ctx, const double* q);
+/* Boundary face f = 2*axis + side (side 1 = high): kind 0 vacuum, kind 1
+ * isotropic inflow of angular flux params[0]. */
+int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
+/* Sizes of level k of the hierarchy. */
+int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);
+
+/* Solves (L - S) psi = f to opt->tol (Sec. 3, Sec. 5.1).  psi [Nsdof][Nadof]
+ * and phi [Nsdof] (scalar flux, may be NULL) receive the result; x0 may be
+ * NULL (zero initial guess).  Pointers are host memory unless
+ * opt->device_ptrs.  st may be NULL. */
+int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
+               double* psi, double* phi, amgt_stats* st);
+
+/* ---- operators of the hot path on device buffers -------------------------- */
+/* All buffers are contiguous [Nsdof][Nadof(level)] of element type `dtype`
+ * unless stated; they must not alias unless stated. */
+
+/* f = volumetric source + boundary inflow terms on level k (Sec. 2.3, Q). */
+int amgt_op_source(amgt_ctx* ctx, int level, int dtype, void* f);
+/* psi = L^-1 b: upwind sweep over the cells per sweep direction, one block
+ * solve per (cell, patch) (Sec. 3).  Exact on these meshes. */
+int amgt_op_sweep(amgt_ctx* ctx, int level, int dtype, const void* b, void* psi);
+/* y = L x (Eq. complete, left-hand side with upwind face fluxes). */
+int amgt_op_apply_L(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
+/* y = S x: Q_[j,q]lm = sum N_li sum_n sigma_{s,n} X X phi (Sec. 4.2), with the
+ * level's scatter order.  dtype AMGT_F32_BF16TC: float buffers, contraction
+ * in BF16 on tensor cores with FP32 accumulation. */
+int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
+/* y = (L - S) x. */
+int amgt_op_apply_A(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
+/* rc = P^T rf from level k to level k+1 (R = P^T, Sec. 4.1). */
+int amgt_op_restrict(amgt_ctx* ctx, int level, int dtype, const void* rf, void* rc);
+/* xf += P xc from level k+1 to level k (Galerkin prolongation, Sec. 4.1). */
+int amgt_op_prolong(amgt_ctx* ctx, int level, int dtype, const void* xc, void* xf);
+/* nu source iterations phi <- L^-1 (S phi + f) on level k (Sec. 4.1);
+ * phi is read and overwritten. */
+int amgt_op_smooth(amgt_ctx* ctx, int level, int dtype, int nu, const void* f, void* phi);
+/* `sweeps` block Gauss-Seidel sweeps on the coarsest level with self-scatter
+ * in each block solve (Sec. 4.2); phi is read and overwritten. */
+int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi);
+/* phi = LMG(0, f, finest) (Fig. lmg).  dtype AMGT_F32_BF16TC runs the FP32
+ * cycle with the BF16 tensor-core scatter. */
+int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi);
+/* phi_s[Nsdof] = sum_{q,d} psi int Psi_[q]d (zeroth flux moment, Sec. 4.2). */
+int amgt_op_scalar_flux(amgt_ctx* ctx, int level, int dtype, const void* psi, void* phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMGT_H */

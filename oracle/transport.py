@@ -146,11 +146,12 @@ class Transport:
         return self.K0[q] + self.sigma_t[c] * self.B[q]
 
     # ---------------------------------------------------------------- operators
-    def apply_L(self, x):
-        """y = L x (Eq. complete, left-hand side, with upwind face fluxes)."""
+    def apply_L(self, x, cells=None):
+        """y = L x (Eq. complete, left-hand side, with upwind face fluxes).
+        With `cells`, only the rows of those cells are computed (others 0)."""
         xb = self.to_blocks(x)
         yb = np.zeros_like(xb)
-        for c in range(self.C):
+        for c in (range(self.C) if cells is None else cells):
             Kc = self.block(c, slice(None))
             yb[c] = np.einsum("qij,qj->qi", Kc, xb[c])
             for f in range(2 * self.dim):
@@ -174,13 +175,16 @@ class Transport:
     def apply_A(self, x):
         return self.apply_L(x) - self.scatter(x)
 
-    def sweep(self, b):
+    def sweep(self, b, patches=None):
         """psi = L^-1 b: per direction, cells in upwind order, all patches of
-        the direction solved block by block (Sec. 3)."""
+        the direction solved block by block (Sec. 3).  L couples a patch only
+        to itself, so with `patches` only those columns are swept (others 0)."""
         bb = self.to_blocks(b)
         psi = np.zeros_like(bb)
         for d in range(self.ndir):
             qs = self.patches_of(d)
+            if patches is not None:
+                qs = np.array([q for q in qs if q in set(patches)], dtype=np.int64)
             if len(qs) == 0:
                 continue
             for c in self.sweep_order(d):

@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) library for the angular-multigrid-preconditioned DG
+transport solver of Lathouwers & Perko (arXiv 2010.04559).
+
+The compute path is libamgt.so (CUDA kernels behind the C ABI of
+include/amgt.h); this package only builds and binds it.
+"""
+from ._capi import (AMGT_F32, AMGT_F32_BF16TC, AMGT_F64, AMGT_MODE_F64, AMGT_MODE_MIXED,
+                    AMGT_PREC_MG, AMGT_PREC_NONE, AMGT_PREC_SWEEP, AmgtError, Context,
+                    EXPORTS, amgt_query_launches, context_from_problem)
+
+__all__ = ["Context", "context_from_problem", "AmgtError", "EXPORTS", "AMGT_F64", "AMGT_F32",
+           "AMGT_F32_BF16TC", "AMGT_PREC_NONE", "AMGT_PREC_SWEEP", "AMGT_PREC_MG",
+           "AMGT_MODE_F64", "AMGT_MODE_MIXED", "amgt_query_launches"]

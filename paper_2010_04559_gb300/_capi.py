@@ -1,0 +1,347 @@
+"""ctypes binding of libamgt.so (include/amgt.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device buffers are passed as torch CUDA tensors (their
+data_ptr); host arrays as NumPy arrays.  Importing this module loads the
+library and raises if it is missing -- there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AMGT_OK = 0
+AMGT_ERR_ARG = -1
+AMGT_ERR_CUDA = -2
+AMGT_ERR_NOMEM = -3
+AMGT_ERR_NOT_CONVERGED = -4
+AMGT_ERR_BREAKDOWN = -5
+AMGT_ERR_NAN = -6
+AMGT_ERR_DEVICE_TIMEOUT = -7
+AMGT_ERR_STATE = -8
+AMGT_ERR_UNSUPPORTED = -9
+
+AMGT_F64 = 0
+AMGT_F32 = 1
+AMGT_F32_BF16TC = 2
+
+AMGT_PREC_NONE = 0
+AMGT_PREC_SWEEP = 1
+AMGT_PREC_MG = 2
+AMGT_MODE_F64 = 0
+AMGT_MODE_MIXED = 1
+
+AMGT_MAX_HIST = 1024
+
+# every exported symbol of include/amgt.h
+EXPORTS = [
+    "amgt_create", "amgt_destroy", "amgt_last_error", "amgt_set_stream", "amgt_sync",
+    "amgt_query_launches",
+    "amgt_set_mesh_cartesian", "amgt_set_materials", "amgt_set_angular_uniform",
+    "amgt_set_angular_aniso", "amgt_set_multigrid", "amgt_set_source_iso",
+    "amgt_set_boundary", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
+    "amgt_op_sweep", "amgt_op_apply_L", "amgt_op_scatter", "amgt_op_apply_A",
+    "amgt_op_restrict", "amgt_op_prolong", "amgt_op_smooth", "amgt_op_coarse_gs",
+    "amgt_op_vcycle", "amgt_op_scalar_flux",
+]
+
+
+class amgt_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("precond", ctypes.c_int), ("mode", ctypes.c_int),
+                ("device_ptrs", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int)]
+
+
+class amgt_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("nhist", ctypes.c_int), ("hist", ctypes.c_double * AMGT_MAX_HIST)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PI = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "amgt_create": ([ctypes.POINTER(_P), _I, _P], _I),
+    "amgt_destroy": ([_P], None),
+    "amgt_last_error": ([_P], ctypes.c_char_p),
+    "amgt_set_stream": ([_P, _P], _I),
+    "amgt_sync": ([_P], _I),
+    "amgt_query_launches": ([_PI64], _I),
+    "amgt_set_mesh_cartesian": ([_P, _I, _PI64, _PD, _PD], _I),
+    "amgt_set_materials": ([_P, _PD, _PD, _I, _PD], _I),
+    "amgt_set_angular_uniform": ([_P, _I, _I], _I),
+    "amgt_set_angular_aniso": ([_P, _I, _PD, _I], _I),
+    "amgt_set_multigrid": ([_P, _I, _PI, _I, _I, _I], _I),
+    "amgt_set_source_iso": ([_P, _PD], _I),
+    "amgt_set_boundary": ([_P, _I, _I, _PD], _I),
+    "amgt_query_sizes": ([_P, _I, _PI64, _PI64], _I),
+    "amgt_solve": ([_P, ctypes.POINTER(amgt_options), _P, _P, _P,
+                    ctypes.POINTER(amgt_stats)], _I),
+    "amgt_op_source": ([_P, _I, _I, _P], _I),
+    "amgt_op_sweep": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_apply_L": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_scatter": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_apply_A": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_restrict": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_prolong": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_smooth": ([_P, _I, _I, _I, _P, _P], _I),
+    "amgt_op_coarse_gs": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_vcycle": ([_P, _I, _P, _P], _I),
+    "amgt_op_scalar_flux": ([_P, _I, _I, _P, _P], _I),
+}
+
+
+def load(path=None):
+    """Load the built library (never builds implicitly unless asked)."""
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libamgt.so is not built: run __graft_entry__.build() "
+                           "or python -m paper_2010_04559_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def amgt_query_launches():
+    """Kernels launched by the library in this process so far."""
+    n = ctypes.c_int64()
+    rc = lib().amgt_query_launches(ctypes.byref(n))
+    if rc != AMGT_OK:
+        raise AmgtError(rc, "amgt_query_launches failed")
+    return n.value
+
+
+class AmgtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"amgt error {code}: {msg}")
+        self.code = code
+
+
+def _dptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+class Context:
+    """Owns one amgt_ctx; methods are one-to-one with the C entry points."""
+
+    def __init__(self, device=0, stream=None):
+        self.lib = lib()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if stream else ctypes.c_void_p()
+        rc = self.lib.amgt_create(ctypes.byref(h), int(device), s)
+        if rc != AMGT_OK:
+            raise AmgtError(rc, "amgt_create failed (is a CUDA device visible?)")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.amgt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != AMGT_OK and rc not in allow:
+            raise AmgtError(rc, self.lib.amgt_last_error(self.h).decode())
+        return rc
+
+    # ---- problem statement
+    def amgt_set_stream(self, stream):
+        return self._check(self.lib.amgt_set_stream(self.h, ctypes.c_void_p(stream)))
+
+    def amgt_sync(self):
+        return self._check(self.lib.amgt_sync(self.h))
+
+    def amgt_set_mesh_cartesian(self, dim, ncell, lo, hi):
+        nc = _np(list(ncell) + [1] * (3 - len(ncell)), np.int64)
+        lo = _np(list(lo)[:3] + [0.0] * (3 - len(lo)), np.float64)
+        hi = _np(list(hi)[:3] + [1.0] * (3 - len(hi)), np.float64)
+        return self._check(self.lib.amgt_set_mesh_cartesian(
+            self.h, int(dim), nc.ctypes.data_as(_PI64), lo.ctypes.data_as(_PD),
+            hi.ctypes.data_as(_PD)))
+
+    def amgt_set_materials(self, sigma_t, sigma_s, N, fmom):
+        st = _np(sigma_t, np.float64)
+        ss = _np(sigma_s, np.float64)
+        fm = _np(fmom, np.float64)
+        return self._check(self.lib.amgt_set_materials(
+            self.h, st.ctypes.data_as(_PD), ss.ctypes.data_as(_PD), int(N),
+            fm.ctypes.data_as(_PD)))
+
+    def amgt_set_angular_uniform(self, basis, level):
+        return self._check(self.lib.amgt_set_angular_uniform(self.h, int(basis), int(level)))
+
+    def amgt_set_angular_aniso(self, basis, axis, lmax):
+        ax = _np(axis, np.float64)
+        return self._check(self.lib.amgt_set_angular_aniso(
+            self.h, int(basis), ax.ctypes.data_as(_PD), int(lmax)))
+
+    def amgt_set_multigrid(self, nlevels, Nr, nu_pre, nu_post, coarse_sweeps):
+        nr = _np(Nr, np.int32)
+        return self._check(self.lib.amgt_set_multigrid(
+            self.h, int(nlevels), nr.ctypes.data_as(_PI), int(nu_pre), int(nu_post),
+            int(coarse_sweeps)))
+
+    def amgt_set_source_iso(self, q):
+        qq = _np(q, np.float64)
+        return self._check(self.lib.amgt_set_source_iso(self.h, qq.ctypes.data_as(_PD)))
+
+    def amgt_set_boundary(self, face, kind, value=0.0):
+        p = _np([value], np.float64)
+        return self._check(self.lib.amgt_set_boundary(self.h, int(face), int(kind),
+                                                      p.ctypes.data_as(_PD)))
+
+    def amgt_query_sizes(self, level=0):
+        a = ctypes.c_int64()
+        b = ctypes.c_int64()
+        self._check(self.lib.amgt_query_sizes(self.h, int(level), ctypes.byref(a),
+                                              ctypes.byref(b)))
+        return a.value, b.value
+
+    def amgt_solve(self, tol=1e-8, restart=20, maxit=1000, precond=AMGT_PREC_MG,
+                   mode=AMGT_MODE_F64, x0=None, psi=None, phi=None, device_ptrs=False,
+                   inner_tol=1e-4, inner_maxit=200, allow_not_converged=False):
+        """Host mode: x0/psi/phi are NumPy float64 arrays (psi/phi allocated when
+        None).  Device mode: torch CUDA float64 tensors."""
+        opt = amgt_options(float(tol), int(restart), int(maxit), int(precond), int(mode),
+                           1 if device_ptrs else 0, float(inner_tol), int(inner_maxit))
+        st = amgt_stats()
+        nsdof, nadof = self.amgt_query_sizes(0)
+        if device_ptrs:
+            px, pp, pf = _dptr(x0), _dptr(psi), _dptr(phi)
+        else:
+            if psi is None:
+                psi = np.empty((nsdof, nadof))
+            if phi is None:
+                phi = np.empty(nsdof)
+            assert psi.dtype == np.float64 and psi.flags.c_contiguous
+            assert phi.dtype == np.float64 and phi.flags.c_contiguous
+            px = ctypes.c_void_p(0 if x0 is None else _np(x0, np.float64).ctypes.data)
+            pp = ctypes.c_void_p(psi.ctypes.data)
+            pf = ctypes.c_void_p(phi.ctypes.data)
+        allow = (AMGT_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        rc = self._check(self.lib.amgt_solve(self.h, ctypes.byref(opt), px, pp, pf,
+                                             ctypes.byref(st)), allow)
+        return psi, phi, st, rc
+
+    # ---- operators on torch CUDA tensors
+    @staticmethod
+    def _dtype_code(t, tc=False):
+        import torch
+        if t.dtype == torch.float64:
+            return AMGT_F64
+        if t.dtype == torch.float32:
+            return AMGT_F32_BF16TC if tc else AMGT_F32
+        raise TypeError("buffers must be float64 or float32 CUDA tensors")
+
+    @staticmethod
+    def _req(*ts):
+        for t in ts:
+            if not (t.is_cuda and t.is_contiguous()):
+                raise ValueError("operator buffers must be contiguous CUDA tensors")
+
+    def amgt_op_source(self, level, f):
+        self._req(f)
+        return self._check(self.lib.amgt_op_source(self.h, level, self._dtype_code(f), _dptr(f)))
+
+    def amgt_op_sweep(self, level, b, psi):
+        self._req(b, psi)
+        return self._check(self.lib.amgt_op_sweep(self.h, level, self._dtype_code(b),
+                                                  _dptr(b), _dptr(psi)))
+
+    def amgt_op_apply_L(self, level, x, y):
+        self._req(x, y)
+        return self._check(self.lib.amgt_op_apply_L(self.h, level, self._dtype_code(x),
+                                                    _dptr(x), _dptr(y)))
+
+    def amgt_op_scatter(self, level, x, y, tc=False):
+        self._req(x, y)
+        return self._check(self.lib.amgt_op_scatter(self.h, level, self._dtype_code(x, tc),
+                                                    _dptr(x), _dptr(y)))
+
+    def amgt_op_apply_A(self, level, x, y, tc=False):
+        self._req(x, y)
+        return self._check(self.lib.amgt_op_apply_A(self.h, level, self._dtype_code(x, tc),
+                                                    _dptr(x), _dptr(y)))
+
+    def amgt_op_restrict(self, level, rf, rc):
+        self._req(rf, rc)
+        return self._check(self.lib.amgt_op_restrict(self.h, level, self._dtype_code(rf),
+                                                     _dptr(rf), _dptr(rc)))
+
+    def amgt_op_prolong(self, level, xc, xf):
+        self._req(xc, xf)
+        return self._check(self.lib.amgt_op_prolong(self.h, level, self._dtype_code(xc),
+                                                    _dptr(xc), _dptr(xf)))
+
+    def amgt_op_smooth(self, level, nu, f, phi, tc=False):
+        self._req(f, phi)
+        return self._check(self.lib.amgt_op_smooth(self.h, level, self._dtype_code(f, tc), nu,
+                                                   _dptr(f), _dptr(phi)))
+
+    def amgt_op_coarse_gs(self, sweeps, f, phi):
+        self._req(f, phi)
+        return self._check(self.lib.amgt_op_coarse_gs(self.h, self._dtype_code(f), sweeps,
+                                                      _dptr(f), _dptr(phi)))
+
+    def amgt_op_vcycle(self, f, phi, tc=False):
+        self._req(f, phi)
+        return self._check(self.lib.amgt_op_vcycle(self.h, self._dtype_code(f, tc), _dptr(f),
+                                                   _dptr(phi)))
+
+    def amgt_op_scalar_flux(self, level, psi, phi):
+        self._req(psi, phi)
+        return self._check(self.lib.amgt_op_scalar_flux(self.h, level, self._dtype_code(psi),
+                                                        _dptr(psi), _dptr(phi)))
+
+
+def context_from_problem(prob, device=0, stream=None, aniso=None):
+    """Create a context and pass a workloads-style problem dict through the
+    set_* entry points (marshalling only)."""
+    ctx = Context(device, stream)
+    dim = prob["dim"]
+    ctx.amgt_set_mesh_cartesian(dim, prob["ncell"], prob["lo"], prob["hi"])
+    ctx.amgt_set_materials(prob["sigma_t"], prob["sigma_s"], prob["N"], prob["fmom"])
+    basis = 1 if prob["basis"] == "lin" else 0
+    if aniso is None:
+        ctx.amgt_set_angular_uniform(basis, prob["level"])
+    else:
+        axis, lmax = aniso
+        ctx.amgt_set_angular_aniso(basis, axis, lmax)
+    mg = prob.get("mg")
+    if mg:
+        ctx.amgt_set_multigrid(mg["nlevels"], mg["Nr"], mg["nu_pre"], mg["nu_post"],
+                               mg["coarse_sweeps"])
+    ctx.amgt_set_source_iso(prob["q"])
+    for f, (kind, val) in enumerate(prob["boundary"]):
+        ctx.amgt_set_boundary(f, kind, val)
+    return ctx

@@ -1,0 +1,1170 @@
+// C ABI of the library: problem statement, set-up, operator entry points, the
+// angular multigrid V-cycle (Fig. lmg) and restarted GMRES (FP64 and the mixed
+// FP64-refinement / FP32-flexible-GMRES form).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <utility>
+
+#include "context.hpp"
+
+using namespace amgt;
+
+namespace {
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+      return e_ == cudaErrorMemoryAllocation ? AMGT_ERR_NOMEM : AMGT_ERR_CUDA;      \
+    }                                                                               \
+  } while (0)
+
+#define TRY(expr)                   \
+  do {                              \
+    int rc_ = (expr);               \
+    if (rc_ != AMGT_OK) return rc_; \
+  } while (0)
+
+int fail(amgt_ctx* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  return code;
+}
+
+template <class T>
+int dalloc(amgt_ctx* ctx, size_t n, T** out) {
+  auto m = std::make_unique<DevMem>();
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&m->p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, AMGT_ERR_NOMEM,
+                "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+  }
+  m->bytes = n * sizeof(T);
+  *out = static_cast<T*>(m->p);
+  ctx->mem.push_back(std::move(m));
+  return AMGT_OK;
+}
+
+template <class Tdev, class Thost>
+int upload(amgt_ctx* ctx, const std::vector<Thost>& h, Tdev** out) {
+  TRY(dalloc<Tdev>(ctx, h.size(), out));
+  std::vector<Tdev> tmp(h.begin(), h.end());
+  CK(cudaMemcpy(*out, tmp.data(), tmp.size() * sizeof(Tdev), cudaMemcpyHostToDevice));
+  return AMGT_OK;
+}
+
+int nmoments(int N) { return (N + 1) * (N + 1); }
+
+// largest number of cells on one wavefront level i + j + k = const
+int max_wavefront_cells(const Geom& g) {
+  std::vector<int> cnt(g.nx + g.ny + g.nz, 0);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) cnt[i + j + k]++;
+  return *std::max_element(cnt.begin(), cnt.end());
+}
+
+// kron(S[s][s], Ang[a][a]) accumulated with factor into out[(s a)^2]
+void kron_add(int s, int a, const double* S, const double* Ang, double fac, double* out) {
+  const int sa = s * a;
+  for (int l = 0; l < s; ++l)
+    for (int i = 0; i < s; ++i) {
+      const double sv = S[l * s + i] * fac;
+      if (sv == 0.0) continue;
+      for (int m = 0; m < a; ++m)
+        for (int d = 0; d < a; ++d) out[(l * a + m) * sa + i * a + d] += sv * Ang[m * a + d];
+    }
+}
+
+template <class T>
+LevelDev<T> level_view(const Level& L, const LevelDevStore<T>& s) {
+  LevelDev<T> v;
+  v.K0 = s.K0;
+  v.B = s.B;
+  v.Kinv = s.Kinv;
+  v.Aax = s.Aax;
+  v.Ginv = s.Ginv;
+  v.X = s.X;
+  v.XFt = s.XFt;
+  v.Sqq = s.Sqq;
+  v.w = s.w;
+  v.pdir = L.d_pdir;
+  v.nmom = L.nmom;
+  return v;
+}
+
+template <class T>
+const LevelDevStore<T>& store(const Level& L);
+template <>
+const LevelDevStore<double>& store<double>(const Level& L) {
+  return L.d64;
+}
+template <>
+const LevelDevStore<float>& store<float>(const Level& L) {
+  return L.d32;
+}
+
+Geom level_geom(const amgt_ctx* ctx, int k) {
+  Geom g = ctx->geom;
+  g.nadof = ctx->lv[k].nadof();
+  g.P = ctx->lv[k].mesh.P;
+  g.a = ctx->lv[k].mesh.a;
+  return g;
+}
+
+CellData cell_data(const amgt_ctx* ctx) {
+  CellData cd;
+  cd.mat = ctx->d_mat;
+  cd.sigma_t = ctx->d_sigt;
+  cd.sigma_s = ctx->d_sigs;
+  cd.sigma_t32 = ctx->d_sigt32;
+  cd.sigma_s32 = ctx->d_sigs32;
+  return cd;
+}
+
+Schedule schedule(const amgt_ctx* ctx, int k) {
+  const Level& L = ctx->lv[k];
+  Schedule sc;
+  sc.cells = ctx->d_cells;
+  sc.level_off = ctx->d_level_off;
+  sc.nlev = ctx->nlev_wave;
+  sc.task_dir = L.d_task_dir;
+  sc.task_q0 = L.d_task_q0;
+  sc.task_nq = L.d_task_nq;
+  sc.ntask = (int)L.task_dir.size();
+  return sc;
+}
+
+// ---------------------------------------------------------------- set-up
+template <class T>
+int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
+                 const std::vector<double>& B, const std::vector<double>& Kinv,
+                 const std::vector<double>& Ginv, const std::vector<double>& X,
+                 const std::vector<double>& XFt, const std::vector<double>& Sqq,
+                 const std::vector<double>& tblk, LevelDevStore<T>& s) {
+  TRY(upload(ctx, K0, &s.K0));
+  TRY(upload(ctx, B, &s.B));
+  TRY(upload(ctx, Kinv, &s.Kinv));
+  TRY(upload(ctx, L.mesh.A, &s.Aax));
+  if (!Ginv.empty()) TRY(upload(ctx, Ginv, &s.Ginv));
+  TRY(upload(ctx, X, &s.X));
+  TRY(upload(ctx, XFt, &s.XFt));
+  TRY(upload(ctx, Sqq, &s.Sqq));
+  TRY(upload(ctx, L.mesh.w, &s.w));
+  TRY(upload(ctx, L.mesh.Aw, &s.Aw));
+  if (!tblk.empty()) TRY(upload(ctx, tblk, &s.tblk));
+  return AMGT_OK;
+}
+
+int build(amgt_ctx* ctx) {
+  if (!ctx->dirty) return AMGT_OK;
+  if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "mesh not set");
+  if (ctx->N < 0) return fail(ctx, AMGT_ERR_STATE, "materials not set");
+  if (ctx->paths.empty()) return fail(ctx, AMGT_ERR_STATE, "angular mesh not set");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->lv.clear();
+  ctx->tr.clear();
+  ctx->ws64.clear();
+  ctx->ws32.clear();
+  ctx->mem.clear();
+  ctx->d_moments = nullptr;
+  ctx->moments_bytes = 0;
+  ctx->d_bf16 = nullptr;
+  ctx->bf16_bytes = 0;
+
+  const int dim = ctx->dim;
+  double h[3] = {1, 1, 1};
+  for (int e = 0; e < dim; ++e) h[e] = (ctx->hi[e] - ctx->lo[e]) / (double)ctx->ncell[e];
+  ctx->q1 = build_q1(dim, h);
+  const Q1& q1 = ctx->q1;
+  const int s = q1.s;
+  Geom& g = ctx->geom;
+  std::memset(&g, 0, sizeof(g));
+  g.dim = dim;
+  g.s = s;
+  g.nx = (int)ctx->ncell[0];
+  g.ny = (int)ctx->ncell[1];
+  g.nz = dim == 3 ? (int)ctx->ncell[2] : 1;
+  g.C = g.nx * g.ny * g.nz;
+  g.nsdof = (long long)g.C * s;
+  const int hs = s / 2;
+  for (int xi = 0; xi < dim; ++xi)
+    for (int jp = 0; jp < hs; ++jp)
+      for (int j = 0; j < hs; ++j) g.facemass[xi][jp][j] = q1.facemass[(xi * hs + jp) * hs + j];
+  for (int i = 0; i < s * s; ++i) g.Nmass[i] = q1.N[i];
+  set_mass_matrix(q1.N.data(), s);
+  CK(cudaGetLastError());
+  const int C = g.C;
+  ctx->C = C;
+
+  // materials: distinct (sigma_t, sigma_s) pairs
+  std::map<std::pair<double, double>, int> mm;
+  ctx->mat.assign(C, 0);
+  ctx->mat_st.clear();
+  ctx->mat_ss.clear();
+  for (int c = 0; c < C; ++c) {
+    auto key = std::make_pair(ctx->sigma_t[c], ctx->sigma_s[c]);
+    auto it = mm.find(key);
+    if (it == mm.end()) {
+      it = mm.emplace(key, (int)ctx->mat_st.size()).first;
+      ctx->mat_st.push_back(key.first);
+      ctx->mat_ss.push_back(key.second);
+    }
+    ctx->mat[c] = it->second;
+  }
+  ctx->nmat = (int)ctx->mat_st.size();
+
+  // angular hierarchy
+  const int L = max_level(ctx->paths);
+  const int nl = ctx->nlevels;
+  if (nl < 1 || L - nl + 1 < 0)
+    return fail(ctx, AMGT_ERR_ARG, "multigrid has more levels than the angular hierarchy");
+  ctx->lv.resize(nl);
+  const int a = ctx->basis == 0 ? 1 : 3;
+  const int sa = s * a;
+  for (int k = 0; k < nl; ++k) {
+    Level& Lv = ctx->lv[k];
+    Lv.mesh = build_mesh(coarsen_paths(ctx->paths, L - k), ctx->basis);
+    Lv.nsdof = g.nsdof;
+    const int P = Lv.mesh.P;
+    const int nadof = Lv.mesh.nadof();
+    Lv.Nr = k < (int)ctx->Nr.size() ? std::min(ctx->Nr[k], ctx->N) : ctx->N;
+    Lv.nmom = nmoments(Lv.Nr);
+    Lv.dense = nadof < 2 * Lv.nmom;
+    const int nm = Lv.nmom;
+    std::vector<double> X = x_table(Lv.mesh, Lv.Nr);
+    std::vector<double> F(nm);
+    for (int n = 0; n <= Lv.Nr; ++n)
+      for (int o = -n; o <= n; ++o) F[n * n + n + o] = ctx->fmom[n];
+    std::vector<double> XFt((size_t)nm * nadof);
+    for (int j = 0; j < nadof; ++j)
+      for (int kk = 0; kk < nm; ++kk) XFt[(size_t)kk * nadof + j] = F[kk] * X[(size_t)j * nm + kk];
+    std::vector<double> Sqq((size_t)P * a * a, 0.0);
+    for (int q = 0; q < P; ++q)
+      for (int m = 0; m < a; ++m)
+        for (int d = 0; d < a; ++d) {
+          double acc = 0.0;
+          for (int kk = 0; kk < nm; ++kk)
+            acc += X[(size_t)(q * a + m) * nm + kk] * F[kk] * X[(size_t)(q * a + d) * nm + kk];
+          Sqq[(q * a + m) * a + d] = acc;
+        }
+    // per-patch blocks
+    std::vector<double> K0((size_t)P * sa * sa, 0.0), B((size_t)P * sa * sa, 0.0);
+    Lv.pdir.resize(P);
+    Lv.octant.resize(P);
+    for (int q = 0; q < P; ++q) {
+      const int o = Lv.mesh.patch[q].octant;
+      Lv.octant[q] = o;
+      Lv.pdir[q] = dim == 2 ? (o >> 1) : o;
+      double* K = &K0[(size_t)q * sa * sa];
+      for (int xi = 0; xi < dim; ++xi) {
+        const int negb = (o >> (2 - xi)) & 1;
+        const double* Ax = &Lv.mesh.A[((size_t)q * 3 + xi) * a * a];
+        for (int side = 0; side < 2; ++side) {
+          const bool outflow = (side == 1) == (negb == 0);
+          if (!outflow) continue;
+          const double nsgn = side ? 1.0 : -1.0;
+          kron_add(s, a, &q1.Fown[(size_t)(2 * xi + side) * s * s], Ax, nsgn, K);
+        }
+        kron_add(s, a, &q1.V[(size_t)xi * s * s], Ax, -1.0, K);
+      }
+      kron_add(s, a, q1.N.data(), &Lv.mesh.M[(size_t)q * a * a], 1.0, &B[(size_t)q * sa * sa]);
+    }
+    const size_t nblk = (size_t)ctx->nmat * P * sa * sa;
+    if (nblk * sizeof(double) > (size_t)2 << 30)
+      return fail(ctx, AMGT_ERR_UNSUPPORTED,
+                  "too many distinct (sigma_t, sigma_s) pairs for per-material block inverses");
+    std::vector<double> Kinv(nblk), Ginv;
+    std::vector<double> blk(sa * sa);
+    for (int mt = 0; mt < ctx->nmat; ++mt)
+      for (int q = 0; q < P; ++q) {
+        for (int i = 0; i < sa * sa; ++i)
+          blk[i] = K0[(size_t)q * sa * sa + i] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + i];
+        if (!invert(sa, blk.data(), &Kinv[((size_t)mt * P + q) * sa * sa]))
+          return fail(ctx, AMGT_ERR_ARG, "singular transport block (sigma_t <= 0?)");
+      }
+    if (k == nl - 1) {
+      Ginv.resize(nblk);
+      std::vector<double> NS(sa * sa);
+      for (int mt = 0; mt < ctx->nmat; ++mt)
+        for (int q = 0; q < P; ++q) {
+          std::fill(NS.begin(), NS.end(), 0.0);
+          kron_add(s, a, q1.N.data(), &Sqq[(size_t)q * a * a], 1.0, NS.data());
+          for (int i = 0; i < sa * sa; ++i)
+            blk[i] = K0[(size_t)q * sa * sa + i] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + i] -
+                     ctx->mat_ss[mt] * NS[i];
+          if (!invert(sa, blk.data(), &Ginv[((size_t)mt * P + q) * sa * sa]))
+            return fail(ctx, AMGT_ERR_ARG, "singular Gauss-Seidel block");
+        }
+    }
+    // directions and sweep tasks
+    Lv.ndir = dim == 2 ? 4 : 8;
+    Lv.dir_begin.assign(Lv.ndir, 0);
+    Lv.dir_end.assign(Lv.ndir, 0);
+    for (int d = 0; d < Lv.ndir; ++d) {
+      int b = -1, e = -1;
+      for (int q = 0; q < P; ++q)
+        if (Lv.pdir[q] == d) {
+          if (b < 0) b = q;
+          e = q + 1;
+        }
+      if (b < 0) b = e = 0;
+      Lv.dir_begin[d] = b;
+      Lv.dir_end[d] = e;
+    }
+    // sweep tasks: groups of G patches of one direction, sized so that a
+    // wavefront level keeps about 256 threads busy
+    Lv.task_dir.clear();
+    Lv.task_q0.clear();
+    Lv.task_nq.clear();
+    const int maxdiag = max_wavefront_cells(g);
+    int G = std::max(1, std::min(16, 256 / std::max(1, maxdiag)));
+    for (int d = 0; d < Lv.ndir; ++d)
+      for (int q0 = Lv.dir_begin[d]; q0 < Lv.dir_end[d]; q0 += G) {
+        Lv.task_dir.push_back(d);
+        Lv.task_q0.push_back(q0);
+        Lv.task_nq.push_back(std::min(G, Lv.dir_end[d] - q0));
+      }
+    TRY(upload(ctx, Lv.pdir, &Lv.d_pdir));
+    TRY(upload(ctx, Lv.octant, &Lv.d_octant));
+    TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
+    TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
+    TRY(upload(ctx, Lv.task_dir, &Lv.d_task_dir));
+    TRY(upload(ctx, Lv.task_q0, &Lv.d_task_q0));
+    TRY(upload(ctx, Lv.task_nq, &Lv.d_task_nq));
+    TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));
+    TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32));
+  }
+  for (int k = 0; k + 1 < nl; ++k) {
+    Level& F = ctx->lv[k];
+    try {
+      ctx->tr.push_back(build_transfer(F.mesh, ctx->lv[k + 1].mesh));
+    } catch (const std::exception& ex) {
+      return fail(ctx, AMGT_ERR_ARG, ex.what());
+    }
+    const Transfer& t = ctx->tr.back();
+    TRY(upload(ctx, t.parent, &F.d_parent));
+    TRY(upload(ctx, t.child_begin, &F.d_cbeg));
+    TRY(upload(ctx, t.child_end, &F.d_cend));
+    TRY(upload(ctx, t.blk, &F.d64.tblk));
+    TRY(upload(ctx, t.blk, &F.d32.tblk));
+  }
+
+  // wavefront schedule in rotated coordinates
+  {
+    const int nlev = g.nx + g.ny + g.nz - 2;
+    std::vector<std::vector<int>> byl(nlev);
+    for (int jz = 0; jz < g.nz; ++jz)
+      for (int jy = 0; jy < g.ny; ++jy)
+        for (int jx = 0; jx < g.nx; ++jx) byl[jx + jy + jz].push_back(jx | (jy << 11) | (jz << 22));
+    std::vector<int> cells, off(1, 0);
+    for (auto& v : byl) {
+      cells.insert(cells.end(), v.begin(), v.end());
+      off.push_back((int)cells.size());
+    }
+    ctx->nlev_wave = nlev;
+    TRY(upload(ctx, cells, &ctx->d_cells));
+    TRY(upload(ctx, off, &ctx->d_level_off));
+  }
+  // cell data and source
+  TRY(upload(ctx, ctx->mat, &ctx->d_mat));
+  TRY(upload(ctx, ctx->sigma_t, &ctx->d_sigt));
+  TRY(upload(ctx, ctx->sigma_s, &ctx->d_sigs));
+  TRY(upload(ctx, ctx->sigma_t, &ctx->d_sigt32));
+  TRY(upload(ctx, ctx->sigma_s, &ctx->d_sigs32));
+  std::vector<double> q = ctx->qsrc;
+  if (q.empty()) q.assign(C, 0.0);
+  TRY(upload(ctx, q, &ctx->d_q));
+  TRY(upload(ctx, std::vector<int>(ctx->bkind, ctx->bkind + 6), &ctx->d_bkind));
+  TRY(upload(ctx, std::vector<double>(ctx->bval, ctx->bval + 6), &ctx->d_bval));
+  TRY(upload(ctx, q1.mu, &ctx->d_mu));
+  TRY(upload(ctx, q1.mf, &ctx->d_mf));
+  // scratch
+  TRY(dalloc(ctx, (size_t)gemv_blocks(1LL << 40) * 64, &ctx->d_partials));
+  TRY(dalloc(ctx, 64, &ctx->d_dots));
+  TRY(dalloc(ctx, 256, &ctx->d_ptrs));
+  TRY(dalloc(ctx, 16, &ctx->d_status));
+  CK(cudaMemset(ctx->d_status, 0, 16 * sizeof(int)));
+  ctx->ws64.assign(nl, {});
+  ctx->ws32.assign(nl, {});
+  ctx->dirty = false;
+  return AMGT_OK;
+}
+
+int check_level(amgt_ctx* ctx, int k) {
+  TRY(build(ctx));
+  if (k < 0 || k >= (int)ctx->lv.size()) return fail(ctx, AMGT_ERR_ARG, "level out of range");
+  return AMGT_OK;
+}
+
+// workspace vector i (0 r, 1 f, 2 phi, 3 tmp, 4 tmp2) of level k in precision T
+template <class T>
+int wsvec(amgt_ctx* ctx, int k, int i, T** out) {
+  auto& ws = sizeof(T) == 8 ? ctx->ws64 : ctx->ws32;
+  auto& v = ws[k];
+  if ((int)v.size() <= i) v.resize(i + 1, nullptr);
+  if (!v[i]) {
+    T* p;
+    TRY(dalloc<T>(ctx, (size_t)ctx->lv[k].nsdof * ctx->lv[k].nadof(), &p));
+    v[i] = p;
+  }
+  *out = static_cast<T*>(v[i]);
+  return AMGT_OK;
+}
+
+int moments_scratch(amgt_ctx* ctx, size_t bytes, void** out) {
+  if (ctx->moments_bytes < bytes) {
+    double* p;
+    TRY(dalloc<double>(ctx, (bytes + 7) / 8, &p));
+    ctx->d_moments = p;
+    ctx->moments_bytes = bytes;
+  }
+  *out = ctx->d_moments;
+  return AMGT_OK;
+}
+
+// dense S_f = X diag(f) X^T on the device (FP64), with FP32 and BF16 copies
+int ensure_dense(amgt_ctx* ctx, int k) {
+  Level& L = ctx->lv[k];
+  if (L.d64.Sf) return AMGT_OK;
+  const int n = L.nadof();
+  double* Sf;
+  float* Sf32;
+  TRY(dalloc(ctx, (size_t)n * n, &Sf));
+  TRY(dalloc(ctx, (size_t)n * n, &Sf32));
+  GemmEpi epi{};
+  epi.mode = 0;
+  launch_gemm<double>(n, n, L.nmom, L.d64.X, L.nmom, L.d64.XFt, n, Sf, n, epi, ctx->stream);
+  launch_convert<double, float>((long long)n * n, Sf, Sf32, ctx->stream);
+  CK(cudaGetLastError());
+  L.d64.Sf = Sf;
+  L.d32.Sf = Sf32;
+  return AMGT_OK;
+}
+
+int ensure_dense_bf16(amgt_ctx* ctx, int k) {
+  Level& L = ctx->lv[k];
+  if (L.Sf_bf16) return AMGT_OK;
+  TRY(ensure_dense(ctx, k));
+  const int n = L.nadof();
+  __nv_bfloat16* p;
+  TRY(dalloc(ctx, (size_t)n * n, &p));
+  // S_f is symmetric, so S_f^T (the K-major B operand) equals S_f
+  launch_convert<double, __nv_bfloat16>((long long)n * n, L.d64.Sf, p, ctx->stream);
+  CK(cudaGetLastError());
+  L.Sf_bf16 = p;
+  return AMGT_OK;
+}
+
+// y = alpha * S x + beta * y + add  (add may be null)
+template <class T>
+int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, double beta,
+                 const T* add) {
+  Level& L = ctx->lv[k];
+  const long long M = L.nsdof;
+  const int n = L.nadof();
+  GemmEpi epi{};
+  epi.mode = 1;
+  epi.alpha = alpha;
+  epi.beta = beta;
+  epi.add = add;
+  epi.s = ctx->geom.s;
+  epi.sig = ctx->d_sigs;
+  epi.sig32 = ctx->d_sigs32;
+  if (tc) {
+    if constexpr (sizeof(T) == 4) {
+      if (!tc_available()) return fail(ctx, AMGT_ERR_UNSUPPORTED, "tensor-core path unavailable");
+      TRY(ensure_dense_bf16(ctx, k));
+      size_t need = (size_t)M * n * sizeof(__nv_bfloat16);
+      if (ctx->bf16_bytes < need) {
+        __nv_bfloat16* p;
+        TRY(dalloc(ctx, (size_t)M * n, &p));
+        ctx->d_bf16 = p;
+        ctx->bf16_bytes = need;
+      }
+      auto* xb = static_cast<__nv_bfloat16*>(ctx->d_bf16);
+      launch_convert<float, __nv_bfloat16>(M * n, x, xb, ctx->stream);
+      int rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, epi, ctx->d_status, ctx->stream);
+      if (rc != 0) return fail(ctx, AMGT_ERR_UNSUPPORTED, "tensor-core GEMM shape not supported");
+      CK(cudaGetLastError());
+      return AMGT_OK;
+    } else {
+      return fail(ctx, AMGT_ERR_ARG, "tensor-core scatter takes float buffers");
+    }
+  }
+  if (L.dense) {
+    TRY(ensure_dense(ctx, k));
+    const T* Sf = store<T>(L).Sf;
+    launch_gemm<T>((int)M, n, n, x, n, Sf, n, y, n, epi, ctx->stream);
+  } else {
+    void* mp;
+    TRY(moments_scratch(ctx, (size_t)M * L.nmom * sizeof(T), &mp));
+    T* Phi = static_cast<T*>(mp);
+    GemmEpi e0{};
+    e0.mode = 0;
+    launch_gemm<T>((int)M, L.nmom, n, x, n, store<T>(L).X, L.nmom, Phi, L.nmom, e0, ctx->stream);
+    launch_gemm<T>((int)M, n, L.nmom, Phi, L.nmom, store<T>(L).XFt, n, y, n, epi, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+template <class T>
+int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
+  const Level& L = ctx->lv[k];
+  launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
+                  schedule(ctx, k), b, psi, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+template <class T>
+int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
+  const Level& L = ctx->lv[k];
+  launch_apply_L<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx), alpha,
+                    beta, x, y, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// y = (L - S) x
+template <class T>
+int applyA_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y) {
+  TRY(scatter_impl<T>(ctx, k, tc, x, y, -1.0, 0.0, nullptr));
+  return applyL_impl<T>(ctx, k, T(1), T(1), x, y);
+}
+
+template <class T>
+int source_impl(amgt_ctx* ctx, int k, T* f) {
+  const Level& L = ctx->lv[k];
+  launch_source<T>(level_geom(ctx, k), store<T>(L).w, store<T>(L).Aw, L.d_octant, ctx->d_q,
+                   ctx->d_bval, ctx->d_bkind, ctx->d_mu, ctx->d_mf, f, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+template <class T>
+int restrict_impl(amgt_ctx* ctx, int k, const T* rf, T* rc) {
+  const Level& F = ctx->lv[k];
+  const Level& Cc = ctx->lv[k + 1];
+  launch_restrict<T>(F.nsdof, Cc.mesh.P, F.mesh.a, F.nadof(), Cc.nadof(), F.d_cbeg, F.d_cend,
+                     store<T>(F).tblk, rf, rc, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+template <class T>
+int prolong_impl(amgt_ctx* ctx, int k, const T* xc, T* xf) {
+  const Level& F = ctx->lv[k];
+  const Level& Cc = ctx->lv[k + 1];
+  launch_prolong<T>(F.nsdof, F.mesh.P, F.mesh.a, F.nadof(), Cc.nadof(), F.d_parent,
+                    store<T>(F).tblk, xc, xf, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// nu steps of phi <- L^-1 (S phi + f); `zero` = phi is known to be zero
+template <class T>
+int smooth_impl(amgt_ctx* ctx, int k, bool tc, int nu, const T* f, T* phi, bool zero) {
+  T* tmp;
+  TRY(wsvec<T>(ctx, k, 3, &tmp));
+  for (int it = 0; it < nu; ++it) {
+    if (zero && it == 0) {
+      TRY(sweep_impl<T>(ctx, k, f, phi));
+      continue;
+    }
+    TRY(scatter_impl<T>(ctx, k, tc, phi, tmp, 1.0, 0.0, f));
+    TRY(sweep_impl<T>(ctx, k, tmp, phi));
+  }
+  return AMGT_OK;
+}
+
+template <class T>
+int coarse_gs_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
+  const int k = (int)ctx->lv.size() - 1;
+  const Level& L = ctx->lv[k];
+  void* mp;
+  TRY(moments_scratch(ctx, (size_t)L.nsdof * L.nmom * sizeof(T), &mp));
+  T* mom = static_cast<T*>(mp);
+  GemmEpi e0{};
+  e0.mode = 0;
+  launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
+                 L.nmom, e0, ctx->stream);
+  int cl = 0;
+  launch_coarse_gs<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
+                      schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom, &cl,
+                      ctx->stream);
+  if (cl == 0) return fail(ctx, AMGT_ERR_CUDA, "coarse Gauss-Seidel cluster launch failed");
+  ctx->gs_cluster = cl;
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// phi = LMG(0, f, k): phi is overwritten
+template <class T>
+int vcycle_impl(amgt_ctx* ctx, int k, bool tc, const T* f, T* phi) {
+  const Level& L = ctx->lv[k];
+  const size_t bytes = (size_t)L.nsdof * L.nadof() * sizeof(T);
+  if (k == (int)ctx->lv.size() - 1) {
+    CK(cudaMemsetAsync(phi, 0, bytes, ctx->stream));
+    return coarse_gs_impl<T>(ctx, ctx->coarse_sweeps, f, phi);
+  }
+  TRY(smooth_impl<T>(ctx, k, tc, ctx->nu_pre, f, phi, true));
+  if (ctx->nu_pre == 0) CK(cudaMemsetAsync(phi, 0, bytes, ctx->stream));
+  T *r, *fc, *phic;
+  TRY(wsvec<T>(ctx, k, 0, &r));
+  TRY(wsvec<T>(ctx, k + 1, 1, &fc));
+  TRY(wsvec<T>(ctx, k + 1, 2, &phic));
+  // r = f - (L - S) phi = (S phi + f) - L phi
+  TRY(scatter_impl<T>(ctx, k, tc, phi, r, 1.0, 0.0, f));
+  TRY(applyL_impl<T>(ctx, k, T(-1), T(1), phi, r));
+  TRY(restrict_impl<T>(ctx, k, r, fc));
+  TRY(vcycle_impl<T>(ctx, k + 1, tc, fc, phic));
+  TRY(prolong_impl<T>(ctx, k, phic, phi));
+  TRY(smooth_impl<T>(ctx, k, tc, ctx->nu_post, f, phi, false));
+  return AMGT_OK;
+}
+
+template <class T>
+int scalar_flux_impl(amgt_ctx* ctx, int k, const T* psi, T* phi) {
+  const Level& L = ctx->lv[k];
+  launch_scalar_flux<T>(L.nsdof, L.nadof(), store<T>(L).w, psi, phi, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// ------------------------------------------------------------------ GMRES
+struct KrylovResult {
+  int its = 0;
+  int cycles = 0;
+  double relres = 0.0;
+  int status = AMGT_OK;
+};
+
+template <class T>
+int dev_dots(amgt_ctx* ctx, int nvec, double* host) {
+  CK(cudaMemcpyAsync(host, ctx->d_dots, sizeof(double) * nvec, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AMGT_OK;
+}
+
+template <class T>
+int norm2(amgt_ctx* ctx, const T* x, long long n, double* out) {
+  const int nblk = gemv_blocks(n);
+  void** slot = ctx->d_ptrs + 200;  // kept apart from the Krylov pointer tables
+  CK(cudaMemcpyAsync(slot, &x, sizeof(void*), cudaMemcpyHostToDevice, ctx->stream));
+  launch_multidot<T>(n, 1, reinterpret_cast<const T* const*>(slot), x, ctx->d_partials,
+                     nblk, ctx->d_dots, ctx->stream);
+  CK(cudaGetLastError());
+  double v;
+  TRY(dev_dots<T>(ctx, 1, &v));
+  *out = std::sqrt(std::max(v, 0.0));
+  return AMGT_OK;
+}
+
+// Right-preconditioned GMRES(m), CGS2, Givens rotations, storing the
+// preconditioned directions (flexible form).  x holds the initial guess
+// (x_zero: known zero) and receives the solution.
+template <class T, class OpA, class OpM>
+int gmres(amgt_ctx* ctx, int k, OpA apply_A, OpM apply_M, const T* b, T* x, bool x_zero,
+          double tol, int m, int maxit, KrylovResult& res, amgt_stats* st, double bnorm_in,
+          int hist_base) {
+  const long long n = ctx->lv[k].nsdof * ctx->lv[k].nadof();
+  const size_t bytes = (size_t)n * sizeof(T);
+  m = std::max(1, std::min(m, 30));
+  std::vector<T*> V(m + 1), Z(m);
+  // Krylov storage is kept in the workspace slots 8.. of level k
+  for (int i = 0; i <= m; ++i) TRY(wsvec<T>(ctx, k, 8 + i, &V[i]));
+  for (int i = 0; i < m; ++i) TRY(wsvec<T>(ctx, k, 8 + m + 1 + i, &Z[i]));
+  T** dV = reinterpret_cast<T**>(ctx->d_ptrs);
+  T** dZ = dV + 64;
+  CK(cudaMemcpyAsync(dV, V.data(), sizeof(T*) * (m + 1), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(dZ, Z.data(), sizeof(T*) * m, cudaMemcpyHostToDevice, ctx->stream));
+  const int nblk = gemv_blocks(n);
+  double bnorm = bnorm_in;
+  if (bnorm < 0) TRY(norm2<T>(ctx, b, n, &bnorm));
+  res = KrylovResult();
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
+    return AMGT_OK;
+  }
+  if (!std::isfinite(bnorm)) return fail(ctx, AMGT_ERR_NAN, "right-hand side is not finite");
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), h1(m + 1), h2(m + 1), y(m);
+  T* r = V[0];
+  while (true) {
+    if (x_zero) {
+      CK(cudaMemcpyAsync(r, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+      TRY(apply_A(x, r));
+      launch_axpby<T>(n, 1.0, b, -1.0, r, ctx->stream);  // r = b - A x
+    }
+    double beta;
+    TRY(norm2<T>(ctx, r, n, &beta));
+    if (!std::isfinite(beta)) return fail(ctx, AMGT_ERR_NAN, "residual is not finite");
+    res.relres = beta / bnorm;
+    if (res.relres < tol || res.its >= maxit) break;
+    launch_scale_copy<T>(n, 1.0 / beta, r, V[0], ctx->stream);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      TRY(apply_M(V[j], Z[j]));
+      T* w = V[j + 1];
+      TRY(apply_A(Z[j], w));
+      launch_multidot<T>(n, j + 1, dV, w, ctx->d_partials, nblk, ctx->d_dots, ctx->stream);
+      CK(cudaGetLastError());
+      TRY(dev_dots<T>(ctx, j + 1, h1.data()));
+      CK(cudaMemcpyAsync(ctx->d_dots + 32, h1.data(), sizeof(double) * (j + 1),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      launch_update_multidot<T>(n, j + 1, dV, ctx->d_dots + 32, w, 1, ctx->d_partials, nblk,
+                                ctx->d_dots, ctx->stream);
+      CK(cudaGetLastError());
+      TRY(dev_dots<T>(ctx, j + 1, h2.data()));
+      CK(cudaMemcpyAsync(ctx->d_dots + 32, h2.data(), sizeof(double) * (j + 1),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      launch_update_multidot<T>(n, j + 1, dV, ctx->d_dots + 32, w, 2, ctx->d_partials, nblk,
+                                ctx->d_dots, ctx->stream);
+      CK(cudaGetLastError());
+      double nrm2;
+      TRY(dev_dots<T>(ctx, 1, &nrm2));
+      const double hn = std::sqrt(std::max(nrm2, 0.0));
+      if (!std::isfinite(hn)) return fail(ctx, AMGT_ERR_NAN, "Arnoldi vector is not finite");
+      for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = den > 0 ? H[j * m + j] / den : 1.0;
+      sn[j] = den > 0 ? H[(j + 1) * m + j] / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      res.its++;
+      jdone = j + 1;
+      const double est = std::fabs(gv[j + 1]) / bnorm;
+      if (st && hist_base + res.its - 1 < AMGT_MAX_HIST) {
+        st->hist[hist_base + res.its - 1] = est;
+        st->nhist = hist_base + res.its;
+      }
+      if (est < tol || res.its >= maxit || hn == 0.0) break;
+      launch_scale_copy<T>(n, 1.0 / hn, w, w, ctx->stream);
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int j2 = i + 1; j2 < jdone; ++j2) acc -= H[i * m + j2] * y[j2];
+      if (H[i * m + i] == 0.0) return fail(ctx, AMGT_ERR_BREAKDOWN, "singular Hessenberg");
+      y[i] = acc / H[i * m + i];
+    }
+    if (x_zero) CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_dots + 32, y.data(), sizeof(double) * jdone,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    launch_lincomb<T>(n, jdone, reinterpret_cast<const T* const*>(dZ), ctx->d_dots + 32, x,
+                      ctx->stream);
+    CK(cudaGetLastError());
+    x_zero = false;
+    res.cycles++;
+  }
+  return AMGT_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int amgt_create(amgt_ctx** out, int device, void* stream) {
+  if (!out) return AMGT_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return AMGT_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return AMGT_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return AMGT_ERR_CUDA;
+  auto* ctx = new amgt_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  *out = ctx;
+  return AMGT_OK;
+}
+
+void amgt_destroy(amgt_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+const char* amgt_last_error(const amgt_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+int amgt_set_stream(amgt_ctx* ctx, void* stream) {
+  if (!ctx) return AMGT_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return AMGT_OK;
+}
+
+int amgt_query_launches(int64_t* count) {
+  if (!count) return AMGT_ERR_ARG;
+  *count = launch_count();
+  return AMGT_OK;
+}
+
+int amgt_sync(amgt_ctx* ctx) {
+  if (!ctx) return AMGT_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AMGT_OK;
+}
+
+int amgt_set_mesh_cartesian(amgt_ctx* ctx, int dim, const int64_t ncell[3], const double lo[3],
+                            const double hi[3]) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if ((dim != 2 && dim != 3) || !ncell || !lo || !hi) return fail(ctx, AMGT_ERR_ARG, "bad mesh");
+  for (int e = 0; e < dim; ++e) {
+    if (ncell[e] < 1 || ncell[e] > 2047) return fail(ctx, AMGT_ERR_ARG, "cells per axis must be 1..2047");
+    if (!(hi[e] > lo[e])) return fail(ctx, AMGT_ERR_ARG, "hi must exceed lo");
+  }
+  ctx->dim = dim;
+  for (int e = 0; e < 3; ++e) {
+    ctx->ncell[e] = e < dim ? ncell[e] : 1;
+    ctx->lo[e] = lo[e];
+    ctx->hi[e] = hi[e];
+  }
+  ctx->sigma_t.clear();
+  ctx->sigma_s.clear();
+  ctx->qsrc.clear();
+  ctx->N = -1;
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_materials(amgt_ctx* ctx, const double* st, const double* ss, int N,
+                       const double* fmom) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "set the mesh first");
+  if (!st || !ss || !fmom || N < 0 || N > 128) return fail(ctx, AMGT_ERR_ARG, "bad materials");
+  const int64_t C = ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2];
+  for (int64_t c = 0; c < C; ++c) {
+    if (!(st[c] > 0.0) || !(ss[c] >= 0.0) || !std::isfinite(st[c]) || !std::isfinite(ss[c]))
+      return fail(ctx, AMGT_ERR_ARG, "need sigma_t > 0 and sigma_s >= 0, finite");
+  }
+  ctx->sigma_t.assign(st, st + C);
+  ctx->sigma_s.assign(ss, ss + C);
+  ctx->fmom.assign(fmom, fmom + N + 1);
+  ctx->N = N;
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_angular_uniform(amgt_ctx* ctx, int basis, int level) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if ((basis != 0 && basis != 1) || level < 0 || level > 7)
+    return fail(ctx, AMGT_ERR_ARG, "basis 0/1 and level 0..7");
+  ctx->basis = basis;
+  ctx->paths = uniform_paths(level);
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_angular_aniso(amgt_ctx* ctx, int basis, const double axis[3], int lmax) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if ((basis != 0 && basis != 1) || lmax < 0 || lmax > 8 || !axis)
+    return fail(ctx, AMGT_ERR_ARG, "basis 0/1, lmax 0..8, axis non-null");
+  if (axis[0] == 0 && axis[1] == 0 && axis[2] == 0) return fail(ctx, AMGT_ERR_ARG, "zero axis");
+  ctx->basis = basis;
+  ctx->paths = aniso_paths(lmax, axis);
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_multigrid(amgt_ctx* ctx, int nlevels, const int* Nr, int nu_pre, int nu_post,
+                       int coarse_sweeps) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (nlevels < 1 || nlevels > 9 || nu_pre < 0 || nu_post < 0 || coarse_sweeps < 0)
+    return fail(ctx, AMGT_ERR_ARG, "bad multigrid parameters");
+  ctx->nlevels = nlevels;
+  ctx->Nr.clear();
+  if (Nr)
+    for (int i = 0; i < nlevels; ++i) {
+      if (Nr[i] < 0) return fail(ctx, AMGT_ERR_ARG, "negative scatter order");
+      ctx->Nr.push_back(Nr[i]);
+    }
+  ctx->nu_pre = nu_pre;
+  ctx->nu_post = nu_post;
+  ctx->coarse_sweeps = coarse_sweeps;
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_source_iso(amgt_ctx* ctx, const double* q) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "set the mesh first");
+  if (!q) return fail(ctx, AMGT_ERR_ARG, "null source");
+  const int64_t C = ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2];
+  ctx->qsrc.assign(q, q + C);
+  if (!ctx->dirty && ctx->d_q) {
+    CK(cudaMemcpy(ctx->d_q, ctx->qsrc.data(), sizeof(double) * C, cudaMemcpyHostToDevice));
+  } else {
+    ctx->dirty = true;
+  }
+  return AMGT_OK;
+}
+
+int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (face < 0 || face >= 6 || kind < 0 || kind > 1)
+    return fail(ctx, AMGT_ERR_ARG, "face 0..5, kind 0 (vacuum) or 1 (isotropic inflow)");
+  if (kind == 1 && !params) return fail(ctx, AMGT_ERR_ARG, "inflow needs params[0]");
+  ctx->bkind[face] = kind;
+  ctx->bval[face] = kind == 1 ? params[0] : 0.0;
+  ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_query_sizes(const amgt_ctx* cctx, int level, int64_t* nsdof, int64_t* nadof) {
+  amgt_ctx* ctx = const_cast<amgt_ctx*>(cctx);
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  if (nsdof) *nsdof = ctx->lv[level].nsdof;
+  if (nadof) *nadof = ctx->lv[level].nadof();
+  return AMGT_OK;
+}
+
+#define DISPATCH(dtype, CALL64, CALL32)                                            \
+  do {                                                                            \
+    if ((dtype) == AMGT_F64) return CALL64;                                       \
+    if ((dtype) == AMGT_F32 || (dtype) == AMGT_F32_BF16TC) return CALL32;         \
+    return fail(ctx, AMGT_ERR_ARG, "dtype must be AMGT_F64, AMGT_F32 or AMGT_F32_BF16TC"); \
+  } while (0)
+
+int amgt_op_source(amgt_ctx* ctx, int level, int dtype, void* f) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  DISPATCH(dtype, source_impl<double>(ctx, level, (double*)f),
+           source_impl<float>(ctx, level, (float*)f));
+}
+
+int amgt_op_sweep(amgt_ctx* ctx, int level, int dtype, const void* b, void* psi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  if (b == psi) return fail(ctx, AMGT_ERR_ARG, "sweep input and output must not alias");
+  DISPATCH(dtype, sweep_impl<double>(ctx, level, (const double*)b, (double*)psi),
+           sweep_impl<float>(ctx, level, (const float*)b, (float*)psi));
+}
+
+int amgt_op_apply_L(amgt_ctx* ctx, int level, int dtype, const void* x, void* y) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  DISPATCH(dtype, applyL_impl<double>(ctx, level, 1.0, 0.0, (const double*)x, (double*)y),
+           applyL_impl<float>(ctx, level, 1.0f, 0.0f, (const float*)x, (float*)y));
+}
+
+int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  DISPATCH(dtype,
+           scatter_impl<double>(ctx, level, false, (const double*)x, (double*)y, 1.0, 0.0, nullptr),
+           scatter_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y,
+                               1.0, 0.0, nullptr));
+}
+
+int amgt_op_apply_A(amgt_ctx* ctx, int level, int dtype, const void* x, void* y) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  DISPATCH(dtype, applyA_impl<double>(ctx, level, false, (const double*)x, (double*)y),
+           applyA_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y));
+}
+
+int amgt_op_restrict(amgt_ctx* ctx, int level, int dtype, const void* rf, void* rc) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  if (level + 1 >= (int)ctx->lv.size()) return fail(ctx, AMGT_ERR_ARG, "no coarser level");
+  DISPATCH(dtype, restrict_impl<double>(ctx, level, (const double*)rf, (double*)rc),
+           restrict_impl<float>(ctx, level, (const float*)rf, (float*)rc));
+}
+
+int amgt_op_prolong(amgt_ctx* ctx, int level, int dtype, const void* xc, void* xf) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  if (level + 1 >= (int)ctx->lv.size()) return fail(ctx, AMGT_ERR_ARG, "no coarser level");
+  DISPATCH(dtype, prolong_impl<double>(ctx, level, (const double*)xc, (double*)xf),
+           prolong_impl<float>(ctx, level, (const float*)xc, (float*)xf));
+}
+
+int amgt_op_smooth(amgt_ctx* ctx, int level, int dtype, int nu, const void* f, void* phi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  if (nu < 0) return fail(ctx, AMGT_ERR_ARG, "nu < 0");
+  DISPATCH(dtype, smooth_impl<double>(ctx, level, false, nu, (const double*)f, (double*)phi, false),
+           smooth_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, nu, (const float*)f,
+                              (float*)phi, false));
+}
+
+int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(build(ctx));
+  if (sweeps < 0) return fail(ctx, AMGT_ERR_ARG, "sweeps < 0");
+  DISPATCH(dtype, coarse_gs_impl<double>(ctx, sweeps, (const double*)f, (double*)phi),
+           coarse_gs_impl<float>(ctx, sweeps, (const float*)f, (float*)phi));
+}
+
+int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(build(ctx));
+  DISPATCH(dtype, vcycle_impl<double>(ctx, 0, false, (const double*)f, (double*)phi),
+           vcycle_impl<float>(ctx, 0, dtype == AMGT_F32_BF16TC, (const float*)f, (float*)phi));
+}
+
+int amgt_op_scalar_flux(amgt_ctx* ctx, int level, int dtype, const void* psi, void* phi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(check_level(ctx, level));
+  DISPATCH(dtype, scalar_flux_impl<double>(ctx, level, (const double*)psi, (double*)phi),
+           scalar_flux_impl<float>(ctx, level, (const float*)psi, (float*)phi));
+}
+
+int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double* psi,
+               double* phi, amgt_stats* st) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (!opt || !psi) return fail(ctx, AMGT_ERR_ARG, "options and psi are required");
+  TRY(build(ctx));
+  const auto t0 = std::chrono::steady_clock::now();
+  if (st) std::memset(st, 0, sizeof(*st));
+  const Level& L0 = ctx->lv[0];
+  const long long n = L0.nsdof * L0.nadof();
+  const size_t bytes = (size_t)n * sizeof(double);
+  const int m = opt->restart > 0 ? opt->restart : 20;
+  const int maxit = opt->maxit > 0 ? opt->maxit : 1000;
+  if (opt->precond == AMGT_PREC_MG && ctx->lv.size() < 2 && opt->mode == AMGT_MODE_F64) {
+    // a one-level "cycle" is the coarse solver alone
+  }
+  double *b, *x;
+  TRY(wsvec<double>(ctx, 0, 1, &b));
+  if (opt->device_ptrs) {
+    x = psi;
+  } else {
+    TRY(wsvec<double>(ctx, 0, 2, &x));
+  }
+  TRY(source_impl<double>(ctx, 0, b));
+  bool x_zero = true;
+  if (x0) {
+    CK(cudaMemcpyAsync(x, x0, bytes, opt->device_ptrs ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, ctx->stream));
+    x_zero = false;
+  }
+  KrylovResult kr;
+  int rc = AMGT_OK;
+  const int prec = opt->precond;
+  if (opt->mode == AMGT_MODE_F64) {
+    auto A64 = [&](const double* xx, double* yy) { return applyA_impl<double>(ctx, 0, false, xx, yy); };
+    auto M64 = [&](const double* v, double* z) -> int {
+      if (prec == AMGT_PREC_SWEEP) return sweep_impl<double>(ctx, 0, v, z);
+      if (prec == AMGT_PREC_MG) return vcycle_impl<double>(ctx, 0, false, v, z);
+      CK(cudaMemcpyAsync(z, v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      return AMGT_OK;
+    };
+    rc = gmres<double>(ctx, 0, A64, M64, b, x, x_zero, opt->tol, m, maxit, kr, st, -1.0, 0);
+    if (st) {
+      st->iterations = kr.its;
+      st->outer_iterations = kr.cycles;
+      st->relres = kr.relres;
+    }
+    if (rc == AMGT_OK && kr.relres >= opt->tol) rc = AMGT_ERR_NOT_CONVERGED;
+  } else if (opt->mode == AMGT_MODE_MIXED) {
+    const bool tc = tc_available();
+    float *r32, *e32;
+    double* r64;
+    TRY(wsvec<double>(ctx, 0, 0, &r64));
+    TRY(wsvec<float>(ctx, 0, 1, &r32));
+    TRY(wsvec<float>(ctx, 0, 2, &e32));
+    double bnorm;
+    TRY(norm2<double>(ctx, b, n, &bnorm));
+    if (bnorm == 0.0) {
+      CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
+    }
+    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, tc, xx, yy); };
+    auto M32 = [&](const float* v, float* z) -> int {
+      if (prec == AMGT_PREC_SWEEP) return sweep_impl<float>(ctx, 0, v, z);
+      if (prec == AMGT_PREC_MG) return vcycle_impl<float>(ctx, 0, tc, v, z);
+      CK(cudaMemcpyAsync(z, v, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+      return AMGT_OK;
+    };
+    int total_its = 0, outer = 0;
+    double relres = 1.0;
+    const double itol = opt->inner_tol > 0 ? opt->inner_tol : 1e-4;
+    const int imax = opt->inner_maxit > 0 ? opt->inner_maxit : 200;
+    while (bnorm > 0.0) {
+      if (x_zero) {
+        CK(cudaMemcpyAsync(r64, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      } else {
+        TRY(applyA_impl<double>(ctx, 0, false, x, r64));
+        launch_axpby<double>(n, 1.0, b, -1.0, r64, ctx->stream);
+      }
+      double rn;
+      TRY(norm2<double>(ctx, r64, n, &rn));
+      if (!std::isfinite(rn)) return fail(ctx, AMGT_ERR_NAN, "residual is not finite");
+      relres = rn / bnorm;
+      if (relres < opt->tol || total_its >= maxit || outer >= 50) break;
+      launch_convert<double, float>(n, r64, r32, ctx->stream);
+      launch_scale_copy<float>(n, 1.0 / rn, r32, r32, ctx->stream);
+      KrylovResult ik;
+      rc = gmres<float>(ctx, 0, A32, M32, r32, e32, true, itol, m,
+                        std::min(imax, maxit - total_its), ik, st, 1.0, total_its);
+      if (rc != AMGT_OK) break;
+      total_its += ik.its;
+      // x += rn * e  (FP64 accumulate)
+      launch_convert<float, double>(n, e32, r64, ctx->stream);
+      if (x_zero) {
+        launch_scale_copy<double>(n, rn, r64, x, ctx->stream);
+      } else {
+        launch_axpby<double>(n, rn, r64, 1.0, x, ctx->stream);
+      }
+      x_zero = false;
+      outer++;
+      if (ik.its == 0) break;
+    }
+    if (st) {
+      st->iterations = total_its;
+      st->outer_iterations = outer;
+      st->relres = relres;
+    }
+    if (rc == AMGT_OK && relres >= opt->tol) rc = AMGT_ERR_NOT_CONVERGED;
+  } else {
+    return fail(ctx, AMGT_ERR_ARG, "unknown mode");
+  }
+  if (rc != AMGT_OK && rc != AMGT_ERR_NOT_CONVERGED) return rc;
+  if (phi) {
+    double* ph;
+    if (opt->device_ptrs) {
+      ph = phi;
+    } else {
+      TRY(wsvec<double>(ctx, 0, 4, &ph));
+    }
+    TRY(scalar_flux_impl<double>(ctx, 0, x, ph));
+    if (!opt->device_ptrs)
+      CK(cudaMemcpyAsync(phi, ph, sizeof(double) * L0.nsdof, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (!opt->device_ptrs) CK(cudaMemcpyAsync(psi, x, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st)
+    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc == AMGT_ERR_NOT_CONVERGED) ctx->err = "GMRES did not reach the tolerance within maxit";
+  return rc;
+}
+
+}  // extern "C"

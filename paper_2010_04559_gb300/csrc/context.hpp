@@ -1,0 +1,106 @@
+// Library context: problem statement, set-up tables on host and device,
+// workspaces.  Internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <array>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/amgt.h"
+#include "kernels.cuh"
+#include "setup.hpp"
+
+namespace amgt {
+
+// device allocation owned by the context
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+};
+
+template <class T>
+struct LevelDevStore {
+  T *K0 = nullptr, *B = nullptr, *Kinv = nullptr, *Aax = nullptr, *Ginv = nullptr, *X = nullptr,
+    *XFt = nullptr, *Sqq = nullptr, *w = nullptr, *Aw = nullptr, *Sf = nullptr, *tblk = nullptr;
+};
+
+struct Level {
+  AngMesh mesh;
+  int Nr = 0, nmom = 1;
+  bool dense = false;   // dense S_f contraction cheaper than the moment form
+  std::vector<int> pdir, octant, dir_begin, dir_end;
+  int ndir = 0;
+  LevelDevStore<double> d64;
+  LevelDevStore<float> d32;
+  __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path
+  int *d_pdir = nullptr, *d_octant = nullptr, *d_dbeg = nullptr, *d_dend = nullptr;
+  // transfer to the next coarser level
+  int *d_parent = nullptr, *d_cbeg = nullptr, *d_cend = nullptr;
+  std::vector<int> task_dir, task_q0, task_nq;
+  int *d_task_dir = nullptr, *d_task_q0 = nullptr, *d_task_nq = nullptr;
+  long long nsdof = 0;
+  int nadof() const { return mesh.nadof(); }
+};
+
+struct Workspace {
+  // per level: r, f, phi, tmp in each precision
+  std::vector<void*> r, f, phi, tmp;
+};
+
+}  // namespace amgt
+
+struct amgt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err = "no error";
+
+  // ---- problem statement
+  int dim = 0;
+  int64_t ncell[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  std::vector<double> sigma_t, sigma_s, fmom;
+  int N = -1;
+  std::vector<double> qsrc;
+  int bkind[6] = {0, 0, 0, 0, 0, 0};
+  double bval[6] = {0, 0, 0, 0, 0, 0};
+  int basis = 1;
+  std::vector<std::vector<uint8_t>> paths;
+  int nlevels = 1;
+  std::vector<int> Nr;
+  int nu_pre = 1, nu_post = 1, coarse_sweeps = 10;
+  bool dirty = true;
+
+  // ---- built state
+  amgt::Q1 q1;
+  amgt::Geom geom{};
+  int C = 0, nmat = 0;
+  std::vector<int> mat;
+  std::vector<double> mat_st, mat_ss;
+  std::vector<amgt::Level> lv;
+  std::vector<amgt::Transfer> tr;
+  std::vector<std::unique_ptr<amgt::DevMem>> mem;  // every device allocation
+  int *d_mat = nullptr, *d_cells = nullptr, *d_level_off = nullptr, *d_bkind = nullptr;
+  double *d_sigt = nullptr, *d_sigs = nullptr, *d_q = nullptr, *d_bval = nullptr, *d_mu = nullptr,
+         *d_mf = nullptr;
+  float *d_sigt32 = nullptr, *d_sigs32 = nullptr;
+  int nlev_wave = 0;
+  // scratch
+  double* d_partials = nullptr;  // [nblk * 64]
+  double* d_dots = nullptr;      // [64]
+  void** d_ptrs = nullptr;       // device pointer arrays for multi-vector kernels [256]
+  int* d_status = nullptr;
+  std::vector<std::vector<void*>> ws64, ws32;  // per level: r, f, phi, tmp
+  void* d_moments = nullptr;                   // moment scratch [nsdof * nmom_max] (double)
+  size_t moments_bytes = 0;
+  void* d_bf16 = nullptr;                      // bf16 operand scratch
+  size_t bf16_bytes = 0;
+  int gs_cluster = 0;
+};

@@ -1,0 +1,131 @@
+// Device kernels of the transport hot path and their launch wrappers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace amgt {
+
+constexpr int kMaxS = 8;   // spatial nodes per cell (3D Q1)
+constexpr int kMaxA = 3;   // angular functions per patch (Lin)
+
+// Geometry and Q1 constants shared by the transport kernels (per launch).
+struct Geom {
+  int dim, s, a;
+  int nx, ny, nz;
+  int C;
+  long long nsdof;
+  int nadof, P;
+  double facemass[3][4][4];  // [axis][own face node][neighbour face node]
+  double Nmass[64];          // spatial mass matrix N (s x s)
+};
+
+// Tables of one angular level in precision T.
+template <class T>
+struct LevelDev {
+  const T* K0;     // [P][sa][sa] streaming part of the diagonal block
+  const T* B;      // [P][sa][sa] kron(N, M_q)
+  const T* Kinv;   // [nmat][P][sa][sa] inverse diagonal blocks
+  const T* Aax;    // [P][3][a][a] A^xi_q
+  const T* Ginv;   // [nmat][P][sa][sa] Gauss-Seidel block inverses (coarsest)
+  const T* X;      // [nadof][nmom]
+  const T* XFt;    // [nmom][nadof] diag(f_n) X^T
+  const T* Sqq;    // [P][a][a] self-scatter blocks X_q F X_q^T
+  const T* w;      // [nadof] int Psi
+  const int* pdir; // [P] sweep direction of each patch
+  int nmom;
+};
+
+struct CellData {
+  const int* mat;         // [C] material index
+  const double* sigma_t;  // [C]
+  const double* sigma_s;  // [C]
+  const float* sigma_t32;
+  const float* sigma_s32;
+};
+
+struct Schedule {
+  const int* cells;      // rotated cell coordinates sorted by wavefront level
+  const int* level_off;  // [nlev+1]
+  int nlev;
+  const int* task_dir;   // [ntask]
+  const int* task_q0;
+  const int* task_nq;
+  int ntask;
+};
+
+// status word written by device-side bounded waits
+struct DevStatus {
+  int* flag;  // device int, 0 = ok
+};
+
+// ---- launch wrappers (all asynchronous on `st`) ---------------------------
+template <class T>
+void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
+                  const T* b, T* psi, cudaStream_t st);
+template <class T>
+void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
+                    const T* x, T* y, cudaStream_t st);
+// C[M][N] = A[M][K] B[K][N] with epilogue (see kernels_gemm.cu)
+struct GemmEpi {
+  int mode;            // 0 store, 1 cell mix: out = alpha*sig_s*Nmix(acc) + beta*out + add
+  double alpha, beta;
+  const void* add;     // optional [M][N] same type, may be null
+  int s;               // rows per cell
+  const double* sig;   // per-cell scale (double) for T=double
+  const float* sig32;  // per-cell scale for T=float
+};
+template <class T>
+void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
+                 const GemmEpi& epi, cudaStream_t st);
+void set_mass_matrix(const double* Nref, int s);  // constant-memory spatial mass (s x s)
+
+template <class T>
+void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
+                     const int* cend, const T* blk, const T* rf, T* rc, cudaStream_t st);
+template <class T>
+void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, const int* parent,
+                    const T* blk, const T* xc, T* xf, cudaStream_t st);
+template <class T>
+void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant,
+                   const double* q, const double* bnd_val, const int* bnd_kind,
+                   const double* mu, const double* mf, T* f, cudaStream_t st);
+template <class T>
+void launch_scalar_flux(long long nsdof, int nadof, const T* w, const T* psi, T* phi,
+                        cudaStream_t st);
+template <class T>
+void launch_coarse_gs(const Geom& g, const LevelDev<T>& t, const CellData& cd,
+                      const Schedule& sc, int ndir, const int* dir_begin, const int* dir_end,
+                      int sweeps, const T* f, T* phi, T* moments, int* status,
+                      cudaStream_t st);
+
+// BLAS-1/2 for GMRES (FP64 or FP32); partials has room for blocks*(nvec)
+template <class T>
+void launch_multidot(long long n, int nvec, const T* const* V, const T* w, double* partials,
+                     int nblk, double* out, cudaStream_t st);
+template <class T>
+void launch_update_multidot(long long n, int nvec, const T* const* V, const double* h, T* w,
+                            int do_dot, double* partials, int nblk, double* out,
+                            cudaStream_t st);
+template <class T>
+void launch_axpby(long long n, double alpha, const T* x, double beta, T* y, cudaStream_t st);
+template <class T>
+void launch_scale_copy(long long n, double alpha, const T* x, T* y, cudaStream_t st);
+template <class Tin, class Tout>
+void launch_convert(long long n, const Tin* x, Tout* y, cudaStream_t st);
+template <class T>
+void launch_lincomb(long long n, int nvec, const T* const* Z, const double* y, T* x,
+                    cudaStream_t st);
+int gemv_blocks(long long n);
+
+// process-wide count of kernels launched by the library
+void note_launch(int n = 1);
+long long launch_count();
+
+// BF16 tensor-core scatter (tcgen05): Y = epilogue(Xb[M][K] * Sb[K][N])
+struct TcGemm;
+bool tc_available();
+int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
+                   float* C, const GemmEpi& epi, int* status, cudaStream_t st);
+
+}  // namespace amgt

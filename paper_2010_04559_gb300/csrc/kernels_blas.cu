@@ -1,0 +1,262 @@
+// Vector kernels of restarted GMRES: fused multi-dot products and updates for
+// classical Gram-Schmidt applied twice (CGS2), linear combinations and
+// precision conversions.  Reductions are deterministic: each block writes its
+// partial sums to `partials[block][v]` and one block sums them in a fixed
+// order.  Partial sums are accumulated in FP64 for FP64 vectors and in FP32
+// per thread (FP64 across threads) for FP32 vectors.
+#include <atomic>
+
+#include "kernels.cuh"
+
+namespace amgt {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxVec = 32;
+
+template <class T>
+struct Acc {
+  using type = double;
+};
+template <>
+struct Acc<float> {
+  using type = float;
+};
+
+template <int NV>
+__device__ void block_reduce_store(double (&v)[NV], int nvec, double* __restrict__ partials) {
+  __shared__ double red[kThreads / 32][kMaxVec];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    if (k >= nvec) break;
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[wid][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+    partials[(long long)blockIdx.x * nvec + threadIdx.x] = s;
+  }
+}
+
+// out[v] = sum_i V[v][i] * w[i]
+template <class T, int NV>
+__global__ void __launch_bounds__(kThreads) multidot_kernel(long long n, int nvec,
+                                                            const T* const* __restrict__ V,
+                                                            const T* __restrict__ w,
+                                                            double* __restrict__ partials) {
+  using A = typename Acc<T>::type;
+  A acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = A(0);
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    const A wi = (A)w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nvec) acc[k] += (A)V[k][i] * wi;
+  }
+  double d[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) d[k] = (double)acc[k];
+  block_reduce_store<NV>(d, nvec, partials);
+}
+
+// w[i] -= sum_v h[v] V[v][i]; then (do_dot == 1) out[v] = sum_i V[v][i] w[i]
+// or (do_dot == 2) out[0] = sum_i w[i]^2
+template <class T, int NV>
+__global__ void __launch_bounds__(kThreads) update_multidot_kernel(
+    long long n, int nvec, const T* const* __restrict__ V, const double* __restrict__ h,
+    T* __restrict__ w, int do_dot, double* __restrict__ partials) {
+  using A = typename Acc<T>::type;
+  __shared__ double hs[kMaxVec];
+  if (threadIdx.x < nvec) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  A acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = A(0);
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    T vk[NV];
+    double wi = (double)w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nvec) {
+        vk[k] = V[k][i];
+        wi -= hs[k] * (double)vk[k];
+      }
+    const T wn = (T)wi;
+    w[i] = wn;
+    if (do_dot == 1) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k < nvec) acc[k] += (A)vk[k] * (A)wn;
+    } else if (do_dot == 2) {
+      acc[0] += (A)wn * (A)wn;
+    }
+  }
+  if (do_dot == 0) return;
+  const int nout = do_dot == 1 ? nvec : 1;
+  double d[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) d[k] = (double)acc[k];
+  block_reduce_store<NV>(d, nout, partials);
+}
+
+__global__ void finish_kernel(int nblk, int nvec, const double* __restrict__ partials,
+                              double* __restrict__ out) {
+  // one warp per output, fixed summation order
+  const int lane = threadIdx.x & 31;
+  for (int v = threadIdx.x >> 5; v < nvec; v += blockDim.x >> 5) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += partials[(long long)b * nvec + v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[v] = s;
+  }
+}
+
+template <class T>
+__global__ void axpby_kernel(long long n, double alpha, const T* __restrict__ x, double beta,
+                             T* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = alpha * (double)x[i];
+    if (beta != 0.0) v += beta * (double)y[i];
+    y[i] = (T)v;
+  }
+}
+
+template <class T>
+__global__ void scale_copy_kernel(long long n, double alpha, const T* __restrict__ x,
+                                  T* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)(alpha * (double)x[i]);
+}
+
+template <class Tin, class Tout>
+__global__ void convert_kernel(long long n, const Tin* __restrict__ x, Tout* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (Tout)x[i];
+}
+
+template <>
+__global__ void convert_kernel<float, __nv_bfloat16>(long long n, const float* __restrict__ x,
+                                                     __nv_bfloat16* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// x[i] += sum_v y[v] Z[v][i]
+template <class T, int NV>
+__global__ void __launch_bounds__(kThreads) lincomb_kernel(long long n, int nvec,
+                                                           const T* const* __restrict__ Z,
+                                                           const double* __restrict__ y,
+                                                           T* __restrict__ x) {
+  __shared__ double ys[kMaxVec];
+  if (threadIdx.x < nvec) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
+       i += (long long)gridDim.x * kThreads) {
+    double v = (double)x[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+      if (k < nvec) v += ys[k] * (double)Z[k][i];
+    x[i] = (T)v;
+  }
+}
+
+int grid_1d(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > 152LL * 8) g = 152LL * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int gemv_blocks(long long n) { return grid_1d(n); }
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+template <class T>
+void launch_multidot(long long n, int nvec, const T* const* V, const T* w, double* partials,
+                     int nblk, double* out, cudaStream_t st) {
+  note_launch(2);
+  if (nvec <= 8)
+    multidot_kernel<T, 8><<<nblk, kThreads, 0, st>>>(n, nvec, V, w, partials);
+  else
+    multidot_kernel<T, kMaxVec><<<nblk, kThreads, 0, st>>>(n, nvec, V, w, partials);
+  finish_kernel<<<1, 1024, 0, st>>>(nblk, nvec, partials, out);
+}
+
+template <class T>
+void launch_update_multidot(long long n, int nvec, const T* const* V, const double* h, T* w,
+                            int do_dot, double* partials, int nblk, double* out,
+                            cudaStream_t st) {
+  note_launch(do_dot ? 2 : 1);
+  if (nvec <= 8)
+    update_multidot_kernel<T, 8><<<nblk, kThreads, 0, st>>>(n, nvec, V, h, w, do_dot, partials);
+  else
+    update_multidot_kernel<T, kMaxVec><<<nblk, kThreads, 0, st>>>(n, nvec, V, h, w, do_dot,
+                                                                   partials);
+  if (do_dot) finish_kernel<<<1, 1024, 0, st>>>(nblk, do_dot == 1 ? nvec : 1, partials, out);
+}
+
+template <class T>
+void launch_axpby(long long n, double alpha, const T* x, double beta, T* y, cudaStream_t st) {
+  note_launch();
+  axpby_kernel<T><<<grid_1d(n), kThreads, 0, st>>>(n, alpha, x, beta, y);
+}
+
+template <class T>
+void launch_scale_copy(long long n, double alpha, const T* x, T* y, cudaStream_t st) {
+  note_launch();
+  scale_copy_kernel<T><<<grid_1d(n), kThreads, 0, st>>>(n, alpha, x, y);
+}
+
+template <class Tin, class Tout>
+void launch_convert(long long n, const Tin* x, Tout* y, cudaStream_t st) {
+  note_launch();
+  convert_kernel<Tin, Tout><<<grid_1d(n), kThreads, 0, st>>>(n, x, y);
+}
+
+template <class T>
+void launch_lincomb(long long n, int nvec, const T* const* Z, const double* y, T* x,
+                    cudaStream_t st) {
+  note_launch();
+  if (nvec <= 8)
+    lincomb_kernel<T, 8><<<grid_1d(n), kThreads, 0, st>>>(n, nvec, Z, y, x);
+  else
+    lincomb_kernel<T, kMaxVec><<<grid_1d(n), kThreads, 0, st>>>(n, nvec, Z, y, x);
+}
+
+#define AMGT_INST(T)                                                                          \
+  template void launch_multidot<T>(long long, int, const T* const*, const T*, double*, int,  \
+                                   double*, cudaStream_t);                                   \
+  template void launch_update_multidot<T>(long long, int, const T* const*, const double*, T*, \
+                                          int, double*, int, double*, cudaStream_t);          \
+  template void launch_axpby<T>(long long, double, const T*, double, T*, cudaStream_t);      \
+  template void launch_scale_copy<T>(long long, double, const T*, T*, cudaStream_t);         \
+  template void launch_lincomb<T>(long long, int, const T* const*, const double*, T*,        \
+                                  cudaStream_t);
+AMGT_INST(double)
+AMGT_INST(float)
+#undef AMGT_INST
+template void launch_convert<double, float>(long long, const double*, float*, cudaStream_t);
+template void launch_convert<float, double>(long long, const float*, double*, cudaStream_t);
+template void launch_convert<float, __nv_bfloat16>(long long, const float*, __nv_bfloat16*,
+                                                   cudaStream_t);
+template void launch_convert<double, __nv_bfloat16>(long long, const double*, __nv_bfloat16*,
+                                                    cudaStream_t);
+
+}  // namespace amgt

@@ -1,0 +1,132 @@
+// Tiled SIMT GEMM for the FP64/FP32 scatter source (Sec. 4.2):
+//   C[M][N] = A[M][K] * B[K][N]   (row major, leading dimensions lda/ldb/ldc)
+// with an epilogue that applies the per-cell spatial mass and scatter cross
+// section along the row (spatial DOF) index:
+//   mode 0: C = acc
+//   mode 1: C[c*s+l][j] = alpha * sig[c] * sum_i N[l][i] acc[c*s+i][j]
+//                         + beta * C_old + add[c*s+l][j]
+// The row tile (64) is a multiple of s (4 or 8), so every cell's rows sit in
+// one tile and the mixing is done from shared memory.
+#include "kernels.cuh"
+
+namespace amgt {
+
+__constant__ double c_Nmass[64];
+
+void set_mass_matrix(const double* Nref, int s) {
+  cudaMemcpyToSymbol(c_Nmass, Nref, sizeof(double) * s * s);
+}
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const T* __restrict__ A,
+                                                   int lda, const T* __restrict__ B, int ldb,
+                                                   T* __restrict__ C, int ldc, GemmEpi epi) {
+  // the epilogue tile reuses the operand tiles' shared memory
+  constexpr int kOperandBytes = (BK * (BM + 1) + BK * BN) * sizeof(T);
+  constexpr int kTileBytes = BM * (BN + 1) * sizeof(T);
+  __shared__ __align__(16) unsigned char smem[kOperandBytes > kTileBytes ? kOperandBytes : kTileBytes];
+  T (*As)[BM + 1] = reinterpret_cast<T (*)[BM + 1]>(smem);
+  T (*Bs)[BN] = reinterpret_cast<T (*)[BN]>(smem + BK * (BM + 1) * sizeof(T));
+  T (*Ct)[BN + 1] = reinterpret_cast<T (*)[BN + 1]>(smem);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    // A tile: 64 x 16, 1024 elements, 4 per thread
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = threadIdx.x + e * 256;
+      const int r = lin / BK, kk = lin % BK;
+      const int gr = bm + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int lin = threadIdx.x + e * 256;
+      const int kk = lin / BN, cc = lin % BN;
+      const int gk = k0 + kk, gc = bn + cc;
+      Bs[kk][cc] = (gk < K && gc < N) ? B[(long long)gk * ldb + gc] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  if (epi.mode == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int gr = bm + ty + 16 * i, gc = bn + tx + 16 * j;
+        if (gr < M && gc < N) C[(long long)gr * ldc + gc] = acc[i][j];
+      }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Ct[ty + 16 * i][tx + 16 * j] = acc[i][j];
+  __syncthreads();
+  const int s = epi.s;
+  const T* add = static_cast<const T*>(epi.add);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 16 * i;
+    const int gr = bm + r;
+    if (gr >= M) continue;
+    const int l = gr % s;
+    const int cell = gr / s;
+    const int r0 = r - l;
+    const double sg =
+        sizeof(T) == 8 ? epi.sig[cell] : (double)epi.sig32[cell];
+    const T scale = (T)(epi.alpha * sg);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int cc = tx + 16 * j;
+      const int gc = bn + cc;
+      if (gc >= N) continue;
+      T mix = T(0);
+      for (int ii = 0; ii < s; ++ii) mix += (T)c_Nmass[l * s + ii] * Ct[r0 + ii][cc];
+      T v = scale * mix;
+      T* o = C + (long long)gr * ldc + gc;
+      if (epi.beta != 0.0) v += (T)epi.beta * (*o);
+      if (add) v += add[(long long)gr * ldc + gc];
+      *o = v;
+    }
+  }
+}
+
+}  // namespace
+
+template <class T>
+void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
+                 const GemmEpi& epi, cudaStream_t st) {
+  note_launch();
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM), block(256);
+  gemm_kernel<T><<<grid, block, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi);
+}
+
+template void launch_gemm<double>(int, int, int, const double*, int, const double*, int,
+                                  double*, int, const GemmEpi&, cudaStream_t);
+template void launch_gemm<float>(int, int, int, const float*, int, const float*, int, float*,
+                                 int, const GemmEpi&, cudaStream_t);
+
+}  // namespace amgt

@@ -1,0 +1,47 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads,
+exports every entry point declared in include/amgt.h, and rejects bad calls
+without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_04559_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "amgt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amgt_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    assert "amgt_solve" in names and "amgt_op_sweep" in names and "amgt_op_scatter" in names
+    from paper_2010_04559_gb300 import EXPORTS
+    assert sorted(EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_null_context_is_rejected(lib):
+    lib.amgt_set_angular_uniform.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    lib.amgt_set_angular_uniform.restype = ctypes.c_int
+    assert lib.amgt_set_angular_uniform(None, 1, 2) == -1
+    lib.amgt_last_error.argtypes = [ctypes.c_void_p]
+    lib.amgt_last_error.restype = ctypes.c_char_p
+    assert lib.amgt_last_error(None) == b"null context"
+    lib.amgt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.amgt_create.restype = ctypes.c_int
+    assert lib.amgt_create(None, 0, None) == -1

@@ -1,0 +1,272 @@
+"""GPU parity of every hot-path operator against the FP64 CPU oracle, through
+the C ABI (include/amgt.h) on seeded inputs.
+
+Tolerances (relative L2 over the compared entries):
+  FP64 operators            1e-12  (deterministic linear maps; rounding only)
+  FP64 solves               1e-10  (both sides solved to relres 1e-13)
+  FP32 operators            2e-5   (unit roundoff 6e-8 times sum lengths <= a few 1e3)
+  BF16 tensor-core scatter  1e-2   (inputs rounded to 8-bit mantissas, FP32 sums)
+  mixed-precision solve     1e-6   (after FP64 iterative refinement to relres 1e-12)
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import angular, gmres, multigrid, transport
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_04559_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _ctx(prob):
+    from paper_2010_04559_gb300 import context_from_problem
+    return context_from_problem(prob, device=0)
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.detach().double().cpu().numpy()
+
+
+def _oracle(prob, level=None, Nscat=None):
+    lev = prob["level"] if level is None else level
+    am = angular.AngularMesh(angular.uniform_paths(lev), prob["basis"])
+    return transport.Transport(prob, am, Nscat)
+
+
+# (dim, ncell, level, basis): spans several wavefront levels, ragged sizes,
+# Const and Lin, 2D and 3D
+CASES = [
+    (2, (7, 5), 1, "lin"),
+    (2, (9, 4), 2, "const"),
+    (2, (4, 6), 0, "lin"),
+    (3, (3, 4, 2), 1, "lin"),
+    (3, (2, 3, 3), 0, "const"),
+]
+IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}" for d, n, l, b in CASES]
+
+
+@pytest.mark.parametrize("dim,nc,level,basis", CASES, ids=IDS)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_transport_operators(dim, nc, level, basis, dtype):
+    prob = W.random_problem(dim, nc, level, 6, 31, basis=basis, inflow=0.4)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    x = W.random_vector((T.nsdof, T.nadof), 32)
+    xd = _dev(x, td)
+    y = torch.empty_like(xd)
+    # sweep L^-1
+    ctx.amgt_op_sweep(0, xd, y)
+    assert _rel(_host(y), T.sweep(x)) < tol
+    # L x
+    ctx.amgt_op_apply_L(0, xd, y)
+    assert _rel(_host(y), T.apply_L(x)) < tol
+    # S x
+    ctx.amgt_op_scatter(0, xd, y)
+    assert _rel(_host(y), T.scatter(x)) < tol
+    # (L - S) x
+    ctx.amgt_op_apply_A(0, xd, y)
+    assert _rel(_host(y), T.apply_A(x)) < tol
+    # source f
+    f = torch.empty_like(xd)
+    ctx.amgt_op_source(0, f)
+    assert _rel(_host(f), T.source()) < tol
+    # scalar flux
+    ph = torch.empty(T.nsdof, device="cuda", dtype=td)
+    ctx.amgt_op_scalar_flux(0, xd, ph)
+    assert _rel(_host(ph), T.scalar_flux(x)) < tol
+    ctx.close()
+
+
+def _mg_problem(dim, nc, level, basis, nlev, Nr, sweeps=4, seed=41):
+    prob = W.random_problem(dim, nc, level, 8, seed, basis=basis, g=0.85)
+    prob["mg"] = dict(nlevels=nlev, Nr=Nr, nu_pre=1, nu_post=1, coarse_sweeps=sweeps)
+    return prob
+
+
+MG_CASES = [
+    (2, (6, 5), 2, "lin", 3, [8, 4, 3]),
+    (2, (5, 7), 2, "const", 2, [8, 5]),
+    (3, (3, 2, 3), 1, "lin", 2, [8, 4]),
+]
+MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ in MG_CASES]
+
+
+@pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype):
+    prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
+    H = multigrid.Hierarchy(prob)
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    T0, T1 = H.levels[0], H.levels[1]
+    # level sizes agree
+    assert ctx.amgt_query_sizes(0) == (T0.nsdof, T0.nadof)
+    assert ctx.amgt_query_sizes(1) == (T1.nsdof, T1.nadof)
+    r = W.random_vector((T0.nsdof, T0.nadof), 42)
+    rc = torch.empty((T1.nsdof, T1.nadof), device="cuda", dtype=td)
+    ctx.amgt_op_restrict(0, _dev(r, td), rc)
+    assert _rel(_host(rc), H.restrict(r, 0)) < tol
+    xc = W.random_vector((T1.nsdof, T1.nadof), 43)
+    xf = _dev(r, td)
+    ctx.amgt_op_prolong(0, _dev(xc, td), xf)
+    assert _rel(_host(xf), r + H.prolong(xc, 0)) < tol
+    # coarse-level scatter with the reduced order
+    y1 = torch.empty_like(rc)
+    ctx.amgt_op_scatter(1, _dev(xc, td), y1)
+    assert _rel(_host(y1), T1.scatter(xc)) < tol
+    # smoother
+    f = W.random_vector((T0.nsdof, T0.nadof), 44)
+    phi0 = W.random_vector((T0.nsdof, T0.nadof), 45)
+    ph = _dev(phi0, td)
+    ctx.amgt_op_smooth(0, 2, _dev(f, td), ph)
+    assert _rel(_host(ph), H.smooth(phi0, f, 0, 2)) < tol
+    # coarse Gauss-Seidel on the coarsest level
+    Tc = H.levels[-1]
+    fc = W.random_vector((Tc.nsdof, Tc.nadof), 46)
+    pc0 = W.random_vector((Tc.nsdof, Tc.nadof), 47)
+    pc = _dev(pc0, td)
+    ctx.amgt_op_coarse_gs(3, _dev(fc, td), pc)
+    assert _rel(_host(pc), multigrid.coarse_gs(Tc, fc, pc0, 3)) < tol * 10
+    # one V-cycle
+    out = torch.empty_like(ph)
+    ctx.amgt_op_vcycle(_dev(f, td), out)
+    assert _rel(_host(out), H.vcycle(f)) < tol * 10
+    ctx.close()
+
+
+@pytest.mark.parametrize("precond", ["sweep", "mg"])
+def test_fp64_solve_matches_oracle(precond):
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_MG, AMGT_PREC_SWEEP
+    prob = _mg_problem(2, (8, 7), 2, "lin", 3, [8, 4, 4], sweeps=10, seed=51)
+    prob["boundary"] = [(1, 0.3), (0, 0.0), (1, 0.1), (0, 0.0)]
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    f = T.source()
+    xo, its, _, rel = gmres.gmres(T.apply_A, f, T.sweep, 1e-13, 20, 1000)
+    ctx = _ctx(prob)
+    pc = AMGT_PREC_SWEEP if precond == "sweep" else AMGT_PREC_MG
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-13, restart=20, maxit=1000, precond=pc,
+                                      mode=AMGT_MODE_F64)
+    assert st.relres < 1e-13
+    assert _rel(psi, xo) < 1e-10
+    assert _rel(phi, T.scalar_flux(xo)) < 1e-10
+    if precond == "mg":
+        _, its_mg, _, _ = gmres.gmres(T.apply_A, f, lambda v: H.vcycle(v), 1e-13, 20, 1000)
+        # same preconditioner and same GMRES: iteration counts agree closely
+        assert abs(st.iterations - its_mg) <= 1
+    ctx.close()
+
+
+def test_mixed_solve_matches_oracle():
+    from paper_2010_04559_gb300 import AMGT_MODE_MIXED, AMGT_PREC_MG
+    prob = _mg_problem(2, (8, 8), 2, "lin", 3, [8, 4, 4], sweeps=10, seed=52)
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    xo, *_ = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+    ctx = _ctx(prob)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-12, restart=20, maxit=1000, precond=AMGT_PREC_MG,
+                                      mode=AMGT_MODE_MIXED, inner_tol=1e-4)
+    assert st.relres < 1e-12
+    assert _rel(psi, xo) < 1e-6
+    ctx.close()
+
+
+def test_config1_square16_fp64_gmres20():
+    """The 16x16 / level-1 / HG g = 0.8 order-8 problem, FP64 GMRES(20) to 1e-8,
+    sweep preconditioner; compared with the oracle solved to 1e-12."""
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_SWEEP
+    prob = W.config1_square16()
+    T = _oracle(prob)
+    xo, *_ = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-12, 20, 2000)
+    ctx = _ctx(prob)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-8, restart=20, maxit=2000,
+                                      precond=AMGT_PREC_SWEEP, mode=AMGT_MODE_F64)
+    assert st.relres < 1e-8
+    # ||x - xo|| <= kappa * 1e-8 in principle; the bound observed is far smaller
+    assert _rel(psi, xo) < 1e-6
+    # scalar flux is positive inside the source region
+    assert phi.min() > 0
+    ctx.close()
+
+
+def test_pure_absorber_single_iteration():
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_SWEEP
+    prob = W.random_problem(2, (5, 5), 1, 4, 61)
+    prob["sigma_s"] = np.zeros_like(prob["sigma_s"])
+    ctx = _ctx(prob)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-12, precond=AMGT_PREC_SWEEP, mode=AMGT_MODE_F64)
+    assert st.iterations == 1 and st.relres < 1e-12
+    ctx.close()
+
+
+def test_infinite_medium_on_gpu():
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_SWEEP
+    C = 6 * 5
+    st_, ss_, q = 3.0, 2.4, 1.0
+    psi_inf = q / (4 * np.pi) / (st_ - ss_)
+    prob = W.problem(2, (6, 5), np.full(C, st_), np.full(C, ss_), 6, W.hg_moments(0.8, 6),
+                     np.full(C, q), 2, boundary=[(1, psi_inf)] * 4)
+    ctx = _ctx(prob)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-13, precond=AMGT_PREC_SWEEP, mode=AMGT_MODE_F64)
+    assert np.abs(psi - psi_inf).max() / psi_inf < 1e-10
+    assert np.abs(phi - q / (st_ - ss_)).max() < 1e-9
+    ctx.close()
+
+
+def test_empty_source_gives_zero():
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_SWEEP
+    prob = W.random_problem(2, (3, 3), 1, 4, 62)
+    prob["q"] = np.zeros_like(prob["q"])
+    ctx = _ctx(prob)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-10, precond=AMGT_PREC_SWEEP, mode=AMGT_MODE_F64)
+    assert np.abs(psi).max() == 0.0 and st.iterations == 0
+    ctx.close()
+
+
+def test_single_cell_mesh():
+    prob = W.random_problem(2, (1, 1), 1, 4, 63, inflow=0.5)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    x = W.random_vector((T.nsdof, T.nadof), 64)
+    y = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=torch.float64)
+    ctx.amgt_op_sweep(0, _dev(x), y)
+    assert _rel(_host(y), T.sweep(x)) < 1e-12
+    ctx.close()
+
+
+def test_bad_arguments_raise():
+    from paper_2010_04559_gb300 import AmgtError
+    prob = W.random_problem(2, (3, 3), 1, 4, 65)
+    ctx = _ctx(prob)
+    x = torch.zeros((36 * 1, 96), device="cuda", dtype=torch.float64)
+    with pytest.raises(AmgtError):
+        ctx.amgt_op_sweep(0, x, x)          # aliasing in/out
+    with pytest.raises(AmgtError):
+        ctx.amgt_op_restrict(0, x, x)       # single-level hierarchy
+    with pytest.raises(AmgtError):
+        ctx.amgt_set_angular_uniform(1, 12)
+    ctx.close()
