@@ -135,6 +135,14 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q);
 /* Boundary face f = 2*axis + side (side 1 = high): kind 0 vacuum, kind 1
  * isotropic inflow of angular flux params[0]. */
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
+/* Kernel tuning knobs (results do not depend on them beyond rounding):
+ *   AMGT_TUNE_GS_KERNEL   0 auto, 1 per-patch coarse Gauss-Seidel kernel,
+ *                         2 direction-blocked kernel (precomputed block
+ *                         lower-triangular inverses; same iteration)
+ *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto) */
+#define AMGT_TUNE_GS_KERNEL 1
+#define AMGT_TUNE_SWEEP_GROUP 2
+int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Sizes of level k of the hierarchy. */
 int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);
 

@@ -35,13 +35,16 @@ AMGT_MODE_MIXED = 1
 
 AMGT_MAX_HIST = 1024
 
+AMGT_TUNE_GS_KERNEL = 1
+AMGT_TUNE_SWEEP_GROUP = 2
+
 # every exported symbol of include/amgt.h
 EXPORTS = [
     "amgt_create", "amgt_destroy", "amgt_last_error", "amgt_set_stream", "amgt_sync",
     "amgt_query_launches",
     "amgt_set_mesh_cartesian", "amgt_set_materials", "amgt_set_angular_uniform",
     "amgt_set_angular_aniso", "amgt_set_multigrid", "amgt_set_source_iso",
-    "amgt_set_boundary", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
+    "amgt_set_boundary", "amgt_set_tuning", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
     "amgt_op_sweep", "amgt_op_apply_L", "amgt_op_scatter", "amgt_op_apply_A",
     "amgt_op_restrict", "amgt_op_prolong", "amgt_op_smooth", "amgt_op_coarse_gs",
     "amgt_op_vcycle", "amgt_op_scalar_flux",
@@ -82,6 +85,7 @@ _SIGS = {
     "amgt_set_multigrid": ([_P, _I, _PI, _I, _I, _I], _I),
     "amgt_set_source_iso": ([_P, _PD], _I),
     "amgt_set_boundary": ([_P, _I, _I, _PD], _I),
+    "amgt_set_tuning": ([_P, _I, _I], _I),
     "amgt_query_sizes": ([_P, _I, _PI64, _PI64], _I),
     "amgt_solve": ([_P, ctypes.POINTER(amgt_options), _P, _P, _P,
                     ctypes.POINTER(amgt_stats)], _I),
@@ -219,6 +223,9 @@ class Context:
         p = _np([value], np.float64)
         return self._check(self.lib.amgt_set_boundary(self.h, int(face), int(kind),
                                                       p.ctypes.data_as(_PD)))
+
+    def amgt_set_tuning(self, key, value):
+        return self._check(self.lib.amgt_set_tuning(self.h, int(key), int(value)))
 
     def amgt_query_sizes(self, level=0):
         a = ctypes.c_int64()

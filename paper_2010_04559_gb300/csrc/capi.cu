@@ -163,6 +163,68 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
   return AMGT_OK;
 }
 
+// Coarse Gauss-Seidel in direction-blocked form: for each material and sweep
+// direction d, T = blockdiag_q(K0_q + sigma_t B_q) - sigma_s N (x) S_dd^{L+D}
+// over the entries e = l*J + (q - q_b)*a + m, and its inverse (stored
+// transposed); S_dd^{L+D} keeps the scatter blocks S_qp with p <= q.
+int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
+                    const std::vector<double>& B, const std::vector<double>& X,
+                    const std::vector<double>& F) {
+  const int s = ctx->q1.s, a = Lv.mesh.a, nm = Lv.nmom, sa = s * a;
+  int Jmax = 0;
+  for (int d = 0; d < Lv.ndir; ++d) Jmax = std::max(Jmax, (Lv.dir_end[d] - Lv.dir_begin[d]) * a);
+  const int Emax = s * Jmax;
+  Lv.Jmax = Jmax;
+  Lv.Emax = Emax;
+  if (Emax > 384) return AMGT_OK;  // the per-patch kernel handles larger directions
+  std::vector<double> SLD((size_t)Lv.ndir * Jmax * Jmax, 0.0);
+  std::vector<double> TinvT((size_t)ctx->nmat * Lv.ndir * Emax * Emax, 0.0);
+  std::vector<double> T((size_t)Emax * Emax), Ti((size_t)Emax * Emax);
+  for (int d = 0; d < Lv.ndir; ++d) {
+    const int qb = Lv.dir_begin[d], J = (Lv.dir_end[d] - qb) * a, E = s * J;
+    double* sl = &SLD[(size_t)d * Jmax * Jmax];
+    for (int j = 0; j < J; ++j)
+      for (int j2 = 0; j2 < J; ++j2) {
+        const int q = j / a, p = j2 / a;
+        if (p > q) continue;
+        double acc = 0.0;
+        const double* xa = &X[(size_t)(qb * a + j) * nm];
+        const double* xb = &X[(size_t)(qb * a + j2) * nm];
+        for (int kk = 0; kk < nm; ++kk) acc += xa[kk] * F[kk] * xb[kk];
+        sl[j * Jmax + j2] = acc;
+      }
+    if (E == 0) continue;
+    for (int mt = 0; mt < ctx->nmat; ++mt) {
+      std::fill(T.begin(), T.begin() + (size_t)E * E, 0.0);
+      for (int l = 0; l < s; ++l)
+        for (int j = 0; j < J; ++j) {
+          const int e = l * J + j, q = j / a, m = j % a;
+          for (int i = 0; i < s; ++i)
+            for (int j2 = 0; j2 < J; ++j2) {
+              const int e2 = i * J + j2, p = j2 / a, dd = j2 % a;
+              double v = 0.0;
+              if (p == q) {
+                const size_t o = (size_t)(qb + q) * sa * sa + (size_t)(l * a + m) * sa + i * a + dd;
+                v += K0[o] + ctx->mat_st[mt] * B[o];
+              }
+              v -= ctx->mat_ss[mt] * ctx->q1.N[l * s + i] * sl[j * Jmax + j2];
+              T[(size_t)e * E + e2] = v;
+            }
+        }
+      if (!invert(E, T.data(), Ti.data()))
+        return fail(ctx, AMGT_ERR_ARG, "singular direction-blocked Gauss-Seidel matrix");
+      double* out = &TinvT[((size_t)mt * Lv.ndir + d) * Emax * Emax];
+      for (int r = 0; r < E; ++r)
+        for (int cc = 0; cc < E; ++cc) out[(size_t)cc * Emax + r] = Ti[(size_t)r * E + cc];
+    }
+  }
+  TRY(upload(ctx, TinvT, &Lv.d64.TinvT));
+  TRY(upload(ctx, TinvT, &Lv.d32.TinvT));
+  TRY(upload(ctx, SLD, &Lv.d64.SLD));
+  TRY(upload(ctx, SLD, &Lv.d32.SLD));
+  return AMGT_OK;
+}
+
 int build(amgt_ctx* ctx) {
   if (!ctx->dirty) return AMGT_OK;
   if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "mesh not set");
@@ -327,6 +389,7 @@ int build(amgt_ctx* ctx) {
     Lv.task_nq.clear();
     const int maxdiag = max_wavefront_cells(g);
     int G = std::max(1, std::min(16, 256 / std::max(1, maxdiag)));
+    if (ctx->sweep_group > 0) G = ctx->sweep_group;
     for (int d = 0; d < Lv.ndir; ++d)
       for (int q0 = Lv.dir_begin[d]; q0 < Lv.dir_end[d]; q0 += G) {
         Lv.task_dir.push_back(d);
@@ -342,6 +405,7 @@ int build(amgt_ctx* ctx) {
     TRY(upload(ctx, Lv.task_nq, &Lv.d_task_nq));
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));
     TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32));
+    if (k == nl - 1) TRY(build_gs_blocks(ctx, Lv, K0, B, X, F));
   }
   for (int k = 0; k + 1 < nl; ++k) {
     Level& F = ctx->lv[k];
@@ -599,9 +663,16 @@ int coarse_gs_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
                  L.nmom, e0, ctx->stream);
   int cl = 0;
-  launch_coarse_gs<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
-                      schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom, &cl,
-                      ctx->stream);
+  if (store<T>(L).TinvT && ctx->gs_kernel != 1) {
+    launch_coarse_gs_block<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
+                              schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom,
+                              store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax, &cl,
+                              ctx->stream);
+  } else {
+    launch_coarse_gs<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
+                        schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom, &cl,
+                        ctx->stream);
+  }
   if (cl == 0) return fail(ctx, AMGT_ERR_CUDA, "coarse Gauss-Seidel cluster launch failed");
   ctx->gs_cluster = cl;
   CK(cudaGetLastError());
@@ -935,6 +1006,22 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
   ctx->bval[face] = kind == 1 ? params[0] : 0.0;
   ctx->dirty = true;
   return AMGT_OK;
+}
+
+int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (key == AMGT_TUNE_GS_KERNEL) {
+    if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0, 1 or 2");
+    ctx->gs_kernel = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_SWEEP_GROUP) {
+    if (value < 0 || value > 16) return fail(ctx, AMGT_ERR_ARG, "sweep group 0..16");
+    if (value != ctx->sweep_group) ctx->dirty = true;
+    ctx->sweep_group = value;
+    return AMGT_OK;
+  }
+  return fail(ctx, AMGT_ERR_ARG, "unknown tuning key");
 }
 
 int amgt_query_sizes(const amgt_ctx* cctx, int level, int64_t* nsdof, int64_t* nadof) {

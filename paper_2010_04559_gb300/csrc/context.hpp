@@ -29,7 +29,8 @@ struct DevMem {
 template <class T>
 struct LevelDevStore {
   T *K0 = nullptr, *B = nullptr, *Kinv = nullptr, *Aax = nullptr, *Ginv = nullptr, *X = nullptr,
-    *XFt = nullptr, *Sqq = nullptr, *w = nullptr, *Aw = nullptr, *Sf = nullptr, *tblk = nullptr;
+    *XFt = nullptr, *Sqq = nullptr, *w = nullptr, *Aw = nullptr, *Sf = nullptr, *tblk = nullptr,
+    *TinvT = nullptr, *SLD = nullptr;
 };
 
 struct Level {
@@ -38,6 +39,7 @@ struct Level {
   bool dense = false;   // dense S_f contraction cheaper than the moment form
   std::vector<int> pdir, octant, dir_begin, dir_end;
   int ndir = 0;
+  int Emax = 0, Jmax = 0;  // direction-blocked Gauss-Seidel table sizes (coarsest level)
   LevelDevStore<double> d64;
   LevelDevStore<float> d32;
   __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path
@@ -103,4 +105,6 @@ struct amgt_ctx {
   void* d_bf16 = nullptr;                      // bf16 operand scratch
   size_t bf16_bytes = 0;
   int gs_cluster = 0;
+  int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
+  int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
 };

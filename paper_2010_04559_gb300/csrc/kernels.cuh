@@ -99,6 +99,14 @@ void launch_coarse_gs(const Geom& g, const LevelDev<T>& t, const CellData& cd,
                       int sweeps, const T* f, T* phi, T* moments, int* status,
                       cudaStream_t st);
 
+// direction-blocked coarse Gauss-Seidel (same iteration, see kernels_gs.cu)
+template <class T>
+void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData& cd,
+                            const Schedule& sc, int ndir, const int* dir_begin,
+                            const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
+                            const T* TinvT, const T* SLD, int Emax, int Jmax, int* status,
+                            cudaStream_t st);
+
 // BLAS-1/2 for GMRES (FP64 or FP32); partials has room for blocks*(nvec)
 template <class T>
 void launch_multidot(long long n, int nvec, const T* const* V, const T* w, double* partials,

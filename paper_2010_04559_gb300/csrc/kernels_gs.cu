@@ -159,6 +159,187 @@ __global__ void __launch_bounds__(512) coarse_gs_kernel(Geom g, LevelDev<T> t, C
   }
 }
 
+// ---------------------------------------------------------------------------
+// Direction-blocked form of the same Gauss-Seidel sweep.  For the patches Q_d
+// of sweep direction d in one cell, visiting them in index order with the
+// latest values is one forward block substitution with the block lower
+// triangle of the cell-direction matrix:
+//   (D_d - sigma_s N (x) S_dd^{L+D}) x_d^new
+//       = f_d - up_d + sigma_s N (x) (S_{d,all} x^cur - S_dd^{L+D} x_d^old),
+// where D_d = blockdiag_q(K0_q + sigma_t B_q), S_dd^{L+D} keeps the blocks
+// S_qp with p <= q, and S_{d,all} x^cur = X_d F Phi_c (moment form).  The
+// inverse of the left-hand matrix, Tinv[mat][d] (E x E, E = s * |Q_d| * a,
+// stored transposed), is precomputed, so the |Q_d| sequential patch solves
+// become one matrix-vector product -- the same result up to rounding.
+// Each warp owns one cell at a time and keeps its data in shared memory.
+template <class T, int DIM, int A>
+__global__ void __launch_bounds__(512) coarse_gs_block_kernel(
+    Geom g, LevelDev<T> t, CellData cd, Schedule sc, int ndir, const int* __restrict__ dir_begin,
+    const int* __restrict__ dir_end, int sweeps, const T* __restrict__ f, T* __restrict__ psi,
+    T* __restrict__ mom, const T* __restrict__ TinvT, const T* __restrict__ SLD, int Emax,
+    int Jmax) {
+  constexpr int S = 1 << DIM;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int wpc = blockDim.x >> 5;
+  const int gw = (int)cluster.block_rank() * wpc + wib;
+  const int W = (int)cluster.num_blocks() * wpc;
+  const int nm = t.nmom;
+  const int nadof = g.nadof;
+  // per-warp workspace: rhs[Emax], xold[Emax], buf[Emax], phi[S*nm]
+  T* ws = reinterpret_cast<T*>(smem_raw) + (size_t)wib * (3 * Emax + S * nm);
+  T* rhs = ws;
+  T* xold = ws + Emax;
+  T* buf = ws + 2 * Emax;
+  T* phs = ws + 3 * Emax;
+  const int stride[3] = {1, g.nx, g.nx * g.ny};
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int d = 0; d < ndir; ++d) {
+      int neg[3];
+      if (DIM == 2) {
+        neg[0] = (d >> 1) & 1; neg[1] = d & 1; neg[2] = 0;
+      } else {
+        neg[0] = (d >> 2) & 1; neg[1] = (d >> 1) & 1; neg[2] = d & 1;
+      }
+      const int qb = dir_begin[d];
+      const int J = (dir_end[d] - qb) * A;
+      const int E = S * J;
+      const T* SLDd = SLD + (size_t)d * Jmax * Jmax;
+      for (int w = 0; w < sc.nlev; ++w) {
+        const int beg = sc.level_off[w];
+        const int cnt = sc.level_off[w + 1] - beg;
+        for (int k = gw; k < cnt; k += W) {
+          const int packed = sc.cells[beg + k];
+          const int jj[3] = {packed & 2047, (packed >> 11) & 2047, packed >> 22};
+          const int ix = neg[0] ? g.nx - 1 - jj[0] : jj[0];
+          const int iy = neg[1] ? g.ny - 1 - jj[1] : jj[1];
+          const int iz = neg[2] ? g.nz - 1 - jj[2] : jj[2];
+          const int c = ix + g.nx * (iy + g.ny * iz);
+          const int mat = cd.mat[c];
+          const T sig_s = (T)cd.sigma_s[c];
+          T* Phi = mom + (long long)c * S * nm;
+          // 1. loads: f - upwind, old values, cell moments
+          for (int e = lane; e < E; e += 32) {
+            const int l = e / J, j = e - (e / J) * J;
+            const int q = qb + j / A, m = j % A;
+            const long long gi = ((long long)c * S + l) * nadof + qb * A + j;
+            T r = f[gi];
+            xold[e] = __ldcg(psi + gi);
+#pragma unroll
+            for (int xi = 0; xi < DIM; ++xi) {
+              if (jj[xi] == 0) continue;
+              const int own = neg[xi];
+              if (((l >> xi) & 1) != own) continue;
+              const int cn = c + (own ? stride[xi] : -stride[xi]);
+              const T nsgn = own ? T(1) : T(-1);
+              const T* An = t.Aax + ((size_t)q * 3 + xi) * A * A + m * A;
+              const int jp = fcompress(l, xi);
+              const T* pn = psi + (long long)cn * S * nadof + q * A;
+              T acc = T(0);
+#pragma unroll
+              for (int j2 = 0; j2 < S / 2; ++j2) {
+                const int i = fnode(j2, xi, 1 - own);
+                T sacc = T(0);
+#pragma unroll
+                for (int dd = 0; dd < A; ++dd) sacc += An[dd] * __ldcg(pn + (long long)i * nadof + dd);
+                acc += T(g.facemass[xi][jp][j2]) * sacc;
+              }
+              r -= nsgn * acc;
+            }
+            rhs[e] = r;
+          }
+          for (int e = lane; e < S * nm; e += 32) phs[e] = __ldcg(Phi + e);
+          __syncwarp();
+          // 2. buf = X_d F Phi - S_dd^{L+D} x_old   (entry (l, j))
+          for (int e = lane; e < E; e += 32) {
+            const int l = e / J, j = e - (e / J) * J;
+            T acc = T(0);
+            const T* xf = t.XFt + qb * A + j;
+            for (int kk = 0; kk < nm; ++kk) acc += xf[(long long)kk * nadof] * phs[l * nm + kk];
+            const T* sl = SLDd + (size_t)j * Jmax;
+            const T* xo = xold + l * J;
+            for (int j2 = 0; j2 < J; ++j2) acc -= sl[j2] * xo[j2];
+            buf[e] = acc;
+          }
+          __syncwarp();
+          // 3. rhs += sigma_s N (x) buf
+          for (int e = lane; e < E; e += 32) {
+            const int l = e / J, j = e - (e / J) * J;
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < S; ++i) acc += (T)g.Nmass[l * S + i] * buf[i * J + j];
+            rhs[e] += sig_s * acc;
+          }
+          __syncwarp();
+          // 4. x_new = Tinv rhs  (Tinv stored transposed: TinvT[col][row])
+          const T* Tm = TinvT + ((size_t)mat * ndir + d) * Emax * Emax;
+          for (int r = lane; r < E; r += 32) {
+            T acc = T(0);
+            for (int cc = 0; cc < E; ++cc) acc += Tm[(size_t)cc * Emax + r] * rhs[cc];
+            buf[r] = acc;
+          }
+          __syncwarp();
+          // 5. store, delta
+          for (int e = lane; e < E; e += 32) {
+            const int l = e / J, j = e - (e / J) * J;
+            const long long gi = ((long long)c * S + l) * nadof + qb * A + j;
+            psi[gi] = buf[e];
+            xold[e] = buf[e] - xold[e];
+          }
+          __syncwarp();
+          // 6. Phi_c += X_d^T delta
+          for (int e = lane; e < S * nm; e += 32) {
+            const int l = e / nm, kk = e - (e / nm) * nm;
+            T acc = T(0);
+            const T* xr = t.X + (long long)(qb * A) * nm + kk;
+            const T* dl = xold + l * J;
+            for (int j = 0; j < J; ++j) acc += xr[(long long)j * nm] * dl[j];
+            Phi[e] = phs[e] + acc;
+          }
+          __syncwarp();
+        }
+        cluster.sync();
+      }
+    }
+  }
+}
+
+template <class T, int DIM, int A>
+cudaError_t launch_gs_block_impl(int cl, int wpc, const Geom& g, const LevelDev<T>& t,
+                                 const CellData& cd, const Schedule& sc, int ndir, const int* db,
+                                 const int* de, int sweeps, const T* f, T* phi, T* mom,
+                                 const T* TinvT, const T* SLD, int Emax, int Jmax,
+                                 cudaStream_t st) {
+  auto kern = coarse_gs_block_kernel<T, DIM, A>;
+  const size_t smem = (size_t)wpc * (3 * Emax + (1 << DIM) * t.nmom) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (cl > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(32 * wpc);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorLaunchOutOfResources;
+  return cudaLaunchKernelEx(&cfg, kern, g, t, cd, sc, ndir, db, de, sweeps, f, phi, mom, TinvT,
+                            SLD, Emax, Jmax);
+}
+
 template <class T, int DIM, int A>
 cudaError_t launch_gs_impl(int cl, const Geom& g, const LevelDev<T>& t, const CellData& cd,
                            const Schedule& sc, int ndir, const int* db, const int* de,
@@ -216,6 +397,45 @@ void launch_coarse_gs(const Geom& g, const LevelDev<T>& t, const CellData& cd,
   }
   if (status) *status = 0;
 }
+
+template <class T>
+void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData& cd,
+                            const Schedule& sc, int ndir, const int* dir_begin,
+                            const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
+                            const T* TinvT, const T* SLD, int Emax, int Jmax, int* status,
+                            cudaStream_t st) {
+  const int sizes[3] = {16, 8, 1};
+  const size_t per_warp = (size_t)(3 * Emax + g.s * t.nmom) * sizeof(T);
+  int wpc = 16;
+  while (wpc > 1 && per_warp * wpc > 200 * 1024) wpc /= 2;
+  for (int cl : sizes) {
+    cudaError_t e;
+    if (g.dim == 2 && g.a == 3)
+      e = launch_gs_block_impl<T, 2, 3>(cl, wpc, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, st);
+    else if (g.dim == 2)
+      e = launch_gs_block_impl<T, 2, 1>(cl, wpc, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, st);
+    else if (g.a == 3)
+      e = launch_gs_block_impl<T, 3, 3>(cl, wpc, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, st);
+    else
+      e = launch_gs_block_impl<T, 3, 1>(cl, wpc, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, st);
+    if (e == cudaSuccess) {
+      note_launch();
+      if (status) *status = cl;
+      return;
+    }
+    cudaGetLastError();
+  }
+  if (status) *status = 0;
+}
+
+template void launch_coarse_gs_block<double>(const Geom&, const LevelDev<double>&, const CellData&,
+                                             const Schedule&, int, const int*, const int*, int,
+                                             const double*, double*, double*, const double*,
+                                             const double*, int, int, int*, cudaStream_t);
+template void launch_coarse_gs_block<float>(const Geom&, const LevelDev<float>&, const CellData&,
+                                            const Schedule&, int, const int*, const int*, int,
+                                            const float*, float*, float*, const float*,
+                                            const float*, int, int, int*, cudaStream_t);
 
 template void launch_coarse_gs<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                        const Schedule&, int, const int*, const int*, int,

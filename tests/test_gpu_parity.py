@@ -116,10 +116,12 @@ MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ i
 
 @pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype):
+@pytest.mark.parametrize("gs_kernel", [1, 2], ids=["gs-per-patch", "gs-blocked"])
+def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
     H = multigrid.Hierarchy(prob)
     ctx = _ctx(prob)
+    ctx.amgt_set_tuning(1, gs_kernel)
     td = torch.float64 if dtype == "f64" else torch.float32
     tol = 1e-12 if dtype == "f64" else 2e-5
     T0, T1 = H.levels[0], H.levels[1]
