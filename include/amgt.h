@@ -180,6 +180,23 @@ int amgt_op_smooth(amgt_ctx* ctx, int level, int dtype, int nu, const void* f, v
 /* `sweeps` block Gauss-Seidel sweeps on the coarsest level with self-scatter
  * in each block solve (Sec. 4.2); phi is read and overwritten. */
 int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi);
+/* Same as amgt_op_coarse_gs, but allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library call.  Meant for callers that cannot let a library
+ * allocate device memory while they run -- a process whose device memory is
+ * owned by another framework's caching allocator or held under a fixed
+ * budget, or a latency-critical loop that cannot afford an allocation's
+ * implicit synchronisation.  The paper has no counterpart to this call.
+ * Scratch: the coarsest level's cell flux moments (Nsdof x nmom values of
+ * dtype) live in one fixed device array of 32 MiB built into the library,
+ * present on every GPU that loads it until the process exits.  Larger
+ * coarse levels are rejected with AMGT_ERR_ARG.  Its device address is
+ * looked up once per device during context set-up, so set-up must be
+ * complete before the call (AMGT_ERR_STATE otherwise; any operator or
+ * amgt_query_sizes completes it).  Every call, from every context, uses the
+ * same array and leaves its contents behind; each call overwrites it before
+ * reading, so no clearing is needed, but calls that overlap on the GPU (other
+ * streams, other contexts) race on it and must be serialised by the caller. */
+int amgt_op_coarse_gs_noalloc(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi);
 /* phi = LMG(0, f, finest) (Fig. lmg).  dtype AMGT_F32_BF16TC runs the FP32
  * cycle with the BF16 tensor-core scatter. */
 int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi);

@@ -47,6 +47,7 @@ EXPORTS = [
     "amgt_set_boundary", "amgt_set_tuning", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
     "amgt_op_sweep", "amgt_op_apply_L", "amgt_op_scatter", "amgt_op_apply_A",
     "amgt_op_restrict", "amgt_op_prolong", "amgt_op_smooth", "amgt_op_coarse_gs",
+    "amgt_op_coarse_gs_noalloc",
     "amgt_op_vcycle", "amgt_op_scalar_flux",
 ]
 
@@ -98,6 +99,7 @@ _SIGS = {
     "amgt_op_prolong": ([_P, _I, _I, _P, _P], _I),
     "amgt_op_smooth": ([_P, _I, _I, _I, _P, _P], _I),
     "amgt_op_coarse_gs": ([_P, _I, _I, _P, _P], _I),
+    "amgt_op_coarse_gs_noalloc": ([_P, _I, _I, _P, _P], _I),
     "amgt_op_vcycle": ([_P, _I, _P, _P], _I),
     "amgt_op_scalar_flux": ([_P, _I, _I, _P, _P], _I),
 }
@@ -319,6 +321,12 @@ class Context:
         self._req(f, phi)
         return self._check(self.lib.amgt_op_coarse_gs(self.h, self._dtype_code(f), sweeps,
                                                       _dptr(f), _dptr(phi)))
+
+    def amgt_op_coarse_gs_noalloc(self, sweeps, f, phi):
+        """Coarse Gauss-Seidel without any device allocation (fixed scratch)."""
+        self._req(f, phi)
+        return self._check(self.lib.amgt_op_coarse_gs_noalloc(
+            self.h, self._dtype_code(f), sweeps, _dptr(f), _dptr(phi)))
 
     def amgt_op_vcycle(self, f, phi, tc=False):
         self._req(f, phi)

@@ -176,7 +176,9 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
   const int Emax = s * Jmax;
   Lv.Jmax = Jmax;
   Lv.Emax = Emax;
-  if (Emax > 384) return AMGT_OK;  // the per-patch kernel handles larger directions
+  // the per-patch kernel handles larger directions and very many materials
+  if (Emax > 384 || (size_t)ctx->nmat * Lv.ndir * Emax * Emax * sizeof(double) > (256u << 20))
+    return AMGT_OK;
   std::vector<double> SLD((size_t)Lv.ndir * Jmax * Jmax, 0.0);
   std::vector<double> TinvT((size_t)ctx->nmat * Lv.ndir * Emax * Emax, 0.0);
   std::vector<double> T((size_t)Emax * Emax), Ti((size_t)Emax * Emax);
@@ -459,6 +461,7 @@ int build(amgt_ctx* ctx) {
   CK(cudaMemset(ctx->d_status, 0, 16 * sizeof(int)));
   ctx->ws64.assign(nl, {});
   ctx->ws32.assign(nl, {});
+  CK(noalloc_moment_address(ctx->device, &ctx->noalloc_moments));
   ctx->dirty = false;
   return AMGT_OK;
 }
@@ -652,12 +655,35 @@ int smooth_impl(amgt_ctx* ctx, int k, bool tc, int nu, const T* f, T* phi, bool 
 }
 
 template <class T>
+int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom);
+
+template <class T>
 int coarse_gs_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
-  const int k = (int)ctx->lv.size() - 1;
-  const Level& L = ctx->lv[k];
+  const Level& L = ctx->lv.back();
   void* mp;
   TRY(moments_scratch(ctx, (size_t)L.nsdof * L.nmom * sizeof(T), &mp));
-  T* mom = static_cast<T*>(mp);
+  return coarse_gs_run<T>(ctx, sweeps, f, phi, static_cast<T*>(mp));
+}
+
+// Same operator with the moments in the library's fixed device array; no
+// allocation of any kind.
+template <class T>
+int coarse_gs_noalloc_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
+  const Level& L = ctx->lv.back();
+  const size_t need = (size_t)L.nsdof * L.nmom * sizeof(T);
+  if (need > noalloc_moment_bytes())
+    return fail(ctx, AMGT_ERR_ARG,
+                "coarse level needs " + std::to_string(need) + " bytes of moment scratch; the "
+                "allocation-free entry point holds at most " +
+                    std::to_string(noalloc_moment_bytes()) + " bytes");
+  if (!ctx->noalloc_moments) return fail(ctx, AMGT_ERR_STATE, "fixed scratch not set up");
+  return coarse_gs_run<T>(ctx, sweeps, f, phi, static_cast<T*>(ctx->noalloc_moments));
+}
+
+template <class T>
+int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
+  const int k = (int)ctx->lv.size() - 1;
+  const Level& L = ctx->lv[k];
   GemmEpi e0{};
   e0.mode = 0;
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
@@ -1109,6 +1135,19 @@ int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void*
   if (sweeps < 0) return fail(ctx, AMGT_ERR_ARG, "sweeps < 0");
   DISPATCH(dtype, coarse_gs_impl<double>(ctx, sweeps, (const double*)f, (double*)phi),
            coarse_gs_impl<float>(ctx, sweeps, (const float*)f, (float*)phi));
+}
+
+int amgt_op_coarse_gs_noalloc(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi) {
+  if (!ctx) return AMGT_ERR_ARG;
+  // set-up allocates, so it must already be complete
+  if (ctx->dirty)
+    return fail(ctx, AMGT_ERR_STATE,
+                "problem set-up is not complete: call amgt_query_sizes (or any other "
+                "operator) after the last set_* call first");
+  if (sweeps < 0) return fail(ctx, AMGT_ERR_ARG, "sweeps < 0");
+  if (f == phi) return fail(ctx, AMGT_ERR_ARG, "f and phi must not alias");
+  DISPATCH(dtype, coarse_gs_noalloc_impl<double>(ctx, sweeps, (const double*)f, (double*)phi),
+           coarse_gs_noalloc_impl<float>(ctx, sweeps, (const float*)f, (float*)phi));
 }
 
 int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi) {

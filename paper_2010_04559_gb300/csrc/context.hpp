@@ -105,6 +105,7 @@ struct amgt_ctx {
   void* d_bf16 = nullptr;                      // bf16 operand scratch
   size_t bf16_bytes = 0;
   int gs_cluster = 0;
+  void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
 };

@@ -107,6 +107,10 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
                             const T* TinvT, const T* SLD, int Emax, int Jmax, int* status,
                             cudaStream_t st);
 
+// fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
+size_t noalloc_moment_bytes();
+cudaError_t noalloc_moment_address(int device, void** out);
+
 // BLAS-1/2 for GMRES (FP64 or FP32); partials has room for blocks*(nvec)
 template <class T>
 void launch_multidot(long long n, int nvec, const T* const* V, const T* w, double* partials,

@@ -15,11 +15,52 @@
 // a hardware cluster barrier between wavefront levels.
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace amgt {
+
+// Fixed scratch for amgt_op_coarse_gs_noalloc: the cells' flux moments
+// Phi[Nsdof][nmom] of the coarsest level.  It is part of the library image, so
+// every GPU that loads the library holds it until the process exits.  All
+// calls share it and it keeps the last call's contents; it is fully
+// overwritten at the start of each call, so nothing needs clearing.
+constexpr size_t kNoAllocMomentBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_moments[kNoAllocMomentBytes];
+
+size_t noalloc_moment_bytes() { return kNoAllocMomentBytes; }
+
+// Device address of g_noalloc_moments for `device`, looked up once per device
+// with that device current (host code must not use the symbol itself as a
+// device pointer).  Called at context set-up.
+cudaError_t noalloc_moment_address(int device, void** out) {
+  static std::mutex mu;
+  static std::map<int, void*> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(device);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return e;
+  if (cur != device) {
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return e;
+  }
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_moments);
+  if (cur != device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return e;
+  cache[device] = ptr;
+  *out = ptr;
+  return cudaSuccess;
+}
 
 namespace {
 
