@@ -137,11 +137,18 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q);
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 /* Kernel tuning knobs (results do not depend on them beyond rounding):
  *   AMGT_TUNE_GS_KERNEL   0 auto, 1 per-patch coarse Gauss-Seidel kernel,
- *                         2 direction-blocked kernel (precomputed block
- *                         lower-triangular inverses; same iteration)
- *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto) */
+ *                         2 direction-blocked kernel, one warp per cell,
+ *                         3 direction-blocked kernel, one thread group per
+ *                         cell with the tables in shared memory when they fit
+ *                         (else as 2) (2 and 3 use
+ *                         precomputed block lower-triangular inverses: the
+ *                         same iteration up to rounding)
+ *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto)
+ *   AMGT_TUNE_SWEEP_STAGES depth of the 2D sweep's copy pipeline (0 = auto,
+ *                         2, 3, 4 or 6 levels) */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
+#define AMGT_TUNE_SWEEP_STAGES 3
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Sizes of level k of the hierarchy. */
 int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);

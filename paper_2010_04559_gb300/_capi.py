@@ -37,6 +37,7 @@ AMGT_MAX_HIST = 1024
 
 AMGT_TUNE_GS_KERNEL = 1
 AMGT_TUNE_SWEEP_GROUP = 2
+AMGT_TUNE_SWEEP_STAGES = 3
 
 # every exported symbol of include/amgt.h
 EXPORTS = [

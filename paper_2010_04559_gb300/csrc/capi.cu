@@ -95,6 +95,7 @@ LevelDev<T> level_view(const Level& L, const LevelDevStore<T>& s) {
   v.XFt = s.XFt;
   v.Sqq = s.Sqq;
   v.w = s.w;
+  v.Mang = s.Mang;
   v.pdir = L.d_pdir;
   v.nmom = L.nmom;
   return v;
@@ -159,6 +160,7 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
   TRY(upload(ctx, Sqq, &s.Sqq));
   TRY(upload(ctx, L.mesh.w, &s.w));
   TRY(upload(ctx, L.mesh.Aw, &s.Aw));
+  TRY(upload(ctx, L.mesh.M, &s.Mang));
   if (!tblk.empty()) TRY(upload(ctx, tblk, &s.tblk));
   return AMGT_OK;
 }
@@ -265,6 +267,19 @@ int build(amgt_ctx* ctx) {
       for (int j = 0; j < hs; ++j) g.facemass[xi][jp][j] = q1.facemass[(xi * hs + jp) * hs + j];
   for (int i = 0; i < s * s; ++i) g.Nmass[i] = q1.N[i];
   set_mass_matrix(q1.N.data(), s);
+  {
+    // G_xi for a positive / negative Omega_xi (outflow through the high / low face)
+    std::vector<double> Gax(3 * 2 * 64, 0.0), Nsp(64, 0.0);
+    for (int xi = 0; xi < dim; ++xi)
+      for (int sg = 0; sg < 2; ++sg)
+        for (int i = 0; i < s * s; ++i) {
+          const double fo = sg == 0 ? q1.Fown[(size_t)(2 * xi + 1) * s * s + i]
+                                    : -q1.Fown[(size_t)(2 * xi) * s * s + i];
+          Gax[(xi * 2 + sg) * 64 + i] = fo - q1.V[(size_t)xi * s * s + i];
+        }
+    for (int i = 0; i < s * s; ++i) Nsp[i] = q1.N[i];
+    set_transport_constants(Gax.data(), Nsp.data());
+  }
   CK(cudaGetLastError());
   const int C = g.C;
   ctx->C = C;
@@ -390,14 +405,32 @@ int build(amgt_ctx* ctx) {
     Lv.task_q0.clear();
     Lv.task_nq.clear();
     const int maxdiag = max_wavefront_cells(g);
-    int G = std::max(1, std::min(16, 256 / std::max(1, maxdiag)));
+    int G;
+    if (dim == 2) {
+      // row-pipelined kernel: ny * G threads per block; prefer >= ~120 blocks
+      G = 8;
+      while (G > 1 && (g.ny * G > 512 || P / G < 120)) G /= 2;
+    } else {
+      G = std::max(1, std::min(16, 256 / std::max(1, maxdiag)));
+    }
     if (ctx->sweep_group > 0) G = ctx->sweep_group;
+    if (dim == 2 && g.ny * G > 512) G = std::max(1, 512 / g.ny);
+    Lv.sweep_G = dim == 2 ? G : 0;
     for (int d = 0; d < Lv.ndir; ++d)
       for (int q0 = Lv.dir_begin[d]; q0 < Lv.dir_end[d]; q0 += G) {
         Lv.task_dir.push_back(d);
         Lv.task_q0.push_back(q0);
         Lv.task_nq.push_back(std::min(G, Lv.dir_end[d] - q0));
       }
+    // 16-byte staging copies need 16-byte aligned segment starts and lengths
+    Lv.chunk16_f32 = Lv.chunk16_f64 = (dim == 2);
+    for (size_t i = 0; i < Lv.task_q0.size(); ++i) {
+      for (int bytes : {4, 8}) {
+        bool ok = ((size_t)nadof * bytes) % 16 == 0 && ((size_t)Lv.task_q0[i] * a * bytes) % 16 == 0 &&
+                  ((size_t)Lv.task_nq[i] * a * bytes) % 16 == 0 && ((size_t)G * a * bytes) % 16 == 0;
+        if (!ok) (bytes == 4 ? Lv.chunk16_f32 : Lv.chunk16_f64) = false;
+      }
+    }
     TRY(upload(ctx, Lv.pdir, &Lv.d_pdir));
     TRY(upload(ctx, Lv.octant, &Lv.d_octant));
     TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
@@ -587,8 +620,10 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
 template <class T>
 int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   const Level& L = ctx->lv[k];
+  const bool c16 = sizeof(T) == 4 ? L.chunk16_f32 : L.chunk16_f64;
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
-                  schedule(ctx, k), b, psi, ctx->stream);
+                  schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, c16, ctx->sweep_stages,
+                  ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -692,8 +727,8 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
   if (store<T>(L).TinvT && ctx->gs_kernel != 1) {
     launch_coarse_gs_block<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                               schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom,
-                              store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax, &cl,
-                              ctx->stream);
+                              store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax, ctx->nmat,
+                              ctx->gs_kernel, &cl, ctx->stream);
   } else {
     launch_coarse_gs<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                         schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom, &cl,
@@ -1037,8 +1072,13 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (!ctx) return AMGT_ERR_ARG;
   if (key == AMGT_TUNE_GS_KERNEL) {
-    if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0, 1 or 2");
+    if (value < 0 || value > 3) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..3");
     ctx->gs_kernel = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_SWEEP_STAGES) {
+    if (value < 0 || value > 6) return fail(ctx, AMGT_ERR_ARG, "sweep stages 0..6");
+    ctx->sweep_stages = value;
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_SWEEP_GROUP) {

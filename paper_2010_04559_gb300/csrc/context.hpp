@@ -30,7 +30,7 @@ template <class T>
 struct LevelDevStore {
   T *K0 = nullptr, *B = nullptr, *Kinv = nullptr, *Aax = nullptr, *Ginv = nullptr, *X = nullptr,
     *XFt = nullptr, *Sqq = nullptr, *w = nullptr, *Aw = nullptr, *Sf = nullptr, *tblk = nullptr,
-    *TinvT = nullptr, *SLD = nullptr;
+    *TinvT = nullptr, *SLD = nullptr, *Mang = nullptr;
 };
 
 struct Level {
@@ -40,6 +40,8 @@ struct Level {
   std::vector<int> pdir, octant, dir_begin, dir_end;
   int ndir = 0;
   int Emax = 0, Jmax = 0;  // direction-blocked Gauss-Seidel table sizes (coarsest level)
+  int sweep_G = 0;         // patches per block of the 2D row-pipelined sweep (0: level kernel)
+  bool chunk16_f32 = false, chunk16_f64 = false;
   LevelDevStore<double> d64;
   LevelDevStore<float> d32;
   __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path
@@ -108,4 +110,5 @@ struct amgt_ctx {
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
+  int sweep_stages = 0; // AMGT_TUNE_SWEEP_STAGES
 };

@@ -32,6 +32,7 @@ struct LevelDev {
   const T* XFt;    // [nmom][nadof] diag(f_n) X^T
   const T* Sqq;    // [P][a][a] self-scatter blocks X_q F X_q^T
   const T* w;      // [nadof] int Psi
+  const T* Mang;   // [P][a][a] angular mass M_q
   const int* pdir; // [P] sweep direction of each patch
   int nmom;
 };
@@ -60,9 +61,12 @@ struct DevStatus {
 };
 
 // ---- launch wrappers (all asynchronous on `st`) ---------------------------
+// G > 0 and dim == 2: row-pipelined kernel with G patches per block (the
+// schedule's tasks must then hold G-patch groups); otherwise the level kernel.
 template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, cudaStream_t st);
+                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst,
+                  cudaStream_t st);
 template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
                     const T* x, T* y, cudaStream_t st);
@@ -79,6 +83,9 @@ template <class T>
 void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
                  const GemmEpi& epi, cudaStream_t st);
 void set_mass_matrix(const double* Nref, int s);  // constant-memory spatial mass (s x s)
+// constant-memory spatial matrices of the Kronecker form of L:
+// Gax[axis][sign][s*s] (sign 1 = negative Omega component) and N[s*s]
+void set_transport_constants(const double* Gax, const double* Nsp);
 
 template <class T>
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
@@ -104,8 +111,8 @@ template <class T>
 void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData& cd,
                             const Schedule& sc, int ndir, const int* dir_begin,
                             const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
-                            const T* TinvT, const T* SLD, int Emax, int Jmax, int* status,
-                            cudaStream_t st);
+                            const T* TinvT, const T* SLD, int Emax, int Jmax, int nmat,
+                            int variant, int* status, cudaStream_t st);
 
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();

@@ -15,6 +15,7 @@
 // a hardware cluster barrier between wavefront levels.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -347,6 +348,286 @@ __global__ void __launch_bounds__(512) coarse_gs_block_kernel(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Thread-group form of the direction-blocked sweep: one group of GT threads
+// (GT >= E, a multiple of 32) per cell, one thread per block entry, and the
+// direction's tables -- the block inverses of every material, X_d, diag(f)X_d^T
+// and S_dd^{L+D} -- staged in shared memory once per direction.  Groups of one
+// thread block synchronise with named barriers; wavefront levels with the
+// cluster barrier.
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <class T, int DIM, int A>
+__global__ void __launch_bounds__(768) coarse_gs_group_kernel(
+    Geom g, LevelDev<T> t, CellData cd, Schedule sc, int ndir, const int* __restrict__ dir_begin,
+    const int* __restrict__ dir_end, int sweeps, const T* __restrict__ f, T* __restrict__ psi,
+    T* __restrict__ mom, const T* __restrict__ TinvT, const T* __restrict__ SLD, int Emax,
+    int Jmax, int nmat, int GT) {
+  constexpr int S = 1 << DIM;
+  constexpr int HS = S / 2;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nm = t.nmom;
+  const int nadof = g.nadof;
+  const int ngroups = blockDim.x / GT;
+  const int gi = threadIdx.x / GT;
+  const int r = threadIdx.x - gi * GT;
+  const int gg = (int)cluster.block_rank() * ngroups + gi;
+  const int G = (int)cluster.num_blocks() * ngroups;
+  const int JS = Jmax + 1;  // padded row stride of S_dd^{L+D}
+  // shared layout
+  T* Tin = reinterpret_cast<T*>(smem_raw);                 // [nmat][Emax][Emax]
+  T* XFs = Tin + (size_t)nmat * Emax * Emax;               // [nm][Jmax]
+  T* Xds = XFs + (size_t)nm * Jmax;                        // [Jmax][nm]
+  T* SLs = Xds + (size_t)Jmax * nm;                        // [Jmax][JS]
+  T* Ns = SLs + (size_t)Jmax * JS;                         // [S*S]
+  T* ws = Ns + S * S + (size_t)gi * (3 * Emax + S * nm + DIM * HS * Jmax);
+  T* rhs = ws;
+  T* xold = ws + Emax;
+  T* buf = ws + 2 * Emax;
+  T* phs = ws + 3 * Emax;
+  T* upw = phs + S * nm;                                   // [DIM][HS][J] neighbour face values
+  const int bid = 1 + gi;  // named barrier of this group (0 is __syncthreads)
+  for (int i = threadIdx.x; i < S * S; i += blockDim.x) Ns[i] = (T)g.Nmass[i];
+  // entries owned by this thread: e = r (+ GT ...) -- prefetch registers
+  constexpr int MAXE = 2;  // E <= 128 -> at most 2 entries per thread for GT >= 64
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int d = 0; d < ndir; ++d) {
+      int n0, n1, n2;
+      if (DIM == 2) {
+        n0 = (d >> 1) & 1; n1 = d & 1; n2 = 0;
+      } else {
+        n0 = (d >> 2) & 1; n1 = (d >> 1) & 1; n2 = d & 1;
+      }
+      const int qb = dir_begin[d];
+      const int J = (dir_end[d] - qb) * A;
+      const int E = S * J;
+      // stage this direction's tables (the previous level ended with a cluster barrier)
+      for (int mt = 0; mt < nmat; ++mt) {
+        const T* src = TinvT + ((size_t)mt * ndir + d) * Emax * Emax;
+        T* dst = Tin + (size_t)mt * Emax * Emax;
+        for (int i = threadIdx.x; i < E * Emax; i += blockDim.x) dst[i] = src[i];
+      }
+      for (int i = threadIdx.x; i < nm * J; i += blockDim.x) {
+        const int kk = i / J, j = i - kk * J;
+        XFs[kk * Jmax + j] = t.XFt[(long long)kk * nadof + qb * A + j];
+        Xds[j * nm + kk] = t.X[(long long)(qb * A + j) * nm + kk];
+      }
+      for (int i = threadIdx.x; i < J * J; i += blockDim.x) {
+        const int j = i / J, j2 = i - j * J;
+        SLs[j * JS + j2] = SLD[((size_t)d * Jmax + j) * Jmax + j2];
+      }
+      __syncthreads();
+      auto cell_of = [&](int w, int k) {
+        const int packed = sc.cells[sc.level_off[w] + k];
+        const int j0 = packed & 2047, j1 = (packed >> 11) & 2047, j2c = packed >> 22;
+        const int ix = n0 ? g.nx - 1 - j0 : j0;
+        const int iy = n1 ? g.ny - 1 - j1 : j1;
+        const int iz = n2 ? g.nz - 1 - j2c : j2c;
+        return ix + g.nx * (iy + g.ny * iz);
+      };
+      // prefetch registers for the group's cell at the next level
+      T pf[MAXE], px[MAXE], pm[4];
+      auto prefetch = [&](int w) {
+        const int cnt = sc.level_off[w + 1] - sc.level_off[w];
+        if (gg >= cnt) return;
+        const int c = cell_of(w, gg);
+#pragma unroll
+        for (int u = 0; u < MAXE; ++u) {
+          const int e = r + u * GT;
+          if (e < E) {
+            const int l = e / J, j = e - l * J;
+            const long long gix = ((long long)c * S + l) * nadof + qb * A + j;
+            pf[u] = f[gix];
+            px[u] = __ldcg(psi + gix);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = r + u * GT;
+          if (e < S * nm) pm[u] = __ldcg(mom + (long long)c * S * nm + e);
+        }
+      };
+      if (sc.nlev > 0) prefetch(0);
+      for (int w = 0; w < sc.nlev; ++w) {
+        const int cnt = sc.level_off[w + 1] - sc.level_off[w];
+        const bool have = gg < cnt;
+        const int k = gg;
+        // move the prefetched values of this level's cell into shared memory
+        if (have) {
+#pragma unroll
+          for (int u = 0; u < MAXE; ++u) {
+            const int e = r + u * GT;
+            if (e < E) {
+              rhs[e] = pf[u];
+              xold[e] = px[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = r + u * GT;
+            if (e < S * nm) phs[e] = pm[u];
+          }
+        }
+        int c = 0, jj0 = 0, jj1 = 0, jj2 = 0;
+        if (have) {
+          const int packed = sc.cells[sc.level_off[w] + k];
+          jj0 = packed & 2047; jj1 = (packed >> 11) & 2047; jj2 = packed >> 22;
+          c = cell_of(w, k);
+          // neighbour face values: DIM x HS nodes x J entries, one load per thread
+          for (int e = r; e < DIM * HS * J; e += GT) {
+            const int xi = e / (HS * J);
+            const int rem = e - xi * HS * J;
+            const int jn = rem / J, j = rem - jn * J;
+            const int jx = xi == 0 ? jj0 : (xi == 1 ? jj1 : jj2);
+            T v = T(0);
+            if (jx > 0) {
+              const int own = xi == 0 ? n0 : (xi == 1 ? n1 : n2);
+              const int strd = xi == 0 ? 1 : (xi == 1 ? g.nx : g.nx * g.ny);
+              const int cn = c + (own ? strd : -strd);
+              const int i = fnode(jn, xi, 1 - own);
+              v = __ldcg(psi + ((long long)cn * S + i) * nadof + qb * A + j);
+            }
+            upw[e] = v;
+          }
+        }
+        // next level's cell: issue its loads now, consume them next level
+        if (w + 1 < sc.nlev) prefetch(w + 1);
+        if (have) {
+          const int mat = cd.mat[c];
+          const T sig_s = (T)cd.sigma_s[c];
+          T* Phi = mom + (long long)c * S * nm;
+          group_bar(bid, GT);
+          // 1. rhs = f - upwind
+          for (int e = r; e < E; e += GT) {
+            const int l = e / J, j = e - l * J;
+            const int q = qb + j / A, m = j % A;
+            T val = rhs[e];
+#pragma unroll
+            for (int xi = 0; xi < DIM; ++xi) {
+              const int jx = xi == 0 ? jj0 : (xi == 1 ? jj1 : jj2);
+              const int own = xi == 0 ? n0 : (xi == 1 ? n1 : n2);
+              if (jx == 0 || ((l >> xi) & 1) != own) continue;
+              const T* An = t.Aax + ((size_t)q * 3 + xi) * A * A + m * A;
+              const int jp = fcompress(l, xi);
+              const int jb = (j / A) * A;
+              T acc = T(0);
+#pragma unroll
+              for (int jn = 0; jn < HS; ++jn) {
+                const T* nv = upw + (xi * HS + jn) * J + jb;
+                T sacc = T(0);
+#pragma unroll
+                for (int dd = 0; dd < A; ++dd) sacc += An[dd] * nv[dd];
+                acc += T(g.facemass[xi][jp][jn]) * sacc;
+              }
+              val -= (own ? T(1) : T(-1)) * acc;
+            }
+            rhs[e] = val;
+          }
+          // 2. buf = X_d F Phi - S_dd^{L+D} x_old
+          for (int e = r; e < E; e += GT) {
+            const int l = e / J, j = e - l * J;
+            T a0 = T(0), a1 = T(0);
+            const T* ph = phs + l * nm;
+            int kk = 0;
+            for (; kk + 1 < nm; kk += 2) {
+              a0 += XFs[kk * Jmax + j] * ph[kk];
+              a1 += XFs[(kk + 1) * Jmax + j] * ph[kk + 1];
+            }
+            if (kk < nm) a0 += XFs[kk * Jmax + j] * ph[kk];
+            const T* sl = SLs + j * JS;
+            const T* xo = xold + l * J;
+            int j3 = 0;
+            for (; j3 + 1 < J; j3 += 2) {
+              a0 -= sl[j3] * xo[j3];
+              a1 -= sl[j3 + 1] * xo[j3 + 1];
+            }
+            if (j3 < J) a0 -= sl[j3] * xo[j3];
+            buf[e] = a0 + a1;
+          }
+          group_bar(bid, GT);
+          // 3. rhs += sigma_s N (x) buf
+          for (int e = r; e < E; e += GT) {
+            const int l = e / J, j = e - l * J;
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < S; ++i) acc += Ns[l * S + i] * buf[i * J + j];
+            rhs[e] += sig_s * acc;
+          }
+          group_bar(bid, GT);
+          // 4. x_new = Tinv rhs
+          const T* Tm = Tin + (size_t)mat * Emax * Emax;
+          for (int rr = r; rr < E; rr += GT) {
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int cc = 0;
+            for (; cc + 3 < E; cc += 4) {
+              a0 += Tm[(size_t)cc * Emax + rr] * rhs[cc];
+              a1 += Tm[(size_t)(cc + 1) * Emax + rr] * rhs[cc + 1];
+              a2 += Tm[(size_t)(cc + 2) * Emax + rr] * rhs[cc + 2];
+              a3 += Tm[(size_t)(cc + 3) * Emax + rr] * rhs[cc + 3];
+            }
+            for (; cc < E; ++cc) a0 += Tm[(size_t)cc * Emax + rr] * rhs[cc];
+            const T xn = (a0 + a1) + (a2 + a3);
+            const int l = rr / J, j = rr - l * J;
+            psi[((long long)c * S + l) * nadof + qb * A + j] = xn;
+            buf[rr] = xn - xold[rr];
+          }
+          group_bar(bid, GT);
+          // 5. Phi_c += X_d^T delta
+          for (int e = r; e < S * nm; e += GT) {
+            const int l = e / nm, kk = e - l * nm;
+            T a0 = T(0), a1 = T(0);
+            const T* dl = buf + l * J;
+            int j = 0;
+            for (; j + 1 < J; j += 2) {
+              a0 += Xds[j * nm + kk] * dl[j];
+              a1 += Xds[(j + 1) * nm + kk] * dl[j + 1];
+            }
+            if (j < J) a0 += Xds[j * nm + kk] * dl[j];
+            Phi[e] = phs[e] + (a0 + a1);
+          }
+        }
+        cluster.sync();
+      }
+    }
+  }
+}
+
+template <class T, int DIM, int A>
+cudaError_t launch_gs_group_impl(int cl, int ngroups, int GT, size_t smem, const Geom& g,
+                                 const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
+                                 int ndir, const int* db, const int* de, int sweeps, const T* f,
+                                 T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
+                                 int nmat, cudaStream_t st) {
+  auto kern = coarse_gs_group_kernel<T, DIM, A>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (cl > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(ngroups * GT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorLaunchOutOfResources;
+  return cudaLaunchKernelEx(&cfg, kern, g, t, cd, sc, ndir, db, de, sweeps, f, phi, mom, TinvT,
+                            SLD, Emax, Jmax, nmat, GT);
+}
+
 template <class T, int DIM, int A>
 cudaError_t launch_gs_block_impl(int cl, int wpc, const Geom& g, const LevelDev<T>& t,
                                  const CellData& cd, const Schedule& sc, int ndir, const int* db,
@@ -443,9 +724,40 @@ template <class T>
 void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData& cd,
                             const Schedule& sc, int ndir, const int* dir_begin,
                             const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
-                            const T* TinvT, const T* SLD, int Emax, int Jmax, int* status,
-                            cudaStream_t st) {
+                            const T* TinvT, const T* SLD, int Emax, int Jmax, int nmat,
+                            int variant, int* status, cudaStream_t st) {
   const int sizes[3] = {16, 8, 1};
+  // thread-group kernel: tables of all materials in shared memory
+  {
+    const int GT = ((Emax + 31) / 32) * 32;
+    const size_t tables = ((size_t)nmat * Emax * Emax + 2 * (size_t)t.nmom * Jmax +
+                           (size_t)Jmax * (Jmax + 1) + 64) * sizeof(T);
+    const size_t per_group =
+        (size_t)(3 * Emax + g.s * t.nmom + g.dim * (g.s / 2) * Jmax) * sizeof(T);
+    int ngroups = std::min(15, 768 / GT);
+    while (ngroups > 1 && tables + ngroups * per_group > 220 * 1024) --ngroups;
+    if (variant != 2 && GT <= 128 && Emax <= 2 * GT && g.s * t.nmom <= 4 * GT &&
+        tables + ngroups * per_group <= 220 * 1024) {
+      const size_t smem = tables + ngroups * per_group;
+      for (int cl : sizes) {
+        cudaError_t e;
+        if (g.dim == 2 && g.a == 3)
+          e = launch_gs_group_impl<T, 2, 3>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
+        else if (g.dim == 2)
+          e = launch_gs_group_impl<T, 2, 1>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
+        else if (g.a == 3)
+          e = launch_gs_group_impl<T, 3, 3>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
+        else
+          e = launch_gs_group_impl<T, 3, 1>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
+        if (e == cudaSuccess) {
+          note_launch();
+          if (status) *status = 100 + cl;
+          return;
+        }
+        cudaGetLastError();
+      }
+    }
+  }
   const size_t per_warp = (size_t)(3 * Emax + g.s * t.nmom) * sizeof(T);
   int wpc = 16;
   while (wpc > 1 && per_warp * wpc > 200 * 1024) wpc /= 2;
@@ -472,11 +784,11 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
 template void launch_coarse_gs_block<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                              const Schedule&, int, const int*, const int*, int,
                                              const double*, double*, double*, const double*,
-                                             const double*, int, int, int*, cudaStream_t);
+                                             const double*, int, int, int, int, int*, cudaStream_t);
 template void launch_coarse_gs_block<float>(const Geom&, const LevelDev<float>&, const CellData&,
                                             const Schedule&, int, const int*, const int*, int,
                                             const float*, float*, float*, const float*,
-                                            const float*, int, int, int*, cudaStream_t);
+                                            const float*, int, int, int, int, int*, cudaStream_t);
 
 template void launch_coarse_gs<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                        const Schedule&, int, const int*, const int*, int,

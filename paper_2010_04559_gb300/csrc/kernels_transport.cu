@@ -124,8 +124,267 @@ __global__ void __launch_bounds__(256) sweep_kernel(Geom g, LevelDev<T> t, CellD
   }
 }
 
+// ---------------------------------------------------------------------------
+// 2D sweep, row-pipelined.  For one direction and a group of nq patches, thread
+// (jy, p) owns rotated row jy and patch p and visits its row's cells
+// jx = 0..nx-1 at wavefront levels w = jx + jy.  The x-upwind values are the
+// thread's own previous output (registers); the y-upwind values come from
+// row jy-1 through a double-buffered shared row buffer; b is staged NST levels
+// ahead with cp.async; the block inverses of the group sit in shared memory.
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <class T, int A, int NST>
+__global__ void __launch_bounds__(512) sweep2d_rows_kernel(Geom g, LevelDev<T> t, CellData cd,
+                                                            Schedule sc, const T* __restrict__ b,
+                                                            T* __restrict__ psi, int G, int nmat_s,
+                                                            int chunk) {
+  constexpr int S = 4;
+  constexpr int SA = S * A;
+  constexpr int KST = SA * SA + 16 / sizeof(T);  // padded inverse stride (bank spread)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int task = blockIdx.x;
+  const int d = sc.task_dir[task], q0 = sc.task_q0[task], nq = sc.task_nq[task];
+  const int negx = (d >> 1) & 1, negy = d & 1;
+  const int nx = g.nx, ny = g.ny, nadof = g.nadof;
+  const int seg = nq * A;                 // elements per (cell, node) row segment
+  const int segp = G * A;                 // padded segment in shared memory
+  T* stage = reinterpret_cast<T*>(smem_raw);                     // [NST][ny][S][segp]
+  T* yface = stage + (size_t)NST * ny * S * segp;                // [2][ny][G][2][A]
+  T* kin = yface + (size_t)2 * ny * G * 2 * A;                   // [nmat_s][G][KST]
+  const int tid = threadIdx.x;
+  const int p = tid % G, jy = tid / G;
+  const bool mine = jy < ny && p < nq;
+  const int q = q0 + p;
+  // inverses of this group into shared memory
+  for (int i = tid; i < nmat_s * nq * SA * SA; i += blockDim.x) {
+    const int mt = i / (nq * SA * SA);
+    const int rem = i - mt * nq * SA * SA;
+    const int pp = rem / (SA * SA), e = rem - pp * SA * SA;
+    kin[((size_t)mt * G + pp) * KST + e] = t.Kinv[((size_t)mt * g.P + q0 + pp) * SA * SA + e];
+  }
+  // per-thread angular tables
+  T Ax[A][A], Ay[A][A];
+  if (mine) {
+#pragma unroll
+    for (int m = 0; m < A; ++m)
+#pragma unroll
+      for (int dd = 0; dd < A; ++dd) {
+        Ax[m][dd] = t.Aax[((size_t)q * 3 + 0) * A * A + m * A + dd];
+        Ay[m][dd] = t.Aax[((size_t)q * 3 + 1) * A * A + m * A + dd];
+      }
+  }
+  const int nchunk_seg = seg * (int)sizeof(T) / chunk;
+  const int per_level = ny * S * nchunk_seg;
+  // This thread's staging copies are the same (row, node, chunk) triples at
+  // every level; only the cell column jx = w - row moves, so the source
+  // address is linear in w.
+  constexpr int UMAX = 12;  // per_level / blockDim <= 4*A*sizeof(T)/chunk <= 12
+  int crow[UMAX];
+  long long csrc[UMAX];
+  int cdst[UMAX];
+  int nu = 0;
+  const long long xstep = (negx ? -1LL : 1LL) * S * nadof * (long long)sizeof(T);
+#pragma unroll
+  for (int u = 0; u < UMAX; ++u) {
+    const int i = tid + u * (int)blockDim.x;
+    crow[u] = -1;
+    if (i < per_level) {
+      const int row = i / (S * nchunk_seg);
+      const int rem = i - row * S * nchunk_seg;
+      const int l = rem / nchunk_seg, ch = rem - l * nchunk_seg;
+      const int ix0 = negx ? nx - 1 : 0;  // column jx = 0
+      const int iy = negy ? ny - 1 - row : row;
+      const int c0 = ix0 + nx * iy;
+      crow[u] = row;
+      csrc[u] = (((long long)c0 * S + l) * nadof + q0 * A) * (long long)sizeof(T) + ch * chunk;
+      cdst[u] = (int)(((size_t)row * S + l) * segp * sizeof(T)) + ch * chunk;
+      nu = u + 1;
+    }
+  }
+  const char* bbase = reinterpret_cast<const char*>(b);
+  char* sbase = reinterpret_cast<char*>(stage);
+  const int stage_bytes = ny * S * segp * (int)sizeof(T);
+  auto issue = [&](int w) {
+    if (w < sc.nlev) {
+      char* st = sbase + (w % NST) * stage_bytes;
+#pragma unroll
+      for (int u = 0; u < UMAX; ++u) {
+        if (u < nu) {
+          const int jx = w - crow[u];
+          if (jx >= 0 && jx < nx) cp_async_bytes(st + cdst[u], bbase + csrc[u] + jx * xstep, chunk);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int w = 0; w < NST - 1; ++w) issue(w);
+  T xf[2][A];  // x-outflow of the previous cell of this row
+  const int ownx = negx, owny = negy;
+  const T fmx00 = T(g.facemass[0][0][0]), fmx01 = T(g.facemass[0][0][1]);
+  const T fmx10 = T(g.facemass[0][1][0]), fmx11 = T(g.facemass[0][1][1]);
+  const T fmy00 = T(g.facemass[1][0][0]), fmy01 = T(g.facemass[1][0][1]);
+  const T fmy10 = T(g.facemass[1][1][0]), fmy11 = T(g.facemass[1][1][1]);
+  const T nsx = ownx ? T(1) : T(-1), nsy = owny ? T(1) : T(-1);
+  int mat_next = 0;
+  if (mine) {
+    const int ix = negx ? nx - 1 : 0, iy = negy ? ny - 1 - jy : jy;
+    mat_next = cd.mat[ix + nx * iy];
+  }
+  for (int w = 0; w < sc.nlev; ++w) {
+    cp_async_wait<NST - 2>();
+    __syncthreads();
+    issue(w + NST - 1);
+    const int jx = w - jy;
+    if (mine && jx >= 0 && jx < nx) {
+      const int ix = negx ? nx - 1 - jx : jx;
+      const int iy = negy ? ny - 1 - jy : jy;
+      const int c = ix + nx * iy;
+      const int mat = mat_next;
+      if (jx + 1 < nx) mat_next = cd.mat[c + (negx ? -1 : 1)];
+      T rhs[SA];
+      const T* st = stage + (size_t)(w % NST) * ny * S * segp + (size_t)jy * S * segp + p * A;
+#pragma unroll
+      for (int l = 0; l < S; ++l)
+#pragma unroll
+        for (int m = 0; m < A; ++m) rhs[l * A + m] = st[l * segp + m];
+      // Node l of the cell is on the x-inflow face when bit 0 of l equals
+      // ownx (face index jp = bit 1 of l), on the y-inflow face when bit 1
+      // equals owny (face index jp = bit 0).  Indices stay compile-time.
+      if (jx > 0) {  // x-upwind from registers
+        T dv[2][A];
+#pragma unroll
+        for (int jp = 0; jp < 2; ++jp)
+#pragma unroll
+          for (int m = 0; m < A; ++m) {
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int dd = 0; dd < A; ++dd) {
+              a0 += Ax[m][dd] * xf[0][dd];
+              a1 += Ax[m][dd] * xf[1][dd];
+            }
+            dv[jp][m] = nsx * (jp == 0 ? fmx00 * a0 + fmx01 * a1 : fmx10 * a0 + fmx11 * a1);
+          }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const bool on = (l & 1) == ownx;
+#pragma unroll
+          for (int m = 0; m < A; ++m) rhs[l * A + m] -= on ? dv[l >> 1][m] : T(0);
+        }
+      }
+      if (jy > 0) {  // y-upwind from row jy-1
+        const T* yf = yface + ((size_t)((w - 1) & 1) * ny * G + (size_t)(jy - 1) * G + p) * 2 * A;
+        T yv[2][A];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int m = 0; m < A; ++m) yv[j][m] = yf[j * A + m];
+        T dv[2][A];
+#pragma unroll
+        for (int jp = 0; jp < 2; ++jp)
+#pragma unroll
+          for (int m = 0; m < A; ++m) {
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int dd = 0; dd < A; ++dd) {
+              a0 += Ay[m][dd] * yv[0][dd];
+              a1 += Ay[m][dd] * yv[1][dd];
+            }
+            dv[jp][m] = nsy * (jp == 0 ? fmy00 * a0 + fmy01 * a1 : fmy10 * a0 + fmy11 * a1);
+          }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const bool on = ((l >> 1) & 1) == owny;
+#pragma unroll
+          for (int m = 0; m < A; ++m) rhs[l * A + m] -= on ? dv[l & 1][m] : T(0);
+        }
+      }
+      // x = Kinv rhs (rows of SA values are 16-byte aligned in shared memory)
+      T x[SA];
+      if (mat < nmat_s) {
+        const T* Ki = kin + ((size_t)mat * G + p) * KST;
+#pragma unroll
+        for (int r = 0; r < SA; ++r) {
+          T acc = T(0);
+#pragma unroll
+          for (int cc = 0; cc < SA; cc += 16 / (int)sizeof(T)) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 k4 = *reinterpret_cast<const float4*>(Ki + r * SA + cc);
+              acc += k4.x * rhs[cc] + k4.y * rhs[cc + 1] + k4.z * rhs[cc + 2] + k4.w * rhs[cc + 3];
+            } else {
+              const double2 k2 = *reinterpret_cast<const double2*>(Ki + r * SA + cc);
+              acc += k2.x * rhs[cc] + k2.y * rhs[cc + 1];
+            }
+          }
+          x[r] = acc;
+        }
+      } else {
+        const T* Ki = t.Kinv + ((size_t)mat * g.P + q) * SA * SA;
+#pragma unroll
+        for (int r = 0; r < SA; ++r) {
+          T acc = T(0);
+#pragma unroll
+          for (int cc = 0; cc < SA; ++cc) acc += __ldg(Ki + r * SA + cc) * rhs[cc];
+          x[r] = acc;
+        }
+      }
+      T* out = psi + (long long)c * S * nadof + q * A;
+#pragma unroll
+      for (int l = 0; l < S; ++l)
+#pragma unroll
+        for (int m = 0; m < A; ++m) out[(long long)l * nadof + m] = x[l * A + m];
+      // outflow faces for the next cell of this row and for row jy+1: nodes
+      // with bit 0 (x) or bit 1 (y) equal to 1 - own
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int m = 0; m < A; ++m)
+          xf[j][m] = ownx ? x[(2 * j) * A + m] : x[(2 * j + 1) * A + m];
+      T* yo = yface + ((size_t)(w & 1) * ny * G + (size_t)jy * G + p) * 2 * A;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int m = 0; m < A; ++m) yo[j * A + m] = owny ? x[j * A + m] : x[(2 + j) * A + m];
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// Spatial matrices of the Kronecker form of the diagonal block
+//   K0_q + sigma_t kron(N, M_q) = sum_xi kron(G_xi^(sign), A^xi_q) + sigma_t kron(N, M_q),
+//   G_xi^(+) = Fown_{xi,high} - V_xi,   G_xi^(-) = -Fown_{xi,low} - V_xi,
+// where the sign is that of Omega_xi on the patch (one outflow face per axis).
+__constant__ double c_Gax[3][2][64];  // [axis][negative sign][s*s]
+__constant__ double c_Nsp[64];
+__constant__ float c_GaxF[3][2][64];
+__constant__ float c_NspF[64];
+
+template <class T>
+__device__ __forceinline__ T gax(int xi, int sg, int e);
+template <>
+__device__ __forceinline__ double gax<double>(int xi, int sg, int e) { return c_Gax[xi][sg][e]; }
+template <>
+__device__ __forceinline__ float gax<float>(int xi, int sg, int e) { return c_GaxF[xi][sg][e]; }
+template <class T>
+__device__ __forceinline__ T nsp(int e);
+template <>
+__device__ __forceinline__ double nsp<double>(int e) { return c_Nsp[e]; }
+template <>
+__device__ __forceinline__ float nsp<float>(int e) { return c_NspF[e]; }
+
 template <class T, int DIM, int A>
-__global__ void __launch_bounds__(256) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
+__global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
                                                       T alpha, T beta, const T* __restrict__ x,
                                                       T* __restrict__ y) {
   constexpr int S = 1 << DIM;
@@ -142,24 +401,65 @@ __global__ void __launch_bounds__(256) apply_L_kernel(Geom g, LevelDev<T> t, Cel
     const int jj[3] = {neg[0] ? g.nx - 1 - ix : ix, neg[1] ? g.ny - 1 - iy : iy,
                        neg[2] ? g.nz - 1 - iz : iz};
     const T* xp = x + (long long)c * S * nadof + q * A;
-    T xv[SA];
+    T xv[S][A];
 #pragma unroll
     for (int l = 0; l < S; ++l)
 #pragma unroll
-      for (int m = 0; m < A; ++m) xv[l * A + m] = xp[(long long)l * nadof + m];
-    const T st = (T)cd.sigma_t[c];
-    const T* K0 = t.K0 + (size_t)q * SA * SA;
-    const T* Bq = t.B + (size_t)q * SA * SA;
+      for (int m = 0; m < A; ++m) xv[l][m] = xp[(long long)l * nadof + m];
     T acc[SA];
 #pragma unroll
-    for (int r = 0; r < SA; ++r) {
-      T s1 = T(0), s2 = T(0);
+    for (int r = 0; r < SA; ++r) acc[r] = T(0);
+    // streaming: sum_xi G_xi X (A^xi)^T
 #pragma unroll
-      for (int cc = 0; cc < SA; ++cc) {
-        s1 += K0[r * SA + cc] * xv[cc];
-        s2 += Bq[r * SA + cc] * xv[cc];
-      }
-      acc[r] = s1 + st * s2;
+    for (int xi = 0; xi < DIM; ++xi) {
+      const T* Aq = t.Aax + ((size_t)q * 3 + xi) * A * A;
+      T a[A][A];
+#pragma unroll
+      for (int m = 0; m < A; ++m)
+#pragma unroll
+        for (int d = 0; d < A; ++d) a[m][d] = Aq[m * A + d];
+      T t1[S][A];
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          T v = T(0);
+#pragma unroll
+          for (int d = 0; d < A; ++d) v += xv[i][d] * a[m][d];
+          t1[i][m] = v;
+        }
+      const int sg = neg[xi];
+#pragma unroll
+      for (int l = 0; l < S; ++l)
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          const T gli = gax<T>(xi, sg, l * S + i);
+#pragma unroll
+          for (int m = 0; m < A; ++m) acc[l * A + m] += gli * t1[i][m];
+        }
+    }
+    // collision: sigma_t N X M^T
+    {
+      const T st = (T)cd.sigma_t[c];
+      const T* Mm = t.Mang + (size_t)q * A * A;
+      T t1[S][A];
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          T v = T(0);
+#pragma unroll
+          for (int d = 0; d < A; ++d) v += xv[i][d] * Mm[m * A + d];
+          t1[i][m] = st * v;
+        }
+#pragma unroll
+      for (int l = 0; l < S; ++l)
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          const T nli = nsp<T>(l * S + i);
+#pragma unroll
+          for (int m = 0; m < A; ++m) acc[l * A + m] += nli * t1[i][m];
+        }
     }
     upwind_term<T, DIM, A>(g, t.Aax, q, x, c, jj, neg, T(1), acc);
     T* out = y + (long long)c * S * nadof + q * A;
@@ -268,6 +568,20 @@ __global__ void prolong_kernel(long long nsdof, int Pf, int a, int nadof_f, int 
   }
 }
 
+}  // namespace
+
+void set_transport_constants(const double* Gax, const double* Nsp) {
+  cudaMemcpyToSymbol(c_Gax, Gax, sizeof(double) * 3 * 2 * 64);
+  cudaMemcpyToSymbol(c_Nsp, Nsp, sizeof(double) * 64);
+  float gf[3 * 2 * 64], nf[64];
+  for (int i = 0; i < 3 * 2 * 64; ++i) gf[i] = (float)Gax[i];
+  for (int i = 0; i < 64; ++i) nf[i] = (float)Nsp[i];
+  cudaMemcpyToSymbol(c_GaxF, gf, sizeof(gf));
+  cudaMemcpyToSymbol(c_NspF, nf, sizeof(nf));
+}
+
+namespace {
+
 int grid_for(long long total, int block) {
   long long g = (total + block - 1) / block;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -278,9 +592,49 @@ int grid_for(long long total, int block) {
 }  // namespace
 
 template <class T>
+size_t sweep2d_smem(const Geom& g, int G, int nmat_s, int nst) {
+  const int SA = 4 * g.a;
+  const size_t kst = SA * SA + 16 / sizeof(T);
+  return ((size_t)nst * g.ny * 4 * G * g.a + (size_t)2 * g.ny * G * 2 * g.a +
+          (size_t)nmat_s * G * kst) * sizeof(T);
+}
+
+template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, cudaStream_t st) {
+                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst,
+                  cudaStream_t st) {
   note_launch();
+  if (g.dim == 2 && G > 0 && g.ny * G <= 512) {
+    int NST = nst > 0 ? nst : (sizeof(T) == 4 ? 4 : 3);
+    NST = NST >= 6 ? 6 : (NST >= 4 ? 4 : (NST >= 3 ? 3 : 2));
+    while (NST > 2 && sweep2d_smem<T>(g, G, 0, NST) > 200 * 1024) NST = NST == 6 ? 4 : NST - 1;
+    int nmat_s = nmat;
+    while (nmat_s > 0 && sweep2d_smem<T>(g, G, nmat_s, NST) > 200 * 1024) --nmat_s;
+    const size_t smem = sweep2d_smem<T>(g, G, nmat_s, NST);
+    // 16-byte copies when every segment start and length is 16-byte aligned
+    const int chunk = chunk16 ? 16 : (int)sizeof(T);
+    const int threads = ((g.ny * G + 31) / 32) * 32;
+    const int seg_chunks = (G * g.a * (int)sizeof(T) + chunk - 1) / chunk;
+    const bool slots_ok = (long long)g.ny * 4 * seg_chunks <= 12LL * threads;
+    if (smem <= 200 * 1024 && slots_ok) {
+      auto launch = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<sc.ntask, threads, smem, st>>>(g, t, cd, sc, b, psi, G, nmat_s, chunk);
+      };
+      if (g.a == 3) {
+        if (NST == 2) launch(sweep2d_rows_kernel<T, 3, 2>);
+        else if (NST == 3) launch(sweep2d_rows_kernel<T, 3, 3>);
+        else if (NST == 4) launch(sweep2d_rows_kernel<T, 3, 4>);
+        else launch(sweep2d_rows_kernel<T, 3, 6>);
+      } else {
+        if (NST == 2) launch(sweep2d_rows_kernel<T, 1, 2>);
+        else if (NST == 3) launch(sweep2d_rows_kernel<T, 1, 3>);
+        else if (NST == 4) launch(sweep2d_rows_kernel<T, 1, 4>);
+        else launch(sweep2d_rows_kernel<T, 1, 6>);
+      }
+      return;
+    }
+  }
   dim3 grid(sc.ntask), block(256);
   if (g.dim == 2 && g.a == 3) sweep_kernel<T, 2, 3><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
   else if (g.dim == 2) sweep_kernel<T, 2, 1><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
@@ -339,7 +693,8 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 
 #define AMGT_INST(T)                                                                          \
   template void launch_sweep<T>(const Geom&, const LevelDev<T>&, const CellData&,             \
-                                const Schedule&, const T*, T*, cudaStream_t);                 \
+                                const Schedule&, const T*, T*, int, int, bool, int,           \
+                                cudaStream_t);                                                \
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
   template void launch_source<T>(const Geom&, const T*, const T*, const int*, const double*,  \

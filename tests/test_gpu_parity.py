@@ -103,11 +103,17 @@ def test_transport_operators(dim, nc, level, basis, dtype):
 def _mg_problem(dim, nc, level, basis, nlev, Nr, sweeps=4, seed=41):
     prob = W.random_problem(dim, nc, level, 8, seed, basis=basis, g=0.85)
     prob["mg"] = dict(nlevels=nlev, Nr=Nr, nu_pre=1, nu_post=1, coarse_sweeps=sweeps)
+    if nc == (12, 10):
+        # two materials in 4x4-cell tiles (the layout the shared-memory tables serve)
+        mat = np.array([((ix // 4) + (iy // 4)) % 2 for iy in range(10) for ix in range(12)])
+        prob["sigma_t"] = np.where(mat == 0, 1.0, 6.0)
+        prob["sigma_s"] = np.where(mat == 0, 0.5, 5.7)
     return prob
 
 
 MG_CASES = [
     (2, (6, 5), 2, "lin", 3, [8, 4, 3]),
+    (2, (12, 10), 2, "lin", 3, [8, 5, 4]),
     (2, (5, 7), 2, "const", 2, [8, 5]),
     (3, (3, 2, 3), 1, "lin", 2, [8, 4]),
 ]
@@ -116,7 +122,7 @@ MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ i
 
 @pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("gs_kernel", [1, 2], ids=["gs-per-patch", "gs-blocked"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3], ids=["gs-per-patch", "gs-warp", "gs-group"])
 def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
     H = multigrid.Hierarchy(prob)
@@ -271,4 +277,26 @@ def test_bad_arguments_raise():
         ctx.amgt_op_restrict(0, x, x)       # single-level hierarchy
     with pytest.raises(AmgtError):
         ctx.amgt_set_angular_uniform(1, 12)
+    ctx.close()
+
+
+@pytest.mark.parametrize("group", [1, 2, 4], ids=["G1", "G2", "G4"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_row_sweep_every_group_size(group, dtype):
+    """The 2D row-pipelined sweep with 1, 2 and 4 patches per block on a
+    32 x 32 mesh (block sizes that are multiples of 32 threads and several
+    copy chunks per thread), sampled on two patches of every direction."""
+    prob = W.random_problem(2, (32, 32), 1, 4, 33, inflow=0.2)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(2, group)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    x = W.random_vector((T.nsdof, T.nadof), 34)
+    y = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=td)
+    ctx.amgt_op_sweep(0, _dev(x, td), y)
+    pats = [q for d in range(T.ndir) for q in T.patches_of(d)[:2]]
+    ref = T.sweep(x, patches=pats)
+    cols = np.concatenate([np.arange(q * T.a, (q + 1) * T.a) for q in pats])
+    assert _rel(_host(y)[:, cols], ref[:, cols]) < tol
     ctx.close()
