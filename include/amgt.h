@@ -65,7 +65,8 @@ typedef enum {
 #define AMGT_PREC_MG 2        /* linear V-cycle of Fig. lmg (Sec. 4)              */
 #define AMGT_MODE_F64 0       /* everything in FP64                               */
 #define AMGT_MODE_MIXED 1     /* FP64 GMRES as iterative refinement around an FP32
-                                 flexible GMRES with FP32 sweeps/transfers and a
+                                 flexible GMRES (FP32 operator) whose multigrid
+                                 preconditioner runs FP32 sweeps/transfers and the
                                  BF16 tensor-core scatter (FP32 accumulation)     */
 
 typedef struct amgt_options {

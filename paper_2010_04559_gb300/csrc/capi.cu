@@ -484,6 +484,7 @@ int build(amgt_ctx* ctx) {
   TRY(upload(ctx, q, &ctx->d_q));
   TRY(upload(ctx, std::vector<int>(ctx->bkind, ctx->bkind + 6), &ctx->d_bkind));
   TRY(upload(ctx, std::vector<double>(ctx->bval, ctx->bval + 6), &ctx->d_bval));
+  TRY(upload(ctx, q1.N, &ctx->d_Nm32));
   TRY(upload(ctx, q1.mu, &ctx->d_mu));
   TRY(upload(ctx, q1.mf, &ctx->d_mf));
   // scratch
@@ -579,6 +580,8 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
   epi.s = ctx->geom.s;
   epi.sig = ctx->d_sigs;
   epi.sig32 = ctx->d_sigs32;
+  // the tensor-core path needs K = Nadof >= 64 (one K step of the tile)
+  if (tc && n < 64) tc = false;
   if (tc) {
     if constexpr (sizeof(T) == 4) {
       if (!tc_available()) return fail(ctx, AMGT_ERR_UNSUPPORTED, "tensor-core path unavailable");
@@ -591,9 +594,14 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
         ctx->bf16_bytes = need;
       }
       auto* xb = static_cast<__nv_bfloat16*>(ctx->d_bf16);
-      launch_convert<float, __nv_bfloat16>(M * n, x, xb, ctx->stream);
-      int rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, epi, ctx->d_status, ctx->stream);
-      if (rc != 0) return fail(ctx, AMGT_ERR_UNSUPPORTED, "tensor-core GEMM shape not supported");
+      // sigma_s and the spatial mass commute with S: applied while rounding to BF16
+      launch_tc_prep(M / ctx->geom.s, ctx->geom.s, n, x, ctx->d_sigs32, ctx->d_Nm32,
+                     (float)alpha, xb, ctx->stream);
+      int rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, add, (float)beta, ctx->d_status,
+                              ctx->stream);
+      if (rc != 0)
+        return fail(ctx, AMGT_ERR_UNSUPPORTED,
+                    "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
       CK(cudaGetLastError());
       return AMGT_OK;
     } else {
@@ -961,6 +969,15 @@ int amgt_query_launches(int64_t* count) {
 int amgt_sync(amgt_ctx* ctx) {
   if (!ctx) return AMGT_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->d_status) {
+    int st = 0;
+    CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+      CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+      return fail(ctx, AMGT_ERR_DEVICE_TIMEOUT,
+                  "a bounded device-side wait gave up (code " + std::to_string(st) + ")");
+    }
+  }
   return AMGT_OK;
 }
 
@@ -1263,7 +1280,9 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     if (bnorm == 0.0) {
       CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
     }
-    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, tc, xx, yy); };
+    // the inner operator keeps the FP32 contraction (its rounding sets how far
+    // each inner solve can go); the preconditioner's scatters use BF16 tensor cores
+    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, false, xx, yy); };
     auto M32 = [&](const float* v, float* z) -> int {
       if (prec == AMGT_PREC_SWEEP) return sweep_impl<float>(ctx, 0, v, z);
       if (prec == AMGT_PREC_MG) return vcycle_impl<float>(ctx, 0, tc, v, z);

@@ -94,7 +94,7 @@ struct amgt_ctx {
   int *d_mat = nullptr, *d_cells = nullptr, *d_level_off = nullptr, *d_bkind = nullptr;
   double *d_sigt = nullptr, *d_sigs = nullptr, *d_q = nullptr, *d_bval = nullptr, *d_mu = nullptr,
          *d_mf = nullptr;
-  float *d_sigt32 = nullptr, *d_sigs32 = nullptr;
+  float *d_sigt32 = nullptr, *d_sigs32 = nullptr, *d_Nm32 = nullptr;
   int nlev_wave = 0;
   // scratch
   double* d_partials = nullptr;  // [nblk * 64]

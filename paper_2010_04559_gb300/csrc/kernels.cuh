@@ -141,10 +141,13 @@ int gemv_blocks(long long n);
 void note_launch(int n = 1);
 long long launch_count();
 
-// BF16 tensor-core scatter (tcgen05): Y = epilogue(Xb[M][K] * Sb[K][N])
-struct TcGemm;
+// BF16 tensor-core scatter (tcgen05), see kernels_tc.cu
 bool tc_available();
-int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt,
-                   float* C, const GemmEpi& epi, int* status, cudaStream_t st);
+// Xb[c*s+l][:] = bf16(alpha * sig[c] * sum_i N[l][i] x[c*s+i][:])
+void launch_tc_prep(long long ncell, int s, int n, const float* x, const float* sig,
+                    const float* Nm, float alpha, __nv_bfloat16* xb, cudaStream_t st);
+// C = A Bt^T (+ beta C + add); returns 0 on a successful launch
+int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
+                   const float* add, float beta, int* err, cudaStream_t st);
 
 }  // namespace amgt

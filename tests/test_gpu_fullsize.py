@@ -78,6 +78,20 @@ def test_fullsize_apply_L_and_scatter_sampled_cells(setup):
         assert _rel(got[i * 4:i * 4 + 4], refc) < TOL32
 
 
+def test_fullsize_bf16_tensor_core_scatter_sampled_cells(setup):
+    prob, ctx, T, _, _ = setup
+    x = W.random_vector((T.nsdof, T.nadof), 90)
+    xd = torch.from_numpy(x).to("cuda", torch.float32)
+    y = torch.empty_like(xd)
+    ctx.amgt_op_scatter(0, xd, y, tc=True)
+    ctx.amgt_sync()
+    Sf = T.angular_scatter_matrix()
+    got = _host(y)
+    for c in [0, 127, 128 * 64 + 63, 128 * 128 - 1, 4095]:
+        refc = T.sigma_s[c] * (T.cell.N @ (x[c * 4:c * 4 + 4] @ Sf.T))
+        assert _rel(got[c * 4:c * 4 + 4], refc) < 1e-2
+
+
 def test_fullsize_transfers(setup):
     prob, ctx, T, _, P = setup
     r = W.random_vector((T.nsdof, T.nadof), 83)

@@ -300,3 +300,30 @@ def test_row_sweep_every_group_size(group, dtype):
     cols = np.concatenate([np.arange(q * T.a, (q + 1) * T.a) for q in pats])
     assert _rel(_host(y)[:, cols], ref[:, cols]) < tol
     ctx.close()
+
+
+TC_CASES = [
+    (2, (7, 5), 1, "lin"),      # N = K = 96: one partial 256-column tile, two K steps
+    (2, (9, 4), 2, "const"),    # N = K = 128
+    (2, (6, 6), 2, "lin"),      # N = K = 384: two column tiles, six K steps
+    (3, (3, 4, 2), 1, "lin"),   # 3D, s = 8
+]
+
+
+@pytest.mark.parametrize("dim,nc,level,basis", TC_CASES,
+                         ids=[f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}" for d, n, l, b in TC_CASES])
+def test_bf16_tensor_core_scatter(dim, nc, level, basis):
+    """Scatter contraction on tcgen05 (BF16 inputs, FP32 accumulation) against
+    the FP64 oracle; also its use inside (L - S) x."""
+    prob = W.random_problem(dim, nc, level, 6, 35, basis=basis)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    x = W.random_vector((T.nsdof, T.nadof), 36)
+    xd = _dev(x, torch.float32)
+    y = torch.empty_like(xd)
+    ctx.amgt_op_scatter(0, xd, y, tc=True)
+    assert _rel(_host(y), T.scatter(x)) < 1e-2
+    ctx.amgt_op_apply_A(0, xd, y, tc=True)
+    assert _rel(_host(y), T.apply_A(x)) < 1e-2
+    ctx.amgt_sync()        # no bounded device wait gave up
+    ctx.close()
