@@ -149,6 +149,38 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """One mixed-precision solve, or one launch each of the sweep, the tensor-
+    core scatter and one coarse Gauss-Seidel sweep, on the benchmark workload."""
+    import torch
+    from paper_2010_04559_gb300 import AMGT_MODE_MIXED, AMGT_PREC_MG, context_from_problem
+    from paper_2010_04559_gb300 import build as _b
+    _b.build()
+    prob = W.config2_checkerboard(n=args.n)
+    ctx = context_from_problem(prob, device=0)
+    ns, na = ctx.amgt_query_sizes(0)
+    if args.profile == "solve":
+        psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+        phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED,
+                                     psi=psi, phi=phi, device_ptrs=True)
+        print(f"solve: {st.iterations} iterations, relres {st.relres:.3e}")
+    else:
+        x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
+        y = torch.empty_like(x)
+        nsc, nac = ctx.amgt_query_sizes(2)
+        fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
+        pc = torch.zeros_like(fc)
+        ctx.amgt_op_sweep(0, x, y)
+        ctx.amgt_op_scatter(0, x, y, tc=True)
+        ctx.amgt_op_coarse_gs(1, fc, pc)
+        ctx.amgt_sync()
+        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep)")
+    torch.cuda.synchronize()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -158,9 +190,13 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--fp64-ref", action="store_true", help="also time one FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["solve", "kernels"], default=None,
+                    help="run one solve, or one launch of each hot kernel, and exit (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -275,11 +311,40 @@ def main():
         kern["coarse_gs_f32_10sweeps"] = {"s": t_gs}
         t_v = timeit(lambda: ctx.amgt_op_vcycle(x32, y32, tc=use_tc), reps=3)
         kern["vcycle_bf16tc" if use_tc else "vcycle_f32"] = {"s": t_v}
-    ach = 8.0 * dof / t_sweep / 1e9
-    roof = {"kernel": "sweep_kernel<float,2,3>", "bound": "hbm", "achieved": ach, "peak": hbm,
-            "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-            "peak_kind": f"{peak_kind} (burst copy)",
-            "algorithmic_bytes": "8 B per unknown (read b, write psi, FP32)"}
+    # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # coarse Gauss-Seidel algorithmic work: per cell, per sweep direction and
+    # per sweep, the sequential per-patch form of the block solves
+    # (moments source s*a*nm, self-scatter s*a*a, mass mix s*a*s, block solve
+    # (s*a)^2, moment update s*nm*a per patch) -> 2 flop per FMA
+    nsc_cells = nsc // 4
+    npd = nac // 3 // 4
+    nm = 25
+    per_patch = 4 * 3 * nm + 4 * 3 * 3 + 4 * 3 * 4 + (4 * 3) ** 2 + 4 * nm * 3
+    gs_flop = 2.0 * per_patch * npd * 4 * nsc_cells * 10
+    rl = {
+        "sweep": {"kernel": "sweep2d_rows_kernel<float,3,4>", "bound": "hbm",
+                  "achieved": 8.0 * dof / t_sweep / 1e9, "peak": hbm, "unit": "GB/s",
+                  "algorithmic": "8 B per unknown (read b, write psi, FP32)"},
+        "apply_L": {"kernel": "apply_L_kernel<float,2,3>", "bound": "hbm",
+                    "achieved": 8.0 * dof / t_L / 1e9, "peak": hbm, "unit": "GB/s",
+                    "algorithmic": "8 B per unknown (read x, write y, FP32)"},
+        "coarse_gs": {"kernel": "coarse_gs_group_kernel<float,2,3>", "bound": "alu",
+                      "achieved": gs_flop / t_gs / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                      "algorithmic": f"{gs_flop/1e9:.2f} GFLOP per 10 sweeps (sequential per-patch form)"},
+    }
+    if use_tc:
+        rl["scatter"] = {"kernel": "tc_prep_kernel + tc_gemm_kernel (tcgen05)", "bound": "tensor",
+                         "achieved": 2.0 * nsdof * nadof * nadof / t_sc / 1e12, "peak": bf16,
+                         "unit": "TFLOP/s", "algorithmic": "2 Nsdof Nadof^2 flop (dense S_f)"}
+    for v in rl.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    # dominant kernel by its share of one solve (launch list: coarse Gauss-Seidel)
+    dom = dict(rl["coarse_gs"])
+    roof = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"],
+            "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+            "peak_kind": "FP32 FMA units x clock (152 x 128 x 2 x 2.07 GHz)",
+            "algorithmic": dom["algorithmic"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -305,7 +370,7 @@ def main():
                            "tol": 1e-8, "l2": "inputs larger than L2 (0.4-0.8 GB per vector)",
                            "parallelism": f"replicas x{world}"},
                 "time_to_tol_s": ms / 1e3, "krylov_iterations": its, "relres": relres,
-                "gpu_launches": int(launches), "roofline": roof, "kernels": kern,
+                "gpu_launches": int(launches), "roofline": roof, "rooflines": rl, "kernels": kern,
                 "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
         if fp64:
             line["fp64_gpu"] = fp64

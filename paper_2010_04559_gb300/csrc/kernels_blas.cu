@@ -2,8 +2,8 @@
 // classical Gram-Schmidt applied twice (CGS2), linear combinations and
 // precision conversions.  Reductions are deterministic: each block writes its
 // partial sums to `partials[block][v]` and one block sums them in a fixed
-// order.  Partial sums are accumulated in FP64 for FP64 vectors and in FP32
-// per thread (FP64 across threads) for FP32 vectors.
+// order.  Arithmetic runs in the vectors' precision; partial sums of FP32
+// vectors are FP32 per thread and FP64 across threads.
 #include <atomic>
 
 #include "kernels.cuh"
@@ -80,15 +80,18 @@ __global__ void __launch_bounds__(kThreads) update_multidot_kernel(
   A acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = A(0);
+  A hA[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hA[k] = k < nvec ? (A)hs[k] : A(0);
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
        i += (long long)gridDim.x * kThreads) {
     T vk[NV];
-    double wi = (double)w[i];
+    A wi = (A)w[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
       if (k < nvec) {
         vk[k] = V[k][i];
-        wi -= hs[k] * (double)vk[k];
+        wi -= hA[k] * (A)vk[k];
       }
     const T wn = (T)wi;
     w[i] = wn;
@@ -124,20 +127,22 @@ __global__ void finish_kernel(int nblk, int nvec, const double* __restrict__ par
 template <class T>
 __global__ void axpby_kernel(long long n, double alpha, const T* __restrict__ x, double beta,
                              T* __restrict__ y) {
+  const T a = (T)alpha, bb = (T)beta;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double v = alpha * (double)x[i];
-    if (beta != 0.0) v += beta * (double)y[i];
-    y[i] = (T)v;
+    T v = a * x[i];
+    if (beta != 0.0) v += bb * y[i];
+    y[i] = v;
   }
 }
 
 template <class T>
 __global__ void scale_copy_kernel(long long n, double alpha, const T* __restrict__ x,
                                   T* __restrict__ y) {
+  const T a = (T)alpha;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    y[i] = (T)(alpha * (double)x[i]);
+    y[i] = a * x[i];
 }
 
 template <class Tin, class Tout>
@@ -161,16 +166,16 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(long long n, int nvec
                                                            const T* const* __restrict__ Z,
                                                            const double* __restrict__ y,
                                                            T* __restrict__ x) {
-  __shared__ double ys[kMaxVec];
-  if (threadIdx.x < nvec) ys[threadIdx.x] = y[threadIdx.x];
+  __shared__ T ys[kMaxVec];
+  if (threadIdx.x < nvec) ys[threadIdx.x] = (T)y[threadIdx.x];
   __syncthreads();
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
        i += (long long)gridDim.x * kThreads) {
-    double v = (double)x[i];
+    T v = x[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      if (k < nvec) v += ys[k] * (double)Z[k][i];
-    x[i] = (T)v;
+      if (k < nvec) v += ys[k] * Z[k][i];
+    x[i] = v;
   }
 }
 
