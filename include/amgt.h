@@ -141,15 +141,22 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         2 direction-blocked kernel, one warp per cell,
  *                         3 direction-blocked kernel, one thread group per
  *                         cell with the tables in shared memory when they fit
- *                         (else as 2) (2 and 3 use
+ *                         (else as 2), 4 the thread-group form over the whole
+ *                         GPU: one block per cell, cooperative launch, bounded
+ *                         grid barrier between wavefront levels (2, 3 and 4 use
  *                         precomputed block lower-triangular inverses: the
  *                         same iteration up to rounding)
  *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto)
  *   AMGT_TUNE_SWEEP_STAGES depth of the 2D sweep's copy pipeline (0 = auto,
- *                         2, 3, 4 or 6 levels) */
+ *                         2, 3, 4 or 6 levels)
+ *   AMGT_TUNE_GS_GRID_BLOCKS blocks of the whole-GPU Gauss-Seidel (0 = auto)
+ *   AMGT_TUNE_GS_CLUSTER  cluster size of the cluster Gauss-Seidel kernels
+ *                         (0 = largest available, else 1, 2, 4, 8 or 16) */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
+#define AMGT_TUNE_GS_GRID_BLOCKS 4
+#define AMGT_TUNE_GS_CLUSTER 5
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Sizes of level k of the hierarchy. */
 int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);

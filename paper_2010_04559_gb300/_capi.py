@@ -38,6 +38,8 @@ AMGT_MAX_HIST = 1024
 AMGT_TUNE_GS_KERNEL = 1
 AMGT_TUNE_SWEEP_GROUP = 2
 AMGT_TUNE_SWEEP_STAGES = 3
+AMGT_TUNE_GS_GRID_BLOCKS = 4
+AMGT_TUNE_GS_CLUSTER = 5
 
 # every exported symbol of include/amgt.h
 EXPORTS = [

@@ -178,6 +178,13 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
   const int Emax = s * Jmax;
   Lv.Jmax = Jmax;
   Lv.Emax = Emax;
+  // 16-byte vector loads need every direction's J to be a multiple of 4 floats / 2 doubles
+  Lv.gs_vec_ok = 3;
+  for (int d = 0; d < Lv.ndir; ++d) {
+    const int J = (Lv.dir_end[d] - Lv.dir_begin[d]) * a;
+    if (J % 4) Lv.gs_vec_ok &= ~1;
+    if (J % 2) Lv.gs_vec_ok &= ~2;
+  }
   // the per-patch kernel handles larger directions and very many materials
   if (Emax > 384 || (size_t)ctx->nmat * Lv.ndir * Emax * Emax * sizeof(double) > (256u << 20))
     return AMGT_OK;
@@ -736,7 +743,10 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
     launch_coarse_gs_block<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                               schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom,
                               store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax, ctx->nmat,
-                              ctx->gs_kernel, &cl, ctx->stream);
+                              ctx->gs_kernel, L.gs_vec_ok, max_wavefront_cells(ctx->geom),
+                              ctx->gs_cluster_size > 0 ? -ctx->gs_cluster_size : ctx->gs_grid_blocks,
+                              reinterpret_cast<unsigned*>(ctx->d_status + 4),
+                              ctx->d_status, &cl, ctx->stream);
   } else {
     launch_coarse_gs<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                         schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom, &cl,
@@ -1089,8 +1099,19 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (!ctx) return AMGT_ERR_ARG;
   if (key == AMGT_TUNE_GS_KERNEL) {
-    if (value < 0 || value > 3) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..3");
+    if (value < 0 || value > 4) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..4");
     ctx->gs_kernel = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_GS_CLUSTER) {
+    if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+      return fail(ctx, AMGT_ERR_ARG, "cluster size 0, 1, 2, 4, 8 or 16");
+    ctx->gs_cluster_size = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_GS_GRID_BLOCKS) {
+    if (value < 0 || value > 4096) return fail(ctx, AMGT_ERR_ARG, "grid blocks 0..4096");
+    ctx->gs_grid_blocks = value;
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_SWEEP_STAGES) {

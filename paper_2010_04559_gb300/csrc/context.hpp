@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/amgt.h"
+#include "amgt.h"
 #include "kernels.cuh"
 #include "setup.hpp"
 
@@ -40,6 +40,7 @@ struct Level {
   std::vector<int> pdir, octant, dir_begin, dir_end;
   int ndir = 0;
   int Emax = 0, Jmax = 0;  // direction-blocked Gauss-Seidel table sizes (coarsest level)
+  int gs_vec_ok = 0;      // bit 0: float, bit 1: double vector path of the group GS kernel
   int sweep_G = 0;         // patches per block of the 2D row-pipelined sweep (0: level kernel)
   bool chunk16_f32 = false, chunk16_f64 = false;
   LevelDevStore<double> d64;
@@ -109,6 +110,8 @@ struct amgt_ctx {
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
+  int gs_grid_blocks = 0;  // AMGT_TUNE_GS_GRID_BLOCKS
+  int gs_cluster_size = 0; // AMGT_TUNE_GS_CLUSTER
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
   int sweep_stages = 0; // AMGT_TUNE_SWEEP_STAGES
 };

@@ -112,7 +112,8 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
                             const Schedule& sc, int ndir, const int* dir_begin,
                             const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
                             const T* TinvT, const T* SLD, int Emax, int Jmax, int nmat,
-                            int variant, int* status, cudaStream_t st);
+                            int variant, int vec_ok, int max_level_cells, int grid_blocks,
+                            unsigned* gbar, int* err, int* status, cudaStream_t st);
 
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <map>
+#include <vector>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -359,40 +360,135 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-template <class T, int DIM, int A>
+// vector of 16 bytes of T and its dot product with another
+template <class T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  __device__ static float dot(const float* a, const float* b) {
+    const float4 x = *reinterpret_cast<const float4*>(a);
+    const float4 y = *reinterpret_cast<const float4*>(b);
+    return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+  }
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  __device__ static double dot(const double* a, const double* b) {
+    const double2 x = *reinterpret_cast<const double2*>(a);
+    const double2 y = *reinterpret_cast<const double2*>(b);
+    return x.x * y.x + x.y * y.y;
+  }
+};
+
+// padded row strides (in elements of T) that spread 16-byte accesses of
+// consecutive rows over distinct bank groups
+template <class T>
+__host__ __device__ inline int gs_pad(int n) {
+  const int vw = 16 / (int)sizeof(T);
+  int p = ((n + vw - 1) / vw) * vw;
+  // rows p elements apart: want (p / vw) odd so 8 consecutive rows hit 8 bank groups
+  if (((p / vw) & 1) == 0) p += vw;
+  return p;
+}
+__host__ __device__ inline size_t gs_round16(size_t elems, size_t esz) {
+  const size_t vw = 16 / esz;
+  return ((elems + vw - 1) / vw) * vw;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident): a
+// counter and a generation word in global memory; the last block to arrive
+// resets the counter and advances the generation.  The wait is bounded (2 s);
+// on timeout the block records code 4 in `err` and continues.
+__device__ __forceinline__ unsigned long long gs_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen,
+                                             int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicExch(bar + 1, gen + 1u);
+    } else {
+      const unsigned long long t0 = gs_now_ns();
+      unsigned it = 0;
+      while (*vgen == gen) {
+        if ((++it & 255u) == 0 && gs_now_ns() - t0 > 2000000000ULL) {
+          atomicExch(err, 4);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  gen += 1u;
+  __syncthreads();
+}
+
+template <class T, int DIM, int A, bool VEC, bool GRID>
 __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
     Geom g, LevelDev<T> t, CellData cd, Schedule sc, int ndir, const int* __restrict__ dir_begin,
     const int* __restrict__ dir_end, int sweeps, const T* __restrict__ f, T* __restrict__ psi,
     T* __restrict__ mom, const T* __restrict__ TinvT, const T* __restrict__ SLD, int Emax,
-    int Jmax, int nmat, int GT) {
+    int Jmax, int nmat, int GT, unsigned* __restrict__ gbar, int* __restrict__ err) {
   constexpr int S = 1 << DIM;
   constexpr int HS = S / 2;
-  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int VW = 16 / (int)sizeof(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nm = t.nmom;
   const int nadof = g.nadof;
   const int ngroups = blockDim.x / GT;
   const int gi = threadIdx.x / GT;
   const int r = threadIdx.x - gi * GT;
-  const int gg = (int)cluster.block_rank() * ngroups + gi;
-  const int G = (int)cluster.num_blocks() * ngroups;
-  const int JS = Jmax + 1;  // padded row stride of S_dd^{L+D}
-  // shared layout
-  T* Tin = reinterpret_cast<T*>(smem_raw);                 // [nmat][Emax][Emax]
-  T* XFs = Tin + (size_t)nmat * Emax * Emax;               // [nm][Jmax]
-  T* Xds = XFs + (size_t)nm * Jmax;                        // [Jmax][nm]
-  T* SLs = Xds + (size_t)Jmax * nm;                        // [Jmax][JS]
-  T* Ns = SLs + (size_t)Jmax * JS;                         // [S*S]
-  T* ws = Ns + S * S + (size_t)gi * (3 * Emax + S * nm + DIM * HS * Jmax);
+  int rank, nblocks;
+  if constexpr (GRID) {
+    rank = blockIdx.x;
+    nblocks = gridDim.x;
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    rank = (int)cl.block_rank();
+    nblocks = (int)cl.num_blocks();
+  }
+  const int gg = rank * ngroups + gi;
+  const int G = nblocks * ngroups;
+  unsigned gen = 0;  // grid barrier generation seen by this block
+  auto level_barrier = [&]() {
+    if constexpr (GRID) {
+      grid_barrier(gbar, (unsigned)nblocks, gen, err);
+    } else {
+      cg::this_cluster().sync();
+    }
+  };
+  const int Ep = gs_pad<T>(Emax), NMp = gs_pad<T>(nm), Jp = gs_pad<T>(Jmax);
+  // shared layout (every sub-array starts on a 16-byte boundary)
+  T* Tin = reinterpret_cast<T*>(smem_raw);                           // [nmat][Emax][Ep]
+  T* XFr = Tin + gs_round16((size_t)nmat * Emax * Ep, sizeof(T));    // [Jmax][NMp]
+  T* Xk = XFr + gs_round16((size_t)Jmax * NMp, sizeof(T));           // [nm][Jp]
+  T* SLr = Xk + gs_round16((size_t)nm * Jp, sizeof(T));              // [Jmax][Jp]
+  T* Ns = SLr + gs_round16((size_t)Jmax * Jp, sizeof(T));            // [S*S]
+  const size_t per_group = gs_round16(3 * (size_t)Emax, sizeof(T)) +
+                           gs_round16((size_t)S * NMp, sizeof(T)) +
+                           gs_round16((size_t)DIM * HS * Jmax, sizeof(T));
+  T* ws = Ns + gs_round16(S * S, sizeof(T)) + (size_t)gi * per_group;
   T* rhs = ws;
   T* xold = ws + Emax;
   T* buf = ws + 2 * Emax;
-  T* phs = ws + 3 * Emax;
-  T* upw = phs + S * nm;                                   // [DIM][HS][J] neighbour face values
+  T* phs = ws + gs_round16(3 * (size_t)Emax, sizeof(T));            // [S][NMp]
+  T* upw = phs + gs_round16((size_t)S * NMp, sizeof(T));             // [DIM][HS][J]
   const int bid = 1 + gi;  // named barrier of this group (0 is __syncthreads)
   for (int i = threadIdx.x; i < S * S; i += blockDim.x) Ns[i] = (T)g.Nmass[i];
-  // entries owned by this thread: e = r (+ GT ...) -- prefetch registers
-  constexpr int MAXE = 2;  // E <= 128 -> at most 2 entries per thread for GT >= 64
+  for (int i = r; i < S * NMp; i += GT) phs[i] = T(0);  // padding stays zero
+  constexpr int MAXE = 2;  // E <= 2 GT
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int d = 0; d < ndir; ++d) {
       int n0, n1, n2;
@@ -406,23 +502,45 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
       const int E = S * J;
       // stage this direction's tables (the previous level ended with a cluster barrier)
       for (int mt = 0; mt < nmat; ++mt) {
-        const T* src = TinvT + ((size_t)mt * ndir + d) * Emax * Emax;
-        T* dst = Tin + (size_t)mt * Emax * Emax;
-        for (int i = threadIdx.x; i < E * Emax; i += blockDim.x) dst[i] = src[i];
+        const T* src = TinvT + ((size_t)mt * ndir + d) * Emax * Emax;  // [col][row]
+        T* dst = Tin + (size_t)mt * Emax * Ep;                           // [row][col]
+        for (int i = threadIdx.x; i < Emax * Emax; i += blockDim.x) {
+          const int col = i / Emax, row = i - col * Emax;
+          dst[(size_t)row * Ep + col] = (row < E && col < E) ? src[i] : T(0);
+        }
       }
-      for (int i = threadIdx.x; i < nm * J; i += blockDim.x) {
-        const int kk = i / J, j = i - kk * J;
-        XFs[kk * Jmax + j] = t.XFt[(long long)kk * nadof + qb * A + j];
-        Xds[j * nm + kk] = t.X[(long long)(qb * A + j) * nm + kk];
+      for (int i = threadIdx.x; i < Jmax * NMp; i += blockDim.x) {
+        const int j = i / NMp, kk = i - j * NMp;
+        XFr[i] = (j < J && kk < nm) ? t.XFt[(long long)kk * nadof + qb * A + j] : T(0);
       }
-      for (int i = threadIdx.x; i < J * J; i += blockDim.x) {
-        const int j = i / J, j2 = i - j * J;
-        SLs[j * JS + j2] = SLD[((size_t)d * Jmax + j) * Jmax + j2];
+      for (int i = threadIdx.x; i < nm * Jp; i += blockDim.x) {
+        const int kk = i / Jp, j = i - kk * Jp;
+        Xk[i] = j < J ? t.X[(long long)(qb * A + j) * nm + kk] : T(0);
+      }
+      for (int i = threadIdx.x; i < Jmax * Jp; i += blockDim.x) {
+        const int j = i / Jp, j2 = i - j * Jp;
+        SLr[i] = (j < J && j2 < J) ? SLD[((size_t)d * Jmax + j) * Jmax + j2] : T(0);
       }
       __syncthreads();
+      // rotated coordinates of the k-th cell of wavefront level w (in 2D by
+      // arithmetic: cells of a level are ordered by increasing row)
+      auto rot_of = [&](int w, int k, int& j0, int& j1, int& j2c) {
+        if (DIM == 2) {
+          j1 = max(0, w - (g.nx - 1)) + k;
+          j0 = w - j1;
+          j2c = 0;
+        } else {
+          const int packed = sc.cells[sc.level_off[w] + k];
+          j0 = packed & 2047; j1 = (packed >> 11) & 2047; j2c = packed >> 22;
+        }
+      };
+      auto count_of = [&](int w) {
+        if (DIM == 2) return min(w, g.ny - 1) - max(0, w - (g.nx - 1)) + 1;
+        return sc.level_off[w + 1] - sc.level_off[w];
+      };
       auto cell_of = [&](int w, int k) {
-        const int packed = sc.cells[sc.level_off[w] + k];
-        const int j0 = packed & 2047, j1 = (packed >> 11) & 2047, j2c = packed >> 22;
+        int j0, j1, j2c;
+        rot_of(w, k, j0, j1, j2c);
         const int ix = n0 ? g.nx - 1 - j0 : j0;
         const int iy = n1 ? g.ny - 1 - j1 : j1;
         const int iz = n2 ? g.nz - 1 - j2c : j2c;
@@ -430,10 +548,10 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
       };
       // prefetch registers for the group's cell at the next level
       T pf[MAXE], px[MAXE], pm[4];
-      auto prefetch = [&](int w) {
-        const int cnt = sc.level_off[w + 1] - sc.level_off[w];
-        if (gg >= cnt) return;
-        const int c = cell_of(w, gg);
+      auto prefetch = [&](int w, int kk) {
+        const int cnt = count_of(w);
+        if (kk >= cnt) return;
+        const int c = cell_of(w, kk);
 #pragma unroll
         for (int u = 0; u < MAXE; ++u) {
           const int e = r + u * GT;
@@ -450,13 +568,14 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
           if (e < S * nm) pm[u] = __ldcg(mom + (long long)c * S * nm + e);
         }
       };
-      if (sc.nlev > 0) prefetch(0);
+      if (sc.nlev > 0) prefetch(0, gg);
       for (int w = 0; w < sc.nlev; ++w) {
-        const int cnt = sc.level_off[w + 1] - sc.level_off[w];
-        const bool have = gg < cnt;
-        const int k = gg;
-        // move the prefetched values of this level's cell into shared memory
-        if (have) {
+        const int cnt = count_of(w);
+        bool prefetched = false;
+       for (int k = gg; k < cnt; k += G) {
+        const bool have = true;
+        if (k == gg) {
+          // the group's first cell of this level was prefetched one level ago
 #pragma unroll
           for (int u = 0; u < MAXE; ++u) {
             const int e = r + u * GT;
@@ -468,15 +587,29 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int e = r + u * GT;
-            if (e < S * nm) phs[e] = pm[u];
+            if (e < S * nm) {
+              const int l = e / nm;
+              phs[l * NMp + (e - l * nm)] = pm[u];
+            }
+          }
+        } else {
+          // further cells of this group on the same level: load directly
+          const int c2 = cell_of(w, k);
+          for (int e = r; e < E; e += GT) {
+            const int l = e / J, j = e - l * J;
+            const long long gix = ((long long)c2 * S + l) * nadof + qb * A + j;
+            rhs[e] = f[gix];
+            xold[e] = __ldcg(psi + gix);
+          }
+          for (int e = r; e < S * nm; e += GT) {
+            const int l = e / nm;
+            phs[l * NMp + (e - l * nm)] = __ldcg(mom + (long long)c2 * S * nm + e);
           }
         }
         int c = 0, jj0 = 0, jj1 = 0, jj2 = 0;
         if (have) {
-          const int packed = sc.cells[sc.level_off[w] + k];
-          jj0 = packed & 2047; jj1 = (packed >> 11) & 2047; jj2 = packed >> 22;
+          rot_of(w, k, jj0, jj1, jj2);
           c = cell_of(w, k);
-          // neighbour face values: DIM x HS nodes x J entries, one load per thread
           for (int e = r; e < DIM * HS * J; e += GT) {
             const int xi = e / (HS * J);
             const int rem = e - xi * HS * J;
@@ -493,14 +626,16 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
             upw[e] = v;
           }
         }
-        // next level's cell: issue its loads now, consume them next level
-        if (w + 1 < sc.nlev) prefetch(w + 1);
+        if (k == gg && w + 1 < sc.nlev) {
+          prefetch(w + 1, gg);  // the registers of this level's first cell are in shared memory
+          prefetched = true;
+        }
         if (have) {
           const int mat = cd.mat[c];
           const T sig_s = (T)cd.sigma_s[c];
           T* Phi = mom + (long long)c * S * nm;
           group_bar(bid, GT);
-          // 1. rhs = f - upwind
+          // 1-2. rhs = f - upwind;  buf = X_d F Phi - S_dd^{L+D} x_old
           for (int e = r; e < E; e += GT) {
             const int l = e / J, j = e - l * J;
             const int q = qb + j / A, m = j % A;
@@ -525,26 +660,20 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
               val -= (own ? T(1) : T(-1)) * acc;
             }
             rhs[e] = val;
-          }
-          // 2. buf = X_d F Phi - S_dd^{L+D} x_old
-          for (int e = r; e < E; e += GT) {
-            const int l = e / J, j = e - l * J;
             T a0 = T(0), a1 = T(0);
-            const T* ph = phs + l * nm;
-            int kk = 0;
-            for (; kk + 1 < nm; kk += 2) {
-              a0 += XFs[kk * Jmax + j] * ph[kk];
-              a1 += XFs[(kk + 1) * Jmax + j] * ph[kk + 1];
+            if constexpr (VEC) {
+              const T* xr = XFr + j * NMp;
+              const T* ph = phs + l * NMp;
+              for (int kk = 0; kk < NMp; kk += VW) a0 += V16<T>::dot(xr + kk, ph + kk);
+              const T* sl = SLr + j * Jp;
+              const T* xo = xold + l * J;
+              for (int j3 = 0; j3 < J; j3 += VW) a1 -= V16<T>::dot(sl + j3, xo + j3);
+            } else {
+              const T* ph = phs + l * NMp;
+              for (int kk = 0; kk < nm; ++kk) a0 += XFr[j * NMp + kk] * ph[kk];
+              const T* xo = xold + l * J;
+              for (int j3 = 0; j3 < J; ++j3) a1 -= SLr[j * Jp + j3] * xo[j3];
             }
-            if (kk < nm) a0 += XFs[kk * Jmax + j] * ph[kk];
-            const T* sl = SLs + j * JS;
-            const T* xo = xold + l * J;
-            int j3 = 0;
-            for (; j3 + 1 < J; j3 += 2) {
-              a0 -= sl[j3] * xo[j3];
-              a1 -= sl[j3 + 1] * xo[j3 + 1];
-            }
-            if (j3 < J) a0 -= sl[j3] * xo[j3];
             buf[e] = a0 + a1;
           }
           group_bar(bid, GT);
@@ -558,18 +687,21 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
           }
           group_bar(bid, GT);
           // 4. x_new = Tinv rhs
-          const T* Tm = Tin + (size_t)mat * Emax * Emax;
+          const T* Tm = Tin + (size_t)mat * Emax * Ep;
           for (int rr = r; rr < E; rr += GT) {
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-            int cc = 0;
-            for (; cc + 3 < E; cc += 4) {
-              a0 += Tm[(size_t)cc * Emax + rr] * rhs[cc];
-              a1 += Tm[(size_t)(cc + 1) * Emax + rr] * rhs[cc + 1];
-              a2 += Tm[(size_t)(cc + 2) * Emax + rr] * rhs[cc + 2];
-              a3 += Tm[(size_t)(cc + 3) * Emax + rr] * rhs[cc + 3];
+            T a0 = T(0), a1 = T(0);
+            const T* row = Tm + (size_t)rr * Ep;
+            if constexpr (VEC) {
+              int cc = 0;
+              for (; cc + 2 * VW <= E; cc += 2 * VW) {
+                a0 += V16<T>::dot(row + cc, rhs + cc);
+                a1 += V16<T>::dot(row + cc + VW, rhs + cc + VW);
+              }
+              for (; cc < E; cc += VW) a0 += V16<T>::dot(row + cc, rhs + cc);
+            } else {
+              for (int cc = 0; cc < E; ++cc) a0 += row[cc] * rhs[cc];
             }
-            for (; cc < E; ++cc) a0 += Tm[(size_t)cc * Emax + rr] * rhs[cc];
-            const T xn = (a0 + a1) + (a2 + a3);
+            const T xn = a0 + a1;
             const int l = rr / J, j = rr - l * J;
             psi[((long long)c * S + l) * nadof + qb * A + j] = xn;
             buf[rr] = xn - xold[rr];
@@ -578,30 +710,73 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
           // 5. Phi_c += X_d^T delta
           for (int e = r; e < S * nm; e += GT) {
             const int l = e / nm, kk = e - l * nm;
-            T a0 = T(0), a1 = T(0);
+            T a0 = T(0);
+            const T* xr = Xk + kk * Jp;
             const T* dl = buf + l * J;
-            int j = 0;
-            for (; j + 1 < J; j += 2) {
-              a0 += Xds[j * nm + kk] * dl[j];
-              a1 += Xds[(j + 1) * nm + kk] * dl[j + 1];
+            if constexpr (VEC) {
+              for (int j = 0; j < J; j += VW) a0 += V16<T>::dot(xr + j, dl + j);
+            } else {
+              for (int j = 0; j < J; ++j) a0 += xr[j] * dl[j];
             }
-            if (j < J) a0 += Xds[j * nm + kk] * dl[j];
-            Phi[e] = phs[e] + (a0 + a1);
+            Phi[e] = phs[l * NMp + kk] + a0;
           }
+          group_bar(bid, GT);  // the workspace is reused by the next cell
         }
-        cluster.sync();
+       }
+        if (!prefetched && w + 1 < sc.nlev) prefetch(w + 1, gg);
+        level_barrier();
       }
     }
   }
 }
 
-template <class T, int DIM, int A>
+template <class T>
+size_t gs_group_tables_bytes(int nmat, int Emax, int Jmax, int nm, int s) {
+  const int Ep = gs_pad<T>(Emax), NMp = gs_pad<T>(nm), Jp = gs_pad<T>(Jmax);
+  return (gs_round16((size_t)nmat * Emax * Ep, sizeof(T)) + gs_round16((size_t)Jmax * NMp, sizeof(T)) +
+          gs_round16((size_t)nm * Jp, sizeof(T)) + gs_round16((size_t)Jmax * Jp, sizeof(T)) +
+          gs_round16((size_t)s * s, sizeof(T))) * sizeof(T);
+}
+template <class T>
+size_t gs_group_bytes(int Emax, int Jmax, int nm, int s, int dim) {
+  const int NMp = gs_pad<T>(nm);
+  return (gs_round16(3 * (size_t)Emax, sizeof(T)) + gs_round16((size_t)s * NMp, sizeof(T)) +
+          gs_round16((size_t)dim * (s / 2) * Jmax, sizeof(T))) * sizeof(T);
+}
+
+template <class T, int DIM, int A, bool VEC>
+cudaError_t launch_gs_grid_impl(int nblocks, int ngroups, int GT, size_t smem, const Geom& g,
+                                const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
+                                int ndir, const int* db, const int* de, int sweeps, const T* f,
+                                T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
+                                int nmat, unsigned* gbar, int* err, cudaStream_t st) {
+  auto kern = coarse_gs_group_kernel<T, DIM, A, VEC, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ngroups * GT, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (per_sm < 1 || nblocks > per_sm * nsm) return cudaErrorCooperativeLaunchTooLarge;
+  e = cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&g, (void*)&t, (void*)&cd, (void*)&sc, (void*)&ndir, (void*)&db,
+                  (void*)&de, (void*)&sweeps, (void*)&f, (void*)&phi, (void*)&mom,
+                  (void*)&TinvT, (void*)&SLD, (void*)&Emax, (void*)&Jmax, (void*)&nmat,
+                  (void*)&GT, (void*)&gbar, (void*)&err};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(ngroups * GT), args, smem,
+                                     st);
+}
+
+template <class T, int DIM, int A, bool VEC>
 cudaError_t launch_gs_group_impl(int cl, int ngroups, int GT, size_t smem, const Geom& g,
                                  const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
                                  int ndir, const int* db, const int* de, int sweeps, const T* f,
                                  T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
                                  int nmat, cudaStream_t st) {
-  auto kern = coarse_gs_group_kernel<T, DIM, A>;
+  auto kern = coarse_gs_group_kernel<T, DIM, A, VEC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (cl > 8) {
@@ -624,8 +799,10 @@ cudaError_t launch_gs_group_impl(int cl, int ngroups, int GT, size_t smem, const
   e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
   if (e != cudaSuccess) return e;
   if (nclusters < 1) return cudaErrorLaunchOutOfResources;
+  unsigned* nobar = nullptr;
+  int* noerr = nullptr;
   return cudaLaunchKernelEx(&cfg, kern, g, t, cd, sc, ndir, db, de, sweeps, f, phi, mom, TinvT,
-                            SLD, Emax, Jmax, nmat, GT);
+                            SLD, Emax, Jmax, nmat, GT, nobar, noerr);
 }
 
 template <class T, int DIM, int A>
@@ -725,30 +902,64 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
                             const Schedule& sc, int ndir, const int* dir_begin,
                             const int* dir_end, int sweeps, const T* f, T* phi, T* moments,
                             const T* TinvT, const T* SLD, int Emax, int Jmax, int nmat,
-                            int variant, int* status, cudaStream_t st) {
-  const int sizes[3] = {16, 8, 1};
+                            int variant, int vec_ok, int max_level_cells, int grid_blocks,
+                            unsigned* gbar, int* err, int* status, cudaStream_t st) {
+  int sizes[3] = {16, 8, 1};
+  if (grid_blocks < 0) {  // negative: a fixed cluster size for the cluster kernels
+    sizes[0] = sizes[1] = sizes[2] = -grid_blocks;
+    grid_blocks = 0;
+  }
   // thread-group kernel: tables of all materials in shared memory
   {
     const int GT = ((Emax + 31) / 32) * 32;
-    const size_t tables = ((size_t)nmat * Emax * Emax + 2 * (size_t)t.nmom * Jmax +
-                           (size_t)Jmax * (Jmax + 1) + 64) * sizeof(T);
-    const size_t per_group =
-        (size_t)(3 * Emax + g.s * t.nmom + g.dim * (g.s / 2) * Jmax) * sizeof(T);
+    const size_t tables = gs_group_tables_bytes<T>(nmat, Emax, Jmax, t.nmom, g.s);
+    const size_t per_group = gs_group_bytes<T>(Emax, Jmax, t.nmom, g.s, g.dim);
     int ngroups = std::min(15, 768 / GT);
     while (ngroups > 1 && tables + ngroups * per_group > 220 * 1024) --ngroups;
+    // the vector path needs every direction's J to be a multiple of 16 bytes
+    const bool vec = (sizeof(T) == 4 ? (vec_ok & 1) : (vec_ok & 2)) != 0;
+    if (variant == 4 && GT <= 128 && Emax <= 2 * GT && g.s * t.nmom <= 4 * GT &&
+        tables + per_group <= 220 * 1024 && gbar) {
+      // whole-GPU form: one group per block, one block per cell of the widest level
+      const size_t smem = tables + per_group;
+      const int nb = std::min(std::max(1, max_level_cells), grid_blocks > 0 ? grid_blocks : 148);
+      cudaError_t e;
+#define AMGT_GS_GRID(DIM_, A_)                                                                   \
+  (vec ? launch_gs_grid_impl<T, DIM_, A_, true>(nb, 1, GT, smem, g, t, cd, sc, ndir, dir_begin,  \
+                                                 dir_end, sweeps, f, phi, moments, TinvT, SLD,   \
+                                                 Emax, Jmax, nmat, gbar, err, st)                \
+       : launch_gs_grid_impl<T, DIM_, A_, false>(nb, 1, GT, smem, g, t, cd, sc, ndir, dir_begin, \
+                                                  dir_end, sweeps, f, phi, moments, TinvT, SLD,  \
+                                                  Emax, Jmax, nmat, gbar, err, st))
+      if (g.dim == 2 && g.a == 3) e = AMGT_GS_GRID(2, 3);
+      else if (g.dim == 2) e = AMGT_GS_GRID(2, 1);
+      else if (g.a == 3) e = AMGT_GS_GRID(3, 3);
+      else e = AMGT_GS_GRID(3, 1);
+#undef AMGT_GS_GRID
+      if (e == cudaSuccess) {
+        note_launch();
+        if (status) *status = 200;
+        return;
+      }
+      cudaGetLastError();
+    }
     if (variant != 2 && GT <= 128 && Emax <= 2 * GT && g.s * t.nmom <= 4 * GT &&
         tables + ngroups * per_group <= 220 * 1024) {
       const size_t smem = tables + ngroups * per_group;
       for (int cl : sizes) {
         cudaError_t e;
-        if (g.dim == 2 && g.a == 3)
-          e = launch_gs_group_impl<T, 2, 3>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
-        else if (g.dim == 2)
-          e = launch_gs_group_impl<T, 2, 1>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
-        else if (g.a == 3)
-          e = launch_gs_group_impl<T, 3, 3>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
-        else
-          e = launch_gs_group_impl<T, 3, 1>(cl, ngroups, GT, smem, g, t, cd, sc, ndir, dir_begin, dir_end, sweeps, f, phi, moments, TinvT, SLD, Emax, Jmax, nmat, st);
+#define AMGT_GS_LAUNCH(DIM_, A_)                                                                 \
+  (vec ? launch_gs_group_impl<T, DIM_, A_, true>(cl, ngroups, GT, smem, g, t, cd, sc, ndir,      \
+                                                  dir_begin, dir_end, sweeps, f, phi, moments,   \
+                                                  TinvT, SLD, Emax, Jmax, nmat, st)              \
+       : launch_gs_group_impl<T, DIM_, A_, false>(cl, ngroups, GT, smem, g, t, cd, sc, ndir,     \
+                                                   dir_begin, dir_end, sweeps, f, phi, moments,  \
+                                                   TinvT, SLD, Emax, Jmax, nmat, st))
+        if (g.dim == 2 && g.a == 3) e = AMGT_GS_LAUNCH(2, 3);
+        else if (g.dim == 2) e = AMGT_GS_LAUNCH(2, 1);
+        else if (g.a == 3) e = AMGT_GS_LAUNCH(3, 3);
+        else e = AMGT_GS_LAUNCH(3, 1);
+#undef AMGT_GS_LAUNCH
         if (e == cudaSuccess) {
           note_launch();
           if (status) *status = 100 + cl;
@@ -784,11 +995,13 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
 template void launch_coarse_gs_block<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                              const Schedule&, int, const int*, const int*, int,
                                              const double*, double*, double*, const double*,
-                                             const double*, int, int, int, int, int*, cudaStream_t);
+                                             const double*, int, int, int, int, int, int, int, unsigned*, int*,
+                                             int*, cudaStream_t);
 template void launch_coarse_gs_block<float>(const Geom&, const LevelDev<float>&, const CellData&,
                                             const Schedule&, int, const int*, const int*, int,
                                             const float*, float*, float*, const float*,
-                                            const float*, int, int, int, int, int*, cudaStream_t);
+                                            const float*, int, int, int, int, int, int, int, unsigned*, int*,
+                                            int*, cudaStream_t);
 
 template void launch_coarse_gs<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                        const Schedule&, int, const int*, const int*, int,

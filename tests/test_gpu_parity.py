@@ -122,7 +122,8 @@ MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ i
 
 @pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("gs_kernel", [1, 2, 3], ids=["gs-per-patch", "gs-warp", "gs-group"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4],
+                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid"])
 def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
     H = multigrid.Hierarchy(prob)
@@ -326,4 +327,29 @@ def test_bf16_tensor_core_scatter(dim, nc, level, basis):
     ctx.amgt_op_apply_A(0, xd, y, tc=True)
     assert _rel(_host(y), T.apply_A(x)) < 1e-2
     ctx.amgt_sync()        # no bounded device wait gave up
+    ctx.close()
+
+
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4], ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid"])
+def test_coarse_gs_more_cells_per_level_than_groups(gs_kernel):
+    """Up to 20 cells per wavefront level on a 20 x 40 mesh, with one-block
+    clusters (8-16 groups) or 4 whole-GPU blocks, so every group handles
+    several cells per level; all must equal the oracle."""
+    n = 20 * 40
+    prob = W.random_problem(2, (20, 40), 1, 4, 37, g=0.8)
+    prob["sigma_t"] = np.where(np.arange(n) % 7 < 3, 1.0, 4.0)
+    prob["sigma_s"] = np.where(np.arange(n) % 7 < 3, 0.6, 3.7)
+    prob["mg"] = dict(nlevels=1, Nr=[3], nu_pre=1, nu_post=1, coarse_sweeps=1)
+    T = _oracle(prob, Nscat=3)
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(1, gs_kernel)
+    ctx.amgt_set_tuning(5, 1)     # one-block clusters
+    ctx.amgt_set_tuning(4, 4)     # four whole-GPU blocks
+    f = W.random_vector((T.nsdof, T.nadof), 38)
+    x0 = W.random_vector((T.nsdof, T.nadof), 39)
+    xd = _dev(x0, torch.float32)
+    ctx.amgt_op_coarse_gs(1, _dev(f, torch.float32), xd)
+    ctx.amgt_sync()
+    ref = multigrid.coarse_gs(T, f, x0, 1)
+    assert _rel(_host(xd), ref) < 2e-4
     ctx.close()
