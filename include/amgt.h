@@ -143,7 +143,10 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         cell with the tables in shared memory when they fit
  *                         (else as 2), 4 the thread-group form over the whole
  *                         GPU: one block per cell, cooperative launch, bounded
- *                         grid barrier between wavefront levels (2, 3 and 4 use
+ *                         grid barrier between wavefront levels, 5 (FP32) the
+ *                         thread-block form with the contractions on tensor
+ *                         cores (split-TF32 MMAs, 8 cells per block); 0 picks
+ *                         3, else 2, else 1 (2, 3, 4 and 5 use
  *                         precomputed block lower-triangular inverses: the
  *                         same iteration up to rounding)
  *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto)

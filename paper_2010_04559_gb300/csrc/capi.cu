@@ -739,6 +739,21 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
                  L.nmom, e0, ctx->stream);
   int cl = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (store<T>(L).TinvT && ctx->gs_kernel == 5) {
+      cl = launch_coarse_gs_tc(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
+                               schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, L.dir_begin.data(),
+                               L.dir_end.data(), sweeps, f, phi, mom, store<T>(L).TinvT,
+                               store<T>(L).SLD, L.Emax, L.Jmax, ctx->nmat, ctx->gs_cluster_size,
+                               ctx->stream);
+      if (cl > 0) {
+        ctx->gs_cluster = 300 + cl;
+        CK(cudaGetLastError());
+        return AMGT_OK;
+      }
+      cl = 0;
+    }
+  }
   if (store<T>(L).TinvT && ctx->gs_kernel != 1) {
     launch_coarse_gs_block<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                               schedule(ctx, k), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi, mom,
@@ -1099,7 +1114,7 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (!ctx) return AMGT_ERR_ARG;
   if (key == AMGT_TUNE_GS_KERNEL) {
-    if (value < 0 || value > 4) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..4");
+    if (value < 0 || value > 5) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..5");
     ctx->gs_kernel = value;
     return AMGT_OK;
   }

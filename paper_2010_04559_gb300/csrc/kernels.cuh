@@ -115,6 +115,14 @@ void launch_coarse_gs_block(const Geom& g, const LevelDev<T>& t, const CellData&
                             int variant, int vec_ok, int max_level_cells, int grid_blocks,
                             unsigned* gbar, int* err, int* status, cudaStream_t st);
 
+// tensor-core form of the direction-blocked coarse Gauss-Seidel (FP32);
+// returns the cluster size used, or < 0 if the shape is not supported
+int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData& cd,
+                        const Schedule& sc, int ndir, const int* dir_begin, const int* dir_end,
+                        const int* hdir_begin, const int* hdir_end, int sweeps, const float* f,
+                        float* phi, float* moments, const float* TinvT, const float* SLD, int Emax,
+                        int Jmax, int nmat, int cluster_req, cudaStream_t st);
+
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();
 cudaError_t noalloc_moment_address(int device, void** out);

@@ -122,8 +122,8 @@ MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ i
 
 @pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4],
-                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5],
+                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc"])
 def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
     H = multigrid.Hierarchy(prob)
@@ -330,7 +330,8 @@ def test_bf16_tensor_core_scatter(dim, nc, level, basis):
     ctx.close()
 
 
-@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4], ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5],
+                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc"])
 def test_coarse_gs_more_cells_per_level_than_groups(gs_kernel):
     """Up to 20 cells per wavefront level on a 20 x 40 mesh, with one-block
     clusters (8-16 groups) or 4 whole-GPU blocks, so every group handles
