@@ -145,14 +145,22 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         GPU: one block per cell, cooperative launch, bounded
  *                         grid barrier between wavefront levels, 5 (FP32) the
  *                         thread-block form with the contractions on tensor
- *                         cores (split-TF32 MMAs, 8 cells per block); 0 picks
- *                         3, else 2, else 1 (2, 3, 4 and 5 use
- *                         precomputed block lower-triangular inverses: the
- *                         same iteration up to rounding)
+ *                         cores (split-TF32 MMAs, 8 cells per block), 6 the
+ *                         row-pipelined form: each block owns whole rows of
+ *                         cells (lines along x) and exchanges face values
+ *                         with the blocks of the neighbouring rows through
+ *                         tagged words, no barrier between wavefront levels
+ *                         (cooperative launch; a face wait gives up after
+ *                         2 s and reports AMGT_ERR_DEVICE_TIMEOUT at the next
+ *                         amgt_sync); 0 picks 6, else 3, else 2, else 1 (2 to
+ *                         6 use precomputed block lower-triangular inverses:
+ *                         the same iteration up to rounding)
  *   AMGT_TUNE_SWEEP_GROUP patches per sweep thread block (0 = auto)
  *   AMGT_TUNE_SWEEP_STAGES depth of the 2D sweep's copy pipeline (0 = auto,
  *                         2, 3, 4 or 6 levels)
- *   AMGT_TUNE_GS_GRID_BLOCKS blocks of the whole-GPU Gauss-Seidel (0 = auto)
+ *   AMGT_TUNE_GS_GRID_BLOCKS blocks of the whole-GPU and of the row-pipelined
+ *                         Gauss-Seidel (0 = auto; fewer blocks than rows give
+ *                         each block several rows)
  *   AMGT_TUNE_GS_CLUSTER  cluster size of the cluster Gauss-Seidel kernels
  *                         (0 = largest available, else 1, 2, 4, 8 or 16) */
 #define AMGT_TUNE_GS_KERNEL 1

@@ -236,6 +236,51 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
   return AMGT_OK;
 }
 
+// Row tables and face-word buffer of the row-pipelined coarse Gauss-Seidel:
+// block b owns the rows R = b, b + nb, ... (R = iy + ny*iz) in every
+// direction, visited in increasing rotated level jy + jz.
+int build_gs_rows(amgt_ctx* ctx) {
+  const int k = (int)ctx->lv.size() - 1;
+  Level& L = ctx->lv[k];
+  L.rows_nb = 0;
+  if (!L.d32.TinvT || !L.d64.TinvT || L.ndir == 0 || ctx->geom.dim < 2) return AMGT_OK;
+  const Geom g = level_geom(ctx, k);
+  const int n32 = coarse_gs_rows_plan<float>(g, ctx->nmat, L.Emax, L.Jmax, L.nmom,
+                                             &L.rows_nmat_s[0], &L.rows_smem[0]);
+  const int n64 = coarse_gs_rows_plan<double>(g, ctx->nmat, L.Emax, L.Jmax, L.nmom,
+                                              &L.rows_nmat_s[1], &L.rows_smem[1]);
+  int nb = std::min(n32, n64);
+  if (ctx->gs_grid_blocks > 0) nb = std::min(nb, ctx->gs_grid_blocks);
+  if (nb <= 0) return AMGT_OK;
+  const int nrows = g.ny * g.nz;
+  const int rpb = (nrows + nb - 1) / nb;
+  std::vector<int> rows((size_t)L.ndir * nb * rpb, -1);
+  for (int d = 0; d < L.ndir; ++d) {
+    const int n1 = g.dim == 2 ? (d & 1) : ((d >> 1) & 1);
+    const int n2 = g.dim == 2 ? 0 : (d & 1);
+    for (int b = 0; b < nb; ++b) {
+      std::vector<std::pair<int, int>> mine;
+      for (int R = b; R < nrows; R += nb) {
+        const int iy = R % g.ny, iz = R / g.ny;
+        const int jy = n1 ? g.ny - 1 - iy : iy, jz = n2 ? g.nz - 1 - iz : iz;
+        mine.emplace_back(jy + jz, R);
+      }
+      std::sort(mine.begin(), mine.end());
+      for (size_t i = 0; i < mine.size(); ++i) rows[((size_t)d * nb + b) * rpb + i] = mine[i].second;
+    }
+  }
+  TRY(upload(ctx, rows, &L.d_rows));
+  // two words per value (enough for FP64)
+  const size_t words = (size_t)(g.dim - 1) * L.ndir * g.C * (g.s / 2) * L.Jmax * 2;
+  TRY(dalloc(ctx, words, &L.d_faces));
+  L.faces_bytes = words * sizeof(unsigned long long);
+  CK(cudaMemset(L.d_faces, 0, L.faces_bytes));
+  ctx->gs_tag = 0;
+  L.rows_nb = nb;
+  L.rows_rpb = rpb;
+  return AMGT_OK;
+}
+
 int build(amgt_ctx* ctx) {
   if (!ctx->dirty) return AMGT_OK;
   if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "mesh not set");
@@ -503,6 +548,7 @@ int build(amgt_ctx* ctx) {
   ctx->ws64.assign(nl, {});
   ctx->ws32.assign(nl, {});
   CK(noalloc_moment_address(ctx->device, &ctx->noalloc_moments));
+  TRY(build_gs_rows(ctx));
   ctx->dirty = false;
   return AMGT_OK;
 }
@@ -738,6 +784,28 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
   e0.mode = 0;
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
                  L.nmom, e0, ctx->stream);
+  // row-pipelined kernel: the default where available
+  if (store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6)) {
+    const int pi = sizeof(T) == 4 ? 0 : 1;
+    if (L.rows_nb > 0) {
+      if (ctx->gs_tag > 0xf0000000u) {  // restart the face-word tags
+        CK(cudaMemsetAsync(L.d_faces, 0, L.faces_bytes, ctx->stream));
+        ctx->gs_tag = 0;
+      }
+      if (launch_coarse_gs_rows<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)),
+                                   cell_data(ctx), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi,
+                                   mom, store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax,
+                                   ctx->nmat, L.rows_nmat_s[pi], L.rows_smem[pi], L.d_rows,
+                                   L.rows_nb, L.rows_rpb, L.d_faces, ctx->gs_tag,
+                                   ctx->d_status, ctx->stream) == 0) {
+        ctx->gs_tag += (unsigned)sweeps;
+        ctx->gs_cluster = 600;
+        return AMGT_OK;
+      }
+    }
+    if (ctx->gs_kernel == 6)
+      return fail(ctx, AMGT_ERR_ARG, "row-pipelined Gauss-Seidel not available for this problem");
+  }
   int cl = 0;
   if constexpr (sizeof(T) == 4) {
     if (store<T>(L).TinvT && ctx->gs_kernel == 5) {
@@ -1114,7 +1182,7 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (!ctx) return AMGT_ERR_ARG;
   if (key == AMGT_TUNE_GS_KERNEL) {
-    if (value < 0 || value > 5) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..5");
+    if (value < 0 || value > 6) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..6");
     ctx->gs_kernel = value;
     return AMGT_OK;
   }
@@ -1126,6 +1194,7 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   }
   if (key == AMGT_TUNE_GS_GRID_BLOCKS) {
     if (value < 0 || value > 4096) return fail(ctx, AMGT_ERR_ARG, "grid blocks 0..4096");
+    if (value != ctx->gs_grid_blocks) ctx->dirty = true;  // the row tables depend on it
     ctx->gs_grid_blocks = value;
     return AMGT_OK;
   }

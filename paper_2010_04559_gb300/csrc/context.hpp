@@ -41,6 +41,15 @@ struct Level {
   int ndir = 0;
   int Emax = 0, Jmax = 0;  // direction-blocked Gauss-Seidel table sizes (coarsest level)
   int gs_vec_ok = 0;      // bit 0: float, bit 1: double vector path of the group GS kernel
+  // row-pipelined coarse Gauss-Seidel (coarsest level): blocks, rows per block,
+  // materials whose block inverses fit in shared memory and the shared bytes,
+  // per precision (blocks 0: not available)
+  int rows_nb = 0, rows_rpb = 0;
+  int rows_nmat_s[2] = {0, 0};
+  size_t rows_smem[2] = {0, 0};
+  int* d_rows = nullptr;                      // [ndir][rows_nb][rows_rpb]
+  unsigned long long* d_faces = nullptr;      // tagged face words between rows
+  size_t faces_bytes = 0;
   int sweep_G = 0;         // patches per block of the 2D row-pipelined sweep (0: level kernel)
   bool chunk16_f32 = false, chunk16_f64 = false;
   LevelDevStore<double> d64;
@@ -110,6 +119,7 @@ struct amgt_ctx {
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
+  unsigned gs_tag = 0;  // sweeps run by the row-pipelined Gauss-Seidel (face-word tags)
   int gs_grid_blocks = 0;  // AMGT_TUNE_GS_GRID_BLOCKS
   int gs_cluster_size = 0; // AMGT_TUNE_GS_CLUSTER
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP

@@ -20,6 +20,7 @@
 #include <vector>
 #include <mutex>
 
+#include "gs_common.cuh"
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -66,16 +67,9 @@ cudaError_t noalloc_moment_address(int device, void** out) {
 
 namespace {
 
-__device__ __forceinline__ int fnode(int j, int axis, int bit) {
-  int lo = j & ((1 << axis) - 1);
-  int hi = (j >> axis) << (axis + 1);
-  return lo | (bit << axis) | hi;
-}
-__device__ __forceinline__ int fcompress(int l, int axis) {
-  int lo = l & ((1 << axis) - 1);
-  int hi = (l >> (axis + 1)) << axis;
-  return lo | hi;
-}
+using gsx::fcompress;
+using gsx::fnode;
+using gsx::V16;
 
 constexpr int kMaxWarps = 32;
 
@@ -360,54 +354,10 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// vector of 16 bytes of T and its dot product with another
-template <class T>
-struct V16;
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int n = 4;
-  __device__ static float dot(const float* a, const float* b) {
-    const float4 x = *reinterpret_cast<const float4*>(a);
-    const float4 y = *reinterpret_cast<const float4*>(b);
-    return x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
-  }
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int n = 2;
-  __device__ static double dot(const double* a, const double* b) {
-    const double2 x = *reinterpret_cast<const double2*>(a);
-    const double2 y = *reinterpret_cast<const double2*>(b);
-    return x.x * y.x + x.y * y.y;
-  }
-};
-
-// padded row strides (in elements of T) that spread 16-byte accesses of
-// consecutive rows over distinct bank groups
-template <class T>
-__host__ __device__ inline int gs_pad(int n) {
-  const int vw = 16 / (int)sizeof(T);
-  int p = ((n + vw - 1) / vw) * vw;
-  // rows p elements apart: want (p / vw) odd so 8 consecutive rows hit 8 bank groups
-  if (((p / vw) & 1) == 0) p += vw;
-  return p;
-}
-__host__ __device__ inline size_t gs_round16(size_t elems, size_t esz) {
-  const size_t vw = 16 / esz;
-  return ((elems + vw - 1) / vw) * vw;
-}
-
 // Grid-wide barrier for a cooperative launch (all blocks co-resident): a
 // counter and a generation word in global memory; the last block to arrive
 // resets the counter and advances the generation.  The wait is bounded (2 s);
 // on timeout the block records code 4 in `err` and continues.
-__device__ __forceinline__ unsigned long long gs_now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen,
                                              int* err) {
   __syncthreads();
@@ -420,10 +370,10 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, un
       __threadfence();
       atomicExch(bar + 1, gen + 1u);
     } else {
-      const unsigned long long t0 = gs_now_ns();
+      const unsigned long long t0 = gsx::now_ns();
       unsigned it = 0;
       while (*vgen == gen) {
-        if ((++it & 255u) == 0 && gs_now_ns() - t0 > 2000000000ULL) {
+        if ((++it & 255u) == 0 && gsx::now_ns() - t0 > 2000000000ULL) {
           atomicExch(err, 4);
           break;
         }
@@ -469,22 +419,22 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
       cg::this_cluster().sync();
     }
   };
-  const int Ep = gs_pad<T>(Emax), NMp = gs_pad<T>(nm), Jp = gs_pad<T>(Jmax);
+  const int Ep = gsx::pad16<T>(Emax), NMp = gsx::pad16<T>(nm), Jp = gsx::pad16<T>(Jmax);
   // shared layout (every sub-array starts on a 16-byte boundary)
   T* Tin = reinterpret_cast<T*>(smem_raw);                           // [nmat][Emax][Ep]
-  T* XFr = Tin + gs_round16((size_t)nmat * Emax * Ep, sizeof(T));    // [Jmax][NMp]
-  T* Xk = XFr + gs_round16((size_t)Jmax * NMp, sizeof(T));           // [nm][Jp]
-  T* SLr = Xk + gs_round16((size_t)nm * Jp, sizeof(T));              // [Jmax][Jp]
-  T* Ns = SLr + gs_round16((size_t)Jmax * Jp, sizeof(T));            // [S*S]
-  const size_t per_group = gs_round16(3 * (size_t)Emax, sizeof(T)) +
-                           gs_round16((size_t)S * NMp, sizeof(T)) +
-                           gs_round16((size_t)DIM * HS * Jmax, sizeof(T));
-  T* ws = Ns + gs_round16(S * S, sizeof(T)) + (size_t)gi * per_group;
+  T* XFr = Tin + gsx::round16((size_t)nmat * Emax * Ep, sizeof(T));    // [Jmax][NMp]
+  T* Xk = XFr + gsx::round16((size_t)Jmax * NMp, sizeof(T));           // [nm][Jp]
+  T* SLr = Xk + gsx::round16((size_t)nm * Jp, sizeof(T));              // [Jmax][Jp]
+  T* Ns = SLr + gsx::round16((size_t)Jmax * Jp, sizeof(T));            // [S*S]
+  const size_t per_group = gsx::round16(3 * (size_t)Emax, sizeof(T)) +
+                           gsx::round16((size_t)S * NMp, sizeof(T)) +
+                           gsx::round16((size_t)DIM * HS * Jmax, sizeof(T));
+  T* ws = Ns + gsx::round16(S * S, sizeof(T)) + (size_t)gi * per_group;
   T* rhs = ws;
   T* xold = ws + Emax;
   T* buf = ws + 2 * Emax;
-  T* phs = ws + gs_round16(3 * (size_t)Emax, sizeof(T));            // [S][NMp]
-  T* upw = phs + gs_round16((size_t)S * NMp, sizeof(T));             // [DIM][HS][J]
+  T* phs = ws + gsx::round16(3 * (size_t)Emax, sizeof(T));            // [S][NMp]
+  T* upw = phs + gsx::round16((size_t)S * NMp, sizeof(T));             // [DIM][HS][J]
   const int bid = 1 + gi;  // named barrier of this group (0 is __syncthreads)
   for (int i = threadIdx.x; i < S * S; i += blockDim.x) Ns[i] = (T)g.Nmass[i];
   for (int i = r; i < S * NMp; i += GT) phs[i] = T(0);  // padding stays zero
@@ -732,16 +682,16 @@ __global__ void __launch_bounds__(768) coarse_gs_group_kernel(
 
 template <class T>
 size_t gs_group_tables_bytes(int nmat, int Emax, int Jmax, int nm, int s) {
-  const int Ep = gs_pad<T>(Emax), NMp = gs_pad<T>(nm), Jp = gs_pad<T>(Jmax);
-  return (gs_round16((size_t)nmat * Emax * Ep, sizeof(T)) + gs_round16((size_t)Jmax * NMp, sizeof(T)) +
-          gs_round16((size_t)nm * Jp, sizeof(T)) + gs_round16((size_t)Jmax * Jp, sizeof(T)) +
-          gs_round16((size_t)s * s, sizeof(T))) * sizeof(T);
+  const int Ep = gsx::pad16<T>(Emax), NMp = gsx::pad16<T>(nm), Jp = gsx::pad16<T>(Jmax);
+  return (gsx::round16((size_t)nmat * Emax * Ep, sizeof(T)) + gsx::round16((size_t)Jmax * NMp, sizeof(T)) +
+          gsx::round16((size_t)nm * Jp, sizeof(T)) + gsx::round16((size_t)Jmax * Jp, sizeof(T)) +
+          gsx::round16((size_t)s * s, sizeof(T))) * sizeof(T);
 }
 template <class T>
 size_t gs_group_bytes(int Emax, int Jmax, int nm, int s, int dim) {
-  const int NMp = gs_pad<T>(nm);
-  return (gs_round16(3 * (size_t)Emax, sizeof(T)) + gs_round16((size_t)s * NMp, sizeof(T)) +
-          gs_round16((size_t)dim * (s / 2) * Jmax, sizeof(T))) * sizeof(T);
+  const int NMp = gsx::pad16<T>(nm);
+  return (gsx::round16(3 * (size_t)Emax, sizeof(T)) + gsx::round16((size_t)s * NMp, sizeof(T)) +
+          gsx::round16((size_t)dim * (s / 2) * Jmax, sizeof(T))) * sizeof(T);
 }
 
 template <class T, int DIM, int A, bool VEC>

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 
+#include "gs_common.cuh"
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -28,16 +29,6 @@ namespace {
 constexpr int NC = 8;      // cells per block per level (the MMA N dimension)
 constexpr int WARPS = 8;
 
-__device__ __forceinline__ int fnode_tc(int j, int axis, int bit) {
-  int lo = j & ((1 << axis) - 1);
-  int hi = (j >> axis) << (axis + 1);
-  return lo | (bit << axis) | hi;
-}
-__device__ __forceinline__ int fcompress_tc(int l, int axis) {
-  int lo = l & ((1 << axis) - 1);
-  int hi = (l >> (axis + 1)) << axis;
-  return lo | hi;
-}
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -205,7 +196,7 @@ __global__ void __launch_bounds__(WARPS * 32) coarse_gs_tc_kernel(
               if (has) {
                 const int strd = xi == 0 ? 1 : (xi == 1 ? g.nx : g.nx * g.ny);
                 const int cn = c + (own ? strd : -strd);
-                const int node = fnode_tc(jn, xi, 1 - own);
+                const int node = gsx::fnode(jn, xi, 1 - own);
                 v = __ldcg(psi + ((long long)cn * S + node) * nadof + qb * A + j);
               }
             }
@@ -239,7 +230,7 @@ __global__ void __launch_bounds__(WARPS * 32) coarse_gs_tc_kernel(
                 const int own = xi == 0 ? n0 : (xi == 1 ? n1 : n2);
                 if (((l >> xi) & 1) != own) continue;
                 const float* An = t.Aax + ((size_t)q * 3 + xi) * A * A + m * A;
-                const int jp = fcompress_tc(l, xi);
+                const int jp = gsx::fcompress(l, xi);
                 const int jb = (j / A) * A;
                 float acc = 0.f;
 #pragma unroll

@@ -122,8 +122,8 @@ MG_IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}-{k}lev" for d, n, l, b, k, _ i
 
 @pytest.mark.parametrize("dim,nc,level,basis,nlev,Nr", MG_CASES, ids=MG_IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5],
-                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5, 6],
+                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc", "gs-rows"])
 def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     prob = _mg_problem(dim, nc, level, basis, nlev, Nr)
     H = multigrid.Hierarchy(prob)
@@ -330,12 +330,13 @@ def test_bf16_tensor_core_scatter(dim, nc, level, basis):
     ctx.close()
 
 
-@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5],
-                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc"])
+@pytest.mark.parametrize("gs_kernel", [1, 2, 3, 4, 5, 6],
+                         ids=["gs-per-patch", "gs-warp", "gs-group", "gs-grid", "gs-tc", "gs-rows"])
 def test_coarse_gs_more_cells_per_level_than_groups(gs_kernel):
     """Up to 20 cells per wavefront level on a 20 x 40 mesh, with one-block
     clusters (8-16 groups) or 4 whole-GPU blocks, so every group handles
-    several cells per level; all must equal the oracle."""
+    several cells per level (the row-pipelined kernel: 4 blocks own 10 rows
+    each); all must equal the oracle."""
     n = 20 * 40
     prob = W.random_problem(2, (20, 40), 1, 4, 37, g=0.8)
     prob["sigma_t"] = np.where(np.arange(n) % 7 < 3, 1.0, 4.0)
@@ -353,4 +354,24 @@ def test_coarse_gs_more_cells_per_level_than_groups(gs_kernel):
     ctx.amgt_sync()
     ref = multigrid.coarse_gs(T, f, x0, 1)
     assert _rel(_host(xd), ref) < 2e-4
+    ctx.close()
+
+
+def test_row_pipelined_gs_3d_several_rows_per_block():
+    """3D mesh of 4 x 3 x 5 cells: 15 rows shared by 2 blocks, each visiting
+    its 7-8 rows in every direction's (y + z) wavefront order and waiting on
+    face words from rows of the other block in both y and z."""
+    prob = W.random_problem(3, (4, 3, 5), 1, 4, 53, g=0.8)
+    prob["mg"] = dict(nlevels=1, Nr=[3], nu_pre=1, nu_post=1, coarse_sweeps=2)
+    T = _oracle(prob, Nscat=3)
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(1, 6)
+    ctx.amgt_set_tuning(4, 2)
+    f = W.random_vector((T.nsdof, T.nadof), 54)
+    x0 = W.random_vector((T.nsdof, T.nadof), 55)
+    for td, tol in ((torch.float64, 1e-12), (torch.float32, 2e-4)):
+        xd = _dev(x0, td)
+        ctx.amgt_op_coarse_gs(2, _dev(f, td), xd)
+        ctx.amgt_sync()
+        assert _rel(_host(xd), multigrid.coarse_gs(T, f, x0, 2)) < tol
     ctx.close()
