@@ -38,6 +38,30 @@ import workloads as W  # noqa: E402
 WORKLOAD = "2D 128x128 Q1, checkerboard sigma_t 1/10 c 0.5/0.99, level-3 Lin (512 patches), HG g=0.9 N=16, 3-level MG Nr=4"
 METRIC = "transport-operator GDOF/s; time-to-residual 1e-8, mixed/batched vs FP64 GPU"
 
+KERNEL_NAMES = {
+    "sweep": "sweep2d_rows_kernel<float,3,4>",
+    "apply_L": "apply_L_kernel<float,2,3>",
+    "scatter_prep": "tc_prep_kernel<4>",
+    "scatter_tc": "tc_gemm_kernel (tcgen05, persistent)",
+    "scatter_f32": "gemm_kernel<float>",
+    "scatter_f64": "gemm_kernel<double>",
+    "coarse_gs": "coarse_gs_rows_kernel<float,2,3>",
+}
+# DRAM bytes (read + write) per launch on this workload from the ncu captures
+# summarised under profiles/; a kernel changed since its capture has no entry
+TRAFFIC = {
+    "coarse_gs": 279.5e6,   # profiles/ncu_coarse_gs_rows_config2.md
+    "sweep": 1029.1e6,      # profiles/ncu_top_kernels_config2.md
+}
+NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
+FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
+PEAK_KINDS = {
+    "alu": "FP32 FMA units x clock (152 x 128 x 2 x 2.07 GHz)",
+    "alu64": "nominal GB300 FP64 rate, 1.25 TFLOP/s",
+    "hbm": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+    "tensor": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",
+}
+
 
 def _peaks():
     try:
@@ -190,6 +214,8 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--fp64-ref", action="store_true", help="also time one FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="tolerance of each inner FP32 solve (0: adaptive)")
     ap.add_argument("--profile", choices=["solve", "kernels"], default=None,
                     help="run one solve, or one launch of each hot kernel, and exit (for ncu)")
     args = ap.parse_args()
@@ -211,9 +237,17 @@ def main():
         print("warmup must be >= 3", file=sys.stderr)
         return 2
 
+    import paper_2010_04559_gb300 as pkg
     from paper_2010_04559_gb300 import (AMGT_F32, AMGT_F32_BF16TC, AMGT_MODE_F64,
-                                        AMGT_MODE_MIXED, AMGT_PREC_MG, amgt_query_launches,
-                                        context_from_problem)
+                                        AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_KERNEL_TIMERS,
+                                        amgt_query_launches, context_from_problem)
+    kt_ids = {"sweep": pkg.AMGT_KT_SWEEP, "apply_L": pkg.AMGT_KT_APPLY_L,
+              "scatter_prep": pkg.AMGT_KT_SCATTER_PREP, "scatter_tc": pkg.AMGT_KT_SCATTER_TC,
+              "scatter_f32": pkg.AMGT_KT_SCATTER_F32, "scatter_f64": pkg.AMGT_KT_SCATTER_F64,
+              "coarse_gs": pkg.AMGT_KT_COARSE_GS}
+
+    def kt_read(reset=True):
+        return {k: ctx.amgt_query_kernel_time(i, reset=reset) for k, i in kt_ids.items()}
     from paper_2010_04559_gb300 import build as _b
     _b.build()
     stream = torch.cuda.Stream()
@@ -227,7 +261,7 @@ def main():
     def solve():
         _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
                                      mode=AMGT_MODE_MIXED, psi=psi, phi=phi, device_ptrs=True,
-                                     inner_tol=1e-4, inner_maxit=200)
+                                     inner_tol=args.inner_tol, inner_maxit=200)
         return st
 
     for _ in range(args.warmup):
@@ -236,8 +270,13 @@ def main():
     if dist:
         dist.barrier()
     its = []
+    outer = []
     relres = []
     l0 = amgt_query_launches()
+    # the library records CUDA events on its stream around each launch of its
+    # main kernels while the timers are on: per-kernel device time in the solve
+    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
+    kt_read()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -246,11 +285,14 @@ def main():
         for _ in range(args.steps):
             st = solve()
             its.append(st.iterations)
+            outer.append(st.outer_iterations)
             relres.append(st.relres)
         e1.record(stream)
         torch.cuda.synchronize()
     launches = amgt_query_launches() - l0
     elapsed = e0.elapsed_time(e1) / 1e3
+    kt_solve = kt_read()
+    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
     if dist:
         t = torch.tensor([elapsed], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -268,7 +310,7 @@ def main():
         ctx.amgt_set_source_iso(qsrc)
         _, _, st2, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
                                       mode=AMGT_MODE_MIXED, psi=psi_h, phi=phi_h,
-                                      inner_tol=1e-4, inner_maxit=200)
+                                      inner_tol=args.inner_tol, inner_maxit=200)
         e2e_its += st2.iterations
     e2e_t = time.perf_counter() - t0
     e2e = {"value": world * dof * e2e_its / e2e_t / 1e9, "unit": "GDOF/s",
@@ -280,36 +322,44 @@ def main():
     kern = {}
     x32 = torch.randn((nsdof, nadof), device="cuda", dtype=torch.float32)
     y32 = torch.empty_like(x32)
+    nsc, nac = ctx.amgt_query_sizes(2)
+    fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
+    pc = torch.zeros_like(fc)
     with torch.cuda.stream(stream):
         def timeit(fn, reps=10):
             for _ in range(2):
                 fn()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
+            ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
+            kt_read()
             a.record(stream)
             for _ in range(reps):
                 fn()
             b.record(stream)
             torch.cuda.synchronize()
-            return a.elapsed_time(b) / reps / 1e3
-        t_sweep = timeit(lambda: ctx.amgt_op_sweep(0, x32, y32))
-        kern["sweep_f32"] = {"s": t_sweep, "GB/s": 8.0 * dof / t_sweep / 1e9}
+            k = kt_read()
+            ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
+            # seconds per call, and per kernel class: seconds per launch
+            per = {n: (v[0] / 1e3 / v[1]) for n, v in k.items() if v[1] > 0}
+            return a.elapsed_time(b) / reps / 1e3, per
+        t_sweep, k_sw = timeit(lambda: ctx.amgt_op_sweep(0, x32, y32))
+        kern["sweep_f32"] = {"s": t_sweep, "GB/s": 8.0 * dof / k_sw["sweep"] / 1e9}
         use_tc = True
         try:
-            t_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32, tc=True))
-            kern["scatter_bf16tc"] = {"s": t_sc, "TFLOP/s": 2.0 * nsdof * nadof * nadof / t_sc / 1e12}
+            t_sc, k_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32, tc=True))
+            kern["scatter_bf16tc"] = {"s": t_sc, "gemm_s": k_sc["scatter_tc"],
+                                      "prep_s": k_sc["scatter_prep"],
+                                      "gemm_TFLOP/s": 2.0 * nsdof * nadof * nadof / k_sc["scatter_tc"] / 1e12}
         except Exception as ex:
             use_tc = False
-            t_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32))
+            t_sc, k_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32))
             kern["scatter_f32"] = {"s": t_sc, "note": str(ex)[:80]}
-        t_L = timeit(lambda: ctx.amgt_op_apply_L(0, x32, y32))
-        kern["apply_L_f32"] = {"s": t_L, "GB/s": 8.0 * dof / t_L / 1e9}
-        nsc, nac = ctx.amgt_query_sizes(2)
-        fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
-        pc = torch.zeros_like(fc)
-        t_gs = timeit(lambda: ctx.amgt_op_coarse_gs(10, fc, pc), reps=2)
-        kern["coarse_gs_f32_10sweeps"] = {"s": t_gs}
-        t_v = timeit(lambda: ctx.amgt_op_vcycle(x32, y32, tc=use_tc), reps=3)
+        t_L, k_L = timeit(lambda: ctx.amgt_op_apply_L(0, x32, y32))
+        kern["apply_L_f32"] = {"s": t_L, "GB/s": 8.0 * dof / k_L["apply_L"] / 1e9}
+        t_gs, k_gs = timeit(lambda: ctx.amgt_op_coarse_gs(10, fc, pc), reps=3)
+        kern["coarse_gs_f32_10sweeps"] = {"s": t_gs, "kernel_s": k_gs["coarse_gs"]}
+        t_v, _ = timeit(lambda: ctx.amgt_op_vcycle(x32, y32, tc=use_tc), reps=3)
         kern["vcycle_bf16tc" if use_tc else "vcycle_f32"] = {"s": t_v}
     # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -322,29 +372,54 @@ def main():
     nm = 25
     per_patch = 4 * 3 * nm + 4 * 3 * 3 + 4 * 3 * 4 + (4 * 3) ** 2 + 4 * nm * 3
     gs_flop = 2.0 * per_patch * npd * 4 * nsc_cells * 10
-    rl = {
-        "sweep": {"kernel": "sweep2d_rows_kernel<float,3,4>", "bound": "hbm",
-                  "achieved": 8.0 * dof / t_sweep / 1e9, "peak": hbm, "unit": "GB/s",
-                  "algorithmic": "8 B per unknown (read b, write psi, FP32)"},
-        "apply_L": {"kernel": "apply_L_kernel<float,2,3>", "bound": "hbm",
-                    "achieved": 8.0 * dof / t_L / 1e9, "peak": hbm, "unit": "GB/s",
-                    "algorithmic": "8 B per unknown (read x, write y, FP32)"},
-        "coarse_gs": {"kernel": "coarse_gs_group_kernel<float,2,3>", "bound": "alu",
-                      "achieved": gs_flop / t_gs / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                      "algorithmic": f"{gs_flop/1e9:.2f} GFLOP per 10 sweeps (sequential per-patch form)"},
+    gs_alg = f"{gs_flop/1e9:.2f} GFLOP per launch of 10 sweeps (sequential per-patch form)"
+    tc_flop = 2.0 * nsdof * nadof * nadof
+    # work per launch of each kernel class on the benchmark workload
+    work = {
+        "sweep": ("hbm", 8.0 * dof / 1e9, hbm, "GB/s", "8 B per unknown (read b, write psi, FP32)"),
+        "apply_L": ("hbm", 8.0 * dof / 1e9, hbm, "GB/s", "8 B per unknown (read x, write y, FP32)"),
+        "scatter_prep": ("hbm", 6.0 * dof / 1e9, hbm, "GB/s",
+                         "6 B per unknown (read FP32 x, write BF16 operand)"),
+        "scatter_tc": ("tensor", tc_flop / 1e12, bf16, "TFLOP/s", "2 Nsdof Nadof^2 flop (dense S_f, BF16)"),
+        "coarse_gs": ("alu", gs_flop / 1e12, alu_peak, "TFLOP/s", gs_alg),
+        # FP64 moment form of the scatter in each refinement residual:
+        # Phi = psi X and Y = Phi (F X^T), 2 Nsdof Nadof nmom flop each
+        "scatter_f64": ("alu", 4.0 * nsdof * nadof * NMOM_FINE / 1e12, FP64_PEAK, "TFLOP/s",
+                        "4 Nsdof Nadof nmom flop per residual (two FP64 GEMMs, nmom = 289)"),
+        "scatter_f32": ("alu", 4.0 * nsdof * nadof * NMOM_FINE / 1e12, alu_peak, "TFLOP/s",
+                        "4 Nsdof Nadof nmom flop per apply (two FP32 GEMMs, nmom = 289)"),
     }
-    if use_tc:
-        rl["scatter"] = {"kernel": "tc_prep_kernel + tc_gemm_kernel (tcgen05)", "bound": "tensor",
-                         "achieved": 2.0 * nsdof * nadof * nadof / t_sc / 1e12, "peak": bf16,
-                         "unit": "TFLOP/s", "algorithmic": "2 Nsdof Nadof^2 flop (dense S_f)"}
-    for v in rl.values():
-        v["frac"] = v["achieved"] / v["peak"]
-    # dominant kernel by its share of one solve (launch list: coarse Gauss-Seidel)
-    dom = dict(rl["coarse_gs"])
-    roof = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"],
-            "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
-            "peak_kind": "FP32 FMA units x clock (152 x 128 x 2 x 2.07 GHz)",
-            "algorithmic": dom["algorithmic"]}
+    rl = {}
+    for name, per_launch in (("sweep", k_sw.get("sweep")), ("apply_L", k_L.get("apply_L")),
+                             ("scatter_prep", k_sc.get("scatter_prep")),
+                             ("scatter_tc", k_sc.get("scatter_tc")),
+                             ("coarse_gs", k_gs.get("coarse_gs"))):
+        if not per_launch:
+            continue
+        bound, w, peak, unit, alg = work[name]
+        rl[name] = {"kernel": KERNEL_NAMES[name], "bound": bound, "achieved": w / per_launch,
+                    "peak": peak, "unit": unit, "frac": w / per_launch / peak,
+                    "launch_s": per_launch, "algorithmic": alg}
+    # in-solve device time per kernel class (timed region, library events)
+    solve_k = {}
+    for name, (msum, n) in kt_solve.items():
+        if n > 0:
+            solve_k[name] = {"ms_per_step": msum / args.steps, "launches_per_step": n / args.steps,
+                             "share": msum / 1e3 / elapsed}
+    dom_name = max(solve_k, key=lambda k: solve_k[k]["share"]) if solve_k else "coarse_gs"
+    if dom_name in work:
+        bound, w, peak, unit, alg = work[dom_name]
+        msum, n = kt_solve[dom_name]
+        per_launch = msum / 1e3 / n
+        roof = {"kernel": KERNEL_NAMES[dom_name], "bound": bound, "achieved": w / per_launch,
+                "peak": peak, "unit": unit, "frac": w / per_launch / peak,
+                "traffic": TRAFFIC.get(dom_name), "share_of_solve": solve_k[dom_name]["share"],
+                "peak_kind": PEAK_KINDS["alu64"] if dom_name == "scatter_f64"
+                else PEAK_KINDS.get(bound, peak_kind), "algorithmic": alg}
+    else:
+        roof = {"kernel": dom_name, "bound": None, "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None,
+                "share_of_solve": solve_k[dom_name]["share"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -367,10 +442,12 @@ def main():
                 "dtype": "f32/bf16 (f64 refinement)", "data": "synthetic",
                 "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128x128", f"{args.n}x{args.n}"),
                            "unknowns": dof, "mode": "mixed", "precond": "MG V(1,1)",
-                           "tol": 1e-8, "l2": "inputs larger than L2 (0.4-0.8 GB per vector)",
+                           "tol": 1e-8, "inner_tol": args.inner_tol if args.inner_tol > 0 else "adaptive",
+                           "l2": "inputs larger than L2 (0.4-0.8 GB per vector)",
                            "parallelism": f"replicas x{world}"},
-                "time_to_tol_s": ms / 1e3, "krylov_iterations": its, "relres": relres,
-                "gpu_launches": int(launches), "roofline": roof, "rooflines": rl, "kernels": kern,
+                "time_to_tol_s": ms / 1e3, "krylov_iterations": its, "refinement_steps": outer, "relres": relres,
+                "gpu_launches": int(launches), "roofline": roof, "rooflines": rl,
+                "solve_kernels": solve_k, "kernels": kern,
                 "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
         if fp64:
             line["fp64_gpu"] = fp64

@@ -76,7 +76,10 @@ typedef struct amgt_options {
   int precond;         /* AMGT_PREC_*                                          */
   int mode;            /* AMGT_MODE_*                                          */
   int device_ptrs;     /* 1: x0/psi/phi of amgt_solve are device pointers      */
-  double inner_tol;    /* mixed mode: relative tol of each inner FP32 solve    */
+  double inner_tol;    /* mixed mode: relative tol of each inner FP32 solve;
+                          0: adaptive, each inner solve aims at the outer tol:
+                          0.3 tol / (current relres), within [3e-5, 1e-2],
+                          and stops after 2 restart cycles at most          */
   int inner_maxit;     /* mixed mode: cap per inner solve                      */
 } amgt_options;
 
@@ -102,6 +105,21 @@ int amgt_set_stream(amgt_ctx* ctx, void* cuda_stream);
 /* Number of CUDA kernels the library has launched in this process so far
  * (all contexts).  Host-side counter; no device work. */
 int amgt_query_launches(int64_t* count);
+/* Device time of the library's main kernels, from CUDA events that the
+ * library records on its stream around each launch while the tuning key
+ * AMGT_TUNE_KERNEL_TIMERS is 1 (no events otherwise).  `kernel` is one of
+ * AMGT_KT_*; *ms receives the summed duration and *launches the number of
+ * timed launches since the last reset (reset != 0 clears them after
+ * reading).  Waits for the recorded events. */
+#define AMGT_KT_SWEEP 0        /* transport sweep L^-1                         */
+#define AMGT_KT_APPLY_L 1      /* L x                                          */
+#define AMGT_KT_SCATTER_PREP 2 /* FP32 -> BF16 operand pass of the TC scatter  */
+#define AMGT_KT_SCATTER_TC 3   /* tcgen05 BF16 scatter GEMM                    */
+#define AMGT_KT_SCATTER_F32 4  /* FP32 scatter contractions (SIMT)             */
+#define AMGT_KT_COARSE_GS 5    /* coarse Gauss-Seidel kernel                   */
+#define AMGT_KT_SCATTER_F64 6  /* FP64 scatter contractions (SIMT)             */
+#define AMGT_KT_COUNT 7
+int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches);
 /* Blocks until all work issued on the context's stream has finished; returns
  * AMGT_ERR_DEVICE_TIMEOUT if a device-side bounded wait gave up since the
  * last check. */
@@ -162,12 +180,15 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         Gauss-Seidel (0 = auto; fewer blocks than rows give
  *                         each block several rows)
  *   AMGT_TUNE_GS_CLUSTER  cluster size of the cluster Gauss-Seidel kernels
- *                         (0 = largest available, else 1, 2, 4, 8 or 16) */
+ *                         (0 = largest available, else 1, 2, 4, 8 or 16)
+ *   AMGT_TUNE_KERNEL_TIMERS 1: time the main kernels with CUDA events (see
+ *                         amgt_query_kernel_time), 0: off (default) */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
 #define AMGT_TUNE_GS_GRID_BLOCKS 4
 #define AMGT_TUNE_GS_CLUSTER 5
+#define AMGT_TUNE_KERNEL_TIMERS 6
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Sizes of level k of the hierarchy. */
 int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);

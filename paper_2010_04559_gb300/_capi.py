@@ -40,11 +40,14 @@ AMGT_TUNE_SWEEP_GROUP = 2
 AMGT_TUNE_SWEEP_STAGES = 3
 AMGT_TUNE_GS_GRID_BLOCKS = 4
 AMGT_TUNE_GS_CLUSTER = 5
+AMGT_TUNE_KERNEL_TIMERS = 6
+AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
+AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
 
 # every exported symbol of include/amgt.h
 EXPORTS = [
     "amgt_create", "amgt_destroy", "amgt_last_error", "amgt_set_stream", "amgt_sync",
-    "amgt_query_launches",
+    "amgt_query_launches", "amgt_query_kernel_time",
     "amgt_set_mesh_cartesian", "amgt_set_materials", "amgt_set_angular_uniform",
     "amgt_set_angular_aniso", "amgt_set_multigrid", "amgt_set_source_iso",
     "amgt_set_boundary", "amgt_set_tuning", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
@@ -82,6 +85,7 @@ _SIGS = {
     "amgt_set_stream": ([_P, _P], _I),
     "amgt_sync": ([_P], _I),
     "amgt_query_launches": ([_PI64], _I),
+    "amgt_query_kernel_time": ([_P, _I, _I, _PD, _PI64], _I),
     "amgt_set_mesh_cartesian": ([_P, _I, _PI64, _PD, _PD], _I),
     "amgt_set_materials": ([_P, _PD, _PD, _I, _PD], _I),
     "amgt_set_angular_uniform": ([_P, _I, _I], _I),
@@ -232,6 +236,14 @@ class Context:
     def amgt_set_tuning(self, key, value):
         return self._check(self.lib.amgt_set_tuning(self.h, int(key), int(value)))
 
+    def amgt_query_kernel_time(self, kernel, reset=False):
+        """(milliseconds, launches) timed for one AMGT_KT_* kernel class."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._check(self.lib.amgt_query_kernel_time(self.h, int(kernel), 1 if reset else 0,
+                                                    ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     def amgt_query_sizes(self, level=0):
         a = ctypes.c_int64()
         b = ctypes.c_int64()
@@ -241,7 +253,7 @@ class Context:
 
     def amgt_solve(self, tol=1e-8, restart=20, maxit=1000, precond=AMGT_PREC_MG,
                    mode=AMGT_MODE_F64, x0=None, psi=None, phi=None, device_ptrs=False,
-                   inner_tol=1e-4, inner_maxit=200, allow_not_converged=False):
+                   inner_tol=0.0, inner_maxit=200, allow_not_converged=False):
         """Host mode: x0/psi/phi are NumPy float64 arrays (psi/phi allocated when
         None).  Device mode: torch CUDA float64 tensors."""
         opt = amgt_options(float(tol), int(restart), int(maxit), int(precond), int(mode),

@@ -120,6 +120,44 @@ Geom level_geom(const amgt_ctx* ctx, int k) {
   return g;
 }
 
+// CUDA events around one launch on the context's stream while the kernel
+// timers are on (RAII: the stop event is recorded when the scope ends)
+struct KernelTimer {
+  amgt_ctx* ctx;
+  int id;
+  cudaEvent_t a = nullptr, b = nullptr;
+  static cudaEvent_t take(amgt_ctx* c) {
+    if (!c->kt_free.empty()) {
+      cudaEvent_t e = c->kt_free.back();
+      c->kt_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  KernelTimer(amgt_ctx* c, int kid) : ctx(c), id(kid) {
+    if (!ctx->ktimers) return;
+    a = take(ctx);
+    b = take(ctx);
+    if (!a || !b) {
+      if (a) ctx->kt_free.push_back(a);
+      if (b) ctx->kt_free.push_back(b);
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecord(a, ctx->stream);
+  }
+  ~KernelTimer() {
+    if (!a) return;
+    cudaEventRecord(b, ctx->stream);
+    ctx->kt_pending.push_back({id, a, b});
+  }
+};
+
 CellData cell_data(const amgt_ctx* ctx) {
   CellData cd;
   cd.mat = ctx->d_mat;
@@ -245,10 +283,12 @@ int build_gs_rows(amgt_ctx* ctx) {
   L.rows_nb = 0;
   if (!L.d32.TinvT || !L.d64.TinvT || L.ndir == 0 || ctx->geom.dim < 2) return AMGT_OK;
   const Geom g = level_geom(ctx, k);
-  const int n32 = coarse_gs_rows_plan<float>(g, ctx->nmat, L.Emax, L.Jmax, L.nmom,
-                                             &L.rows_nmat_s[0], &L.rows_smem[0]);
-  const int n64 = coarse_gs_rows_plan<double>(g, ctx->nmat, L.Emax, L.Jmax, L.nmom,
-                                              &L.rows_nmat_s[1], &L.rows_smem[1]);
+  const int n32 = coarse_gs_rows_plan<float>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
+                                             &L.rows_nmat_s[0], &L.rows_threads[0],
+                                             &L.rows_smem[0]);
+  const int n64 = coarse_gs_rows_plan<double>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
+                                              &L.rows_nmat_s[1], &L.rows_threads[1],
+                                              &L.rows_smem[1]);
   int nb = std::min(n32, n64);
   if (ctx->gs_grid_blocks > 0) nb = std::min(nb, ctx->gs_grid_blocks);
   if (nb <= 0) return AMGT_OK;
@@ -648,10 +688,17 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
       }
       auto* xb = static_cast<__nv_bfloat16*>(ctx->d_bf16);
       // sigma_s and the spatial mass commute with S: applied while rounding to BF16
-      launch_tc_prep(M / ctx->geom.s, ctx->geom.s, n, x, ctx->d_sigs32, ctx->d_Nm32,
-                     (float)alpha, xb, ctx->stream);
-      int rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, add, (float)beta, ctx->d_status,
-                              ctx->stream);
+      {
+        KernelTimer kt(ctx, AMGT_KT_SCATTER_PREP);
+        launch_tc_prep(M / ctx->geom.s, ctx->geom.s, n, x, ctx->d_sigs32, ctx->d_Nm32,
+                       (float)alpha, xb, ctx->stream);
+      }
+      int rc;
+      {
+        KernelTimer kt(ctx, AMGT_KT_SCATTER_TC);
+        rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, add, (float)beta, ctx->d_status,
+                            ctx->stream);
+      }
       if (rc != 0)
         return fail(ctx, AMGT_ERR_UNSUPPORTED,
                     "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
@@ -664,6 +711,7 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
   if (L.dense) {
     TRY(ensure_dense(ctx, k));
     const T* Sf = store<T>(L).Sf;
+    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32);
     launch_gemm<T>((int)M, n, n, x, n, Sf, n, y, n, epi, ctx->stream);
   } else {
     void* mp;
@@ -671,6 +719,7 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
     T* Phi = static_cast<T*>(mp);
     GemmEpi e0{};
     e0.mode = 0;
+    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32);
     launch_gemm<T>((int)M, L.nmom, n, x, n, store<T>(L).X, L.nmom, Phi, L.nmom, e0, ctx->stream);
     launch_gemm<T>((int)M, n, L.nmom, Phi, L.nmom, store<T>(L).XFt, n, y, n, epi, ctx->stream);
   }
@@ -682,6 +731,7 @@ template <class T>
 int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   const Level& L = ctx->lv[k];
   const bool c16 = sizeof(T) == 4 ? L.chunk16_f32 : L.chunk16_f64;
+  KernelTimer kt(ctx, AMGT_KT_SWEEP);
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                   schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, c16, ctx->sweep_stages,
                   ctx->stream);
@@ -692,6 +742,7 @@ int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
 template <class T>
 int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
   const Level& L = ctx->lv[k];
+  KernelTimer kt(ctx, AMGT_KT_APPLY_L);
   launch_apply_L<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx), alpha,
                     beta, x, y, ctx->stream);
   CK(cudaGetLastError());
@@ -784,6 +835,7 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
   e0.mode = 0;
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
                  L.nmom, e0, ctx->stream);
+  KernelTimer kt(ctx, AMGT_KT_COARSE_GS);
   // row-pipelined kernel: the default where available
   if (store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6)) {
     const int pi = sizeof(T) == 4 ? 0 : 1;
@@ -795,7 +847,8 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
       if (launch_coarse_gs_rows<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)),
                                    cell_data(ctx), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi,
                                    mom, store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax,
-                                   ctx->nmat, L.rows_nmat_s[pi], L.rows_smem[pi], L.d_rows,
+                                   ctx->nmat, L.rows_nmat_s[pi], L.rows_threads[pi],
+                                   L.rows_smem[pi], L.d_rows,
                                    L.rows_nb, L.rows_rpb, L.d_faces, ctx->gs_tag,
                                    ctx->d_status, ctx->stream) == 0) {
         ctx->gs_tag += (unsigned)sweeps;
@@ -1059,6 +1112,28 @@ int amgt_query_launches(int64_t* count) {
   return AMGT_OK;
 }
 
+int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (kernel < 0 || kernel >= AMGT_KT_COUNT) return fail(ctx, AMGT_ERR_ARG, "unknown kernel id");
+  for (auto& p : ctx->kt_pending) {
+    CK(cudaEventSynchronize(p.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p.a, p.b));
+    ctx->kt_ms[p.id] += t;
+    ctx->kt_n[p.id] += 1;
+    ctx->kt_free.push_back(p.a);
+    ctx->kt_free.push_back(p.b);
+  }
+  ctx->kt_pending.clear();
+  if (ms) *ms = ctx->kt_ms[kernel];
+  if (launches) *launches = ctx->kt_n[kernel];
+  if (reset) {
+    ctx->kt_ms[kernel] = 0.0;
+    ctx->kt_n[kernel] = 0;
+  }
+  return AMGT_OK;
+}
+
 int amgt_sync(amgt_ctx* ctx) {
   if (!ctx) return AMGT_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1196,6 +1271,11 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
     if (value < 0 || value > 4096) return fail(ctx, AMGT_ERR_ARG, "grid blocks 0..4096");
     if (value != ctx->gs_grid_blocks) ctx->dirty = true;  // the row tables depend on it
     ctx->gs_grid_blocks = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_KERNEL_TIMERS) {
+    if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "kernel timers 0 or 1");
+    ctx->ktimers = value == 1;
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_SWEEP_STAGES) {
@@ -1396,8 +1476,15 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     };
     int total_its = 0, outer = 0;
     double relres = 1.0;
-    const double itol = opt->inner_tol > 0 ? opt->inner_tol : 1e-4;
+    // inner tolerance: fixed, or aimed at the outer tolerance from the current
+    // residual (the FP32 operator's rounding bounds how far one solve can go)
+    auto inner_tol_for = [&](double rr) {
+      if (opt->inner_tol > 0) return opt->inner_tol;
+      return std::min(1e-2, std::max(3e-5, 0.3 * opt->tol / rr));
+    };
     const int imax = opt->inner_maxit > 0 ? opt->inner_maxit : 200;
+    // an adaptive inner solve that stalls above its target stops after two cycles
+    const int imax_solve = opt->inner_tol > 0 ? imax : std::min(imax, 2 * m);
     while (bnorm > 0.0) {
       if (x_zero) {
         CK(cudaMemcpyAsync(r64, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1413,8 +1500,8 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       launch_convert<double, float>(n, r64, r32, ctx->stream);
       launch_scale_copy<float>(n, 1.0 / rn, r32, r32, ctx->stream);
       KrylovResult ik;
-      rc = gmres<float>(ctx, 0, A32, M32, r32, e32, true, itol, m,
-                        std::min(imax, maxit - total_its), ik, st, 1.0, total_its);
+      rc = gmres<float>(ctx, 0, A32, M32, r32, e32, true, inner_tol_for(relres), m,
+                        std::min(imax_solve, maxit - total_its), ik, st, 1.0, total_its);
       if (rc != AMGT_OK) break;
       total_its += ik.its;
       // x += rn * e  (FP64 accumulate)

@@ -45,7 +45,7 @@ struct Level {
   // materials whose block inverses fit in shared memory and the shared bytes,
   // per precision (blocks 0: not available)
   int rows_nb = 0, rows_rpb = 0;
-  int rows_nmat_s[2] = {0, 0};
+  int rows_nmat_s[2] = {0, 0}, rows_threads[2] = {0, 0};
   size_t rows_smem[2] = {0, 0};
   int* d_rows = nullptr;                      // [ndir][rows_nb][rows_rpb]
   unsigned long long* d_faces = nullptr;      // tagged face words between rows
@@ -124,4 +124,21 @@ struct amgt_ctx {
   int gs_cluster_size = 0; // AMGT_TUNE_GS_CLUSTER
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
   int sweep_stages = 0; // AMGT_TUNE_SWEEP_STAGES
+  // per-kernel device timers (AMGT_TUNE_KERNEL_TIMERS)
+  bool ktimers = false;
+  struct KtPending {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<KtPending> kt_pending;
+  std::vector<cudaEvent_t> kt_free;
+  double kt_ms[AMGT_KT_COUNT] = {};
+  long long kt_n[AMGT_KT_COUNT] = {};
+  ~amgt_ctx() {
+    for (auto& p : kt_pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : kt_free) cudaEventDestroy(e);
+  }
 };

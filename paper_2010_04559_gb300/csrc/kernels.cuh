@@ -126,18 +126,19 @@ int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData&
 // row-pipelined form of the direction-blocked coarse Gauss-Seidel (see
 // kernels_gs_rows.cu).  plan: returns the number of thread blocks that can be
 // resident at once (capped by the number of rows ny*nz; 0 if the shapes are
-// not supported) with the materials whose inverses fit in shared memory and
-// the shared bytes per block.  launch: returns 0 on a successful launch.
+// not supported) with the materials whose inverses fit in shared memory, the
+// threads and the shared bytes per block.  launch: returns 0 on a successful
+// launch.
 template <class T>
-int coarse_gs_rows_plan(const Geom& g, int nmat, int Emax, int Jmax, int nmom, int* nmat_s,
-                        size_t* smem);
+int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
+                        int* threads, size_t* smem);
 template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
                           T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, size_t smem, const int* rows, int nblocks,
-                          int rpb, unsigned long long* faces, unsigned tag0, int* err,
-                          cudaStream_t st);
+                          int nmat, int nmat_s, int threads, size_t smem, const int* rows,
+                          int nblocks, int rpb, unsigned long long* faces, unsigned tag0,
+                          int* err, cudaStream_t st);
 
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();

@@ -37,15 +37,64 @@ namespace amgt {
 
 namespace {
 
-constexpr int kRowsThreads = 384;  // 96 four-lane groups
-constexpr int kRowsMaxU = 2;       // padded cell unknowns per thread
-constexpr int kRowsMaxM = 8;       // cell moments per thread
+constexpr int kRowsMaxThreads = 512;
+constexpr int kRowsMaxU = 2;  // padded cell unknowns per thread
+constexpr int kRowsMaxM = 8;  // cell moments per thread
 // give up a face wait after this long: the block records code 5 in the
 // status word and goes on; every later wait of every block then returns at once
 constexpr unsigned long long kRowsWaitNs = 2000000000ULL;
 
 using gsx::fcompress;
 using gsx::V16;
+
+// Row stride (elements of T) for tables read by four-lane groups, each lane
+// taking every fourth 16-byte chunk of a row: a stride of 64 bytes modulo 128
+// puts the two rows read by one quarter warp on disjoint banks.
+template <class T>
+__host__ __device__ inline int qpad(int n) {
+  const int vw = 16 / (int)sizeof(T);
+  int p = ((n + vw - 1) / vw) * vw;
+  while ((p * (int)sizeof(T)) % 128 != 64) p += vw;
+  return p;
+}
+
+// Shared-memory layout of one block (byte offsets, 16-byte aligned).
+template <class T>
+struct RowsLayout {
+  int Jv, Ev, Evp, NMp, Jp;
+  size_t o_Tin, o_XFr, o_Xk, o_SLr, o_Ns, o_Ad, o_lj, o_lk, o_rhs, o_xold, o_buf, o_phs, o_xfc,
+      o_yup, bytes;
+  __host__ __device__ RowsLayout(int nmat_s, int Jmax, int nm, int S, int dim, int A, int ndir) {
+    const int vw = 16 / (int)sizeof(T);
+    Jv = ((Jmax + vw - 1) / vw) * vw;
+    Ev = S * Jv;
+    Evp = qpad<T>(Ev);
+    NMp = qpad<T>(nm);
+    Jp = qpad<T>(Jv);
+    size_t o = 0;
+    auto take = [&](size_t nbytes) {
+      const size_t at = o;
+      o += (nbytes + 15) / 16 * 16;
+      return at;
+    };
+    const size_t t = sizeof(T);
+    o_Tin = take((size_t)nmat_s * Ev * Evp * t);
+    o_XFr = take((size_t)Jv * NMp * t);
+    o_Xk = take((size_t)nm * Jp * t);
+    o_SLr = take((size_t)Jv * Jp * t);
+    o_Ns = take((size_t)S * S * t);
+    o_Ad = take((size_t)Jmax * dim * A * t);   // [patch][axis][A][A]
+    o_lj = take((size_t)ndir * Ev * sizeof(int));
+    o_lk = take((size_t)S * nm * sizeof(int));
+    o_rhs = take((size_t)Ev * t);
+    o_xold = take((size_t)Ev * t);
+    o_buf = take((size_t)2 * Ev * t);
+    o_phs = take((size_t)2 * S * NMp * t);
+    o_xfc = take((size_t)(S / 2) * Jv * t);
+    o_yup = take((size_t)(dim - 1) * (S / 2) * Jv * t);
+    bytes = o;
+  }
+};
 
 __device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -119,7 +168,7 @@ struct RowsArgs {
 };
 
 template <class T, int DIM, int A>
-__global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T> p) {
+__global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArgs<T> p) {
   constexpr int S = 1 << DIM;
   constexpr int HS = S / 2;
   constexpr int VW = V16<T>::n;
@@ -130,26 +179,34 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
   const int tid = threadIdx.x, NT = blockDim.x;
   const int qd = tid >> 2, l4 = tid & 3, NQ = NT >> 2;
   const int nb = gridDim.x, b = blockIdx.x;
+  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nm, S, DIM, A, ndir);
   // padded shapes: a direction's J unknowns per node are stored Jv apart
-  const int Jv = ((p.Jmax + VW - 1) / VW) * VW;
-  const int Ev = S * Jv;
-  const int Evp = gsx::pad16<T>(Ev), NMp = gsx::pad16<T>(nm), Jp = gsx::pad16<T>(Jv);
+  const int Jv = Ly.Jv, Ev = Ly.Ev, Evp = Ly.Evp, NMp = Ly.NMp, Jp = Ly.Jp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Tin = reinterpret_cast<T*>(smem_raw);                        // [nmat_s][Ev][Evp]
-  T* XFr = Tin + gsx::round16((size_t)p.nmat_s * Ev * Evp, sizeof(T));  // [Jv][NMp]
-  T* Xk = XFr + gsx::round16((size_t)Jv * NMp, sizeof(T));        // [nm][Jp]
-  T* SLr = Xk + gsx::round16((size_t)nm * Jp, sizeof(T));         // [Jv][Jp]
-  T* Ns = SLr + gsx::round16((size_t)Jv * Jp, sizeof(T));         // [S][S]
-  T* rhs = Ns + gsx::round16(S * S, sizeof(T));                   // [S][Jv]
-  T* xold = rhs + gsx::round16(Ev, sizeof(T));                    // [S][Jv]
-  T* buf = xold + gsx::round16(Ev, sizeof(T));                    // [S][Jv]
-  T* phs = buf + gsx::round16(Ev, sizeof(T));                     // [S][NMp]
-  T* xfc = phs + gsx::round16((size_t)S * NMp, sizeof(T));        // [HS][Jv] x-outflow
-  T* yup = xfc + gsx::round16((size_t)HS * Jv, sizeof(T));        // [NF][HS][Jv] inflow
+  T* Tin = reinterpret_cast<T*>(smem_raw + Ly.o_Tin);    // [nmat_s][Ev][Evp]
+  T* XFr = reinterpret_cast<T*>(smem_raw + Ly.o_XFr);    // [Jv][NMp]  (diag(f) X_d^T)^T
+  T* Xk = reinterpret_cast<T*>(smem_raw + Ly.o_Xk);      // [nm][Jp]   X_d^T
+  T* SLr = reinterpret_cast<T*>(smem_raw + Ly.o_SLr);    // [Jv][Jp]   S_dd^{L+D}
+  T* Ns = reinterpret_cast<T*>(smem_raw + Ly.o_Ns);      // [S][S]
+  T* Ad = reinterpret_cast<T*>(smem_raw + Ly.o_Ad);      // [patch][axis][A][A]
+  int* slj = reinterpret_cast<int*>(smem_raw + Ly.o_lj); // [ndir][Ev] l<<16|j, -1 past J
+  int* slk = reinterpret_cast<int*>(smem_raw + Ly.o_lk); // [S*nm] l<<16|k
+  T* rhs = reinterpret_cast<T*>(smem_raw + Ly.o_rhs);    // [S][Jv]
+  T* xold = reinterpret_cast<T*>(smem_raw + Ly.o_xold);  // [S][Jv]
+  T* bufs = reinterpret_cast<T*>(smem_raw + Ly.o_buf);   // [2][S][Jv] by cell parity
+  T* phss = reinterpret_cast<T*>(smem_raw + Ly.o_phs);   // [2][S][NMp] by cell parity
+  T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
+  T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [NF][HS][Jv] y/z inflow
   for (int i = tid; i < S * S; i += NT) Ns[i] = (T)g.Nmass[i];
-  for (int i = tid; i < Ev; i += NT) rhs[i] = xold[i] = buf[i] = T(0);
-  for (int i = tid; i < S * NMp; i += NT) phs[i] = T(0);
-  const int nrow_cells = nx;
+  for (int i = tid; i < 2 * Ev; i += NT) bufs[i] = T(0);
+  for (int i = tid; i < 2 * S * NMp; i += NT) phss[i] = T(0);
+  for (int i = tid; i < ndir * Ev; i += NT) {
+    const int d = i / Ev, pe = i - d * Ev;
+    const int J = (p.dir_end[d] - p.dir_begin[d]) * A;
+    const int l = pe / Jv, j = pe - l * Jv;
+    slj[i] = j < J ? (l << 16) | j : -1;
+  }
+  for (int i = tid; i < S * nm; i += NT) slk[i] = ((i / nm) << 16) | (i % nm);
   const int* myrows = p.rows + (size_t)b * p.rpb;  // + d * nb * rpb per direction
   auto row_of = [&](int d, int ri) -> int {
     return ri < p.rpb ? myrows[(size_t)d * nb * p.rpb + ri] : -1;
@@ -161,24 +218,28 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
       n0 = (d >> 2) & 1; n1 = (d >> 1) & 1; n2 = d & 1;
     }
   };
+  __syncthreads();
   // prefetch registers for the next cell
   T pf[kRowsMaxU], px[kRowsMaxU], pm[kRowsMaxM];
+  int pmat = 0;
+  T psig = T(0);
+  long long c_next = -1;
   auto prefetch = [&](int d, int R, int k) {
     int n0, n1, n2;
     dir_bits(d, n0, n1, n2);
     const int ix = n0 ? nx - 1 - k : k;
     const long long c = ix + (long long)nx * R;
-    const int qb = p.dir_begin[d];
-    const int J = (p.dir_end[d] - qb) * A;
+    c_next = c;
+    const int qa = p.dir_begin[d] * A;
 #pragma unroll
     for (int u = 0; u < kRowsMaxU; ++u) {
       const int pe = tid + u * NT;
       pf[u] = T(0);
       px[u] = T(0);
       if (pe < Ev) {
-        const int l = pe / Jv, j = pe - l * Jv;
-        if (j < J) {
-          const long long gix = (c * S + l) * nadof + qb * A + j;
+        const int lj = slj[d * Ev + pe];
+        if (lj >= 0) {
+          const long long gix = (c * S + (lj >> 16)) * nadof + qa + (lj & 0xffff);
           pf[u] = p.f[gix];
           px[u] = __ldcg(p.psi + gix);
         }
@@ -189,12 +250,42 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
       const int e = tid + u * NT;
       if (e < S * nm) pm[u] = __ldcg(p.mom + c * S * nm + e);
     }
+    pmat = p.cd.mat[c];
+    psig = (T)p.cd.sigma_s[c];
   };
-  long long prev_cell = -1;
+  // Phi_c += X_d^T delta for the cell `cp` whose delta is in buffer `slot`;
+  // also into the other buffer when the next cell is the same cell
+  auto update_moments = [&](long long cp, int slot, bool next_same) {
+    const T* bf = bufs + (size_t)slot * Ev;
+    T* ph = phss + (size_t)slot * S * NMp;
+    T* ph2 = phss + (size_t)(slot ^ 1) * S * NMp;
+    for (int base = 0; base < S * nm; base += NQ) {
+      const int e = base + qd;
+      int lk = 0;
+      T a = T(0);
+      if (e < S * nm) {
+        lk = slk[e];
+        const T* xr = Xk + (lk & 0xffff) * Jp;
+        const T* dl = bf + (lk >> 16) * Jv;
+        for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a += V16<T>::dot(xr + ch, dl + ch);
+      }
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      if (e < S * nm && l4 == 0) {
+        const int o = (lk >> 16) * NMp + (lk & 0xffff);
+        const T v = ph[o] + a;
+        p.mom[cp * S * nm + e] = v;
+        if (next_same) ph2[o] = v;
+      }
+    }
+  };
   {
     const int R0 = row_of(0, 0);
     if (R0 >= 0 && p.sweeps > 0) prefetch(0, R0, 0);
   }
+  long long last = -1;  // last cell solved
+  bool pend = false;    // its moment update is still to be done
+  long long kc = 0;     // cells solved by this block (buffer parity)
   for (int sw = 0; sw < p.sweeps; ++sw) {
     const unsigned tag = p.tag0 + (unsigned)sw + 1u;
     for (int d = 0; d < ndir; ++d) {
@@ -203,8 +294,13 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
       const int qb = p.dir_begin[d];
       const int J = (p.dir_end[d] - qb) * A;
       const int E = S * J;
-      // stage this direction's tables (padded, zero filled)
+      const int* lj_d = slj + d * Ev;
+      // the pending moment update uses the previous direction's tables
       __syncthreads();
+      if (pend) update_moments(last, (int)((kc - 1) & 1), c_next == last);
+      pend = false;
+      __syncthreads();
+      // stage this direction's tables (padded, zero filled)
       for (int mt = 0; mt < p.nmat_s; ++mt) {
         const T* src = p.TinvT + ((size_t)mt * ndir + d) * p.Emax * p.Emax;  // [col][row]
         T* dst = Tin + (size_t)mt * Ev * Evp;
@@ -227,6 +323,20 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
         const int j = i / Jp, j2 = i - j * Jp;
         SLr[i] = (j < J && j2 < J) ? p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2] : T(0);
       }
+      for (int i = tid; i < (J / A) * DIM * A * A; i += NT) {
+        const int jq = i / (DIM * A * A), rem = i - jq * DIM * A * A;
+        const int xi = rem / (A * A), e = rem - xi * A * A;
+        Ad[i] = p.t.Aax[((size_t)(qb + jq) * 3 + xi) * A * A + e];
+      }
+      // this thread's face word (axis, face node, unknown), if it polls one
+      const int npoll = NF * HS * J;
+      int pa = 0, pjn = 0, pj = 0;
+      if (tid < npoll) {
+        pa = tid / (HS * J);
+        const int rem = tid - pa * HS * J;
+        pjn = rem / J;
+        pj = rem - pjn * J;
+      }
       __syncthreads();
       for (int ri = 0;; ++ri) {
         const int R = row_of(d, ri);
@@ -234,12 +344,15 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
         const int iy = R % g.ny, iz = R / g.ny;
         const int jy = n1 ? g.ny - 1 - iy : iy;
         const int jz = n2 ? g.nz - 1 - iz : iz;
-        for (int k = 0; k < nrow_cells; ++k) {
-          const int ix = n0 ? nx - 1 - k : k;
-          const long long c = ix + (long long)nx * R;
-          const int mat = p.cd.mat[c];
-          const T sig_s = (T)p.cd.sigma_s[c];
-          // ---- A: the cell's data into shared memory; first look at the faces
+        for (int k = 0; k < nx; ++k) {
+          const long long c = c_next;
+          const int slot = (int)(kc & 1);
+          T* buf = bufs + (size_t)slot * Ev;
+          T* phs = phss + (size_t)slot * S * NMp;
+          const int mat = pmat;
+          const T sig_s = psig;
+          // ---- 1: the cell's data into shared memory; first look at the faces;
+          //         the previous cell's moment update
 #pragma unroll
           for (int u = 0; u < kRowsMaxU; ++u) {
             const int pe = tid + u * NT;
@@ -248,27 +361,20 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
               xold[pe] = px[u];
             }
           }
-          if (c != prev_cell) {
+          if (c != last) {
 #pragma unroll
             for (int u = 0; u < kRowsMaxM; ++u) {
               const int e = tid + u * NT;
               if (e < S * nm) {
-                const int l = e / nm;
-                phs[l * NMp + (e - l * nm)] = pm[u];
+                const int lk = slk[e];
+                phs[(lk >> 16) * NMp + (lk & 0xffff)] = pm[u];
               }
             }
           }
-          // face words this thread waits for: (axis, face node, unknown)
-          const int npoll = NF * HS * J;
           bool need = false;
           const unsigned long long* wp = nullptr;
           unsigned long long fw[W];
-          int pa = 0, pjn = 0, pj = 0;
           if (tid < npoll) {
-            pa = tid / (HS * J);
-            const int rem = tid - pa * HS * J;
-            pjn = rem / J;
-            pj = rem - pjn * J;
             const int jr = pa == 0 ? jy : jz;
             if (jr > 0) {
               const int own = pa == 0 ? n1 : n2;
@@ -280,31 +386,35 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
               FaceWords<T>::load(wp, fw);
             }
           }
+          if (pend) update_moments(last, slot ^ 1, c == last);
           __syncthreads();
-          // the next cell of this block's sequence into registers
+          // ---- 2: the next cell of this block's sequence into registers;
+          //         buf = X_d F Phi - S_dd^{L+D} x_old (four lanes per unknown)
           {
-            int d2 = d, ri2 = ri, k2 = k + 1, sw2 = sw;
+            int d2 = d, ri2 = ri, k2 = k + 1, sw2 = sw, R2 = R;
             bool more = true;
-            if (k2 >= nrow_cells) {
+            if (k2 >= nx) {
               k2 = 0;
               ++ri2;
-              if (row_of(d2, ri2) < 0) {
+              R2 = row_of(d2, ri2);
+              if (R2 < 0) {
                 ri2 = 0;
                 if (++d2 >= ndir) {
                   d2 = 0;
                   more = ++sw2 < p.sweeps;
                 }
+                if (more) R2 = row_of(d2, ri2);
               }
             }
-            if (more) prefetch(d2, row_of(d2, ri2), k2);
+            if (more) prefetch(d2, R2, k2);
+            else c_next = -2;
           }
-          // ---- B: buf = X_d F Phi - S_dd^{L+D} x_old (four lanes per unknown)
           for (int base = 0; base < Ev; base += NQ) {
             const int pe = base + qd;
-            const int l = pe / Jv, j = pe - l * Jv;
-            const bool valid = pe < Ev && j < J;
+            const int lj = pe < Ev ? lj_d[pe] : -1;
             T a = T(0);
-            if (valid) {
+            if (lj >= 0) {
+              const int l = lj >> 16, j = lj & 0xffff;
               const T* xr = XFr + j * NMp;
               const T* ph = phs + l * NMp;
               for (int ch = l4 * VW; ch < NMp; ch += 4 * VW) a += V16<T>::dot(xr + ch, ph + ch);
@@ -314,7 +424,7 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
             }
             a += __shfl_xor_sync(0xffffffffu, a, 1);
             a += __shfl_xor_sync(0xffffffffu, a, 2);
-            if (pe < Ev && l4 == 0) buf[pe] = valid ? a : T(0);
+            if (pe < Ev && l4 == 0) buf[pe] = a;
           }
           // the upwind rows' face words
           if (need) {
@@ -333,11 +443,12 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
             yup[(pa * HS + pjn) * Jv + pj] = FaceWords<T>::value(fw);
           }
           __syncthreads();
-          // ---- C: rhs = f - upwind + sigma_s N buf
+          // ---- 3: rhs = f - upwind + sigma_s N buf
           for (int pe = tid; pe < Ev; pe += NT) {
-            const int l = pe / Jv, j = pe - l * Jv;
-            if (j >= J) continue;
-            const int q = qb + j / A, m = j % A, jb = (j / A) * A;
+            const int lj = lj_d[pe];
+            if (lj < 0) continue;
+            const int l = lj >> 16, j = lj & 0xffff;
+            const int jq = j / A, m = j - jq * A, jb = jq * A;
             T val = rhs[pe];
 #pragma unroll
             for (int xi = 0; xi < DIM; ++xi) {
@@ -345,14 +456,14 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
               const int jr = xi == 0 ? k : (xi == 1 ? jy : jz);
               if (jr == 0 || ((l >> xi) & 1) != own) continue;
               const T* up = xi == 0 ? xfc : yup + (size_t)(xi - 1) * HS * Jv;
-              const T* An = p.t.Aax + ((size_t)q * 3 + xi) * A * A + m * A;
+              const T* An = Ad + ((size_t)jq * DIM + xi) * A * A + m * A;
               const int jp = fcompress(l, xi);
               T acc = T(0);
 #pragma unroll
               for (int jn = 0; jn < HS; ++jn) {
                 T sacc = T(0);
 #pragma unroll
-                for (int dd = 0; dd < A; ++dd) sacc += __ldg(An + dd) * up[jn * Jv + jb + dd];
+                for (int dd = 0; dd < A; ++dd) sacc += An[dd] * up[jn * Jv + jb + dd];
                 acc += T(g.facemass[xi][jp][jn]) * sacc;
               }
               val -= (own ? T(1) : T(-1)) * acc;
@@ -363,18 +474,18 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
             rhs[pe] = val + sig_s * mix;
           }
           __syncthreads();
-          // ---- D: x_new = Tinv rhs (four lanes per row); outputs
+          // ---- 4: x_new = Tinv rhs (four lanes per row); outputs
           for (int base = 0; base < Ev; base += NQ) {
             const int pe = base + qd;
-            const int l = pe / Jv, j = pe - l * Jv;
-            const bool valid = pe < Ev && j < J;
+            const int lj = pe < Ev ? lj_d[pe] : -1;
             T a = T(0);
-            if (valid) {
+            if (lj >= 0) {
               if (mat < p.nmat_s) {
                 const T* row = Tin + ((size_t)mat * Ev + pe) * Evp;
                 for (int ch = l4 * VW; ch < Ev; ch += 4 * VW) a += V16<T>::dot(row + ch, rhs + ch);
               } else {
-                const T* col = p.TinvT + ((size_t)mat * ndir + d) * p.Emax * p.Emax + l * J + j;
+                const int r = (lj >> 16) * J + (lj & 0xffff);
+                const T* col = p.TinvT + ((size_t)mat * ndir + d) * p.Emax * p.Emax + r;
                 for (int cc = l4; cc < E; cc += 4) {
                   const int lc = cc / J;
                   a += __ldg(col + (size_t)cc * p.Emax) * rhs[lc * Jv + (cc - lc * J)];
@@ -384,7 +495,8 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
             a += __shfl_xor_sync(0xffffffffu, a, 1);
             a += __shfl_xor_sync(0xffffffffu, a, 2);
             if (pe < Ev && l4 == 0) {
-              if (valid) {
+              if (lj >= 0) {
+                const int l = lj >> 16, j = lj & 0xffff;
                 p.psi[(c * S + l) * nadof + qb * A + j] = a;
                 buf[pe] = a - xold[pe];
                 if (((l & 1) ^ n0) == 1) xfc[fcompress(l, 0) * Jv + j] = a;
@@ -405,58 +517,28 @@ __global__ void __launch_bounds__(kRowsThreads) coarse_gs_rows_kernel(RowsArgs<T
             }
           }
           __syncthreads();
-          // ---- E: Phi_c += X_d^T delta
-          for (int base = 0; base < S * nm; base += NQ) {
-            const int e = base + qd;
-            const int l = e / nm, kk = e - l * nm;
-            T a = T(0);
-            if (e < S * nm) {
-              const T* xr = Xk + kk * Jp;
-              const T* dl = buf + l * Jv;
-              for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a += V16<T>::dot(xr + ch, dl + ch);
-            }
-            a += __shfl_xor_sync(0xffffffffu, a, 1);
-            a += __shfl_xor_sync(0xffffffffu, a, 2);
-            if (e < S * nm && l4 == 0) {
-              const T v = phs[l * NMp + kk] + a;
-              phs[l * NMp + kk] = v;
-              p.mom[c * S * nm + e] = v;
-            }
-          }
-          prev_cell = c;
-          __syncthreads();
+          last = c;
+          pend = true;
+          ++kc;
         }
       }
     }
   }
-}
-
-template <class T>
-size_t rows_smem_bytes(int nmat_s, int Emax, int Jmax, int nm, int s) {
-  const int vw = 16 / (int)sizeof(T);
-  const int Jv = ((Jmax + vw - 1) / vw) * vw, Ev = s * Jv;
-  const int Evp = gsx::pad16<T>(Ev), NMp = gsx::pad16<T>(nm), Jp = gsx::pad16<T>(Jv);
-  (void)Emax;
-  const size_t e = gsx::round16((size_t)nmat_s * Ev * Evp, sizeof(T)) +
-                   gsx::round16((size_t)Jv * NMp, sizeof(T)) + gsx::round16((size_t)nm * Jp, sizeof(T)) +
-                   gsx::round16((size_t)Jv * Jp, sizeof(T)) + gsx::round16((size_t)s * s, sizeof(T)) +
-                   3 * gsx::round16((size_t)Ev, sizeof(T)) + gsx::round16((size_t)s * NMp, sizeof(T)) +
-                   gsx::round16((size_t)(s / 2) * Jv, sizeof(T)) +
-                   gsx::round16((size_t)2 * (s / 2) * Jv, sizeof(T));
-  return e * sizeof(T);
+  if (pend) update_moments(last, (int)((kc - 1) & 1), false);
 }
 
 template <class T, int DIM, int A>
-cudaError_t rows_launch(const RowsArgs<T>& a, int nblocks, size_t smem, cudaStream_t st) {
+cudaError_t rows_launch(const RowsArgs<T>& a, int nblocks, int threads, size_t smem,
+                        cudaStream_t st) {
   auto kern = coarse_gs_rows_kernel<T, DIM, A>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(kRowsThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(threads), args, smem, st);
 }
 
 template <class T, int DIM, int A>
-int rows_max_blocks(size_t smem) {
+int rows_max_blocks(int threads, size_t smem) {
   auto kern = coarse_gs_rows_kernel<T, DIM, A>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
@@ -464,7 +546,7 @@ int rows_max_blocks(size_t smem) {
     return 0;
   }
   int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowsThreads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -477,24 +559,29 @@ int rows_max_blocks(size_t smem) {
 }  // namespace
 
 template <class T>
-int coarse_gs_rows_plan(const Geom& g, int nmat, int Emax, int Jmax, int nmom, int* nmat_s,
-                        size_t* smem) {
-  const int vw = 16 / (int)sizeof(T);
-  const int Jv = ((Jmax + vw - 1) / vw) * vw, Ev = g.s * Jv;
+int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
+                        int* threads, size_t* smem) {
   if (g.a != 1 && g.a != 3) return 0;
-  if (Ev > kRowsMaxU * kRowsThreads || g.s * nmom > kRowsMaxM * kRowsThreads ||
-      (g.dim - 1) * (g.s / 2) * Jmax > kRowsThreads || g.nx < 1)
+  const int S = g.s;
+  // four lanes per padded unknown and per moment, within one block
+  const RowsLayout<T> l0(0, Jmax, nmom, S, g.dim, g.a, ndir);
+  int nt = 4 * std::max(l0.Ev, S * nmom);
+  nt = std::max(128, std::min(kRowsMaxThreads, (nt + 31) / 32 * 32));
+  if (l0.Ev > kRowsMaxU * nt || S * nmom > kRowsMaxM * nt || (g.dim - 1) * (S / 2) * Jmax > nt ||
+      g.nx < 1)
     return 0;
   int ns = nmat;
-  while (ns > 0 && rows_smem_bytes<T>(ns, Emax, Jmax, nmom, g.s) > 200 * 1024) --ns;
-  const size_t bytes = rows_smem_bytes<T>(ns, Emax, Jmax, nmom, g.s);
+  while (ns > 0 && RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir).bytes > 200 * 1024) --ns;
+  const size_t bytes = RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir).bytes;
   if (bytes > 200 * 1024) return 0;
   int nb;
-  if (g.dim == 2) nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(bytes) : rows_max_blocks<T, 2, 1>(bytes);
-  else nb = g.a == 3 ? rows_max_blocks<T, 3, 3>(bytes) : rows_max_blocks<T, 3, 1>(bytes);
-  const int nrows = g.ny * g.nz;
-  nb = std::min(nb, nrows);
+  if (g.dim == 2)
+    nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(nt, bytes) : rows_max_blocks<T, 2, 1>(nt, bytes);
+  else
+    nb = g.a == 3 ? rows_max_blocks<T, 3, 3>(nt, bytes) : rows_max_blocks<T, 3, 1>(nt, bytes);
+  nb = std::min(nb, g.ny * g.nz);
   *nmat_s = ns;
+  *threads = nt;
   *smem = bytes;
   return nb;
 }
@@ -503,14 +590,18 @@ template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
                           T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, size_t smem, const int* rows, int nblocks,
-                          int rpb, unsigned long long* faces, unsigned tag0, int* err,
-                          cudaStream_t st) {
+                          int nmat, int nmat_s, int threads, size_t smem, const int* rows,
+                          int nblocks, int rpb, unsigned long long* faces, unsigned tag0,
+                          int* err, cudaStream_t st) {
   RowsArgs<T> a{g, t, cd, ndir, dir_begin, dir_end, sweeps, f, phi, mom, TinvT, SLD,
                 Emax, Jmax, nmat, nmat_s, rows, rpb, faces, tag0, err};
   cudaError_t e;
-  if (g.dim == 2) e = g.a == 3 ? rows_launch<T, 2, 3>(a, nblocks, smem, st) : rows_launch<T, 2, 1>(a, nblocks, smem, st);
-  else e = g.a == 3 ? rows_launch<T, 3, 3>(a, nblocks, smem, st) : rows_launch<T, 3, 1>(a, nblocks, smem, st);
+  if (g.dim == 2)
+    e = g.a == 3 ? rows_launch<T, 2, 3>(a, nblocks, threads, smem, st)
+                 : rows_launch<T, 2, 1>(a, nblocks, threads, smem, st);
+  else
+    e = g.a == 3 ? rows_launch<T, 3, 3>(a, nblocks, threads, smem, st)
+                 : rows_launch<T, 3, 1>(a, nblocks, threads, smem, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -519,17 +610,17 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
   return 0;
 }
 
-template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, int*, size_t*);
-template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, int*, size_t*);
+template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, int*, int*, size_t*);
+template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, int*, int*, size_t*);
 template int launch_coarse_gs_rows<float>(const Geom&, const LevelDev<float>&, const CellData&, int,
                                           const int*, const int*, int, const float*, float*,
                                           float*, const float*, const float*, int, int, int, int,
-                                          size_t, const int*, int, int, unsigned long long*,
+                                          int, size_t, const int*, int, int, unsigned long long*,
                                           unsigned, int*, cudaStream_t);
 template int launch_coarse_gs_rows<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                            int, const int*, const int*, int, const double*,
                                            double*, double*, const double*, const double*, int,
-                                           int, int, int, size_t, const int*, int, int,
+                                           int, int, int, int, size_t, const int*, int, int,
                                            unsigned long long*, unsigned, int*, cudaStream_t);
 
 }  // namespace amgt

@@ -6,14 +6,16 @@
 // The per-cell factor sigma_s N (a mixing of the s rows of one cell) commutes
 // with the right-multiplication by the angular matrix S, so it is applied in
 // the FP32 -> BF16 operand pass (`tc_prep_kernel`) and the GEMM epilogue only
-// adds.  GEMM: one 128 x 256 output tile per CTA, K in steps of 64; A = X
-// (row-major, K-major) and B = S^T = S (symmetric, K-major) are loaded by TMA
-// with the 128-byte swizzle into a 4-stage shared-memory ring guarded by
-// mbarriers; one thread issues tcgen05.mma (M=128, N=256, K=16, BF16 inputs,
-// FP32 accumulation in tensor memory); all four warps read the accumulator
-// back with tcgen05.ld.  Every wait is bounded: after 2 s the kernel records
-// an error code, lets its in-flight copies and MMAs finish (bounded again),
-// releases its tensor memory and returns.
+// adds.  GEMM: a persistent kernel, one CTA per SM walking the 128 x 256
+// output tiles; A = X (row-major, K-major) and B = S^T = S (symmetric,
+// K-major) are loaded by TMA with the 128-byte swizzle into a 4-stage
+// shared-memory ring guarded by mbarriers; one thread issues tcgen05.mma
+// (M=128, N=256, K=16, BF16 inputs, FP32 accumulation) into one of two
+// 256-column tensor-memory accumulators, so that eight epilogue warps drain
+// tile i (tcgen05.ld, FP32 stores) while the MMAs of tile i+1 run.  Every
+// wait is bounded: after 2 s the kernel records an error code, lets its
+// in-flight copies and MMAs finish (bounded again), releases its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,7 +32,9 @@ constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int EPI_WARPS = 8;                      // two per accumulator lane quarter
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epilogue
+constexpr uint32_t TMEM_COLS = 2 * BN;            // two accumulators
 constexpr unsigned long long kWaitNs = 2000000000ULL;
 constexpr size_t kSmemBytes = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 
@@ -138,21 +142,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                          const __grid_constant__ CUtensorMap tmB,
-                                                          TcArgs args) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// one accumulator chunk (32 columns of this thread's row) to global memory
+__device__ __forceinline__ void store_chunk(float* out, const float* ad, const float4 (&a4)[8],
+                                            const uint32_t (&v)[32], float beta, bool vec,
+                                            int ncols) {
+  if (vec) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      float4 o = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                             __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+      if (beta != 0.0f) {
+        const float4 b = *reinterpret_cast<const float4*>(out + j);
+        o.x += beta * b.x;
+        o.y += beta * b.y;
+        o.z += beta * b.z;
+        o.w += beta * b.w;
+      }
+      if (ad) {
+        o.x += a4[j / 4].x;
+        o.y += a4[j / 4].y;
+        o.z += a4[j / 4].z;
+        o.w += a4[j / 4].w;
+      }
+      __stcs(reinterpret_cast<float4*>(out + j), o);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {  // static register indices
+      if (j < ncols) {
+        float o = __uint_as_float(v[j]);
+        if (beta != 0.0f) o += beta * out[j];
+        if (ad) o += ad[j];
+        out[j] = o;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                 const __grid_constant__ CUtensorMap tmB,
+                                                                 TcArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* accf = empty + STAGES;  // [2] accumulator ready (MMA -> epilogue)
+  uint64_t* acce = accf + 2;        // [2] accumulator drained (epilogue -> MMA)
+  uint64_t* done = acce + 2;        // every issued MMA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = (args.N + BN - 1) / BN;
-  const int tile_n = blockIdx.x % n_tiles, tile_m = blockIdx.x / n_tiles;
-  const int m0 = tile_m * BM, n0 = tile_n * BN;
+  const int m_tiles = (args.M + BM - 1) / BM;
+  const int total = n_tiles * m_tiles;
   const int kiters = (args.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
@@ -160,7 +207,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], EPI_WARPS);
+    }
+    mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -177,103 +228,129 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // TMA producer
-    int issued = 0;
-    for (int k = 0; k < kiters; ++k) {
-      const int s = k % STAGES;
-      const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
-        *abort_flag = 1;
-        atomicExch(args.err, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: the ring runs continuously across this CTA's tiles
+      int g = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        for (int k = 0; k < kiters; ++k, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+            *abort_flag = 1;
+            atomicExch(args.err, 1);
+            break;
+          }
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(sa, &tmA, &full[s], k * BK, m0);
+          tma_load_2d(sa + A_BYTES, &tmB, &full[s], k * BK, n0);
+        }
       }
-      uint8_t* sa = smem + s * STAGE_BYTES;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(sa, &tmA, &full[s], k * BK, m0);
-      tma_load_2d(sa + A_BYTES, &tmB, &full[s], k * BK, n0);
-      issued = k + 1;
-    }
-    if (*abort_flag) {
-      // let the copies already issued land before the CTA exits
-      for (int k = issued > STAGES ? issued - STAGES : 0; k < issued; ++k) {
-        volatile int never = 0;
-        mbar_wait(&full[k % STAGES], (uint32_t)(k / STAGES) & 1u, &never);
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA exits
+        for (int k = g > STAGES ? g - STAGES : 0; k < g; ++k) {
+          volatile int never = 0;
+          mbar_wait(&full[k % STAGES], (uint32_t)(k / STAGES) & 1u, &never);
+        }
       }
     }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    for (int k = 0; k < kiters; ++k) {
-      const int s = k % STAGES;
-      const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph, abort_flag)) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      int g = 0, i = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t use = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(&acce[buf], use ^ 1u, abort_flag)) {
+          *abort_flag = 1;
+          atomicExch(args.err, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int k = 0; k < kiters; ++k, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            *abort_flag = 1;
+            atomicExch(args.err, 2);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+          const uint64_t adesc = sw128_desc(sa);
+          const uint64_t bdesc = sw128_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_bf16(dt, adesc + 2ull * kk, bdesc + 2ull * kk, (k | kk) != 0 ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&accf[buf]);
+      }
+      // completion of every MMA issued above (also on abort)
+      umma_commit(done);
+      volatile int never = 0;
+      if (!mbar_wait(done, 0, &never)) atomicExch(args.err, 2);
+    }
+  } else {
+    // epilogue: warp w reads accumulator lanes 32 (w % 4) .. +31 (its rows) and
+    // one half of the columns
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const bool vec = (args.N & 3) == 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+      const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      const int buf = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1) & 1u;
+      bool ok = mbar_wait(&accf[buf], use, abort_flag);
+      ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // tcgen05.ld is warp-collective
+      if (!ok) {
         *abort_flag = 1;
-        atomicExch(args.err, 2);
+        atomicExch(args.err, 3);
         break;
       }
       tc_fence_after();
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      const uint64_t adesc = sw128_desc(sa);
-      const uint64_t bdesc = sw128_desc(sa + A_BYTES);
+      const int row = m0 + q * 32 + lane;
+      const bool rowok = row < args.M;
+      const int cbase = n0 + h * (BN / 2);
+      const float* adrow = args.add ? args.add + (long long)row * args.N : nullptr;
+      // add for chunk c+1 is loaded while chunk c is stored (two register sets)
+      float4 aA[8], aB[8];
+      auto load_add = [&](int c, float4(&dst)[8]) {
+        const int col0 = cbase + c * 32;
+        if (adrow && rowok && vec && col0 + 32 <= args.N) {
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        umma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, (k | kk) != 0 ? 1u : 0u);
-      umma_commit(&empty[s]);
-    }
-    // completion of every MMA issued above (also on abort) is signalled here
-    umma_commit(accf);
-  }
-  __syncwarp();
-  // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
-  bool ok;
-  {
-    volatile int never = 0;
-    ok = mbar_wait(accf, 0, &never);
-  }
-  // keep the epilogue warp-uniform (tcgen05.ld is a warp-collective instruction)
-  ok = __all_sync(0xffffffffu, ok && !*abort_flag);
-  if (!ok) atomicExch(args.err, 3);
-  if (ok) {
-    tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    for (int c = 0; c < BN / 32; ++c) {
-      const int col0 = n0 + c * 32;
-      if (col0 >= args.N) break;
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      if (row < args.M) {
-        float* out = args.C + (long long)row * args.N + col0;
-        const float* ad = args.add ? args.add + (long long)row * args.N + col0 : nullptr;
-        if (col0 + 32 <= args.N && (args.N & 3) == 0) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 o = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                   __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-            if (args.beta != 0.0f) {
-              const float4 b = *reinterpret_cast<const float4*>(out + j);
-              o.x += args.beta * b.x;
-              o.y += args.beta * b.y;
-              o.z += args.beta * b.z;
-              o.w += args.beta * b.w;
-            }
-            if (ad) {
-              const float4 a4 = *reinterpret_cast<const float4*>(ad + j);
-              o.x += a4.x;
-              o.y += a4.y;
-              o.z += a4.z;
-              o.w += a4.w;
-            }
-            *reinterpret_cast<float4*>(out + j) = o;
-          }
-        } else {
-          for (int j = 0; j < 32 && col0 + j < args.N; ++j) {
-            float o = __uint_as_float(v[j]);
-            if (args.beta != 0.0f) o += args.beta * out[j];
-            if (ad) o += ad[j];
-            out[j] = o;
-          }
+          for (int j = 0; j < 8; ++j)
+            dst[j] = __ldcs(reinterpret_cast<const float4*>(adrow + col0) + j);
         }
-      }
+      };
+      auto drain = [&](int c, const float4(&cur)[8]) {
+        const int col0 = cbase + c * 32;
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * (BN / 2) + c * 32), v);
+        if (rowok && col0 < args.N) {
+          const int ncols = min(32, args.N - col0);
+          store_chunk(args.C + (long long)row * args.N + col0, adrow ? adrow + col0 : nullptr, cur,
+                      v, args.beta, vec && ncols == 32, ncols);
+        }
+      };
+      static_assert(BN / 64 == 4, "four 32-column chunks per epilogue warp");
+      load_add(0, aA);
+      load_add(1, aB);
+      drain(0, aA);
+      load_add(2, aA);
+      drain(1, aB);
+      load_add(3, aB);
+      drain(2, aA);
+      drain(3, aB);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
     }
   }
   tc_fence_before();
@@ -370,9 +447,17 @@ int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
     attr_set = true;
   }
   TcArgs args{M, N, K, C, add, beta, err};
-  const int grid = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  const int grid = tiles < nsm ? tiles : nsm;
   note_launch();
-  tc_gemm_kernel<<<grid, 128, kSmemBytes, st>>>(ta, tb, args);
+  tc_gemm_kernel<<<grid, TC_THREADS, kSmemBytes, st>>>(ta, tb, args);
   return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 

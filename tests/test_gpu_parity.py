@@ -375,3 +375,28 @@ def test_row_pipelined_gs_3d_several_rows_per_block():
         ctx.amgt_sync()
         assert _rel(_host(xd), multigrid.coarse_gs(T, f, x0, 2)) < tol
     ctx.close()
+
+
+def test_kernel_timers_count_launches():
+    """The library's per-kernel event timers: off by default (nothing
+    recorded), on: one timed launch per operator call with positive time."""
+    import paper_2010_04559_gb300 as pkg
+    prob = W.random_problem(2, (12, 10), 2, 8, 91)
+    ctx = _ctx(prob)
+    ns, na = ctx.amgt_query_sizes(0)
+    x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    ctx.amgt_op_sweep(0, x, y)
+    assert ctx.amgt_query_kernel_time(pkg.AMGT_KT_SWEEP) == (0.0, 0)
+    ctx.amgt_set_tuning(pkg.AMGT_TUNE_KERNEL_TIMERS, 1)
+    for _ in range(3):
+        ctx.amgt_op_sweep(0, x, y)
+    ctx.amgt_op_apply_L(0, x, y)
+    ms, n = ctx.amgt_query_kernel_time(pkg.AMGT_KT_SWEEP, reset=True)
+    assert n == 3 and ms > 0
+    assert ctx.amgt_query_kernel_time(pkg.AMGT_KT_APPLY_L)[1] == 1
+    assert ctx.amgt_query_kernel_time(pkg.AMGT_KT_SWEEP) == (0.0, 0)
+    ctx.amgt_set_tuning(pkg.AMGT_TUNE_KERNEL_TIMERS, 0)
+    ctx.amgt_op_sweep(0, x, y)
+    assert ctx.amgt_query_kernel_time(pkg.AMGT_KT_SWEEP)[1] == 0
+    ctx.close()
