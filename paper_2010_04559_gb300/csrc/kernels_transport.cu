@@ -9,6 +9,8 @@
 // and an inflow face f couples to the upwind neighbour through
 // kron(Fnb_f, A_{f,q}) with A_{f,q} = n_xi A^xi_q.  Fnb_f only links the face
 // nodes of the two cells, with the Q1 face mass `facemass[xi]`.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace amgt {
@@ -144,7 +146,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <class T, int A, int NST>
+template <class T, int A, int NST, int UMAX>
 __global__ void __launch_bounds__(512) sweep2d_rows_kernel(Geom g, LevelDev<T> t, CellData cd,
                                                             Schedule sc, const T* __restrict__ b,
                                                             T* __restrict__ psi, int G, int nmat_s,
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(512) sweep2d_rows_kernel(Geom g, LevelDev<T> t
   // This thread's staging copies are the same (row, node, chunk) triples at
   // every level; only the cell column jx = w - row moves, so the source
   // address is linear in w.
-  constexpr int UMAX = 12;  // per_level / blockDim <= 4*A*sizeof(T)/chunk <= 12
+  // UMAX: copy slots per thread and level, ceil(per_level / blockDim), <= 12
   int crow[UMAX];
   long long csrc[UMAX];
   int cdst[UMAX];
@@ -621,17 +623,24 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<sc.ntask, threads, smem, st>>>(g, t, cd, sc, b, psi, G, nmat_s, chunk);
       };
-      if (g.a == 3) {
-        if (NST == 2) launch(sweep2d_rows_kernel<T, 3, 2>);
-        else if (NST == 3) launch(sweep2d_rows_kernel<T, 3, 3>);
-        else if (NST == 4) launch(sweep2d_rows_kernel<T, 3, 4>);
-        else launch(sweep2d_rows_kernel<T, 3, 6>);
-      } else {
-        if (NST == 2) launch(sweep2d_rows_kernel<T, 1, 2>);
-        else if (NST == 3) launch(sweep2d_rows_kernel<T, 1, 3>);
-        else if (NST == 4) launch(sweep2d_rows_kernel<T, 1, 4>);
-        else launch(sweep2d_rows_kernel<T, 1, 6>);
-      }
+      // copy slots per thread: exactly the chunks one level needs
+      const int per_level = g.ny * 4 * seg_chunks;
+      const int need = (per_level + threads - 1) / threads;
+      auto pick = [&](auto a_tag) {
+        constexpr int AA = decltype(a_tag)::value;
+        auto by_u = [&](auto nst_tag) {
+          constexpr int NS = decltype(nst_tag)::value;
+          if (need <= 3) launch(sweep2d_rows_kernel<T, AA, NS, 3>);
+          else if (need <= 6) launch(sweep2d_rows_kernel<T, AA, NS, 6>);
+          else launch(sweep2d_rows_kernel<T, AA, NS, 12>);
+        };
+        if (NST == 2) by_u(std::integral_constant<int, 2>());
+        else if (NST == 3) by_u(std::integral_constant<int, 3>());
+        else if (NST == 4) by_u(std::integral_constant<int, 4>());
+        else by_u(std::integral_constant<int, 6>());
+      };
+      if (g.a == 3) pick(std::integral_constant<int, 3>());
+      else pick(std::integral_constant<int, 1>());
       return;
     }
   }
