@@ -51,7 +51,8 @@ KERNEL_NAMES = {
 # summarised under profiles/; a kernel changed since its capture has no entry
 TRAFFIC = {
     "coarse_gs": 279.5e6,   # profiles/ncu_coarse_gs_rows_config2.md
-    "sweep": 1029.1e6,      # profiles/ncu_top_kernels_config2.md
+    "sweep": 955.5e6,       # profiles/ncu_top_kernels_config2.md
+    "scatter_tc": 554.3e6,  # profiles/ncu_top_kernels_config2.md
 }
 NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
@@ -198,8 +199,10 @@ def run_profile(args):
         ctx.amgt_op_sweep(0, x, y)
         ctx.amgt_op_scatter(0, x, y, tc=True)
         ctx.amgt_op_coarse_gs(1, fc, pc)
+        x64 = x.double()
+        ctx.amgt_op_scatter(0, x64, torch.empty_like(x64))
         ctx.amgt_sync()
-        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep)")
+        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep), FP64 scatter")
     torch.cuda.synchronize()
     ctx.close()
     return 0
@@ -399,7 +402,7 @@ def main():
         bound, w, peak, unit, alg = work[name]
         rl[name] = {"kernel": KERNEL_NAMES[name], "bound": bound, "achieved": w / per_launch,
                     "peak": peak, "unit": unit, "frac": w / per_launch / peak,
-                    "launch_s": per_launch, "algorithmic": alg}
+                    "launch_s": per_launch, "traffic": TRAFFIC.get(name), "algorithmic": alg}
     # in-solve device time per kernel class (timed region, library events)
     solve_k = {}
     for name, (msum, n) in kt_solve.items():
