@@ -250,6 +250,34 @@ int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi);
 /* phi_s[Nsdof] = sum_{q,d} psi int Psi_[q]d (zeroth flux moment, Sec. 4.2). */
 int amgt_op_scalar_flux(amgt_ctx* ctx, int level, int dtype, const void* psi, void* phi);
 
+/* ---- adjoint and detector-response gradients ------------------------------ */
+/* adjoint = 1: every operator, sweep, cycle and solve of this context acts
+ * with the transposed operator A^T = L^T - S instead of A.  On these meshes
+ * L^T is the same DG operator with every direction reversed (Omega -> -Omega
+ * in the streaming terms, upwind sides flipped; Q1 integration by parts and
+ * symmetric face and angular mass matrices), and S is symmetric, so the
+ * context rebuilds its tables with reversed directions.  With the source of
+ * an isotropic emission 4 pi * w[c] (amgt_set_source_iso) and vacuum
+ * boundaries, amgt_solve then returns lambda = A^-T g for the response
+ * R = sum_c w[c] int_cell phi_s dV.  Returns AMGT_OK; rebuilds lazily. */
+int amgt_set_adjoint(amgt_ctx* ctx, int adjoint);
+/* R = g^T psi with g this context's source vector on the finest level (for
+ * a source 4 pi * w: the response above).  psi [Nsdof][Nadof] FP64, a device
+ * pointer if device != 0, else host memory; *R on the host. */
+int amgt_response(amgt_ctx* ctx, int device, const double* psi, double* R);
+/* Gradients of R = g^T psi, A psi = f, from psi and lambda = A^-T g (both
+ * [Nsdof][Nadof] FP64 of the finest level; device pointers if device != 0,
+ * else host), with A = L - S of this context's problem (Eq. complete,
+ * Sec. 4.2):
+ *   dsigma_t[c] = -sum_q lambda_cq^T (N (x) M_q) psi_cq          [C]
+ *   dsigma_s[c] =  lambda_c^T (N (x) S_f) psi_c                   [C]
+ *   dfmom[n]    =  sum_c sigma_s[c] lambda_c^T (N (x) X_n X_n^T) psi_c   [N+1]
+ * (S_f = X diag(f_n) X^T, X_n the degree-n harmonics moments; sigma_s[c] the
+ * cell's n = 0 scatter cross section).  Outputs in the same memory space as
+ * the inputs; the call returns after they are written. */
+int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const double* lambda,
+                            double* dsigma_t, double* dsigma_s, double* dfmom);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,7 @@ EXPORTS = [
     "amgt_op_restrict", "amgt_op_prolong", "amgt_op_smooth", "amgt_op_coarse_gs",
     "amgt_op_coarse_gs_noalloc",
     "amgt_op_vcycle", "amgt_op_scalar_flux",
+    "amgt_set_adjoint", "amgt_response", "amgt_response_gradients",
 ]
 
 
@@ -109,6 +110,9 @@ _SIGS = {
     "amgt_op_coarse_gs_noalloc": ([_P, _I, _I, _P, _P], _I),
     "amgt_op_vcycle": ([_P, _I, _P, _P], _I),
     "amgt_op_scalar_flux": ([_P, _I, _I, _P, _P], _I),
+    "amgt_set_adjoint": ([_P, _I], _I),
+    "amgt_response": ([_P, _I, _P, _PD], _I),
+    "amgt_response_gradients": ([_P, _I, _P, _P, _P, _P, _P], _I),
 }
 
 
@@ -352,6 +356,36 @@ class Context:
         self._req(psi, phi)
         return self._check(self.lib.amgt_op_scalar_flux(self.h, level, self._dtype_code(psi),
                                                         _dptr(psi), _dptr(phi)))
+
+    # ---- adjoint and gradients
+    def amgt_set_adjoint(self, on):
+        return self._check(self.lib.amgt_set_adjoint(self.h, 1 if on else 0))
+
+    @staticmethod
+    def _mem(x):
+        """(device flag, pointer) of a torch CUDA float64 tensor or a NumPy
+        float64 array."""
+        if isinstance(x, np.ndarray):
+            assert x.dtype == np.float64 and x.flags.c_contiguous
+            return 0, ctypes.c_void_p(x.ctypes.data)
+        assert x.dtype.__str__() == "torch.float64" and x.is_contiguous()
+        return 1, _dptr(x)
+
+    def amgt_response(self, psi):
+        dev, p = self._mem(psi)
+        R = ctypes.c_double(0.0)
+        self._check(self.lib.amgt_response(self.h, dev, p, ctypes.byref(R)))
+        return R.value
+
+    def amgt_response_gradients(self, psi, lam, dsigt, dsigs, dfmom):
+        """Fill dsigt [C], dsigs [C], dfmom [N+1] (same memory space as psi)."""
+        dev, p = self._mem(psi)
+        dev2, l = self._mem(lam)
+        assert dev == dev2
+        outs = [self._mem(a) for a in (dsigt, dsigs, dfmom)]
+        assert all(o[0] == dev for o in outs)
+        return self._check(self.lib.amgt_response_gradients(self.h, dev, p, l, outs[0][1],
+                                                            outs[1][1], outs[2][1]))
 
 
 def context_from_problem(prob, device=0, stream=None, aniso=None):

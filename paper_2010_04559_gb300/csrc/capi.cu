@@ -404,6 +404,13 @@ int build(amgt_ctx* ctx) {
   for (int k = 0; k < nl; ++k) {
     Level& Lv = ctx->lv[k];
     Lv.mesh = build_mesh(coarsen_paths(ctx->paths, L - k), ctx->basis);
+    if (ctx->adjoint) {
+      // A^T = the same operator with every direction reversed (Omega -> -Omega
+      // in the streaming terms, upwind sides flipped); S is symmetric
+      for (double& v : Lv.mesh.A) v = -v;
+      for (double& v : Lv.mesh.Aw) v = -v;
+      for (auto& pt : Lv.mesh.patch) pt.octant ^= 7;
+    }
     Lv.nsdof = g.nsdof;
     const int P = Lv.mesh.P;
     const int nadof = Lv.mesh.nadof();
@@ -1251,6 +1258,94 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
   ctx->bkind[face] = kind;
   ctx->bval[face] = kind == 1 ? params[0] : 0.0;
   ctx->dirty = true;
+  return AMGT_OK;
+}
+
+int amgt_set_adjoint(amgt_ctx* ctx, int adjoint) {
+  if (!ctx) return AMGT_ERR_ARG;
+  if (adjoint != 0 && adjoint != 1) return fail(ctx, AMGT_ERR_ARG, "adjoint 0 or 1");
+  if ((adjoint == 1) != ctx->adjoint) ctx->dirty = true;
+  ctx->adjoint = adjoint == 1;
+  return AMGT_OK;
+}
+
+int amgt_response(amgt_ctx* ctx, int device, const double* psi, double* R) {
+  if (!ctx || !psi || !R) return AMGT_ERR_ARG;
+  TRY(build(ctx));
+  const Level& L0 = ctx->lv[0];
+  const long long n = L0.nsdof * L0.nadof();
+  double *g, *x;
+  TRY(wsvec<double>(ctx, 0, 7, &g));
+  TRY(source_impl<double>(ctx, 0, g));
+  if (device) {
+    x = const_cast<double*>(psi);
+  } else {
+    TRY(wsvec<double>(ctx, 0, 5, &x));
+    CK(cudaMemcpyAsync(x, psi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  const int nblk = gemv_blocks(n);
+  void** slot = ctx->d_ptrs + 200;
+  const double* gp = g;
+  CK(cudaMemcpyAsync(slot, &gp, sizeof(void*), cudaMemcpyHostToDevice, ctx->stream));
+  launch_multidot<double>(n, 1, reinterpret_cast<const double* const*>(slot), x, ctx->d_partials,
+                          nblk, ctx->d_dots, ctx->stream);
+  CK(cudaGetLastError());
+  TRY(dev_dots<double>(ctx, 1, R));
+  return AMGT_OK;
+}
+
+int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const double* lambda,
+                            double* dsigma_t, double* dsigma_s, double* dfmom) {
+  if (!ctx || !psi || !lambda || !dsigma_t || !dsigma_s || !dfmom) return AMGT_ERR_ARG;
+  TRY(build(ctx));
+  const Level& L0 = ctx->lv[0];
+  const long long n = L0.nsdof * L0.nadof();
+  const int C = ctx->geom.C, nm = L0.nmom, N = L0.Nr;
+  if ((int)ctx->fmom.size() < N + 1) return fail(ctx, AMGT_ERR_STATE, "Legendre moments not set");
+  const double *p, *l;
+  if (device) {
+    p = psi;
+    l = lambda;
+  } else {
+    double *pp, *ll;
+    TRY(wsvec<double>(ctx, 0, 5, &pp));
+    TRY(wsvec<double>(ctx, 0, 6, &ll));
+    CK(cudaMemcpyAsync(pp, psi, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ll, lambda, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream));
+    p = pp;
+    l = ll;
+  }
+  // scratch: both moment sets, the outputs, f_n
+  const size_t need = ((size_t)2 * L0.nsdof * nm + 2 * (size_t)C + 2 * (size_t)(N + 1)) * 8;
+  if (ctx->grad_bytes < need) {
+    double* q;
+    TRY(dalloc<double>(ctx, need / 8, &q));
+    ctx->d_grad = q;
+    ctx->grad_bytes = need;
+  }
+  double* PhiP = ctx->d_grad;
+  double* PhiL = PhiP + (size_t)L0.nsdof * nm;
+  double* dt = PhiL + (size_t)L0.nsdof * nm;
+  double* ds = dt + C;
+  double* df = ds + C;
+  double* fm = df + (N + 1);
+  CK(cudaMemcpyAsync(fm, ctx->fmom.data(), (size_t)(N + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(df, 0, (size_t)(N + 1) * 8, ctx->stream));
+  GemmEpi e0{};
+  e0.mode = 0;
+  launch_gemm<double>((int)L0.nsdof, nm, L0.nadof(), p, L0.nadof(), L0.d64.X, nm, PhiP, nm, e0,
+                      ctx->stream);
+  launch_gemm<double>((int)L0.nsdof, nm, L0.nadof(), l, L0.nadof(), L0.d64.X, nm, PhiL, nm, e0,
+                      ctx->stream);
+  const Geom g = level_geom(ctx, 0);
+  launch_grad_sigma_t(g, L0.d64.Mang, p, l, dt, ctx->stream);
+  launch_grad_moments(g, nm, N, PhiP, PhiL, fm, ctx->d_sigs, ds, df, ctx->stream);
+  CK(cudaGetLastError());
+  const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(dsigma_t, dt, (size_t)C * 8, kind, ctx->stream));
+  CK(cudaMemcpyAsync(dsigma_s, ds, (size_t)C * 8, kind, ctx->stream));
+  CK(cudaMemcpyAsync(dfmom, df, (size_t)(N + 1) * 8, kind, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return AMGT_OK;
 }
 

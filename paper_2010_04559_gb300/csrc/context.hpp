@@ -118,6 +118,9 @@ struct amgt_ctx {
   size_t bf16_bytes = 0;
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
+  bool adjoint = false;  // amgt_set_adjoint: operators of the transposed problem
+  double* d_grad = nullptr;  // gradient scratch (moments, outputs)
+  size_t grad_bytes = 0;
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
   unsigned gs_tag = 0;  // sweeps run by the row-pipelined Gauss-Seidel (face-word tags)
   int gs_grid_blocks = 0;  // AMGT_TUNE_GS_GRID_BLOCKS

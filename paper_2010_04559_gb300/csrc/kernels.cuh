@@ -140,6 +140,16 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
                           int nblocks, int rpb, unsigned long long* faces, unsigned tag0,
                           int* err, cudaStream_t st);
 
+// detector-response gradients (kernels_adjoint.cu), FP64:
+// dsigt[c] = -sum_q lam_cq^T kron(N, M_q) psi_cq;
+// dsigs[c] = sum_k f_deg(k) (PhiL_c^T N PhiP_c)_kk, dfn[n] += sigma_s[c] * the degree-n part
+// (dfn must be zeroed first)
+void launch_grad_sigma_t(const Geom& g, const double* Mang, const double* psi, const double* lam,
+                         double* dsigt, cudaStream_t st);
+void launch_grad_moments(const Geom& g, int nmom, int N, const double* PhiP, const double* PhiL,
+                         const double* fmom, const double* sig_s, double* dsigs, double* dfn,
+                         cudaStream_t st);
+
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();
 cudaError_t noalloc_moment_address(int device, void** out);
