@@ -217,6 +217,7 @@ def main():
     ap.add_argument("--n", type=int, default=128, help="cells per axis")
     ap.add_argument("--fp64-ref", action="store_true", help="also time one FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="tolerance of each inner FP32 solve (0: adaptive)")
     ap.add_argument("--profile", choices=["solve", "kernels"], default=None,
@@ -424,6 +425,47 @@ def main():
                 "unit": None, "frac": None, "traffic": None,
                 "share_of_solve": solve_k[dom_name]["share"]}
 
+    # ---- adjoint: lambda = A^-T g for the flux integral over a 16x16-cell
+    # corner block, then the response and its gradients (mixed solve to 1e-8)
+    adj = None
+    if not args.no_adjoint:
+        from paper_2010_04559_gb300.adjoint import response_problem
+        nx = args.n
+        weight = np.zeros(nx * nx)
+        for iy in range(16):
+            weight[iy * nx:iy * nx + 16] = 1.0
+        actx = context_from_problem(response_problem(prob, weight), device=local,
+                                    stream=stream.cuda_stream)
+        actx.amgt_set_adjoint(1)
+        lam = torch.empty_like(psi)
+        C = nx * nx
+        dt = torch.empty(C, device="cuda", dtype=torch.float64)
+        ds = torch.empty_like(dt)
+        df = torch.empty(prob["N"] + 1, device="cuda", dtype=torch.float64)
+
+        def adjoint_step():
+            _, _, sta, _ = actx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
+                                           mode=AMGT_MODE_MIXED, psi=lam, phi=phi,
+                                           device_ptrs=True, inner_tol=args.inner_tol)
+            R = actx.amgt_response(psi)
+            ctx.amgt_response_gradients(psi, lam, dt, ds, df)
+            return sta, R
+        solve()                     # psi of the forward problem
+        adjoint_step()              # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sta, R = adjoint_step()
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ctx.amgt_response_gradients(psi, lam, dt, ds, df)
+        t_grad = time.perf_counter() - t0
+        adj = {"workload": "flux integral over the 16x16-cell corner block; dR/dsigma_t, "
+                           "dR/dsigma_s per cell and dR/df_n (N=16)",
+               "adjoint_solve_and_gradients_s": t_adj, "gradients_s": t_grad,
+               "iterations": sta.iterations, "relres": sta.relres, "response": R}
+        actx.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -454,6 +496,8 @@ def main():
                 "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
         if fp64:
             line["fp64_gpu"] = fp64
+        if adj:
+            line["adjoint"] = adj
         print(json.dumps(line))
     ctx.close()
     if dist:

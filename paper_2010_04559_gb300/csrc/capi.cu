@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <stdexcept>
+#include <thread>
+#include <type_traits>
 #include <utility>
 
 #include "context.hpp"
@@ -55,12 +58,42 @@ int dalloc(amgt_ctx* ctx, size_t n, T** out) {
 template <class Tdev, class Thost>
 int upload(amgt_ctx* ctx, const std::vector<Thost>& h, Tdev** out) {
   TRY(dalloc<Tdev>(ctx, h.size(), out));
-  std::vector<Tdev> tmp(h.begin(), h.end());
-  CK(cudaMemcpy(*out, tmp.data(), tmp.size() * sizeof(Tdev), cudaMemcpyHostToDevice));
+  if constexpr (std::is_same<Thost, Tdev>::value) {
+    CK(cudaMemcpy(*out, h.data(), h.size() * sizeof(Tdev), cudaMemcpyHostToDevice));
+  } else {
+    // converted in chunks (tables of many materials reach tens of GB)
+    const size_t chunk = (size_t)1 << 24;
+    std::vector<Tdev> tmp(std::min(chunk, h.size()));
+    for (size_t b = 0; b < h.size(); b += chunk) {
+      const size_t n = std::min(chunk, h.size() - b);
+      for (size_t i = 0; i < n; ++i) tmp[i] = (Tdev)h[b + i];
+      CK(cudaMemcpy(*out + b, tmp.data(), n * sizeof(Tdev), cudaMemcpyHostToDevice));
+    }
+  }
   return AMGT_OK;
 }
 
 int nmoments(int N) { return (N + 1) * (N + 1); }
+
+// fn(i) for i in [0, n) on the host's cores (set-up tables: one block inverse
+// per (material, patch) -- millions when every cell has its own sigma_t)
+template <class F>
+void parallel_for(long long n, F fn) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 64) nt = 64;
+  if (n < 256 || nt == 1) {
+    for (long long i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::atomic<long long> next{0};
+  std::vector<std::thread> ts;
+  for (unsigned t = 0; t < nt; ++t)
+    ts.emplace_back([&] {
+      for (long long i; (i = next.fetch_add(1)) < n;) fn(i);
+    });
+  for (auto& t : ts) t.join();
+}
 
 // largest number of cells on one wavefront level i + j + k = const
 int max_wavefront_cells(const Geom& g) {
@@ -224,11 +257,10 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
     if (J % 2) Lv.gs_vec_ok &= ~2;
   }
   // the per-patch kernel handles larger directions and very many materials
-  if (Emax > 384 || (size_t)ctx->nmat * Lv.ndir * Emax * Emax * sizeof(double) > (256u << 20))
+  if (Emax > 384 || (size_t)ctx->nmat * Lv.ndir * Emax * Emax * sizeof(double) > ((size_t)8 << 30))
     return AMGT_OK;
   std::vector<double> SLD((size_t)Lv.ndir * Jmax * Jmax, 0.0);
   std::vector<double> TinvT((size_t)ctx->nmat * Lv.ndir * Emax * Emax, 0.0);
-  std::vector<double> T((size_t)Emax * Emax), Ti((size_t)Emax * Emax);
   for (int d = 0; d < Lv.ndir; ++d) {
     const int qb = Lv.dir_begin[d], J = (Lv.dir_end[d] - qb) * a, E = s * J;
     double* sl = &SLD[(size_t)d * Jmax * Jmax];
@@ -243,8 +275,10 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
         sl[j * Jmax + j2] = acc;
       }
     if (E == 0) continue;
-    for (int mt = 0; mt < ctx->nmat; ++mt) {
-      std::fill(T.begin(), T.begin() + (size_t)E * E, 0.0);
+    std::atomic<int> singular{0};
+    parallel_for(ctx->nmat, [&](long long mi) {
+      const int mt = (int)mi;
+      std::vector<double> T((size_t)E * E, 0.0), Ti((size_t)E * E);
       for (int l = 0; l < s; ++l)
         for (int j = 0; j < J; ++j) {
           const int e = l * J + j, q = j / a, m = j % a;
@@ -260,12 +294,15 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
               T[(size_t)e * E + e2] = v;
             }
         }
-      if (!invert(E, T.data(), Ti.data()))
-        return fail(ctx, AMGT_ERR_ARG, "singular direction-blocked Gauss-Seidel matrix");
+      if (!invert(E, T.data(), Ti.data())) {
+        singular = 1;
+        return;
+      }
       double* out = &TinvT[((size_t)mt * Lv.ndir + d) * Emax * Emax];
       for (int r = 0; r < E; ++r)
         for (int cc = 0; cc < E; ++cc) out[(size_t)cc * Emax + r] = Ti[(size_t)r * E + cc];
-    }
+    });
+    if (singular) return fail(ctx, AMGT_ERR_ARG, "singular direction-blocked Gauss-Seidel matrix");
   }
   TRY(upload(ctx, TinvT, &Lv.d64.TinvT));
   TRY(upload(ctx, TinvT, &Lv.d32.TinvT));
@@ -457,31 +494,33 @@ int build(amgt_ctx* ctx) {
       kron_add(s, a, q1.N.data(), &Lv.mesh.M[(size_t)q * a * a], 1.0, &B[(size_t)q * sa * sa]);
     }
     const size_t nblk = (size_t)ctx->nmat * P * sa * sa;
-    if (nblk * sizeof(double) > (size_t)2 << 30)
+    if (nblk * sizeof(double) > (size_t)48 << 30)
       return fail(ctx, AMGT_ERR_UNSUPPORTED,
                   "too many distinct (sigma_t, sigma_s) pairs for per-material block inverses");
     std::vector<double> Kinv(nblk), Ginv;
-    std::vector<double> blk(sa * sa);
-    for (int mt = 0; mt < ctx->nmat; ++mt)
-      for (int q = 0; q < P; ++q) {
-        for (int i = 0; i < sa * sa; ++i)
-          blk[i] = K0[(size_t)q * sa * sa + i] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + i];
-        if (!invert(sa, blk.data(), &Kinv[((size_t)mt * P + q) * sa * sa]))
-          return fail(ctx, AMGT_ERR_ARG, "singular transport block (sigma_t <= 0?)");
-      }
+    std::atomic<int> singular{0};
+    parallel_for((long long)ctx->nmat * P, [&](long long i) {
+      const int mt = (int)(i / P), q = (int)(i % P);
+      std::vector<double> blk(sa * sa);
+      for (int e = 0; e < sa * sa; ++e)
+        blk[e] = K0[(size_t)q * sa * sa + e] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + e];
+      if (!invert(sa, blk.data(), &Kinv[((size_t)mt * P + q) * sa * sa])) singular = 1;
+    });
+    if (singular) return fail(ctx, AMGT_ERR_ARG, "singular transport block (sigma_t <= 0?)");
     if (k == nl - 1) {
       Ginv.resize(nblk);
-      std::vector<double> NS(sa * sa);
-      for (int mt = 0; mt < ctx->nmat; ++mt)
-        for (int q = 0; q < P; ++q) {
-          std::fill(NS.begin(), NS.end(), 0.0);
-          kron_add(s, a, q1.N.data(), &Sqq[(size_t)q * a * a], 1.0, NS.data());
-          for (int i = 0; i < sa * sa; ++i)
-            blk[i] = K0[(size_t)q * sa * sa + i] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + i] -
-                     ctx->mat_ss[mt] * NS[i];
-          if (!invert(sa, blk.data(), &Ginv[((size_t)mt * P + q) * sa * sa]))
-            return fail(ctx, AMGT_ERR_ARG, "singular Gauss-Seidel block");
-        }
+      std::vector<double> NSq((size_t)P * sa * sa, 0.0);  // kron(N, S_qq) per patch
+      for (int q = 0; q < P; ++q)
+        kron_add(s, a, q1.N.data(), &Sqq[(size_t)q * a * a], 1.0, &NSq[(size_t)q * sa * sa]);
+      parallel_for((long long)ctx->nmat * P, [&](long long i) {
+        const int mt = (int)(i / P), q = (int)(i % P);
+        std::vector<double> blk(sa * sa);
+        for (int e = 0; e < sa * sa; ++e)
+          blk[e] = K0[(size_t)q * sa * sa + e] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + e] -
+                   ctx->mat_ss[mt] * NSq[(size_t)q * sa * sa + e];
+        if (!invert(sa, blk.data(), &Ginv[((size_t)mt * P + q) * sa * sa])) singular = 1;
+      });
+      if (singular) return fail(ctx, AMGT_ERR_ARG, "singular Gauss-Seidel block");
     }
     // directions and sweep tasks
     Lv.ndir = dim == 2 ? 4 : 8;
