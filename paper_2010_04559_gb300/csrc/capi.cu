@@ -394,21 +394,19 @@ int build(amgt_ctx* ctx) {
   for (int xi = 0; xi < dim; ++xi)
     for (int jp = 0; jp < hs; ++jp)
       for (int j = 0; j < hs; ++j) g.facemass[xi][jp][j] = q1.facemass[(xi * hs + jp) * hs + j];
-  for (int i = 0; i < s * s; ++i) g.Nmass[i] = q1.N[i];
-  set_mass_matrix(q1.N.data(), s);
-  {
-    // G_xi for a positive / negative Omega_xi (outflow through the high / low face)
-    std::vector<double> Gax(3 * 2 * 64, 0.0), Nsp(64, 0.0);
-    for (int xi = 0; xi < dim; ++xi)
-      for (int sg = 0; sg < 2; ++sg)
-        for (int i = 0; i < s * s; ++i) {
-          const double fo = sg == 0 ? q1.Fown[(size_t)(2 * xi + 1) * s * s + i]
-                                    : -q1.Fown[(size_t)(2 * xi) * s * s + i];
-          Gax[(xi * 2 + sg) * 64 + i] = fo - q1.V[(size_t)xi * s * s + i];
-        }
-    for (int i = 0; i < s * s; ++i) Nsp[i] = q1.N[i];
-    set_transport_constants(Gax.data(), Nsp.data());
+  for (int i = 0; i < s * s; ++i) {
+    g.Nmass[i] = q1.N[i];
+    g.NmassF[i] = (float)q1.N[i];
   }
+  // G_xi for a positive / negative Omega_xi (outflow through the high / low face)
+  for (int xi = 0; xi < dim; ++xi)
+    for (int sg = 0; sg < 2; ++sg)
+      for (int i = 0; i < s * s; ++i) {
+        const double fo = sg == 0 ? q1.Fown[(size_t)(2 * xi + 1) * s * s + i]
+                                  : -q1.Fown[(size_t)(2 * xi) * s * s + i];
+        g.Gax[xi][sg][i] = fo - q1.V[(size_t)xi * s * s + i];
+        g.GaxF[xi][sg][i] = (float)g.Gax[xi][sg][i];
+      }
   CK(cudaGetLastError());
   const int C = g.C;
   ctx->C = C;
@@ -717,6 +715,7 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
   epi.beta = beta;
   epi.add = add;
   epi.s = ctx->geom.s;
+  for (int i = 0; i < epi.s * epi.s; ++i) epi.Nm[i] = ctx->geom.Nmass[i];
   epi.sig = ctx->d_sigs;
   epi.sig32 = ctx->d_sigs32;
   // the tensor-core path needs K = Nadof >= 64 (one K step of the tile)

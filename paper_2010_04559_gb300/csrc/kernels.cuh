@@ -18,6 +18,11 @@ struct Geom {
   int nadof, P;
   double facemass[3][4][4];  // [axis][own face node][neighbour face node]
   double Nmass[64];          // spatial mass matrix N (s x s)
+  float NmassF[64];
+  // streaming matrices of the Kronecker form of L's diagonal block:
+  // G[axis][negative Omega component][s*s] (see kernels_transport.cu)
+  double Gax[3][2][64];
+  float GaxF[3][2][64];
 };
 
 // Tables of one angular level in precision T.
@@ -78,14 +83,11 @@ struct GemmEpi {
   int s;               // rows per cell
   const double* sig;   // per-cell scale (double) for T=double
   const float* sig32;  // per-cell scale for T=float
+  double Nm[64];       // spatial mass matrix N (s x s) for the cell mixing
 };
 template <class T>
 void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
                  const GemmEpi& epi, cudaStream_t st);
-void set_mass_matrix(const double* Nref, int s);  // constant-memory spatial mass (s x s)
-// constant-memory spatial matrices of the Kronecker form of L:
-// Gax[axis][sign][s*s] (sign 1 = negative Omega component) and N[s*s]
-void set_transport_constants(const double* Gax, const double* Nsp);
 
 template <class T>
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,

@@ -11,12 +11,6 @@
 
 namespace amgt {
 
-__constant__ double c_Nmass[64];
-
-void set_mass_matrix(const double* Nref, int s) {
-  cudaMemcpyToSymbol(c_Nmass, Nref, sizeof(double) * s * s);
-}
-
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
@@ -104,7 +98,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, const T*
       const int gc = bn + cc;
       if (gc >= N) continue;
       T mix = T(0);
-      for (int ii = 0; ii < s; ++ii) mix += (T)c_Nmass[l * s + ii] * Ct[r0 + ii][cc];
+      for (int ii = 0; ii < s; ++ii) mix += (T)epi.Nm[l * s + ii] * Ct[r0 + ii][cc];
       T v = scale * mix;
       T* o = C + (long long)gr * ldc + gc;
       if (epi.beta != 0.0) v += (T)epi.beta * (*o);

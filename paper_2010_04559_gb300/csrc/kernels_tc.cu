@@ -439,21 +439,15 @@ int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return -1;
   CUtensorMap ta, tb;
   if (!encode_kmajor(&ta, A, M, K, BM) || !encode_kmajor(&tb, Bt, N, K, BN)) return -2;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes) != cudaSuccess)
-      return -3;
-    attr_set = true;
-  }
+  // per launch: the attribute and the SM count belong to the current device
+  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSmemBytes) != cudaSuccess)
+    return -3;
   TcArgs args{M, N, K, C, add, beta, err};
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = tiles < nsm ? tiles : nsm;
   note_launch();

@@ -367,23 +367,22 @@ __global__ void __launch_bounds__(512) sweep2d_rows_kernel(Geom g, LevelDev<T> t
 //   K0_q + sigma_t kron(N, M_q) = sum_xi kron(G_xi^(sign), A^xi_q) + sigma_t kron(N, M_q),
 //   G_xi^(+) = Fown_{xi,high} - V_xi,   G_xi^(-) = -Fown_{xi,low} - V_xi,
 // where the sign is that of Omega_xi on the patch (one outflow face per axis).
-__constant__ double c_Gax[3][2][64];  // [axis][negative sign][s*s]
-__constant__ double c_Nsp[64];
-__constant__ float c_GaxF[3][2][64];
-__constant__ float c_NspF[64];
-
 template <class T>
-__device__ __forceinline__ T gax(int xi, int sg, int e);
+__device__ __forceinline__ T gax(const Geom& g, int xi, int sg, int e);
 template <>
-__device__ __forceinline__ double gax<double>(int xi, int sg, int e) { return c_Gax[xi][sg][e]; }
+__device__ __forceinline__ double gax<double>(const Geom& g, int xi, int sg, int e) {
+  return g.Gax[xi][sg][e];
+}
 template <>
-__device__ __forceinline__ float gax<float>(int xi, int sg, int e) { return c_GaxF[xi][sg][e]; }
+__device__ __forceinline__ float gax<float>(const Geom& g, int xi, int sg, int e) {
+  return g.GaxF[xi][sg][e];
+}
 template <class T>
-__device__ __forceinline__ T nsp(int e);
+__device__ __forceinline__ T nsp(const Geom& g, int e);
 template <>
-__device__ __forceinline__ double nsp<double>(int e) { return c_Nsp[e]; }
+__device__ __forceinline__ double nsp<double>(const Geom& g, int e) { return g.Nmass[e]; }
 template <>
-__device__ __forceinline__ float nsp<float>(int e) { return c_NspF[e]; }
+__device__ __forceinline__ float nsp<float>(const Geom& g, int e) { return g.NmassF[e]; }
 
 template <class T, int DIM, int A>
 __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
@@ -435,7 +434,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, 
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const T gli = gax<T>(xi, sg, l * S + i);
+          const T gli = gax<T>(g, xi, sg, l * S + i);
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += gli * t1[i][m];
         }
@@ -458,7 +457,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, 
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const T nli = nsp<T>(l * S + i);
+          const T nli = nsp<T>(g, l * S + i);
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += nli * t1[i][m];
         }
@@ -572,15 +571,6 @@ __global__ void prolong_kernel(long long nsdof, int Pf, int a, int nadof_f, int 
 
 }  // namespace
 
-void set_transport_constants(const double* Gax, const double* Nsp) {
-  cudaMemcpyToSymbol(c_Gax, Gax, sizeof(double) * 3 * 2 * 64);
-  cudaMemcpyToSymbol(c_Nsp, Nsp, sizeof(double) * 64);
-  float gf[3 * 2 * 64], nf[64];
-  for (int i = 0; i < 3 * 2 * 64; ++i) gf[i] = (float)Gax[i];
-  for (int i = 0; i < 64; ++i) nf[i] = (float)Nsp[i];
-  cudaMemcpyToSymbol(c_GaxF, gf, sizeof(gf));
-  cudaMemcpyToSymbol(c_NspF, nf, sizeof(nf));
-}
 
 namespace {
 

@@ -400,3 +400,27 @@ def test_kernel_timers_count_launches():
     ctx.amgt_op_sweep(0, x, y)
     assert ctx.amgt_query_kernel_time(pkg.AMGT_KT_SWEEP)[1] == 0
     ctx.close()
+
+
+def test_two_contexts_with_different_geometry_interleaved():
+    """Each context carries its own spatial matrices: operators of two live
+    contexts with different cell shapes, called alternately, each match
+    their own oracle."""
+    pa = W.random_problem(2, (6, 5), 1, 4, 141)
+    pb = W.random_problem(2, (9, 7), 1, 4, 142)
+    pb["hi"] = [2.0, 0.5, 1.0]
+    Ta, Tb = _oracle(pa), _oracle(pb)
+    ca, cb = _ctx(pa), _ctx(pb)
+    ca.amgt_query_sizes(0)
+    cb.amgt_query_sizes(0)
+    xa = W.random_vector((Ta.nsdof, Ta.nadof), 143)
+    xb = W.random_vector((Tb.nsdof, Tb.nadof), 144)
+    ya = torch.empty((Ta.nsdof, Ta.nadof), device="cuda", dtype=torch.float64)
+    yb = torch.empty((Tb.nsdof, Tb.nadof), device="cuda", dtype=torch.float64)
+    for _ in range(2):
+        ca.amgt_op_apply_A(0, _dev(xa), ya)
+        cb.amgt_op_apply_A(0, _dev(xb), yb)
+        assert _rel(_host(ya), Ta.apply_A(xa)) < 1e-12
+        assert _rel(_host(yb), Tb.apply_A(xb)) < 1e-12
+    ca.close()
+    cb.close()
