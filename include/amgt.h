@@ -182,14 +182,27 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *   AMGT_TUNE_GS_CLUSTER  cluster size of the cluster Gauss-Seidel kernels
  *                         (0 = largest available, else 1, 2, 4, 8 or 16)
  *   AMGT_TUNE_KERNEL_TIMERS 1: time the main kernels with CUDA events (see
- *                         amgt_query_kernel_time), 0: off (default) */
+ *                         amgt_query_kernel_time), 0: off (default)
+ *   AMGT_TUNE_GRAPHS      1: amgt_solve applies the multigrid preconditioner
+ *                         by replaying a CUDA graph of the V-cycle captured on
+ *                         its first use (input and output through two fixed
+ *                         device buffers); 0: direct launches (default).
+ *                         Ignored while the kernel timers are on and on
+ *                         the default stream (which cannot be captured). */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
 #define AMGT_TUNE_GS_GRID_BLOCKS 4
 #define AMGT_TUNE_GS_CLUSTER 5
 #define AMGT_TUNE_KERNEL_TIMERS 6
+#define AMGT_TUNE_GRAPHS 7
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
+/* Times the sweep's patches per block and copy depth (what bit 0) and the
+ * coarse Gauss-Seidel kernel (what bit 1) on this context's own hierarchy
+ * (CUDA events on its stream, FP32) and keeps the fastest; results are
+ * cached per problem shape for the process.  choice (may be NULL) receives
+ * {patches per block, copy stages, Gauss-Seidel kernel, 1 if cached}. */
+int amgt_autotune(amgt_ctx* ctx, int what, int* choice);
 /* Sizes of level k of the hierarchy. */
 int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* nadof);
 
@@ -199,6 +212,18 @@ int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* na
  * opt->device_ptrs.  st may be NULL. */
 int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
                double* psi, double* phi, amgt_stats* st);
+
+/* Solves n independent problems, one context each, concurrently: nthreads
+ * host threads (0: min(n, 16)) each drive amgt_solve on the next context,
+ * and every context issues its work on its own stream -- give each context
+ * its own stream, contexts sharing a stream run one after another.  opt
+ * applies to all; psi[i] / phi[i] (phi may be NULL) as in amgt_solve, stats
+ * (may be NULL) receives n entries.  While the batch runs, contexts whose
+ * coarse solver is a cooperative kernel (auto, 4, 6: blocks that wait on one
+ * another) use the cluster kernel (3) instead.  Returns the first non-OK
+ * status of the n solves (all of them run). */
+int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
+                     double* const* phi, amgt_stats* stats, int nthreads);
 
 /* ---- operators of the hot path on device buffers -------------------------- */
 /* All buffers are contiguous [Nsdof][Nadof(level)] of element type `dtype`

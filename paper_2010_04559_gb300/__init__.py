@@ -7,11 +7,13 @@ include/amgt.h); this package only builds and binds it.
 from ._capi import (AMGT_F32, AMGT_F32_BF16TC, AMGT_F64, AMGT_MODE_F64, AMGT_MODE_MIXED,
                     AMGT_KT_APPLY_L, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_PREP,
                     AMGT_KT_SCATTER_F32, AMGT_KT_SCATTER_F64, AMGT_KT_SCATTER_TC, AMGT_KT_SWEEP, AMGT_PREC_MG,
-                    AMGT_PREC_NONE, AMGT_PREC_SWEEP, AMGT_TUNE_KERNEL_TIMERS, AmgtError, Context,
-                    EXPORTS, amgt_query_launches, context_from_problem)
+                    AMGT_PREC_NONE, AMGT_PREC_SWEEP, AMGT_TUNE_GRAPHS, AMGT_TUNE_KERNEL_TIMERS, AmgtError,
+                    Context,
+                    EXPORTS, amgt_query_launches, amgt_solve_batch, context_from_problem)
 
 __all__ = ["Context", "context_from_problem", "AmgtError", "EXPORTS", "AMGT_F64", "AMGT_F32",
            "AMGT_F32_BF16TC", "AMGT_PREC_NONE", "AMGT_PREC_SWEEP", "AMGT_PREC_MG",
            "AMGT_MODE_F64", "AMGT_MODE_MIXED", "amgt_query_launches", "AMGT_TUNE_KERNEL_TIMERS",
+           "AMGT_TUNE_GRAPHS", "amgt_solve_batch",
            "AMGT_KT_SWEEP", "AMGT_KT_APPLY_L", "AMGT_KT_SCATTER_PREP", "AMGT_KT_SCATTER_TC",
            "AMGT_KT_SCATTER_F32", "AMGT_KT_SCATTER_F64", "AMGT_KT_COARSE_GS"]

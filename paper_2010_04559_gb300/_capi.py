@@ -41,6 +41,7 @@ AMGT_TUNE_SWEEP_STAGES = 3
 AMGT_TUNE_GS_GRID_BLOCKS = 4
 AMGT_TUNE_GS_CLUSTER = 5
 AMGT_TUNE_KERNEL_TIMERS = 6
+AMGT_TUNE_GRAPHS = 7
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
 
@@ -56,6 +57,7 @@ EXPORTS = [
     "amgt_op_coarse_gs_noalloc",
     "amgt_op_vcycle", "amgt_op_scalar_flux",
     "amgt_set_adjoint", "amgt_response", "amgt_response_gradients",
+    "amgt_autotune", "amgt_solve_batch",
 ]
 
 
@@ -113,6 +115,10 @@ _SIGS = {
     "amgt_set_adjoint": ([_P, _I], _I),
     "amgt_response": ([_P, _I, _P, _PD], _I),
     "amgt_response_gradients": ([_P, _I, _P, _P, _P, _P, _P], _I),
+    "amgt_autotune": ([_P, _I, _PI], _I),
+    "amgt_solve_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(amgt_options),
+                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(amgt_stats), _I],
+                         _I),
 }
 
 
@@ -357,6 +363,12 @@ class Context:
         return self._check(self.lib.amgt_op_scalar_flux(self.h, level, self._dtype_code(psi),
                                                         _dptr(psi), _dptr(phi)))
 
+    def amgt_autotune(self, what=3):
+        """(patches per block, copy stages, Gauss-Seidel kernel, cached)."""
+        ch = (ctypes.c_int * 4)()
+        self._check(self.lib.amgt_autotune(self.h, int(what), ch))
+        return tuple(ch)
+
     # ---- adjoint and gradients
     def amgt_set_adjoint(self, on):
         return self._check(self.lib.amgt_set_adjoint(self.h, 1 if on else 0))
@@ -386,6 +398,26 @@ class Context:
         assert all(o[0] == dev for o in outs)
         return self._check(self.lib.amgt_response_gradients(self.h, dev, p, l, outs[0][1],
                                                             outs[1][1], outs[2][1]))
+
+
+def amgt_solve_batch(contexts, psis, phis=None, tol=1e-8, restart=20, maxit=1000,
+                     precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, inner_tol=0.0,
+                     inner_maxit=200, nthreads=0, allow_not_converged=False):
+    """Solve the problems of `contexts` concurrently (one stream each) into the
+    torch CUDA float64 tensors `psis` (and `phis`); returns the stats list."""
+    n = len(contexts)
+    opt = amgt_options(float(tol), int(restart), int(maxit), int(precond), int(mode), 1,
+                       float(inner_tol), int(inner_maxit))
+    hs = (_P * n)(*[c.h for c in contexts])
+    pp = (_P * n)(*[_dptr(p).value for p in psis])
+    pf = (_P * n)(*[_dptr(p).value for p in phis]) if phis is not None else None
+    st = (amgt_stats * n)()
+    rc = lib().amgt_solve_batch(hs, n, ctypes.byref(opt), pp, pf, st, int(nthreads))
+    allow = (AMGT_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    if rc != AMGT_OK and rc not in allow:
+        raise AmgtError(rc, "amgt_solve_batch failed: " +
+                        "; ".join(c.lib.amgt_last_error(c.h).decode() for c in contexts[:3]))
+    return list(st)
 
 
 def context_from_problem(prob, device=0, stream=None, aniso=None):

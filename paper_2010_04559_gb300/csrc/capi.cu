@@ -8,7 +8,9 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <stdexcept>
+#include <string>
 #include <thread>
 #include <type_traits>
 #include <utility>
@@ -311,6 +313,59 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
   return AMGT_OK;
 }
 
+// Captured V-cycle graphs refer to the context's buffers and tuning: dropped
+// whenever either changes.
+void drop_graphs(amgt_ctx* ctx) {
+  for (auto& row : ctx->vgraph)
+    for (auto& v : row) {
+      if (v.exec) cudaGraphExecDestroy(v.exec);
+      v = amgt_ctx::VGraph();
+    }
+}
+
+// Sweep tasks of one level: groups of G patches of one sweep direction (2D:
+// the row-pipelined kernel's blocks of ny * G threads; 3D: enough patches per
+// block to keep about 256 threads busy on a wavefront level).  Gwant > 0
+// forces G (autotuning); else the context's AMGT_TUNE_SWEEP_GROUP or the
+// heuristic.  Uploads the task arrays.
+int make_sweep_tasks(amgt_ctx* ctx, Level& Lv, const Geom& g, int Gwant) {
+  const int dim = g.dim, P = Lv.mesh.P, a = Lv.mesh.a, nadof = Lv.nadof();
+  Lv.task_dir.clear();
+  Lv.task_q0.clear();
+  Lv.task_nq.clear();
+  int G;
+  if (dim == 2) {
+    // prefer >= ~120 blocks
+    G = 8;
+    while (G > 1 && (g.ny * G > 512 || P / G < 120)) G /= 2;
+  } else {
+    G = std::max(1, std::min(16, 256 / std::max(1, max_wavefront_cells(g))));
+  }
+  if (ctx->sweep_group > 0) G = ctx->sweep_group;
+  if (Gwant > 0) G = Gwant;
+  if (dim == 2 && g.ny * G > 512) G = std::max(1, 512 / g.ny);
+  Lv.sweep_G = dim == 2 ? G : 0;
+  for (int d = 0; d < Lv.ndir; ++d)
+    for (int q0 = Lv.dir_begin[d]; q0 < Lv.dir_end[d]; q0 += G) {
+      Lv.task_dir.push_back(d);
+      Lv.task_q0.push_back(q0);
+      Lv.task_nq.push_back(std::min(G, Lv.dir_end[d] - q0));
+    }
+  // 16-byte staging copies need 16-byte aligned segment starts and lengths
+  Lv.chunk16_f32 = Lv.chunk16_f64 = (dim == 2);
+  for (size_t i = 0; i < Lv.task_q0.size(); ++i) {
+    for (int bytes : {4, 8}) {
+      bool ok = ((size_t)nadof * bytes) % 16 == 0 && ((size_t)Lv.task_q0[i] * a * bytes) % 16 == 0 &&
+                ((size_t)Lv.task_nq[i] * a * bytes) % 16 == 0 && ((size_t)G * a * bytes) % 16 == 0;
+      if (!ok) (bytes == 4 ? Lv.chunk16_f32 : Lv.chunk16_f64) = false;
+    }
+  }
+  TRY(upload(ctx, Lv.task_dir, &Lv.d_task_dir));
+  TRY(upload(ctx, Lv.task_q0, &Lv.d_task_q0));
+  TRY(upload(ctx, Lv.task_nq, &Lv.d_task_nq));
+  return AMGT_OK;
+}
+
 // Row tables and face-word buffer of the row-pipelined coarse Gauss-Seidel:
 // block b owns the rows R = b, b + nb, ... (R = iy + ny*iz) in every
 // direction, visited in increasing rotated level jy + jz.
@@ -360,6 +415,7 @@ int build_gs_rows(amgt_ctx* ctx) {
 
 int build(amgt_ctx* ctx) {
   if (!ctx->dirty) return AMGT_OK;
+  drop_graphs(ctx);
   if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "mesh not set");
   if (ctx->N < 0) return fail(ctx, AMGT_ERR_STATE, "materials not set");
   if (ctx->paths.empty()) return fail(ctx, AMGT_ERR_STATE, "angular mesh not set");
@@ -535,45 +591,11 @@ int build(amgt_ctx* ctx) {
       Lv.dir_begin[d] = b;
       Lv.dir_end[d] = e;
     }
-    // sweep tasks: groups of G patches of one direction, sized so that a
-    // wavefront level keeps about 256 threads busy
-    Lv.task_dir.clear();
-    Lv.task_q0.clear();
-    Lv.task_nq.clear();
-    const int maxdiag = max_wavefront_cells(g);
-    int G;
-    if (dim == 2) {
-      // row-pipelined kernel: ny * G threads per block; prefer >= ~120 blocks
-      G = 8;
-      while (G > 1 && (g.ny * G > 512 || P / G < 120)) G /= 2;
-    } else {
-      G = std::max(1, std::min(16, 256 / std::max(1, maxdiag)));
-    }
-    if (ctx->sweep_group > 0) G = ctx->sweep_group;
-    if (dim == 2 && g.ny * G > 512) G = std::max(1, 512 / g.ny);
-    Lv.sweep_G = dim == 2 ? G : 0;
-    for (int d = 0; d < Lv.ndir; ++d)
-      for (int q0 = Lv.dir_begin[d]; q0 < Lv.dir_end[d]; q0 += G) {
-        Lv.task_dir.push_back(d);
-        Lv.task_q0.push_back(q0);
-        Lv.task_nq.push_back(std::min(G, Lv.dir_end[d] - q0));
-      }
-    // 16-byte staging copies need 16-byte aligned segment starts and lengths
-    Lv.chunk16_f32 = Lv.chunk16_f64 = (dim == 2);
-    for (size_t i = 0; i < Lv.task_q0.size(); ++i) {
-      for (int bytes : {4, 8}) {
-        bool ok = ((size_t)nadof * bytes) % 16 == 0 && ((size_t)Lv.task_q0[i] * a * bytes) % 16 == 0 &&
-                  ((size_t)Lv.task_nq[i] * a * bytes) % 16 == 0 && ((size_t)G * a * bytes) % 16 == 0;
-        if (!ok) (bytes == 4 ? Lv.chunk16_f32 : Lv.chunk16_f64) = false;
-      }
-    }
+    TRY(make_sweep_tasks(ctx, Lv, g, 0));
     TRY(upload(ctx, Lv.pdir, &Lv.d_pdir));
     TRY(upload(ctx, Lv.octant, &Lv.d_octant));
     TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
     TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
-    TRY(upload(ctx, Lv.task_dir, &Lv.d_task_dir));
-    TRY(upload(ctx, Lv.task_q0, &Lv.d_task_q0));
-    TRY(upload(ctx, Lv.task_nq, &Lv.d_task_nq));
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));
     TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32));
     if (k == nl - 1) TRY(build_gs_blocks(ctx, Lv, K0, B, X, F));
@@ -885,7 +907,9 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
   if (store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6)) {
     const int pi = sizeof(T) == 4 ? 0 : 1;
     if (L.rows_nb > 0) {
-      if (ctx->gs_tag > 0xf0000000u) {  // restart the face-word tags
+      // restart the face-word tags: before wrap-around, and inside a captured
+      // graph (every replay then starts from cleared words and tag 0)
+      if (ctx->gs_tag > 0xf0000000u || ctx->capturing) {
         CK(cudaMemsetAsync(L.d_faces, 0, L.faces_bytes, ctx->stream));
         ctx->gs_tag = 0;
       }
@@ -896,7 +920,7 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
                                    L.rows_smem[pi], L.d_rows,
                                    L.rows_nb, L.rows_rpb, L.d_faces, ctx->gs_tag,
                                    ctx->d_status, ctx->stream) == 0) {
-        ctx->gs_tag += (unsigned)sweeps;
+        if (!ctx->capturing) ctx->gs_tag += (unsigned)sweeps;
         ctx->gs_cluster = 600;
         return AMGT_OK;
       }
@@ -961,6 +985,57 @@ int vcycle_impl(amgt_ctx* ctx, int k, bool tc, const T* f, T* phi) {
   TRY(vcycle_impl<T>(ctx, k + 1, tc, fc, phic));
   TRY(prolong_impl<T>(ctx, k, phic, phi));
   TRY(smooth_impl<T>(ctx, k, tc, ctx->nu_post, f, phi, false));
+  return AMGT_OK;
+}
+
+// phi = LMG(0, f) on the finest level through a captured CUDA graph: the
+// first call runs the cycle directly (every lazy allocation happens there)
+// and then captures it reading a fixed input buffer and writing a fixed
+// output buffer; later calls copy f in, replay, and copy phi out.
+template <class T>
+int vcycle_graph(amgt_ctx* ctx, bool tc, const T* f, T* phi) {
+  const Level& L0 = ctx->lv[0];
+  const size_t bytes = (size_t)L0.nsdof * L0.nadof() * sizeof(T);
+  amgt_ctx::VGraph& G = ctx->vgraph[sizeof(T) == 8 ? 1 : 0][tc ? 1 : 0];
+  if (!G.exec) {
+    TRY(vcycle_impl<T>(ctx, 0, tc, f, phi));
+    if (!G.in) {
+      T *in, *out;
+      TRY(dalloc<T>(ctx, (size_t)L0.nsdof * L0.nadof(), &in));
+      TRY(dalloc<T>(ctx, (size_t)L0.nsdof * L0.nadof(), &out));
+      G.in = in;
+      G.out = out;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    const long long n0 = launch_count();
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    const int rc = vcycle_impl<T>(ctx, 0, tc, static_cast<const T*>(G.in), static_cast<T*>(G.out));
+    ctx->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc != AMGT_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, AMGT_ERR_CUDA, std::string("V-cycle capture: ") + cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      G.exec = nullptr;
+      cudaGetLastError();
+      return fail(ctx, AMGT_ERR_CUDA, std::string("V-cycle graph: ") + cudaGetErrorString(ei));
+    }
+    G.nlaunch = launch_count() - n0;
+    return AMGT_OK;
+  }
+  CK(cudaMemcpyAsync(G.in, f, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaGraphLaunch(G.exec, ctx->stream));
+  CK(cudaMemcpyAsync(phi, G.out, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  note_launch((int)G.nlaunch);
   return AMGT_OK;
 }
 
@@ -1115,6 +1190,40 @@ int gmres(amgt_ctx* ctx, int k, OpA apply_A, OpM apply_M, const T* b, T* x, bool
 }  // namespace
 
 // =================================================================== C ABI
+namespace {
+struct TuneChoice {
+  int G = 0, stages = 0, gs_kernel = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+
+// seconds per call of fn() on the context's stream (events, after one warm-up)
+template <class F>
+int time_on_stream(amgt_ctx* ctx, int reps, F fn, double* sec) {
+  TRY(fn());
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, ctx->stream));
+  for (int r = 0; r < reps; ++r) {
+    const int rc = fn();
+    if (rc != AMGT_OK) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return rc;
+    }
+  }
+  CK(cudaEventRecord(b, ctx->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *sec = ms / 1e3 / reps;
+  return AMGT_OK;
+}
+}  // namespace
+
 extern "C" {
 
 int amgt_create(amgt_ctx** out, int device, void* stream) {
@@ -1387,8 +1496,138 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
   return AMGT_OK;
 }
 
+// ---- batched solves and autotuning
+
+int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
+                     double* const* phi, amgt_stats* stats, int nthreads) {
+  if (!ctxs || n < 0 || !opt || !psi) return AMGT_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || !psi[i]) return AMGT_ERR_ARG;
+  // kernels whose blocks wait on one another through memory (cooperative
+  // launches) could starve each other of SMs when several problems run at
+  // once: the batch uses the cluster Gauss-Seidel kernels instead
+  std::vector<int> saved(n);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = ctxs[i]->gs_kernel;
+    if (saved[i] == 0 || saved[i] == 4 || saved[i] == 6) {
+      if (ctxs[i]->gs_kernel != 3) drop_graphs(ctxs[i]);
+      ctxs[i]->gs_kernel = 3;
+    }
+  }
+  int nt = nthreads > 0 ? nthreads : std::min(n, 16);
+  nt = std::max(1, std::min(nt, std::max(1, n)));
+  std::vector<int> rc(n, AMGT_OK);
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int i; (i = next.fetch_add(1)) < n;) {
+      cudaSetDevice(ctxs[i]->device);
+      rc[i] = amgt_solve(ctxs[i], opt, nullptr, psi[i], phi ? phi[i] : nullptr,
+                         stats ? &stats[i] : nullptr);
+    }
+  };
+  std::vector<std::thread> ts;
+  for (int t = 0; t < nt; ++t) ts.emplace_back(work);
+  for (auto& t : ts) t.join();
+  for (int i = 0; i < n; ++i) {
+    if (ctxs[i]->gs_kernel != saved[i]) drop_graphs(ctxs[i]);
+    ctxs[i]->gs_kernel = saved[i];
+  }
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != AMGT_OK) return rc[i];
+  return AMGT_OK;
+}
+
+
+int amgt_autotune(amgt_ctx* ctx, int what, int* choice) {
+  if (!ctx) return AMGT_ERR_ARG;
+  TRY(build(ctx));
+  drop_graphs(ctx);
+  const Geom g0 = level_geom(ctx, 0);
+  const int nl = (int)ctx->lv.size();
+  std::string key = std::to_string(g0.dim) + "/" + std::to_string(g0.nx) + "x" +
+                    std::to_string(g0.ny) + "x" + std::to_string(g0.nz) + "/" +
+                    std::to_string(ctx->basis);
+  for (int k = 0; k < nl; ++k) key += "/" + std::to_string(ctx->lv[k].mesh.P) + ":" + std::to_string(ctx->lv[k].nmom);
+  key += "/" + std::to_string(std::min(ctx->nmat, 64));
+  TuneChoice best;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  float *x, *y;
+  TRY(wsvec<float>(ctx, 0, 3, &x));
+  TRY(wsvec<float>(ctx, 0, 4, &y));
+  if (!cached) {
+    CK(cudaMemsetAsync(x, 0, (size_t)ctx->lv[0].nsdof * ctx->lv[0].nadof() * 4, ctx->stream));
+    best.G = ctx->sweep_group;
+    best.stages = ctx->sweep_stages;
+    best.gs_kernel = ctx->gs_kernel;
+    if (what & 1) {
+      // sweep: patches per block (all levels) and, in 2D, the copy depth
+      double tbest = 1e30;
+      const std::vector<int> Gs = g0.dim == 2 ? std::vector<int>{1, 2, 4, 8}
+                                              : std::vector<int>{1, 2, 4, 8, 16};
+      const std::vector<int> Ss = g0.dim == 2 ? std::vector<int>{2, 3, 4, 6} : std::vector<int>{0};
+      for (int G : Gs) {
+        if (g0.dim == 2 && g0.ny * G > 512) continue;
+        ctx->sweep_group = G;
+        for (int k = 0; k < nl; ++k) TRY(make_sweep_tasks(ctx, ctx->lv[k], level_geom(ctx, k), G));
+        for (int st : Ss) {
+          ctx->sweep_stages = st;
+          double t;
+          TRY(time_on_stream(ctx, 3, [&] { return sweep_impl<float>(ctx, 0, x, y); }, &t));
+          if (t < tbest) {
+            tbest = t;
+            best.G = G;
+            best.stages = st;
+          }
+        }
+      }
+    }
+    if (what & 2) {
+      // coarse solver: row-pipelined, thread-group (cluster) and warp kernels
+      const Level& Lc = ctx->lv[nl - 1];
+      float *fc, *xc;
+      TRY(wsvec<float>(ctx, nl - 1, 3, &fc));
+      TRY(wsvec<float>(ctx, nl - 1, 4, &xc));
+      CK(cudaMemsetAsync(fc, 0, (size_t)Lc.nsdof * Lc.nadof() * 4, ctx->stream));
+      double tbest = 1e30;
+      for (int v : {6, 3, 2}) {
+        if (v == 6 && Lc.rows_nb == 0) continue;
+        ctx->gs_kernel = v;
+        double t;
+        const int rc = time_on_stream(ctx, 1, [&] { return coarse_gs_impl<float>(ctx, 2, fc, xc); }, &t);
+        if (rc != AMGT_OK) continue;
+        if (t < tbest) {
+          tbest = t;
+          best.gs_kernel = v;
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  ctx->sweep_group = best.G;
+  ctx->sweep_stages = best.stages;
+  ctx->gs_kernel = best.gs_kernel;
+  for (int k = 0; k < nl; ++k) TRY(make_sweep_tasks(ctx, ctx->lv[k], level_geom(ctx, k), best.G));
+  if (choice) {
+    choice[0] = best.G;
+    choice[1] = best.stages;
+    choice[2] = best.gs_kernel;
+    choice[3] = cached ? 1 : 0;
+  }
+  return AMGT_OK;
+}
+
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (!ctx) return AMGT_ERR_ARG;
+  drop_graphs(ctx);  // a captured cycle holds the old choices
   if (key == AMGT_TUNE_GS_KERNEL) {
     if (value < 0 || value > 6) return fail(ctx, AMGT_ERR_ARG, "GS kernel 0..6");
     ctx->gs_kernel = value;
@@ -1404,6 +1643,12 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
     if (value < 0 || value > 4096) return fail(ctx, AMGT_ERR_ARG, "grid blocks 0..4096");
     if (value != ctx->gs_grid_blocks) ctx->dirty = true;  // the row tables depend on it
     ctx->gs_grid_blocks = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_GRAPHS) {
+    if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "graphs 0 or 1");
+    ctx->use_graphs = value == 1;
+    drop_graphs(ctx);
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_KERNEL_TIMERS) {
@@ -1571,11 +1816,16 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
   KrylovResult kr;
   int rc = AMGT_OK;
   const int prec = opt->precond;
+  // graphs and the per-kernel event timers exclude each other; the legacy
+  // default stream cannot be captured
+  const bool graphs = ctx->use_graphs && !ctx->ktimers && ctx->stream != nullptr &&
+                      ctx->stream != cudaStreamLegacy && ctx->stream != cudaStreamPerThread;
   if (opt->mode == AMGT_MODE_F64) {
     auto A64 = [&](const double* xx, double* yy) { return applyA_impl<double>(ctx, 0, false, xx, yy); };
     auto M64 = [&](const double* v, double* z) -> int {
       if (prec == AMGT_PREC_SWEEP) return sweep_impl<double>(ctx, 0, v, z);
-      if (prec == AMGT_PREC_MG) return vcycle_impl<double>(ctx, 0, false, v, z);
+      if (prec == AMGT_PREC_MG)
+        return graphs ? vcycle_graph<double>(ctx, false, v, z) : vcycle_impl<double>(ctx, 0, false, v, z);
       CK(cudaMemcpyAsync(z, v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       return AMGT_OK;
     };
@@ -1603,7 +1853,8 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, false, xx, yy); };
     auto M32 = [&](const float* v, float* z) -> int {
       if (prec == AMGT_PREC_SWEEP) return sweep_impl<float>(ctx, 0, v, z);
-      if (prec == AMGT_PREC_MG) return vcycle_impl<float>(ctx, 0, tc, v, z);
+      if (prec == AMGT_PREC_MG)
+        return graphs ? vcycle_graph<float>(ctx, tc, v, z) : vcycle_impl<float>(ctx, 0, tc, v, z);
       CK(cudaMemcpyAsync(z, v, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
       return AMGT_OK;
     };

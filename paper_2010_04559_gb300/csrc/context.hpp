@@ -119,6 +119,18 @@ struct amgt_ctx {
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   bool adjoint = false;  // amgt_set_adjoint: operators of the transposed problem
+  // V-cycle replayed from a captured CUDA graph (AMGT_TUNE_GRAPHS): per
+  // precision (0 FP32, 1 FP64) and scatter path (1 tensor cores); the graph
+  // reads `in` and writes `out`
+  struct VGraph {
+    cudaGraphExec_t exec = nullptr;
+    void* in = nullptr;
+    void* out = nullptr;
+    long long nlaunch = 0;
+  };
+  VGraph vgraph[2][2];
+  bool use_graphs = false;
+  bool capturing = false;  // a V-cycle is being captured on the stream
   double* d_grad = nullptr;  // gradient scratch (moments, outputs)
   size_t grad_bytes = 0;
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
@@ -138,6 +150,9 @@ struct amgt_ctx {
   double kt_ms[AMGT_KT_COUNT] = {};
   long long kt_n[AMGT_KT_COUNT] = {};
   ~amgt_ctx() {
+    for (auto& row : vgraph)
+      for (auto& v : row)
+        if (v.exec) cudaGraphExecDestroy(v.exec);
     for (auto& p : kt_pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);

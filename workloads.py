@@ -125,6 +125,28 @@ def config3_cube(n=32, level=2, N=32):
     return problem(3, (n, n, n), st, ss, N, hg_moments(0.95, N), q, level, mg=mg)
 
 
+def config4_batch(nprob=256, nmin=16, nmax=96, seed_k=4):
+    """Batch of independent 2D problems of uneven size: n ~ U{nmin..nmax}
+    cells per axis on the unit square, angular level ~ U{1..3} (Lin), per-cell
+    sigma_t ~ lognormal(0, 0.7), HG g ~ U[0.7, 0.95] at order 2*level + 4,
+    scatter ratio per problem ~ U[0.5, 0.95], centred unit source of side
+    0.25, vacuum; 2-level multigrid with coarse order min(N, 4)."""
+    rng = _rng(4000 + seed_k)
+    out = []
+    for _ in range(nprob):
+        n = int(rng.integers(nmin, nmax + 1))
+        level = int(rng.integers(1, 4))
+        N = 2 * level + 4
+        C = n * n
+        st = np.exp(rng.normal(0.0, 0.7, size=C))
+        ss = st * rng.uniform(0.5, 0.95)
+        g = rng.uniform(0.7, 0.95)
+        q = _central_source(2, (n, n), (0, 0, 0), (1, 1, 1), 0.25)
+        mg = dict(nlevels=2, Nr=[N, min(N, 4)], nu_pre=1, nu_post=1, coarse_sweeps=10)
+        out.append(problem(2, (n, n), st, ss, N, hg_moments(g, N), q, level, mg=mg))
+    return out
+
+
 def random_problem(dim, ncell, level, N, seed_k, basis="lin", g=0.8,
                    inflow=None):
     """Small random problem for parity tests: lognormal sigma_t, scatter ratio
