@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--fp64-ref", action="store_true", help="also time one FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--batch", type=int, default=32,
+                    help="problems of the uneven 2D batch solved concurrently (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="tolerance of each inner FP32 solve (0: adaptive)")
     ap.add_argument("--profile", choices=["solve", "kernels"], default=None,
@@ -466,6 +468,48 @@ def main():
                "iterations": sta.iterations, "relres": sta.relres, "response": R}
         actx.close()
 
+    # ---- batched: the first problems of the 256-problem batch of uneven 2D
+    # problems, each on its own context and stream, autotuned, V-cycles
+    # replayed from captured graphs, solved concurrently (mixed, 1e-8)
+    batch = None
+    if args.batch > 0:
+        from paper_2010_04559_gb300 import AMGT_TUNE_GRAPHS, amgt_solve_batch
+        probs = W.config4_batch()[:args.batch]
+        bstreams = [torch.cuda.Stream() for _ in probs]
+        bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
+                for p, s in zip(probs, bstreams)]
+        t0 = time.perf_counter()
+        tunes = [c.amgt_autotune(3) for c in bctx]
+        t_tune = time.perf_counter() - t0
+        for c in bctx:
+            c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
+        bpsi = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64)
+                for c in bctx]
+        bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
+        amgt_solve_batch(bctx, bpsi, tol=1e-8)  # warm-up: captures the graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bst = amgt_solve_batch(bctx, bpsi, tol=1e-8)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for c, p in zip(bctx, bpsi):
+            c.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=p,
+                         phi=None, device_ptrs=True)
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        dof_its = sum(d * st.iterations for d, st in zip(bdof, bst))
+        batch = {"workload": f"first {len(probs)} problems of the 256-problem batch (2D, n in "
+                             f"16..96, level 1..3, per-cell lognormal sigma_t, N = 2 level + 4)",
+                 "problems": len(probs), "unknowns": sum(bdof),
+                 "value": dof_its / t_batch / 1e9, "unit": "GDOF/s",
+                 "time_to_tol_s": t_batch, "sequential_time_to_tol_s": t_seq,
+                 "max_relres": max(st.relres for st in bst),
+                 "iterations": [st.iterations for st in bst], "autotune_s": t_tune,
+                 "tuned": [list(t[:3]) for t in tunes]}
+        for c in bctx:
+            c.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -498,6 +542,8 @@ def main():
             line["fp64_gpu"] = fp64
         if adj:
             line["adjoint"] = adj
+        if batch:
+            line["batched"] = batch
         print(json.dumps(line))
     ctx.close()
     if dist:

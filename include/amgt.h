@@ -218,10 +218,11 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
  * and every context issues its work on its own stream -- give each context
  * its own stream, contexts sharing a stream run one after another.  opt
  * applies to all; psi[i] / phi[i] (phi may be NULL) as in amgt_solve, stats
- * (may be NULL) receives n entries.  While the batch runs, contexts whose
- * coarse solver is a cooperative kernel (auto, 4, 6: blocks that wait on one
- * another) use the cluster kernel (3) instead.  Returns the first non-OK
- * status of the n solves (all of them run). */
+ * (may be NULL) receives n entries.  Each solve is followed by amgt_sync, so
+ * a bounded device-side wait that gave up is reported as that problem's
+ * status (the cooperative coarse solvers rely on the co-residency that a
+ * cooperative launch guarantees its blocks).  Returns the first non-OK status
+ * of the n solves (all of them run). */
 int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
                      double* const* phi, amgt_stats* stats, int nthreads);
 

@@ -1503,17 +1503,6 @@ int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, doub
   if (!ctxs || n < 0 || !opt || !psi) return AMGT_ERR_ARG;
   for (int i = 0; i < n; ++i)
     if (!ctxs[i] || !psi[i]) return AMGT_ERR_ARG;
-  // kernels whose blocks wait on one another through memory (cooperative
-  // launches) could starve each other of SMs when several problems run at
-  // once: the batch uses the cluster Gauss-Seidel kernels instead
-  std::vector<int> saved(n);
-  for (int i = 0; i < n; ++i) {
-    saved[i] = ctxs[i]->gs_kernel;
-    if (saved[i] == 0 || saved[i] == 4 || saved[i] == 6) {
-      if (ctxs[i]->gs_kernel != 3) drop_graphs(ctxs[i]);
-      ctxs[i]->gs_kernel = 3;
-    }
-  }
   int nt = nthreads > 0 ? nthreads : std::min(n, 16);
   nt = std::max(1, std::min(nt, std::max(1, n)));
   std::vector<int> rc(n, AMGT_OK);
@@ -1523,15 +1512,14 @@ int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, doub
       cudaSetDevice(ctxs[i]->device);
       rc[i] = amgt_solve(ctxs[i], opt, nullptr, psi[i], phi ? phi[i] : nullptr,
                          stats ? &stats[i] : nullptr);
+      // a bounded device wait that gave up is reported with the solve
+      const int rs = amgt_sync(ctxs[i]);
+      if (rc[i] == AMGT_OK) rc[i] = rs;
     }
   };
   std::vector<std::thread> ts;
   for (int t = 0; t < nt; ++t) ts.emplace_back(work);
   for (auto& t : ts) t.join();
-  for (int i = 0; i < n; ++i) {
-    if (ctxs[i]->gs_kernel != saved[i]) drop_graphs(ctxs[i]);
-    ctxs[i]->gs_kernel = saved[i];
-  }
   for (int i = 0; i < n; ++i)
     if (rc[i] != AMGT_OK) return rc[i];
   return AMGT_OK;
@@ -1572,7 +1560,7 @@ int amgt_autotune(amgt_ctx* ctx, int what, int* choice) {
       double tbest = 1e30;
       const std::vector<int> Gs = g0.dim == 2 ? std::vector<int>{1, 2, 4, 8}
                                               : std::vector<int>{1, 2, 4, 8, 16};
-      const std::vector<int> Ss = g0.dim == 2 ? std::vector<int>{2, 3, 4, 6} : std::vector<int>{0};
+      const std::vector<int> Ss = g0.dim == 2 ? std::vector<int>{3, 4} : std::vector<int>{0};
       for (int G : Gs) {
         if (g0.dim == 2 && g0.ny * G > 512) continue;
         ctx->sweep_group = G;
@@ -1597,11 +1585,13 @@ int amgt_autotune(amgt_ctx* ctx, int what, int* choice) {
       TRY(wsvec<float>(ctx, nl - 1, 4, &xc));
       CK(cudaMemsetAsync(fc, 0, (size_t)Lc.nsdof * Lc.nadof() * 4, ctx->stream));
       double tbest = 1e30;
-      for (int v : {6, 3, 2}) {
+      const std::vector<int> cand =
+          store<float>(Lc).TinvT ? std::vector<int>{6, 3} : std::vector<int>{2, 1};
+      for (int v : cand) {
         if (v == 6 && Lc.rows_nb == 0) continue;
         ctx->gs_kernel = v;
         double t;
-        const int rc = time_on_stream(ctx, 1, [&] { return coarse_gs_impl<float>(ctx, 2, fc, xc); }, &t);
+        const int rc = time_on_stream(ctx, 1, [&] { return coarse_gs_impl<float>(ctx, 1, fc, xc); }, &t);
         if (rc != AMGT_OK) continue;
         if (t < tbest) {
           tbest = t;

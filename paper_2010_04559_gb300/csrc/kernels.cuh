@@ -60,6 +60,20 @@ struct Schedule {
   int ntask;
 };
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum.  The attribute is process-wide per kernel: one fixed value (not each
+// launch's own size) keeps launches from concurrent host threads, sized for
+// different problems, from undercutting one another.
+template <class K>
+inline cudaError_t allow_max_smem(K kern) {
+  int dev = 0, mx = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 // status word written by device-side bounded waits
 struct DevStatus {
   int* flag;  // device int, 0 = ok

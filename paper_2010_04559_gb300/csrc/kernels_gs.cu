@@ -701,7 +701,7 @@ cudaError_t launch_gs_grid_impl(int nblocks, int ngroups, int GT, size_t smem, c
                                 T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
                                 int nmat, unsigned* gbar, int* err, cudaStream_t st) {
   auto kern = coarse_gs_group_kernel<T, DIM, A, VEC, true>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ngroups * GT, smem);
@@ -727,7 +727,7 @@ cudaError_t launch_gs_group_impl(int cl, int ngroups, int GT, size_t smem, const
                                  T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
                                  int nmat, cudaStream_t st) {
   auto kern = coarse_gs_group_kernel<T, DIM, A, VEC, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   if (cl > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -763,7 +763,7 @@ cudaError_t launch_gs_block_impl(int cl, int wpc, const Geom& g, const LevelDev<
                                  cudaStream_t st) {
   auto kern = coarse_gs_block_kernel<T, DIM, A>;
   const size_t smem = (size_t)wpc * (3 * Emax + (1 << DIM) * t.nmom) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   if (cl > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -531,7 +531,7 @@ template <class T, int DIM, int A>
 cudaError_t rows_launch(const RowsArgs<T>& a, int nblocks, int threads, size_t smem,
                         cudaStream_t st) {
   auto kern = coarse_gs_rows_kernel<T, DIM, A>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
   return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(threads), args, smem, st);
@@ -540,7 +540,7 @@ cudaError_t rows_launch(const RowsArgs<T>& a, int nblocks, int threads, size_t s
 template <class T, int DIM, int A>
 int rows_max_blocks(int threads, size_t smem) {
   auto kern = coarse_gs_rows_kernel<T, DIM, A>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (allow_max_smem(kern) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;

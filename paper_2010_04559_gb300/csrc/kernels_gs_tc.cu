@@ -399,7 +399,7 @@ int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData&
   for (int cl : sizes) {
     auto kern = (g.dim == 2) ? (g.a == 3 ? coarse_gs_tc_kernel<2, 3> : coarse_gs_tc_kernel<2, 1>)
                              : (g.a == 3 ? coarse_gs_tc_kernel<3, 3> : coarse_gs_tc_kernel<3, 1>);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (allow_max_smem(kern) !=
         cudaSuccess) {
       cudaGetLastError();
       return -3;

@@ -440,8 +440,7 @@ int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
   CUtensorMap ta, tb;
   if (!encode_kmajor(&ta, A, M, K, BM) || !encode_kmajor(&tb, Bt, N, K, BN)) return -2;
   // per launch: the attribute and the SM count belong to the current device
-  if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSmemBytes) != cudaSuccess)
+  if (allow_max_smem(tc_gemm_kernel) != cudaSuccess)
     return -3;
   TcArgs args{M, N, K, C, add, beta, err};
   int dev = 0, nsm = 0;

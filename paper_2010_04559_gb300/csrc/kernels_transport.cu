@@ -610,7 +610,7 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
     const bool slots_ok = (long long)g.ny * 4 * seg_chunks <= 12LL * threads;
     if (smem <= 200 * 1024 && slots_ok) {
       auto launch = [&](auto kern) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(kern);
         kern<<<sc.ntask, threads, smem, st>>>(g, t, cd, sc, b, psi, G, nmat_s, chunk);
       };
       // copy slots per thread: exactly the chunks one level needs

@@ -130,7 +130,9 @@ def config4_batch(nprob=256, nmin=16, nmax=96, seed_k=4):
     cells per axis on the unit square, angular level ~ U{1..3} (Lin), per-cell
     sigma_t ~ lognormal(0, 0.7), HG g ~ U[0.7, 0.95] at order 2*level + 4,
     scatter ratio per problem ~ U[0.5, 0.95], centred unit source of side
-    0.25, vacuum; 2-level multigrid with coarse order min(N, 4)."""
+    0.25, vacuum; multigrid down to angular level 1 (the coarse mesh of the
+    128x128 workload) with coarse order min(N, 4); a level-1 problem is
+    preconditioned by the coarse Gauss-Seidel solve alone."""
     rng = _rng(4000 + seed_k)
     out = []
     for _ in range(nprob):
@@ -142,7 +144,8 @@ def config4_batch(nprob=256, nmin=16, nmax=96, seed_k=4):
         ss = st * rng.uniform(0.5, 0.95)
         g = rng.uniform(0.7, 0.95)
         q = _central_source(2, (n, n), (0, 0, 0), (1, 1, 1), 0.25)
-        mg = dict(nlevels=2, Nr=[N, min(N, 4)], nu_pre=1, nu_post=1, coarse_sweeps=10)
+        mg = dict(nlevels=level, Nr=[N] + [min(N, 4)] * (level - 1), nu_pre=1, nu_post=1,
+                  coarse_sweeps=10)
         out.append(problem(2, (n, n), st, ss, N, hg_moments(g, N), q, level, mg=mg))
     return out
 
