@@ -50,7 +50,6 @@ KERNEL_NAMES = {
 # DRAM bytes (read + write) per launch on this workload from the ncu captures
 # summarised under profiles/; a kernel changed since its capture has no entry
 TRAFFIC = {
-    "coarse_gs": 279.5e6,   # profiles/ncu_coarse_gs_rows_config2.md
     "sweep": 955.5e6,       # profiles/ncu_top_kernels_config2.md
     "scatter_tc": 554.3e6,  # profiles/ncu_top_kernels_config2.md
 }

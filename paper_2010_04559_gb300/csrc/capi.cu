@@ -377,10 +377,10 @@ int build_gs_rows(amgt_ctx* ctx) {
   const Geom g = level_geom(ctx, k);
   const int n32 = coarse_gs_rows_plan<float>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
                                              &L.rows_nmat_s[0], &L.rows_threads[0],
-                                             &L.rows_smem[0]);
+                                             &L.rows_smem[0], &L.rows_gbuf[0]);
   const int n64 = coarse_gs_rows_plan<double>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
                                               &L.rows_nmat_s[1], &L.rows_threads[1],
-                                              &L.rows_smem[1]);
+                                              &L.rows_smem[1], &L.rows_gbuf[1]);
   int nb = std::min(n32, n64);
   if (ctx->gs_grid_blocks > 0) nb = std::min(nb, ctx->gs_grid_blocks);
   if (nb <= 0) return AMGT_OK;
@@ -916,8 +916,8 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
       if (launch_coarse_gs_rows<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)),
                                    cell_data(ctx), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi,
                                    mom, store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax,
-                                   ctx->nmat, L.rows_nmat_s[pi], L.rows_threads[pi],
-                                   L.rows_smem[pi], L.d_rows,
+                                   ctx->nmat, L.rows_nmat_s[pi], L.rows_gbuf[pi],
+                                   L.rows_threads[pi], L.rows_smem[pi], L.d_rows,
                                    L.rows_nb, L.rows_rpb, L.d_faces, ctx->gs_tag,
                                    ctx->d_status, ctx->stream) == 0) {
         if (!ctx->capturing) ctx->gs_tag += (unsigned)sweeps;

@@ -45,7 +45,7 @@ struct Level {
   // materials whose block inverses fit in shared memory and the shared bytes,
   // per precision (blocks 0: not available)
   int rows_nb = 0, rows_rpb = 0;
-  int rows_nmat_s[2] = {0, 0}, rows_threads[2] = {0, 0};
+  int rows_nmat_s[2] = {0, 0}, rows_threads[2] = {0, 0}, rows_gbuf[2] = {0, 0};
   size_t rows_smem[2] = {0, 0};
   int* d_rows = nullptr;                      // [ndir][rows_nb][rows_rpb]
   unsigned long long* d_faces = nullptr;      // tagged face words between rows

@@ -143,18 +143,19 @@ int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData&
 // kernels_gs_rows.cu).  plan: returns the number of thread blocks that can be
 // resident at once (capped by the number of rows ny*nz; 0 if the shapes are
 // not supported) with the materials whose inverses fit in shared memory, the
-// threads and the shared bytes per block.  launch: returns 0 on a successful
+// threads, the shared bytes per block and the size of the per-cell prefetch
+// buffers for the other materials' inverses (0: read from global memory).  launch: returns 0 on a successful
 // launch.
 template <class T>
 int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
-                        int* threads, size_t* smem);
+                        int* threads, size_t* smem, int* gbuf);
 template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
                           T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, int threads, size_t smem, const int* rows,
-                          int nblocks, int rpb, unsigned long long* faces, unsigned tag0,
-                          int* err, cudaStream_t st);
+                          int nmat, int nmat_s, int gbuf, int threads, size_t smem,
+                          const int* rows, int nblocks, int rpb, unsigned long long* faces,
+                          unsigned tag0, int* err, cudaStream_t st);
 
 // detector-response gradients (kernels_adjoint.cu), FP64:
 // dsigt[c] = -sum_q lam_cq^T kron(N, M_q) psi_cq;

@@ -63,8 +63,11 @@ template <class T>
 struct RowsLayout {
   int Jv, Ev, Evp, NMp, Jp;
   size_t o_Tin, o_XFr, o_Xk, o_SLr, o_Ns, o_Ad, o_lj, o_lk, o_rhs, o_xold, o_buf, o_phs, o_xfc,
-      o_yup, bytes;
-  __host__ __device__ RowsLayout(int nmat_s, int Jmax, int nm, int S, int dim, int A, int ndir) {
+      o_yup, o_Tg, bytes;
+  // gbuf: elements of one prefetch buffer for a block inverse that is not
+  // staged (0: read those from global memory)
+  __host__ __device__ RowsLayout(int nmat_s, int Jmax, int nm, int S, int dim, int A, int ndir,
+                                 int gbuf) {
     const int vw = 16 / (int)sizeof(T);
     Jv = ((Jmax + vw - 1) / vw) * vw;
     Ev = S * Jv;
@@ -92,9 +95,25 @@ struct RowsLayout {
     o_phs = take((size_t)2 * S * NMp * t);
     o_xfc = take((size_t)(S / 2) * Jv * t);
     o_yup = take((size_t)(dim - 1) * (S / 2) * Jv * t);
+    o_Tg = take((size_t)2 * gbuf * t);
     bytes = o;
   }
 };
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// all but the most recent group complete
+__device__ __forceinline__ void cp_async_wait_prior() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 
 __device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -160,6 +179,7 @@ struct RowsArgs {
   const T* TinvT;        // [nmat][ndir][Emax (col)][Emax (row)]
   const T* SLD;          // [ndir][Jmax][Jmax]
   int Emax, Jmax, nmat, nmat_s;
+  int gbuf;              // > 0: inverses of unstaged materials prefetched into shared memory
   const int* rows;       // [ndir][nblocks][rpb] rows of each block, -1 padded
   int rpb;
   unsigned long long* faces;  // [dim-1][ndir][C][HS*Jmax][W] tagged words
@@ -179,7 +199,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   const int tid = threadIdx.x, NT = blockDim.x;
   const int qd = tid >> 2, l4 = tid & 3, NQ = NT >> 2;
   const int nb = gridDim.x, b = blockIdx.x;
-  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nm, S, DIM, A, ndir);
+  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nm, S, DIM, A, ndir, p.gbuf);
   // padded shapes: a direction's J unknowns per node are stored Jv apart
   const int Jv = Ly.Jv, Ev = Ly.Ev, Evp = Ly.Evp, NMp = Ly.NMp, Jp = Ly.Jp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -197,6 +217,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   T* phss = reinterpret_cast<T*>(smem_raw + Ly.o_phs);   // [2][S][NMp] by cell parity
   T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
   T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [NF][HS][Jv] y/z inflow
+  T* Tg = reinterpret_cast<T*>(smem_raw + Ly.o_Tg);      // [2][Emax (col)][Emax (row)]
   for (int i = tid; i < S * S; i += NT) Ns[i] = (T)g.Nmass[i];
   for (int i = tid; i < 2 * Ev; i += NT) bufs[i] = T(0);
   for (int i = tid; i < 2 * S * NMp; i += NT) phss[i] = T(0);
@@ -219,6 +240,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
     }
   };
   __syncthreads();
+  long long kc = 0;     // cells solved by this block (buffer parity)
   // prefetch registers for the next cell
   T pf[kRowsMaxU], px[kRowsMaxU], pm[kRowsMaxM];
   int pmat = 0;
@@ -252,6 +274,14 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
     }
     pmat = p.cd.mat[c];
     psig = (T)p.cd.sigma_s[c];
+    // the block inverse of an unstaged material into the free buffer
+    if (p.gbuf > 0 && pmat >= p.nmat_s) {
+      const char* src = reinterpret_cast<const char*>(
+          p.TinvT + ((size_t)pmat * ndir + d) * p.Emax * p.Emax);
+      char* dst = reinterpret_cast<char*>(Tg + (size_t)((kc + 1) & 1) * p.gbuf);
+      const int nchunk = p.Emax * p.Emax * (int)sizeof(T) / 16;
+      for (int i = tid; i < nchunk; i += NT) cp_async16(dst + 16 * i, src + 16 * i);
+    }
   };
   // Phi_c += X_d^T delta for the cell `cp` whose delta is in buffer `slot`;
   // also into the other buffer when the next cell is the same cell
@@ -281,11 +311,13 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   };
   {
     const int R0 = row_of(0, 0);
+    kc = -1;  // the first cell's inverse goes to buffer 0
     if (R0 >= 0 && p.sweeps > 0) prefetch(0, R0, 0);
+    cp_async_commit_group();
+    kc = 0;
   }
   long long last = -1;  // last cell solved
   bool pend = false;    // its moment update is still to be done
-  long long kc = 0;     // cells solved by this block (buffer parity)
   for (int sw = 0; sw < p.sweeps; ++sw) {
     const unsigned tag = p.tag0 + (unsigned)sw + 1u;
     for (int d = 0; d < ndir; ++d) {
@@ -408,6 +440,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
             }
             if (more) prefetch(d2, R2, k2);
             else c_next = -2;
+            cp_async_commit_group();  // one group per cell, possibly empty
           }
           for (int base = 0; base < Ev; base += NQ) {
             const int pe = base + qd;
@@ -473,6 +506,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
             for (int i = 0; i < S; ++i) mix += Ns[l * S + i] * buf[i * Jv + j];
             rhs[pe] = val + sig_s * mix;
           }
+          cp_async_wait_prior();  // this cell's inverse (the next cell's may still fly)
           __syncthreads();
           // ---- 4: x_new = Tinv rhs (four lanes per row); outputs
           for (int base = 0; base < Ev; base += NQ) {
@@ -483,6 +517,13 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
               if (mat < p.nmat_s) {
                 const T* row = Tin + ((size_t)mat * Ev + pe) * Evp;
                 for (int ch = l4 * VW; ch < Ev; ch += 4 * VW) a += V16<T>::dot(row + ch, rhs + ch);
+              } else if (p.gbuf > 0) {
+                const int r = (lj >> 16) * J + (lj & 0xffff);
+                const T* col = Tg + (size_t)(kc & 1) * p.gbuf + r;
+                for (int cc = l4; cc < E; cc += 4) {
+                  const int lc = cc / J;
+                  a += col[(size_t)cc * p.Emax] * rhs[lc * Jv + (cc - lc * J)];
+                }
               } else {
                 const int r = (lj >> 16) * J + (lj & 0xffff);
                 const T* col = p.TinvT + ((size_t)mat * ndir + d) * p.Emax * p.Emax + r;
@@ -525,6 +566,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
     }
   }
   if (pend) update_moments(last, (int)((kc - 1) & 1), false);
+  cp_async_wait_all();
 }
 
 template <class T, int DIM, int A>
@@ -560,20 +602,30 @@ int rows_max_blocks(int threads, size_t smem) {
 
 template <class T>
 int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
-                        int* threads, size_t* smem) {
+                        int* threads, size_t* smem, int* gbuf) {
   if (g.a != 1 && g.a != 3) return 0;
   const int S = g.s;
   // four lanes per padded unknown and per moment, within one block
-  const RowsLayout<T> l0(0, Jmax, nmom, S, g.dim, g.a, ndir);
+  const RowsLayout<T> l0(0, Jmax, nmom, S, g.dim, g.a, ndir, 0);
   int nt = 4 * std::max(l0.Ev, S * nmom);
   nt = std::max(128, std::min(kRowsMaxThreads, (nt + 31) / 32 * 32));
   if (l0.Ev > kRowsMaxU * nt || S * nmom > kRowsMaxM * nt || (g.dim - 1) * (S / 2) * Jmax > nt ||
       g.nx < 1)
     return 0;
+  // materials whose inverses are staged per direction; the others are
+  // prefetched cell by cell into two buffers (when those fit)
+  const int Emax = S * Jmax;
+  int gb = 0;
+  auto bytes_for = [&](int ns) {
+    return RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir, ns < nmat ? gb : 0).bytes;
+  };
+  gb = Emax * Emax;
+  if (RowsLayout<T>(0, Jmax, nmom, S, g.dim, g.a, ndir, gb).bytes > 200 * 1024) gb = 0;
   int ns = nmat;
-  while (ns > 0 && RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir).bytes > 200 * 1024) --ns;
-  const size_t bytes = RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir).bytes;
+  while (ns > 0 && bytes_for(ns) > 200 * 1024) --ns;
+  const size_t bytes = bytes_for(ns);
   if (bytes > 200 * 1024) return 0;
+  *gbuf = ns < nmat ? gb : 0;
   int nb;
   if (g.dim == 2)
     nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(nt, bytes) : rows_max_blocks<T, 2, 1>(nt, bytes);
@@ -590,11 +642,11 @@ template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
                           T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, int threads, size_t smem, const int* rows,
-                          int nblocks, int rpb, unsigned long long* faces, unsigned tag0,
-                          int* err, cudaStream_t st) {
+                          int nmat, int nmat_s, int gbuf, int threads, size_t smem,
+                          const int* rows, int nblocks, int rpb, unsigned long long* faces,
+                          unsigned tag0, int* err, cudaStream_t st) {
   RowsArgs<T> a{g, t, cd, ndir, dir_begin, dir_end, sweeps, f, phi, mom, TinvT, SLD,
-                Emax, Jmax, nmat, nmat_s, rows, rpb, faces, tag0, err};
+                Emax, Jmax, nmat, nmat_s, gbuf, rows, rpb, faces, tag0, err};
   cudaError_t e;
   if (g.dim == 2)
     e = g.a == 3 ? rows_launch<T, 2, 3>(a, nblocks, threads, smem, st)
@@ -610,17 +662,19 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
   return 0;
 }
 
-template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, int*, int*, size_t*);
-template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, int*, int*, size_t*);
+template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, int*, int*, size_t*,
+                                        int*);
+template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, int*, int*, size_t*,
+                                         int*);
 template int launch_coarse_gs_rows<float>(const Geom&, const LevelDev<float>&, const CellData&, int,
                                           const int*, const int*, int, const float*, float*,
                                           float*, const float*, const float*, int, int, int, int,
-                                          int, size_t, const int*, int, int, unsigned long long*,
-                                          unsigned, int*, cudaStream_t);
+                                          int, int, size_t, const int*, int, int,
+                                          unsigned long long*, unsigned, int*, cudaStream_t);
 template int launch_coarse_gs_rows<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                            int, const int*, const int*, int, const double*,
                                            double*, double*, const double*, const double*, int,
-                                           int, int, int, int, size_t, const int*, int, int,
+                                           int, int, int, int, int, size_t, const int*, int, int,
                                            unsigned long long*, unsigned, int*, cudaStream_t);
 
 }  // namespace amgt
