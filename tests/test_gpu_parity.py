@@ -424,3 +424,25 @@ def test_two_contexts_with_different_geometry_interleaved():
         assert _rel(_host(yb), Tb.apply_A(xb)) < 1e-12
     ca.close()
     cb.close()
+
+
+def test_fokker_planck_equivalent_moments_solve():
+    """The paper's Fokker-Planck-equivalent Legendre moments (alpha = 1,
+    N = 6: sigma_{s,0} = 21, strongly forward-peaked) with absorption 1:
+    multigrid-preconditioned FP64 solve against the oracle."""
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_MG
+    s0, f = W.fp_moments(1.0, 6)
+    prob = _mg_problem(2, (8, 7), 2, "lin", 3, [6, 4, 3], sweeps=10, seed=57)
+    C = 8 * 7
+    prob["sigma_s"] = np.full(C, s0)
+    prob["sigma_t"] = np.full(C, s0 + 1.0)
+    prob["fmom"] = f
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    xo, _, _, _ = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 2000)
+    ctx = _ctx(prob)
+    psi, phi, st, _ = ctx.amgt_solve(tol=1e-13, restart=20, maxit=2000, precond=AMGT_PREC_MG,
+                                     mode=AMGT_MODE_F64)
+    assert st.relres < 1e-13
+    assert _rel(psi, xo) < 1e-9
+    ctx.close()

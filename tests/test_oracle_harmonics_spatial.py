@@ -72,6 +72,31 @@ def test_hg_moments_are_legendre_moments(g):
         assert abs(val - f[n]) < 1e-10
 
 
+@pytest.mark.parametrize("alpha,N", [(1.0, 4), (0.5, 12), (2.0, 24)])
+def test_fp_equivalent_moments(alpha, N):
+    # the momentum-transfer cross section sigma_{s,0} - sigma_{s,1} equals
+    # alpha (Sec. 5: a transport cross section of 1 means alpha = 1); the
+    # expansion vanishes at n = N, and sigma_{s,0} - sigma_{s,n} grows with
+    # the Laplace-Beltrami eigenvalues n(n+1), checked on a harmonic: the
+    # surface Laplacian of P_n(mu) is -n(n+1) P_n(mu)
+    s0, f = W.fp_moments(alpha, N)
+    sn = s0 * f
+    assert abs((sn[0] - sn[1]) - alpha) < 1e-12 * max(1.0, s0)
+    assert abs(sn[N]) < 1e-12 * s0 and abs(f[0] - 1.0) < 1e-15
+    import sympy
+    x = sympy.symbols("x")
+    mu = [sympy.Rational(k, 10) for k in (-9, -4, 0, 3, 8)]
+    for n in range(N + 1):
+        # (1 - x^2) P'' - 2 x P' is the surface Laplacian of a zonal function
+        # (exact rational arithmetic)
+        p = sympy.legendre(n, x)
+        lap = (1 - x ** 2) * sympy.diff(p, x, 2) - 2 * x * sympy.diff(p, x)
+        lam = sn[0] - sn[n]
+        for m in mu:
+            v = float(0.5 * alpha * lap.subs(x, m)) + lam * float(p.subs(x, m))
+            assert abs(v) < 1e-9 * max(1.0, lam)
+
+
 def _m1(h):
     return h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
 

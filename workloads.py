@@ -37,6 +37,17 @@ def hg_moments(g, N):
     return np.array([g ** n for n in range(N + 1)], dtype=np.float64)
 
 
+def fp_moments(alpha, N):
+    """Fokker-Planck-equivalent Legendre moments (Sec. 2.4): sigma_{s,n} =
+    alpha/2 (N(N+1) - n(n+1)), n = 0..N.  Returns (sigma_{s,0}, the shape
+    f_n = sigma_{s,n} / sigma_{s,0}); sigma_{s,0} - sigma_{s,n} is alpha/2
+    times the eigenvalue n(n+1) of the Laplace-Beltrami operator, so the
+    truncated expansion acts like alpha/2 times angular diffusion."""
+    s0 = 0.5 * alpha * N * (N + 1)
+    sn = np.array([0.5 * alpha * (N * (N + 1) - n * (n + 1)) for n in range(N + 1)])
+    return s0, sn / s0
+
+
 def _central_source(dim, ncell, lo, hi, width, strength=1.0):
     """Unit isotropic source in the centred box of side `width` (cell-aligned
     when the mesh is)."""
