@@ -81,7 +81,12 @@ typedef struct amgt_options {
                           0.3 tol / (current relres), within [3e-5, 1e-2],
                           and stops after 2 restart cycles at most          */
   int inner_maxit;     /* mixed mode: cap per inner solve                      */
+  int krylov;          /* AMGT_KRYLOV_GMRES (restarted GMRES(restart)) or
+                          AMGT_KRYLOV_BICGSTAB (the paper's method, Sec. 3);
+                          in mixed mode it is the inner FP32 solver          */
 } amgt_options;
+#define AMGT_KRYLOV_GMRES 0
+#define AMGT_KRYLOV_BICGSTAB 1
 
 #define AMGT_MAX_HIST 1024
 typedef struct amgt_stats {

@@ -42,6 +42,7 @@ AMGT_TUNE_GS_GRID_BLOCKS = 4
 AMGT_TUNE_GS_CLUSTER = 5
 AMGT_TUNE_KERNEL_TIMERS = 6
 AMGT_TUNE_GRAPHS = 7
+AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
 
@@ -65,7 +66,7 @@ class amgt_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("precond", ctypes.c_int), ("mode", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("inner_maxit", ctypes.c_int)]
+                ("inner_maxit", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class amgt_stats(ctypes.Structure):
@@ -263,11 +264,14 @@ class Context:
 
     def amgt_solve(self, tol=1e-8, restart=20, maxit=1000, precond=AMGT_PREC_MG,
                    mode=AMGT_MODE_F64, x0=None, psi=None, phi=None, device_ptrs=False,
-                   inner_tol=0.0, inner_maxit=200, allow_not_converged=False):
+                   inner_tol=0.0, inner_maxit=200, allow_not_converged=False,
+                   krylov=0):
         """Host mode: x0/psi/phi are NumPy float64 arrays (psi/phi allocated when
-        None).  Device mode: torch CUDA float64 tensors."""
+        None).  Device mode: torch CUDA float64 tensors.  krylov: 0 GMRES,
+        1 BiCGStab."""
         opt = amgt_options(float(tol), int(restart), int(maxit), int(precond), int(mode),
-                           1 if device_ptrs else 0, float(inner_tol), int(inner_maxit))
+                           1 if device_ptrs else 0, float(inner_tol), int(inner_maxit),
+                           int(krylov))
         st = amgt_stats()
         nsdof, nadof = self.amgt_query_sizes(0)
         if device_ptrs:
@@ -407,7 +411,7 @@ def amgt_solve_batch(contexts, psis, phis=None, tol=1e-8, restart=20, maxit=1000
     torch CUDA float64 tensors `psis` (and `phis`); returns the stats list."""
     n = len(contexts)
     opt = amgt_options(float(tol), int(restart), int(maxit), int(precond), int(mode), 1,
-                       float(inner_tol), int(inner_maxit))
+                       float(inner_tol), int(inner_maxit), 0)
     hs = (_P * n)(*[c.h for c in contexts])
     pp = (_P * n)(*[_dptr(p).value for p in psis])
     pf = (_P * n)(*[_dptr(p).value for p in phis]) if phis is not None else None

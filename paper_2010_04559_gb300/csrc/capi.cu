@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -1187,6 +1188,133 @@ int gmres(amgt_ctx* ctx, int k, OpA apply_A, OpM apply_M, const T* b, T* x, bool
   return AMGT_OK;
 }
 
+// inner products <vecs[i], w>, i < vecs.size() <= 8, in FP64, on the host
+template <class T>
+int dots_with(amgt_ctx* ctx, long long n, std::initializer_list<const T*> vecs, const T* w,
+              double* out) {
+  const int nv = (int)vecs.size();
+  const T* arr[8];
+  int i = 0;
+  for (const T* v : vecs) arr[i++] = v;
+  void** slot = ctx->d_ptrs + 200;
+  CK(cudaMemcpyAsync(slot, arr, sizeof(void*) * nv, cudaMemcpyHostToDevice, ctx->stream));
+  launch_multidot<T>(n, nv, reinterpret_cast<const T* const*>(slot), w, ctx->d_partials,
+                     gemv_blocks(n), ctx->d_dots, ctx->stream);
+  CK(cudaGetLastError());
+  return dev_dots<T>(ctx, nv, out);
+}
+
+// Right-preconditioned BiCGStab (Sec. 3): shadow residual = initial residual,
+// a BiCG step along M^-1 p and a minimal-residual step along M^-1 s per
+// iteration; stops on the recursive residual and reports the true one.  A
+// vanishing <r^, r> restarts from the current iterate.
+template <class T, class OpA, class OpM>
+int bicgstab(amgt_ctx* ctx, int k, OpA apply_A, OpM apply_M, const T* b, T* x, bool x_zero,
+             double tol, int maxit, KrylovResult& res, amgt_stats* st, double bnorm_in,
+             int hist_base) {
+  const long long n = ctx->lv[k].nsdof * ctx->lv[k].nadof();
+  const size_t bytes = (size_t)n * sizeof(T);
+  T *r, *rh, *p, *v, *s, *t, *ph, *sh;
+  TRY(wsvec<T>(ctx, k, 8, &r));
+  TRY(wsvec<T>(ctx, k, 9, &rh));
+  TRY(wsvec<T>(ctx, k, 10, &p));
+  TRY(wsvec<T>(ctx, k, 11, &v));
+  TRY(wsvec<T>(ctx, k, 12, &s));
+  TRY(wsvec<T>(ctx, k, 13, &t));
+  TRY(wsvec<T>(ctx, k, 14, &ph));
+  TRY(wsvec<T>(ctx, k, 15, &sh));
+  double bnorm = bnorm_in;
+  if (bnorm < 0) TRY(norm2<T>(ctx, b, n, &bnorm));
+  res = KrylovResult();
+  res.cycles = 1;
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
+    return AMGT_OK;
+  }
+  if (!std::isfinite(bnorm)) return fail(ctx, AMGT_ERR_NAN, "right-hand side is not finite");
+  auto residual = [&]() -> int {  // r = b - A x
+    if (x_zero) {
+      CK(cudaMemcpyAsync(r, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
+      x_zero = false;
+    } else {
+      TRY(apply_A(x, r));
+      launch_axpby<T>(n, 1.0, b, -1.0, r, ctx->stream);
+    }
+    return AMGT_OK;
+  };
+  TRY(residual());
+  double rr;
+  TRY(norm2<T>(ctx, r, n, &rr));
+  res.relres = rr / bnorm;
+  double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+  bool fresh = true;  // shadow residual and directions to (re)set
+  while (res.relres >= tol && res.its < maxit) {
+    if (fresh) {
+      CK(cudaMemcpyAsync(rh, r, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      CK(cudaMemsetAsync(p, 0, bytes, ctx->stream));
+      CK(cudaMemsetAsync(v, 0, bytes, ctx->stream));
+      rho_old = alpha = omega = 1.0;
+      fresh = false;
+    }
+    double rho;
+    TRY(dots_with<T>(ctx, n, {rh}, r, &rho));
+    if (!std::isfinite(rho)) return fail(ctx, AMGT_ERR_NAN, "BiCGStab inner product is not finite");
+    if (rho == 0.0) {
+      fresh = true;
+      continue;
+    }
+    const double beta = (rho / rho_old) * (alpha / omega);
+    launch_axpby<T>(n, -omega, v, 1.0, p, ctx->stream);  // p = r + beta (p - omega v)
+    launch_axpby<T>(n, 1.0, r, beta, p, ctx->stream);
+    TRY(apply_M(p, ph));
+    TRY(apply_A(ph, v));
+    double rhv;
+    TRY(dots_with<T>(ctx, n, {rh}, v, &rhv));
+    if (rhv == 0.0) return fail(ctx, AMGT_ERR_BREAKDOWN, "BiCGStab: <r^, v> = 0");
+    alpha = rho / rhv;
+    launch_scale_copy<T>(n, 1.0, r, s, ctx->stream);  // s = r - alpha v
+    launch_axpby<T>(n, -alpha, v, 1.0, s, ctx->stream);
+    double ss;
+    TRY(dots_with<T>(ctx, n, {s}, s, &ss));
+    res.its++;
+    const double srel = std::sqrt(std::max(ss, 0.0)) / bnorm;
+    if (srel < tol) {
+      launch_axpby<T>(n, alpha, ph, 1.0, x, ctx->stream);
+      res.relres = srel;
+      if (st && hist_base + res.its - 1 < AMGT_MAX_HIST) {
+        st->hist[hist_base + res.its - 1] = srel;
+        st->nhist = hist_base + res.its;
+      }
+      break;
+    }
+    TRY(apply_M(s, sh));
+    TRY(apply_A(sh, t));
+    double ts[2];
+    TRY(dots_with<T>(ctx, n, {s, t}, t, ts));  // <s, t>, <t, t>
+    if (ts[1] == 0.0) return fail(ctx, AMGT_ERR_BREAKDOWN, "BiCGStab: t = 0");
+    omega = ts[0] / ts[1];
+    launch_axpby<T>(n, alpha, ph, 1.0, x, ctx->stream);  // x += alpha ph + omega sh
+    launch_axpby<T>(n, omega, sh, 1.0, x, ctx->stream);
+    launch_scale_copy<T>(n, 1.0, s, r, ctx->stream);  // r = s - omega t
+    launch_axpby<T>(n, -omega, t, 1.0, r, ctx->stream);
+    TRY(dots_with<T>(ctx, n, {r}, r, &rr));
+    res.relres = std::sqrt(std::max(rr, 0.0)) / bnorm;
+    if (!std::isfinite(res.relres)) return fail(ctx, AMGT_ERR_NAN, "residual is not finite");
+    if (st && hist_base + res.its - 1 < AMGT_MAX_HIST) {
+      st->hist[hist_base + res.its - 1] = res.relres;
+      st->nhist = hist_base + res.its;
+    }
+    rho_old = rho;
+    if (omega == 0.0) fresh = true;
+  }
+  // the true residual decides
+  TRY(residual());
+  TRY(norm2<T>(ctx, r, n, &rr));
+  res.relres = rr / bnorm;
+  return AMGT_OK;
+}
+
 }  // namespace
 
 // =================================================================== C ABI
@@ -1778,6 +1906,8 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
                double* phi, amgt_stats* st) {
   if (!ctx) return AMGT_ERR_ARG;
   if (!opt || !psi) return fail(ctx, AMGT_ERR_ARG, "options and psi are required");
+  if (opt->krylov != AMGT_KRYLOV_GMRES && opt->krylov != AMGT_KRYLOV_BICGSTAB)
+    return fail(ctx, AMGT_ERR_ARG, "krylov: AMGT_KRYLOV_GMRES or AMGT_KRYLOV_BICGSTAB");
   TRY(build(ctx));
   const auto t0 = std::chrono::steady_clock::now();
   if (st) std::memset(st, 0, sizeof(*st));
@@ -1819,7 +1949,10 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       CK(cudaMemcpyAsync(z, v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       return AMGT_OK;
     };
-    rc = gmres<double>(ctx, 0, A64, M64, b, x, x_zero, opt->tol, m, maxit, kr, st, -1.0, 0);
+    if (opt->krylov == AMGT_KRYLOV_BICGSTAB)
+      rc = bicgstab<double>(ctx, 0, A64, M64, b, x, x_zero, opt->tol, maxit, kr, st, -1.0, 0);
+    else
+      rc = gmres<double>(ctx, 0, A64, M64, b, x, x_zero, opt->tol, m, maxit, kr, st, -1.0, 0);
     if (st) {
       st->iterations = kr.its;
       st->outer_iterations = kr.cycles;
@@ -1874,8 +2007,12 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       launch_convert<double, float>(n, r64, r32, ctx->stream);
       launch_scale_copy<float>(n, 1.0 / rn, r32, r32, ctx->stream);
       KrylovResult ik;
-      rc = gmres<float>(ctx, 0, A32, M32, r32, e32, true, inner_tol_for(relres), m,
-                        std::min(imax_solve, maxit - total_its), ik, st, 1.0, total_its);
+      if (opt->krylov == AMGT_KRYLOV_BICGSTAB)
+        rc = bicgstab<float>(ctx, 0, A32, M32, r32, e32, true, inner_tol_for(relres),
+                             std::min(imax_solve, maxit - total_its), ik, st, 1.0, total_its);
+      else
+        rc = gmres<float>(ctx, 0, A32, M32, r32, e32, true, inner_tol_for(relres), m,
+                          std::min(imax_solve, maxit - total_its), ik, st, 1.0, total_its);
       if (rc != AMGT_OK) break;
       total_its += ik.its;
       // x += rn * e  (FP64 accumulate)

@@ -446,3 +446,28 @@ def test_fokker_planck_equivalent_moments_solve():
     assert st.relres < 1e-13
     assert _rel(psi, xo) < 1e-9
     ctx.close()
+
+
+@pytest.mark.parametrize("precond", ["sweep", "mg"])
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_bicgstab_solve_matches_oracle(precond, mode):
+    """The paper's Krylov method (Sec. 3): right-preconditioned BiCGStab with
+    the sweep or the multigrid cycle, FP64 or as the inner FP32 solver of the
+    mixed refinement, against the oracle's BiCGStab solution."""
+    from oracle import bicgstab
+    from paper_2010_04559_gb300 import (AMGT_KRYLOV_BICGSTAB, AMGT_MODE_F64, AMGT_MODE_MIXED,
+                                        AMGT_PREC_MG, AMGT_PREC_SWEEP)
+    prob = _mg_problem(2, (8, 7), 2, "lin", 3, [8, 4, 4], sweeps=10, seed=61)
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    xo, _, _, rel = bicgstab.bicgstab(T.apply_A, T.source(), T.sweep, 1e-13, 1000)
+    assert rel < 1e-12
+    ctx = _ctx(prob)
+    pc = AMGT_PREC_SWEEP if precond == "sweep" else AMGT_PREC_MG
+    md = AMGT_MODE_F64 if mode == "f64" else AMGT_MODE_MIXED
+    tol = 1e-13 if mode == "f64" else 1e-10
+    psi, phi, st, _ = ctx.amgt_solve(tol=tol, maxit=1000, precond=pc, mode=md,
+                                     krylov=AMGT_KRYLOV_BICGSTAB)
+    assert st.relres < tol
+    assert _rel(psi, xo) < (1e-10 if mode == "f64" else 1e-6)
+    ctx.close()
