@@ -157,7 +157,14 @@ int amgt_set_multigrid(amgt_ctx* ctx, int nlevels, const int* Nr, int nu_pre,
 /* Isotropic volumetric source: q[C] scalar emission density, Q = q/(4 pi). */
 int amgt_set_source_iso(amgt_ctx* ctx, const double* q);
 /* Boundary face f = 2*axis + side (side 1 = high): kind 0 vacuum, kind 1
- * isotropic inflow of angular flux params[0]. */
+ * isotropic inflow of angular flux params[0], kind 2 a normally incident
+ * pencil beam of strength S = params[0] (particles per unit face area),
+ * uniform over the face (Sec. 5.4): psi_b = S delta(Omega - Omega_b) with
+ * Omega_b the inward normal, taken in the DG weak form.  Omega_b is a vertex
+ * of k = 4 patches; each receives S Psi_m(Omega_b) / k times the face
+ * integral of the spatial basis function.  params is read at the call
+ * (needs params[0] for kinds 1 and 2); AMGT_ERR_ARG for a face or kind out of
+ * range. */
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 /* Kernel tuning knobs (results do not depend on them beyond rounding):
  *   AMGT_TUNE_GS_KERNEL   0 auto, 1 per-patch coarse Gauss-Seidel kernel,

@@ -51,6 +51,9 @@ class ReversedMesh:
         self.octant = am.octant ^ 7
         self.M = am.M
         self.w = am.w
+        # patch q covers -D_q: vertices negated, same basis
+        self.verts = -am.verts
+        self.basis = am.basis
 
     def X(self, N):
         return self._am.X(N)

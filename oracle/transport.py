@@ -27,6 +27,15 @@ Readings
 * The isotropic source q is a scalar emission density: Q(r, Omega) = q/(4 pi).
 * An isotropic inflow of angular flux psi_b on a boundary face adds
   -psi_b int_face Phi_l int_{D_q} (Omega.n) Psi_m to f for inflow patches.
+* A normally incident pencil beam (Sec. 5.4: Dirac boundary data taken in the
+  DG weak form) of strength S on a face with outward normal n is
+  psi_b = S delta(Omega - Omega_b), Omega_b = -n, uniform over the face.  Its
+  inflow term is -S int_face Phi_l (Omega_b.n) Psi_m(Omega_b) for a patch
+  holding Omega_b.  Omega_b is a vertex of k patches (k = 4: the octahedron
+  vertex keeps a right angle in each of the 4 octants around it at every
+  level), and the Dirac mass is split equally, 1/k to each; this is the limit
+  of a uniform inflow over a shrinking cap around Omega_b, each of whose
+  quarters lies in one of those patches.
 """
 import itertools
 
@@ -34,6 +43,20 @@ import numpy as np
 
 from . import angular, harmonics
 from .spatial import Q1Cell
+
+
+def beam_weights(amesh, omega_b):
+    """wb[P, a]: Psi_[q]m(omega_b) / k on the k patches whose closed spherical
+    triangle holds omega_b, zero elsewhere (the Dirac mass split equally
+    among them).  A patch holds omega_b iff omega_b is a non-negative
+    combination of its vertices."""
+    wb = np.zeros((amesh.P, amesh.a))
+    hits = [q for q in range(amesh.P)
+            if np.linalg.solve(amesh.verts[q].T, omega_b).min() > -1e-12]
+    for q in hits:
+        wb[q] = angular.basis_eval(amesh.verts[q], amesh.octant[q], amesh.basis,
+                                   omega_b) / len(hits)
+    return wb
 
 
 class Transport:
@@ -209,11 +232,22 @@ class Transport:
         for f, (kind, val) in enumerate(self.prob["boundary"]):
             if kind == 0:
                 continue
-            if kind != 1:
-                raise ValueError("oracle supports vacuum and isotropic inflow")
+            if kind not in (1, 2):
+                raise ValueError("oracle supports vacuum, isotropic inflow and the beam")
             xi, side = divmod(f, 2)
             sgn = 2.0 * side - 1.0
             inflow = ~self.outflow[f]
+            if kind == 2:
+                n = np.zeros(3)
+                n[xi] = sgn
+                omega_b = -n
+                wb = beam_weights(self.am, omega_b)       # Psi_m(Omega_b) / k
+                assert not wb[~inflow].any()
+                term = -val * (omega_b @ n) * self.cell.mf[f][None, :, None] * wb[:, None, :]
+                for c in range(self.C):
+                    if self.neighbour(c, f) < 0:
+                        fb[c] += term
+                continue
             ndotpsi = sgn * self.am.Aw[:, xi, :]          # int (Omega.n) Psi_m
             for c in range(self.C):
                 if self.neighbour(c, f) >= 0:

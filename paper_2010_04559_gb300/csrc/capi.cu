@@ -414,6 +414,45 @@ int build_gs_rows(amgt_ctx* ctx) {
   return AMGT_OK;
 }
 
+// Pencil beam on face f (kind 2, Sec. 5.4): psi_b = S delta(Omega - Omega_b)
+// with Omega_b = -n the inward normal, taken in the DG weak form.  Its inflow
+// term on a boundary cell is -S int_face Phi_l (Omega_b.n) Psi_m(Omega_b) =
+// S mf_l Psi_m(Omega_b) on a patch holding Omega_b.  Omega_b is an octahedron
+// vertex, hence a vertex of one patch in each of the 4 octants around it at
+// every refinement level; the Dirac mass is split equally among those k
+// patches.  Table: beam[f][q a + m] = S Psi_[q]m(Omega_b) / k.  Adjoint
+// contexts hold reversed directions, so their patch q covers -D_q.
+int build_beam(amgt_ctx* ctx, Level& Lv, int dim) {
+  bool any = false;
+  for (int f = 0; f < 2 * dim; ++f) any |= ctx->bkind[f] == 2;
+  if (!any) return AMGT_OK;
+  const int a = Lv.mesh.a, nadof = Lv.mesh.nadof();
+  const double sg = ctx->adjoint ? -1.0 : 1.0;
+  std::vector<double> beam((size_t)2 * dim * nadof, 0.0);
+  for (int f = 0; f < 2 * dim; ++f) {
+    if (ctx->bkind[f] != 2) continue;
+    double ob[3] = {0.0, 0.0, 0.0};
+    ob[f / 2] = (f & 1) ? -1.0 : 1.0;
+    std::vector<int> hits;
+    for (int q = 0; q < Lv.mesh.P; ++q)
+      for (int v = 0; v < 3; ++v) {
+        const double* x = Lv.mesh.patch[q].v[v];
+        if (std::fabs(sg * x[0] - ob[0]) + std::fabs(sg * x[1] - ob[1]) +
+                std::fabs(sg * x[2] - ob[2]) < 1e-12)
+          hits.push_back(q);
+      }
+    if (hits.empty()) return fail(ctx, AMGT_ERR_UNSUPPORTED, "beam direction is no patch vertex");
+    for (int q : hits) {
+      const double om[3] = {sg * ob[0], sg * ob[1], sg * ob[2]};
+      double psi[3];
+      basis_values(Lv.mesh, q, om, psi);
+      for (int m = 0; m < a; ++m)
+        beam[(size_t)f * nadof + q * a + m] = ctx->bval[f] * psi[m] / (double)hits.size();
+    }
+  }
+  return upload(ctx, beam, &Lv.d_beam);
+}
+
 int build(amgt_ctx* ctx) {
   if (!ctx->dirty) return AMGT_OK;
   drop_graphs(ctx);
@@ -595,6 +634,7 @@ int build(amgt_ctx* ctx) {
     TRY(make_sweep_tasks(ctx, Lv, g, 0));
     TRY(upload(ctx, Lv.pdir, &Lv.d_pdir));
     TRY(upload(ctx, Lv.octant, &Lv.d_octant));
+    TRY(build_beam(ctx, Lv, dim));
     TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
     TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));
@@ -828,7 +868,7 @@ template <class T>
 int source_impl(amgt_ctx* ctx, int k, T* f) {
   const Level& L = ctx->lv[k];
   launch_source<T>(level_geom(ctx, k), store<T>(L).w, store<T>(L).Aw, L.d_octant, ctx->d_q,
-                   ctx->d_bval, ctx->d_bkind, ctx->d_mu, ctx->d_mf, f, ctx->stream);
+                   ctx->d_bval, ctx->d_bkind, L.d_beam, ctx->d_mu, ctx->d_mf, f, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1527,11 +1567,12 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q) {
 
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
   if (!ctx) return AMGT_ERR_ARG;
-  if (face < 0 || face >= 6 || kind < 0 || kind > 1)
-    return fail(ctx, AMGT_ERR_ARG, "face 0..5, kind 0 (vacuum) or 1 (isotropic inflow)");
-  if (kind == 1 && !params) return fail(ctx, AMGT_ERR_ARG, "inflow needs params[0]");
+  if (face < 0 || face >= 6 || kind < 0 || kind > 2)
+    return fail(ctx, AMGT_ERR_ARG,
+                "face 0..5, kind 0 (vacuum), 1 (isotropic inflow) or 2 (pencil beam)");
+  if (kind != 0 && !params) return fail(ctx, AMGT_ERR_ARG, "inflow needs params[0]");
   ctx->bkind[face] = kind;
-  ctx->bval[face] = kind == 1 ? params[0] : 0.0;
+  ctx->bval[face] = kind != 0 ? params[0] : 0.0;
   ctx->dirty = true;
   return AMGT_OK;
 }

@@ -56,6 +56,8 @@ struct Level {
   LevelDevStore<float> d32;
   __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path
   int *d_pdir = nullptr, *d_octant = nullptr, *d_dbeg = nullptr, *d_dend = nullptr;
+  // pencil-beam inflow weights [2 dim][nadof] (null without a beam face)
+  double* d_beam = nullptr;
   // transfer to the next coarser level
   int *d_parent = nullptr, *d_cbeg = nullptr, *d_cend = nullptr;
   std::vector<int> task_dir, task_q0, task_nq;

@@ -112,7 +112,8 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 template <class T>
 void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant,
                    const double* q, const double* bnd_val, const int* bnd_kind,
-                   const double* mu, const double* mf, T* f, cudaStream_t st);
+                   const double* beam, const double* mu, const double* mf, T* f,
+                   cudaStream_t st);
 template <class T>
 void launch_scalar_flux(long long nsdof, int nadof, const T* w, const T* psi, T* phi,
                         cudaStream_t st);

@@ -474,13 +474,15 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, 
   }
 }
 
-// f[c*s+l][q*a+m] = q_c/(4 pi) mu_l w_qm + boundary inflow terms
+// f[c*s+l][q*a+m] = q_c/(4 pi) mu_l w_qm + boundary inflow terms (isotropic
+// inflow from the per-patch current integrals Aw, the pencil beam from its
+// per-face table)
 template <class T>
 __global__ void source_kernel(Geom g, const T* __restrict__ w, const T* __restrict__ Aw,
                               const int* __restrict__ octant, const double* __restrict__ qsrc,
                               const double* __restrict__ bval, const int* __restrict__ bkind,
-                              const double* __restrict__ mu, const double* __restrict__ mf,
-                              T* __restrict__ f) {
+                              const double* __restrict__ beam, const double* __restrict__ mu,
+                              const double* __restrict__ mf, T* __restrict__ f) {
   const long long total = g.nsdof * g.nadof;
   const int a = g.a, s = g.s;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -497,8 +499,12 @@ __global__ void source_kernel(Geom g, const T* __restrict__ w, const T* __restri
     for (int xi = 0; xi < g.dim; ++xi) {
       for (int side = 0; side < 2; ++side) {
         const int face = 2 * xi + side;
-        if (bkind[face] != 1) continue;
+        if (bkind[face] == 0) continue;
         if (side == 0 ? ic[xi] != 0 : ic[xi] != n[xi] - 1) continue;
+        if (bkind[face] == 2) {  // pencil beam: S mf_l Psi_m(Omega_b) / k
+          v += beam[(size_t)face * g.nadof + j] * mf[face * s + l];
+          continue;
+        }
         // inflow iff the patch moves into the domain through this face
         const bool inflow = side == 0 ? (negb[xi] == 0) : (negb[xi] == 1);
         if (!inflow) continue;
@@ -658,11 +664,11 @@ void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T a
 
 template <class T>
 void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant, const double* q,
-                   const double* bval, const int* bkind, const double* mu, const double* mf,
-                   T* f, cudaStream_t st) {
+                   const double* bval, const int* bkind, const double* beam, const double* mu,
+                   const double* mf, T* f, cudaStream_t st) {
   note_launch();
   const int grid = grid_for(g.nsdof * g.nadof, 256);
-  source_kernel<T><<<grid, 256, 0, st>>>(g, w, Aw, octant, q, bval, bkind, mu, mf, f);
+  source_kernel<T><<<grid, 256, 0, st>>>(g, w, Aw, octant, q, bval, bkind, beam, mu, mf, f);
 }
 
 template <class T>
@@ -697,8 +703,8 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
   template void launch_source<T>(const Geom&, const T*, const T*, const int*, const double*,  \
-                                 const double*, const int*, const double*, const double*, T*, \
-                                 cudaStream_t);                                               \
+                                 const double*, const int*, const double*, const double*,     \
+                                 const double*, T*, cudaStream_t);                            \
   template void launch_scalar_flux<T>(long long, int, const T*, const T*, T*, cudaStream_t);  \
   template void launch_restrict<T>(long long, int, int, int, int, const int*, const int*,     \
                                    const T*, const T*, T*, cudaStream_t);                     \

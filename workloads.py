@@ -15,7 +15,9 @@ A problem is a dict with keys
   fmom           float64[N+1] moment shape f_n (sigma_{s,n} = sigma_s * f_n), f_0 = 1
   q              float64[C]  isotropic volumetric source (scalar emission density)
   boundary       list of 2*dim (kind, value): kind 0 vacuum, 1 isotropic inflow
-                 of angular flux `value`; face f = 2*axis + side (side 1 = high)
+                 of angular flux `value`, 2 normally incident pencil beam of
+                 strength `value` uniform over the face; face f = 2*axis + side
+                 (side 1 = high)
   basis          "lin" or "const"
   level          uniform angular level of the finest mesh
   mg             dict(nlevels, Nr (per level, finest first), nu_pre, nu_post,
@@ -181,3 +183,17 @@ def random_problem(dim, ncell, level, N, seed_k, basis="lin", g=0.8,
 def random_vector(shape, seed_k, dtype=np.float64):
     """Seeded standard-normal test vector."""
     return _rng(5000 + seed_k).standard_normal(shape).astype(dtype)
+
+
+def config5_beam(n=256, level=4, N=64, nlevels=4, Nr=12, g=0.98):
+    """2D unit square, n x n cells, sigma_t = 5, sigma_s = 4.95, HG g at order
+    N, a normally incident pencil beam of unit strength over the whole low-x
+    edge, vacuum elsewhere, no volumetric source, uniform angular level
+    `level`, `nlevels`-level multigrid with scatter order Nr below the finest
+    level."""
+    C = n * n
+    bnd = [(2, 1.0), (0, 0.0), (0, 0.0), (0, 0.0)]
+    mg = dict(nlevels=nlevels, Nr=[N] + [min(N, Nr)] * (nlevels - 1), nu_pre=1, nu_post=1,
+              coarse_sweeps=10)
+    return problem(2, (n, n), np.full(C, 5.0), np.full(C, 4.95), N, hg_moments(g, N),
+                   np.zeros(C), level, boundary=bnd, mg=mg)
