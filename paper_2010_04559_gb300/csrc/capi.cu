@@ -421,7 +421,8 @@ int build_gs_rows(amgt_ctx* ctx) {
 // vertex, hence a vertex of one patch in each of the 4 octants around it at
 // every refinement level; the Dirac mass is split equally among those k
 // patches.  Table: beam[f][q a + m] = S Psi_[q]m(Omega_b) / k.  Adjoint
-// contexts hold reversed directions, so their patch q covers -D_q.
+// contexts hold reversed directions, so their patch q covers -D_q: the table
+// is built from the forward mesh (before the reversal) at -Omega_b.
 int build_beam(amgt_ctx* ctx, Level& Lv, int dim) {
   bool any = false;
   for (int f = 0; f < 2 * dim; ++f) any |= ctx->bkind[f] == 2;
@@ -535,6 +536,7 @@ int build(amgt_ctx* ctx) {
   for (int k = 0; k < nl; ++k) {
     Level& Lv = ctx->lv[k];
     Lv.mesh = build_mesh(coarsen_paths(ctx->paths, L - k), ctx->basis);
+    TRY(build_beam(ctx, Lv, dim));  // from the forward patches
     if (ctx->adjoint) {
       // A^T = the same operator with every direction reversed (Omega -> -Omega
       // in the streaming terms, upwind sides flipped); S is symmetric
@@ -634,7 +636,6 @@ int build(amgt_ctx* ctx) {
     TRY(make_sweep_tasks(ctx, Lv, g, 0));
     TRY(upload(ctx, Lv.pdir, &Lv.d_pdir));
     TRY(upload(ctx, Lv.octant, &Lv.d_octant));
-    TRY(build_beam(ctx, Lv, dim));
     TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
     TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));

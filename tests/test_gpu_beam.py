@@ -143,3 +143,30 @@ def test_forward_peaked_beam_workload_reduced_mixed_vs_fp64():
     avg = (f64.reshape(n * n, 4) @ mu).reshape(n, n)
     assert np.abs(avg - avg[::-1]).max() < 1e-9 * np.abs(avg).max()
     ctx.close()
+
+
+def test_forward_peaked_beam_workload_full_size_mixed():
+    """The full beam workload: 256^2 cells, uniform level 4 (2048 patches,
+    6144 angular DOF), HG g = 0.98 at order 64, 4-level multigrid with coarse
+    order 12 -- 1.61e9 unknowns.  The mixed solve reaches 1e-8 (FP64 true
+    residual); the scalar flux is mirror-symmetric about y = 1/2 and larger
+    at the beam edge than at the far edge."""
+    from paper_2010_04559_gb300 import AMGT_MODE_MIXED, AMGT_PREC_MG, context_from_problem
+    n = 256
+    prob = W.config5_beam()
+    stream = torch.cuda.Stream()
+    ctx = context_from_problem(prob, device=0, stream=stream.cuda_stream)
+    ns, na = ctx.amgt_query_sizes(0)
+    assert (ns, na) == (4 * n * n, 6144)
+    psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+    phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+    with torch.cuda.stream(stream):
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=8, precond=AMGT_PREC_MG,
+                                     mode=AMGT_MODE_MIXED, psi=psi, phi=phi, device_ptrs=True)
+    torch.cuda.synchronize()
+    ctx.close()
+    del psi
+    assert st.relres < 1e-8
+    avg = phi.cpu().numpy().reshape(n * n, 4).sum(axis=1).reshape(n, n)
+    assert np.abs(avg - avg[::-1]).max() < 1e-7 * np.abs(avg).max()
+    assert avg[:, 0].mean() > avg[:, -1].mean() > 0
