@@ -58,6 +58,14 @@ typedef enum {
 #define AMGT_F32 1      /* float                                               */
 #define AMGT_F32_BF16TC 2 /* float in/out, scatter contraction on BF16 tensor
                              cores with FP32 accumulation (amgt_op_scatter)   */
+#define AMGT_F64_SPLIT 3  /* double in/out, scatter contraction to FP64
+                             accuracy from BF16 tensor-core products: the
+                             operands are cut into integer digit slices whose
+                             products the FP32 accumulator holds exactly
+                             (error-free splitting of Ozaki et al., 2012),
+                             summed in FP64; falls back to the FP64 SIMT
+                             contraction where the angular size is below 64,
+                             not a multiple of 8, or tcgen05 is absent       */
 
 /* preconditioners and precision modes of amgt_solve */
 #define AMGT_PREC_NONE 0
@@ -123,7 +131,9 @@ int amgt_query_launches(int64_t* count);
 #define AMGT_KT_SCATTER_F32 4  /* FP32 scatter contractions (SIMT)             */
 #define AMGT_KT_COARSE_GS 5    /* coarse Gauss-Seidel kernel                   */
 #define AMGT_KT_SCATTER_F64 6  /* FP64 scatter contractions (SIMT)             */
-#define AMGT_KT_COUNT 7
+#define AMGT_KT_SPLIT_TC 7     /* tcgen05 GEMMs of the split FP64 scatter      */
+#define AMGT_KT_SPLIT_AUX 8    /* digit slicing and FP64 accumulation of it    */
+#define AMGT_KT_COUNT 9
 int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches);
 /* Blocks until all work issued on the context's stream has finished; returns
  * AMGT_ERR_DEVICE_TIMEOUT if a device-side bounded wait gave up since the
@@ -200,7 +210,15 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         its first use (input and output through two fixed
  *                         device buffers); 0: direct launches (default).
  *                         Ignored while the kernel timers are on and on
- *                         the default stream (which cannot be captured). */
+ *                         the default stream (which cannot be captured).
+ *   AMGT_TUNE_FP64_SCATTER the FP64 scatter contraction: 0 auto (the mixed
+ *                         solve's FP64 refinement residuals in the split
+ *                         form of AMGT_F64_SPLIT, every other FP64 scatter
+ *                         on the FP64 SIMT GEMM), 1 FP64 SIMT everywhere,
+ *                         2 split form everywhere (FP64 solves too)
+ *   AMGT_TUNE_SPLIT_ROWS  rows of psi per pass of the split form (0 = auto:
+ *                         as many as keep its digit slices within ~8 GB;
+ *                         else rounded up to a multiple of 128). */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
@@ -208,6 +226,8 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 #define AMGT_TUNE_GS_CLUSTER 5
 #define AMGT_TUNE_KERNEL_TIMERS 6
 #define AMGT_TUNE_GRAPHS 7
+#define AMGT_TUNE_FP64_SCATTER 8
+#define AMGT_TUNE_SPLIT_ROWS 9
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Times the sweep's patches per block and copy depth (what bit 0) and the
  * coarse Gauss-Seidel kernel (what bit 1) on this context's own hierarchy
@@ -251,7 +271,11 @@ int amgt_op_sweep(amgt_ctx* ctx, int level, int dtype, const void* b, void* psi)
 int amgt_op_apply_L(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
 /* y = S x: Q_[j,q]lm = sum N_li sum_n sigma_{s,n} X X phi (Sec. 4.2), with the
  * level's scatter order.  dtype AMGT_F32_BF16TC: float buffers, contraction
- * in BF16 on tensor cores with FP32 accumulation. */
+ * in BF16 on tensor cores with FP32 accumulation; AMGT_F64_SPLIT: double
+ * buffers, the dense S_f contraction to FP64 accuracy from BF16 tensor-core
+ * products (also accepted by amgt_op_apply_A, amgt_op_smooth and
+ * amgt_op_vcycle, where every FP64 scatter takes that form; other operators
+ * treat it as AMGT_F64). */
 int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
 /* y = (L - S) x. */
 int amgt_op_apply_A(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);

@@ -26,6 +26,7 @@ AMGT_ERR_UNSUPPORTED = -9
 AMGT_F64 = 0
 AMGT_F32 = 1
 AMGT_F32_BF16TC = 2
+AMGT_F64_SPLIT = 3
 
 AMGT_PREC_NONE = 0
 AMGT_PREC_SWEEP = 1
@@ -42,9 +43,12 @@ AMGT_TUNE_GS_GRID_BLOCKS = 4
 AMGT_TUNE_GS_CLUSTER = 5
 AMGT_TUNE_KERNEL_TIMERS = 6
 AMGT_TUNE_GRAPHS = 7
+AMGT_TUNE_FP64_SCATTER = 8
+AMGT_TUNE_SPLIT_ROWS = 9
 AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
+AMGT_KT_SPLIT_TC, AMGT_KT_SPLIT_AUX = 7, 8
 
 # every exported symbol of include/amgt.h
 EXPORTS = [
@@ -296,7 +300,7 @@ class Context:
     def _dtype_code(t, tc=False):
         import torch
         if t.dtype == torch.float64:
-            return AMGT_F64
+            return AMGT_F64_SPLIT if tc else AMGT_F64
         if t.dtype == torch.float32:
             return AMGT_F32_BF16TC if tc else AMGT_F32
         raise TypeError("buffers must be float64 or float32 CUDA tensors")

@@ -766,7 +766,154 @@ int ensure_dense_bf16(amgt_ctx* ctx, int k) {
   return AMGT_OK;
 }
 
-// y = alpha * S x + beta * y + add  (add may be null)
+// Slice width and pair groups of the split FP64 contraction for inner
+// dimension K (kernels_split64.cu): `bits` b is the largest (at most 7, so
+// that digits up to 2^7 are exact in BF16) with K 2^(2b) <= 2^24, the range
+// of exact FP32 integers; nsl = ceil(50 / b) slices keep 50 bits of each
+// operand; the pairs (i, j) of slices with i + j = d < nsl are grouped so
+// that the sum of their bounds K D_i D_j (D_0 = 2^b, D_i = 2^(b-1)) stays
+// within 2^24, and each group is accumulated on the tensor cores before one
+// FP64 accumulation.  bits = 0: the split form does not apply.
+struct SplitPlan {
+  int bits = 0, nsl = 0;
+  std::vector<int> gd;  // diagonal d of each group
+  std::vector<std::vector<std::pair<int, int>>> groups;
+};
+
+SplitPlan split_plan(int K) {
+  SplitPlan p;
+  int b = 7;
+  const double lim = std::ldexp(1.0, 24);
+  while (b > 0 && (double)K * std::ldexp(1.0, 2 * b) > lim) --b;
+  if (b < 2) return p;
+  p.bits = b;
+  p.nsl = (50 + b - 1) / b;
+  auto D = [&](int i) { return std::ldexp(1.0, i == 0 ? b : b - 1); };
+  for (int d = 0; d < p.nsl; ++d) {
+    std::vector<std::pair<int, int>> cur;
+    double acc = 0.0;
+    for (int i = 0; i <= d; ++i) {
+      const double bound = (double)K * D(i) * D(d - i);
+      if (!cur.empty() && acc + bound > lim) {
+        p.groups.push_back(cur);
+        p.gd.push_back(d);
+        cur.clear();
+        acc = 0.0;
+      }
+      cur.push_back({i, d - i});
+      acc += bound;
+    }
+    p.groups.push_back(cur);
+    p.gd.push_back(d);
+  }
+  return p;
+}
+
+bool split_applies(amgt_ctx* ctx, int k) {
+  const int n = ctx->lv[k].nadof();
+  return tc_available() && n >= 64 && n % 8 == 0 && split_plan(n).bits > 0 &&
+         (ctx->geom.s == 4 || ctx->geom.s == 8);
+}
+
+// FP64 scatter contraction in split form on this call?  `refinement`: the
+// call computes a refinement residual of the mixed solve.
+bool use_split64(amgt_ctx* ctx, bool refinement) {
+  if (ctx->fp64_scatter == 1) return false;
+  if (ctx->fp64_scatter == 2) return true;
+  return refinement;
+}
+
+// the rows of S_f (symmetric, so also its columns) as digit slices
+int ensure_split(amgt_ctx* ctx, int k, const SplitPlan& sp) {
+  Level& L = ctx->lv[k];
+  if (L.Sf_split) return AMGT_OK;
+  TRY(ensure_dense(ctx, k));
+  const int n = L.nadof();
+  __nv_bfloat16* sl;
+  double* nu;
+  TRY(dalloc(ctx, (size_t)sp.nsl * n * n, &sl));
+  TRY(dalloc(ctx, (size_t)n, &nu));
+  launch_split_rows(n, n, 4, false, L.d64.Sf, nullptr, nullptr, sp.nsl, sp.bits, nu, sl,
+                    (long long)n * n, ctx->stream);
+  CK(cudaGetLastError());
+  L.Sf_split = sl;
+  L.Sf_nu = nu;
+  return AMGT_OK;
+}
+
+// y = alpha S x + beta y + add to FP64 accuracy: the cell-mixed rows
+// sig_s N x and the rows of S_f are cut into BF16 digit slices, the slice
+// products run as tcgen05 GEMMs whose FP32 sums are exact integers, and each
+// group of products is scaled by a power of two and accumulated in FP64.
+// Rows are processed in chunks that keep the slices within ~8 GB.
+int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alpha, double beta,
+                    const double* add) {
+  Level& L = ctx->lv[k];
+  const long long M = L.nsdof;
+  const int n = L.nadof();
+  const int S = ctx->geom.s;
+  const SplitPlan sp = split_plan(n);
+  TRY(ensure_split(ctx, k, sp));
+  const long long total = M * n;
+  if (add) {
+    launch_axpby<double>(total, 1.0, add, beta, y, ctx->stream);
+  } else if (beta == 0.0) {
+    CK(cudaMemsetAsync(y, 0, (size_t)total * sizeof(double), ctx->stream));
+  } else if (beta != 1.0) {
+    launch_scale_copy<double>(total, beta, y, y, ctx->stream);
+  }
+  const size_t per_row = (size_t)sp.nsl * n * 2 + (size_t)n * 4 + 8;
+  long long Mc = (long long)(((size_t)8 << 30) / per_row) / 128 * 128;
+  if (ctx->split_rows > 0) Mc = ((long long)ctx->split_rows + 127) / 128 * 128;
+  if (Mc < 128) Mc = 128;
+  if (Mc > M) Mc = M;
+  const size_t slice_bytes = (size_t)sp.nsl * Mc * n * 2;
+  const size_t p_off = (slice_bytes + 255) / 256 * 256;
+  const size_t mu_off = p_off + ((size_t)Mc * n * 4 + 255) / 256 * 256;
+  const size_t need = mu_off + (size_t)Mc * 8;
+  if (ctx->split_bytes < need) {
+    unsigned char* p;
+    TRY(dalloc(ctx, need, &p));
+    ctx->d_split = p;
+    ctx->split_bytes = need;
+  }
+  auto* base = static_cast<unsigned char*>(ctx->d_split);
+  auto* xs = reinterpret_cast<__nv_bfloat16*>(base);
+  auto* P = reinterpret_cast<float*>(base + p_off);
+  auto* mu = reinterpret_cast<double*>(base + mu_off);
+  for (long long r0 = 0; r0 < M; r0 += Mc) {
+    const long long rows = std::min(Mc, M - r0);
+    {
+      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX);
+      launch_split_rows(rows, n, S, true, x + r0 * n, ctx->d_sigs + r0 / S, ctx->geom.Nmass,
+                        sp.nsl, sp.bits, mu, xs, rows * n, ctx->stream);
+    }
+    for (size_t g = 0; g < sp.groups.size(); ++g) {
+      const auto& grp = sp.groups[g];
+      for (size_t e = 0; e < grp.size(); ++e) {
+        const int i = grp[e].first, j = grp[e].second;
+        int rc;
+        {
+          KernelTimer kt(ctx, AMGT_KT_SPLIT_TC);
+          rc = launch_tc_gemm((int)rows, n, n, xs + (size_t)i * rows * n,
+                              L.Sf_split + (size_t)j * n * n, P, nullptr, e == 0 ? 0.0f : 1.0f,
+                              ctx->d_status, ctx->stream);
+        }
+        if (rc != 0)
+          return fail(ctx, AMGT_ERR_UNSUPPORTED,
+                      "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
+      }
+      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX);
+      launch_split_flush(rows, n, P, mu, L.Sf_nu, alpha * std::ldexp(1.0, -sp.bits * (sp.gd[g] + 2)),
+                         y + r0 * n, ctx->stream);
+    }
+  }
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// y = alpha * S x + beta * y + add  (add may be null).  For T = double, `tc`
+// selects the split form (where it applies; else the FP64 SIMT contraction).
 template <class T>
 int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, double beta,
                  const T* add) {
@@ -814,7 +961,7 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
       CK(cudaGetLastError());
       return AMGT_OK;
     } else {
-      return fail(ctx, AMGT_ERR_ARG, "tensor-core scatter takes float buffers");
+      if (split_applies(ctx, k)) return scatter_split64(ctx, k, x, y, alpha, beta, add);
     }
   }
   if (L.dense) {
@@ -1811,6 +1958,16 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
     drop_graphs(ctx);
     return AMGT_OK;
   }
+  if (key == AMGT_TUNE_FP64_SCATTER) {
+    if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "FP64 scatter 0, 1 or 2");
+    ctx->fp64_scatter = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_SPLIT_ROWS) {
+    if (value < 0) return fail(ctx, AMGT_ERR_ARG, "split rows >= 0");
+    ctx->split_rows = value;
+    return AMGT_OK;
+  }
   if (key == AMGT_TUNE_KERNEL_TIMERS) {
     if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "kernel timers 0 or 1");
     ctx->ktimers = value == 1;
@@ -1841,9 +1998,10 @@ int amgt_query_sizes(const amgt_ctx* cctx, int level, int64_t* nsdof, int64_t* n
 
 #define DISPATCH(dtype, CALL64, CALL32)                                            \
   do {                                                                            \
-    if ((dtype) == AMGT_F64) return CALL64;                                       \
+    if ((dtype) == AMGT_F64 || (dtype) == AMGT_F64_SPLIT) return CALL64;          \
     if ((dtype) == AMGT_F32 || (dtype) == AMGT_F32_BF16TC) return CALL32;         \
-    return fail(ctx, AMGT_ERR_ARG, "dtype must be AMGT_F64, AMGT_F32 or AMGT_F32_BF16TC"); \
+    return fail(ctx, AMGT_ERR_ARG,                                                \
+                "dtype must be AMGT_F64, AMGT_F64_SPLIT, AMGT_F32 or AMGT_F32_BF16TC"); \
   } while (0)
 
 int amgt_op_source(amgt_ctx* ctx, int level, int dtype, void* f) {
@@ -1872,7 +2030,7 @@ int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y)
   if (!ctx) return AMGT_ERR_ARG;
   TRY(check_level(ctx, level));
   DISPATCH(dtype,
-           scatter_impl<double>(ctx, level, false, (const double*)x, (double*)y, 1.0, 0.0, nullptr),
+           scatter_impl<double>(ctx, level, dtype == AMGT_F64_SPLIT, (const double*)x, (double*)y, 1.0, 0.0, nullptr),
            scatter_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y,
                                1.0, 0.0, nullptr));
 }
@@ -1880,7 +2038,7 @@ int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y)
 int amgt_op_apply_A(amgt_ctx* ctx, int level, int dtype, const void* x, void* y) {
   if (!ctx) return AMGT_ERR_ARG;
   TRY(check_level(ctx, level));
-  DISPATCH(dtype, applyA_impl<double>(ctx, level, false, (const double*)x, (double*)y),
+  DISPATCH(dtype, applyA_impl<double>(ctx, level, dtype == AMGT_F64_SPLIT, (const double*)x, (double*)y),
            applyA_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y));
 }
 
@@ -1904,7 +2062,7 @@ int amgt_op_smooth(amgt_ctx* ctx, int level, int dtype, int nu, const void* f, v
   if (!ctx) return AMGT_ERR_ARG;
   TRY(check_level(ctx, level));
   if (nu < 0) return fail(ctx, AMGT_ERR_ARG, "nu < 0");
-  DISPATCH(dtype, smooth_impl<double>(ctx, level, false, nu, (const double*)f, (double*)phi, false),
+  DISPATCH(dtype, smooth_impl<double>(ctx, level, dtype == AMGT_F64_SPLIT, nu, (const double*)f, (double*)phi, false),
            smooth_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, nu, (const float*)f,
                               (float*)phi, false));
 }
@@ -1933,7 +2091,7 @@ int amgt_op_coarse_gs_noalloc(amgt_ctx* ctx, int dtype, int sweeps, const void* 
 int amgt_op_vcycle(amgt_ctx* ctx, int dtype, const void* f, void* phi) {
   if (!ctx) return AMGT_ERR_ARG;
   TRY(build(ctx));
-  DISPATCH(dtype, vcycle_impl<double>(ctx, 0, false, (const double*)f, (double*)phi),
+  DISPATCH(dtype, vcycle_impl<double>(ctx, 0, dtype == AMGT_F64_SPLIT, (const double*)f, (double*)phi),
            vcycle_impl<float>(ctx, 0, dtype == AMGT_F32_BF16TC, (const float*)f, (float*)phi));
 }
 
@@ -1983,11 +2141,12 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
   const bool graphs = ctx->use_graphs && !ctx->ktimers && ctx->stream != nullptr &&
                       ctx->stream != cudaStreamLegacy && ctx->stream != cudaStreamPerThread;
   if (opt->mode == AMGT_MODE_F64) {
-    auto A64 = [&](const double* xx, double* yy) { return applyA_impl<double>(ctx, 0, false, xx, yy); };
+    const bool split = use_split64(ctx, false);
+    auto A64 = [&](const double* xx, double* yy) { return applyA_impl<double>(ctx, 0, split, xx, yy); };
     auto M64 = [&](const double* v, double* z) -> int {
       if (prec == AMGT_PREC_SWEEP) return sweep_impl<double>(ctx, 0, v, z);
       if (prec == AMGT_PREC_MG)
-        return graphs ? vcycle_graph<double>(ctx, false, v, z) : vcycle_impl<double>(ctx, 0, false, v, z);
+        return graphs ? vcycle_graph<double>(ctx, split, v, z) : vcycle_impl<double>(ctx, 0, split, v, z);
       CK(cudaMemcpyAsync(z, v, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       return AMGT_OK;
     };
@@ -2038,7 +2197,7 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       if (x_zero) {
         CK(cudaMemcpyAsync(r64, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       } else {
-        TRY(applyA_impl<double>(ctx, 0, false, x, r64));
+        TRY(applyA_impl<double>(ctx, 0, use_split64(ctx, true), x, r64));
         launch_axpby<double>(n, 1.0, b, -1.0, r64, ctx->stream);
       }
       double rn;

@@ -55,6 +55,9 @@ struct Level {
   LevelDevStore<double> d64;
   LevelDevStore<float> d32;
   __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path
+  // FP64 scatter in split form: the rows of S_f cut into BF16 digit slices
+  __nv_bfloat16* Sf_split = nullptr;  // [nsl][n][n]
+  double* Sf_nu = nullptr;            // [n] row scales (powers of two)
   int *d_pdir = nullptr, *d_octant = nullptr, *d_dbeg = nullptr, *d_dend = nullptr;
   // pencil-beam inflow weights [2 dim][nadof] (null without a beam face)
   double* d_beam = nullptr;
@@ -118,6 +121,10 @@ struct amgt_ctx {
   size_t moments_bytes = 0;
   void* d_bf16 = nullptr;                      // bf16 operand scratch
   size_t bf16_bytes = 0;
+  void* d_split = nullptr;                     // split-form slices, products, row scales
+  size_t split_bytes = 0;
+  int fp64_scatter = 0;                        // AMGT_TUNE_FP64_SCATTER
+  int split_rows = 0;                          // AMGT_TUNE_SPLIT_ROWS
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   bool adjoint = false;  // amgt_set_adjoint: operators of the transposed problem

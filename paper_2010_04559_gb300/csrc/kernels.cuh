@@ -204,4 +204,18 @@ void launch_tc_prep(long long ncell, int s, int n, const float* x, const float* 
 int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
                    const float* add, float beta, int* err, cudaStream_t st);
 
+// Error-free splitting of FP64 rows into BF16 digit slices (kernels_split64.cu):
+// per row r of z (x itself, or with mix the per-cell rows sig[c] N x of S
+// spatial nodes) mu[r] = 2^e > max |z[r]|, and slice i (0 <= i < nsl) holds
+// the integer digits d_i with z = mu sum_i d_i 2^(-bits (i+1)) + remainder.
+struct NmassArg {
+  double v[64];
+};
+void launch_split_rows(long long rows, int K, int S, bool mix, const double* x,
+                       const double* sig, const double* Nm, int nsl, int bits, double* mu,
+                       __nv_bfloat16* out, long long slice_stride, cudaStream_t st);
+// y[r][c] += sc mu[r] nu[c] P[r][c] for r < M, c < N (row strides N)
+void launch_split_flush(long long M, int N, const float* P, const double* mu, const double* nu,
+                        double sc, double* y, cudaStream_t st);
+
 }  // namespace amgt
