@@ -46,6 +46,8 @@ KERNEL_NAMES = {
     "scatter_f32": "gemm_kernel<float>",
     "scatter_f64": "gemm_kernel<double>",
     "coarse_gs": "coarse_gs_rows_kernel<float,2,3>",
+    "split_tc": "tc_gemm_kernel (tcgen05, slice products of the split FP64 scatter)",
+    "split_aux": "split_rows_kernel + split_flush_kernel (digit slicing, FP64 accumulation)",
 }
 # DRAM bytes (read + write) per launch on this workload from the ncu captures
 # summarised under profiles/; a kernel changed since its capture has no entry
@@ -200,8 +202,10 @@ def run_profile(args):
         ctx.amgt_op_coarse_gs(1, fc, pc)
         x64 = x.double()
         ctx.amgt_op_scatter(0, x64, torch.empty_like(x64))
+        ctx.amgt_op_scatter(0, x64, torch.empty_like(x64), tc=True)
         ctx.amgt_sync()
-        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep), FP64 scatter")
+        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep), FP64 scatter "
+              "(SIMT, then split form)")
     torch.cuda.synchronize()
     ctx.close()
     return 0
@@ -249,7 +253,8 @@ def main():
     kt_ids = {"sweep": pkg.AMGT_KT_SWEEP, "apply_L": pkg.AMGT_KT_APPLY_L,
               "scatter_prep": pkg.AMGT_KT_SCATTER_PREP, "scatter_tc": pkg.AMGT_KT_SCATTER_TC,
               "scatter_f32": pkg.AMGT_KT_SCATTER_F32, "scatter_f64": pkg.AMGT_KT_SCATTER_F64,
-              "coarse_gs": pkg.AMGT_KT_COARSE_GS}
+              "coarse_gs": pkg.AMGT_KT_COARSE_GS, "split_tc": pkg.AMGT_KT_SPLIT_TC,
+              "split_aux": pkg.AMGT_KT_SPLIT_AUX}
 
     def kt_read(reset=True):
         return {k: ctx.amgt_query_kernel_time(i, reset=reset) for k, i in kt_ids.items()}
@@ -360,6 +365,15 @@ def main():
             use_tc = False
             t_sc, k_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32))
             kern["scatter_f32"] = {"s": t_sc, "note": str(ex)[:80]}
+        x64 = x32.double()
+        y64 = torch.empty_like(x64)
+        t_sp, k_sp = timeit(lambda: ctx.amgt_op_scatter(0, x64, y64, tc=True), reps=3)
+        if k_sp.get("split_tc"):
+            kern["scatter_f64_split"] = {"s": t_sp, "gemm_s_per_launch": k_sp["split_tc"],
+                                         "gemm_TFLOP/s": 2.0 * nsdof * nadof * nadof / k_sp["split_tc"] / 1e12}
+        t_64, k_64 = timeit(lambda: ctx.amgt_op_scatter(0, x64, y64), reps=2)
+        kern["scatter_f64_simt"] = {"s": t_64}
+        del x64, y64
         t_L, k_L = timeit(lambda: ctx.amgt_op_apply_L(0, x32, y32))
         kern["apply_L_f32"] = {"s": t_L, "GB/s": 8.0 * dof / k_L["apply_L"] / 1e9}
         t_gs, k_gs = timeit(lambda: ctx.amgt_op_coarse_gs(10, fc, pc), reps=3)
@@ -393,11 +407,15 @@ def main():
                         "4 Nsdof Nadof nmom flop per residual (two FP64 GEMMs, nmom = 289)"),
         "scatter_f32": ("alu", 4.0 * nsdof * nadof * NMOM_FINE / 1e12, alu_peak, "TFLOP/s",
                         "4 Nsdof Nadof nmom flop per apply (two FP32 GEMMs, nmom = 289)"),
+        # one slice-pair product of the split FP64 scatter per launch
+        "split_tc": ("tensor", tc_flop / 1e12, bf16, "TFLOP/s",
+                     "2 Nsdof Nadof^2 flop per slice-pair GEMM (BF16 digits, dense S_f)"),
     }
     rl = {}
     for name, per_launch in (("sweep", k_sw.get("sweep")), ("apply_L", k_L.get("apply_L")),
                              ("scatter_prep", k_sc.get("scatter_prep")),
                              ("scatter_tc", k_sc.get("scatter_tc")),
+                             ("split_tc", k_sp.get("split_tc")),
                              ("coarse_gs", k_gs.get("coarse_gs"))):
         if not per_launch:
             continue
