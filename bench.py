@@ -39,7 +39,7 @@ WORKLOAD = "2D 128x128 Q1, checkerboard sigma_t 1/10 c 0.5/0.99, level-3 Lin (51
 METRIC = "transport-operator GDOF/s; time-to-residual 1e-8, mixed/batched vs FP64 GPU"
 
 KERNEL_NAMES = {
-    "sweep": "sweep2d_rows_kernel<float,3,4>",
+    "sweep": "sweep2d_warp_kernel<float,3,4,4,3>",
     "apply_L": "apply_L_kernel<float,2,3>",
     "scatter_prep": "tc_prep_kernel<4>",
     "scatter_tc": "tc_gemm_kernel (tcgen05, persistent)",
@@ -52,7 +52,7 @@ KERNEL_NAMES = {
 # DRAM bytes (read + write) per launch on this workload from the ncu captures
 # summarised under profiles/; a kernel changed since its capture has no entry
 TRAFFIC = {
-    "sweep": 955.5e6,       # profiles/ncu_top_kernels_config2.md
+    "sweep": 769.9e6,       # profiles/ncu_sweep_warp_config2.md
     "scatter_tc": 554.3e6,  # profiles/ncu_top_kernels_config2.md
 }
 NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
@@ -185,7 +185,17 @@ def run_profile(args):
     prob = W.config2_checkerboard(n=args.n)
     ctx = context_from_problem(prob, device=0)
     ns, na = ctx.amgt_query_sizes(0)
-    if args.profile == "solve":
+    if args.profile == "sweeps":
+        from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
+        x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
+        y = torch.empty_like(x)
+        for _ in range(2):  # one warm-up launch of each variant, then one each
+            for k in (1, 2):
+                ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, k)
+                ctx.amgt_op_sweep(0, x, y)
+        ctx.amgt_sync()
+        print("kernels: level-synchronous row sweep, warp-pipelined sweep (x2)")
+    elif args.profile == "solve":
         psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
         phi = torch.empty(ns, device="cuda", dtype=torch.float64)
         _, _, st, _ = ctx.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED,
@@ -225,7 +235,7 @@ def main():
                     help="problems of the uneven 2D batch solved concurrently (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="tolerance of each inner FP32 solve (0: adaptive)")
-    ap.add_argument("--profile", choices=["solve", "kernels"], default=None,
+    ap.add_argument("--profile", choices=["solve", "kernels", "sweeps"], default=None,
                     help="run one solve, or one launch of each hot kernel, and exit (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -218,7 +218,16 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         2 split form everywhere (FP64 solves too)
  *   AMGT_TUNE_SPLIT_ROWS  rows of psi per pass of the split form (0 = auto:
  *                         as many as keep its digit slices within ~8 GB;
- *                         else rounded up to a multiple of 128). */
+ *                         else rounded up to a multiple of 128)
+ *   AMGT_TUNE_SWEEP_KERNEL the 2D sweep: 0 auto, 1 level-synchronous row
+ *                         kernel (one block barrier per wavefront level),
+ *                         2 warp-pipelined kernel (Lin basis, 2, 4 or 8
+ *                         patches per block: each warp runs its own skewed
+ *                         wavefront over its rows and hands the boundary
+ *                         row to the next warp through a shared ring with a
+ *                         step counter; a wait gives up after 2 s and
+ *                         reports AMGT_ERR_DEVICE_TIMEOUT at the next
+ *                         amgt_sync); cases outside 2's scope run 1. */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
@@ -228,6 +237,7 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 #define AMGT_TUNE_GRAPHS 7
 #define AMGT_TUNE_FP64_SCATTER 8
 #define AMGT_TUNE_SPLIT_ROWS 9
+#define AMGT_TUNE_SWEEP_KERNEL 10
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Times the sweep's patches per block and copy depth (what bit 0) and the
  * coarse Gauss-Seidel kernel (what bit 1) on this context's own hierarchy

@@ -45,6 +45,7 @@ AMGT_TUNE_KERNEL_TIMERS = 6
 AMGT_TUNE_GRAPHS = 7
 AMGT_TUNE_FP64_SCATTER = 8
 AMGT_TUNE_SPLIT_ROWS = 9
+AMGT_TUNE_SWEEP_KERNEL = 10
 AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6

@@ -990,7 +990,7 @@ int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   KernelTimer kt(ctx, AMGT_KT_SWEEP);
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                   schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, c16, ctx->sweep_stages,
-                  ctx->stream);
+                  ctx->sweep_kernel, ctx->d_status, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1961,6 +1961,11 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
   if (key == AMGT_TUNE_FP64_SCATTER) {
     if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "FP64 scatter 0, 1 or 2");
     ctx->fp64_scatter = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_SWEEP_KERNEL) {
+    if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "sweep kernel 0, 1 or 2");
+    ctx->sweep_kernel = value;
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_SPLIT_ROWS) {

@@ -125,6 +125,7 @@ struct amgt_ctx {
   size_t split_bytes = 0;
   int fp64_scatter = 0;                        // AMGT_TUNE_FP64_SCATTER
   int split_rows = 0;                          // AMGT_TUNE_SPLIT_ROWS
+  int sweep_kernel = 0;                        // AMGT_TUNE_SWEEP_KERNEL
   int gs_cluster = 0;
   void* noalloc_moments = nullptr;  // device address of the fixed moment scratch
   bool adjoint = false;  // amgt_set_adjoint: operators of the transposed problem

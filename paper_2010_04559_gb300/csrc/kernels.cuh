@@ -83,9 +83,11 @@ struct DevStatus {
 // G > 0 and dim == 2: row-pipelined kernel with G patches per block (the
 // schedule's tasks must then hold G-patch groups); otherwise the level kernel.
 template <class T>
+// variant: 0 auto, 1 level-synchronous row kernel, 2 warp-pipelined (2D, Lin);
+// err: status word for the bounded waits of the warp-pipelined form
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst,
-                  cudaStream_t st);
+                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst, int variant,
+                  int* err, cudaStream_t st);
 template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
                     const T* x, T* y, cudaStream_t st);

@@ -11,6 +11,7 @@
 // nodes of the two cells, with the Q1 face mass `facemass[xi]`.
 #include <type_traits>
 
+#include "gs_common.cuh"
 #include "kernels.cuh"
 
 namespace amgt {
@@ -363,6 +364,375 @@ __global__ void __launch_bounds__(512) sweep2d_rows_kernel(Geom g, LevelDev<T> t
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------
+// 2D sweep, warp-pipelined.  The task split is that of sweep2d_rows_kernel
+// (one block per direction and patch group), without a block barrier per
+// wavefront level: warp w owns the RW = 32 / G rows RW w .. RW w + RW - 1
+// (lane = r G + p: row r, patch p) and runs its own steps t = 0, 1, ...,
+// in which lane (r, p) solves cell jx = t - r of its row.  Row r > 0 takes its
+// y-upwind values from row r - 1's output of the step before (a shuffle); row
+// 0 takes them from the previous warp's last row through a ring of R cell
+// slots in shared memory, published by a per-warp step counter (release /
+// acquire at block scope); a writer reuses a slot only after the reader has
+// passed it.  Every warp waits only on its two neighbours, and a writer at
+// step t' needs its reader at step >= t' - RW + 2 - R while the reader at step
+// t needs the writer at step >= t + RW, so no two warps wait on each other
+// (R >= 2).  Waits give up after 2 s (status code 7, AMGT_ERR_DEVICE_TIMEOUT
+// at the next amgt_sync) or as soon as another wait gave up.  b is staged per
+// warp NST steps ahead with cp.async; the block inverses sit in shared memory.
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.b32 %0, [%1];"
+               : "=r"(v)
+               : "r"((unsigned)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+  asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+               "r"(v)
+               : "memory");
+}
+constexpr unsigned long long kSweepWaitNs = 2000000000ULL;
+// lane 0 waits until *p >= target; false once it gave up
+__device__ __forceinline__ bool wait_at_least(const int* p, int target, int* err) {
+  if (ld_acquire_cta(p) >= target) return true;
+  const unsigned long long t0 = gsx::now_ns();
+  unsigned it = 0;
+  while (ld_acquire_cta(p) < target) {
+    if ((++it & 63u) == 0) {
+      if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+      if (gsx::now_ns() - t0 > kSweepWaitNs) {
+        atomicExch(err, 7);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+constexpr int kSweepRing = 16;
+
+// Row stride (elements) of a warp's staged rows [RW][S][G A]: the smallest
+// 16-byte multiple >= S G A for which the reads of one (node, unknown) by the
+// warp's lanes (row r, patch p: element r RS + p A) fall on distinct banks.
+template <class T, int G, int A>
+__host__ __device__ constexpr int warp_row_stride() {
+  constexpr int S = 4, RW = 32 / G, vw = 16 / (int)sizeof(T), wpe = (int)sizeof(T) / 4;
+  int best = S * G * A, bestc = 1 << 30;
+  for (int k = 0; k < 8; ++k) {
+    const int rs = ((S * G * A + vw - 1) / vw + k) * vw;
+    int cnt[32] = {};
+    int worst = 0;
+    for (int r = 0; r < RW; ++r)
+      for (int p = 0; p < G; ++p) {
+        const int bank = ((r * rs + p * A) * wpe) % 32;
+        const int c = ++cnt[bank];
+        worst = c > worst ? c : worst;
+      }
+    if (worst < bestc) {
+      bestc = worst;
+      best = rs;
+    }
+  }
+  return best;
+}
+
+template <class T>
+size_t sweep2d_warp_smem(int ny, int G, int a, int nmat_s, int nst) {
+  const int RW = 32 / G, nwarp = (ny + RW - 1) / RW;
+  const int SA = 4 * a;
+  const size_t kst = SA * SA + 16 / sizeof(T);
+  const int rs = G == 2 ? warp_row_stride<T, 2, 3>()
+                        : (G == 4 ? warp_row_stride<T, 4, 3>() : warp_row_stride<T, 8, 3>());
+  return ((size_t)nwarp * (nst + 1) * RW * rs + (size_t)nwarp * kSweepRing * G * 2 * a +
+          (size_t)nmat_s * G * kst) * sizeof(T) + (size_t)nwarp * sizeof(int);
+}
+
+template <class T, int A, int G, int NST, int UMAX>
+__global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t, CellData cd,
+                                                            Schedule sc, const T* __restrict__ b,
+                                                            T* __restrict__ psi, int nmat_s,
+                                                            int chunk, int* err) {
+  constexpr int S = 4, HS = 2;
+  constexpr int SA = S * A;
+  constexpr int RW = 32 / G;
+  constexpr int SEGP = G * A;                    // (row, node) segment
+  constexpr int RS = warp_row_stride<T, G, A>();  // staged row stride
+  constexpr int KST = SA * SA + 16 / sizeof(T);  // padded inverse stride
+  constexpr int R = kSweepRing;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int task = blockIdx.x;
+  const int d = sc.task_dir[task], q0 = sc.task_q0[task], nq = sc.task_nq[task];
+  const int negx = (d >> 1) & 1, negy = d & 1;
+  const int nx = g.nx, ny = g.ny, nadof = g.nadof;
+  const int nwarp = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = lane / G, p = lane - (lane / G) * G;
+  const int jy = warp * RW + r;
+  const bool mine = jy < ny && p < nq;
+  const int q = q0 + p;
+  const int seg = nq * A;
+  T* stage = reinterpret_cast<T*>(smem_raw);                 // [nwarp][NST + 1][RW][RS]
+  T* ring = stage + (size_t)nwarp * (NST + 1) * RW * RS;    // [nwarp][R][G][HS*A]
+  T* kin = ring + (size_t)nwarp * R * G * HS * A;                  // [nmat_s][G][KST]
+  int* prog = reinterpret_cast<int*>(kin + (size_t)nmat_s * G * KST);  // [nwarp] steps done
+  for (int i = tid; i < nmat_s * nq * SA * SA; i += blockDim.x) {
+    const int mt = i / (nq * SA * SA);
+    const int rem = i - mt * nq * SA * SA;
+    const int pp = rem / (SA * SA), e = rem - pp * SA * SA;
+    kin[((size_t)mt * G + pp) * KST + e] = t.Kinv[((size_t)mt * g.P + q0 + pp) * SA * SA + e];
+  }
+  if (tid < nwarp) prog[tid] = 0;
+  T Ax[A][A], Ay[A][A];
+  if (mine) {
+#pragma unroll
+    for (int m = 0; m < A; ++m)
+#pragma unroll
+      for (int dd = 0; dd < A; ++dd) {
+        Ax[m][dd] = t.Aax[((size_t)q * 3 + 0) * A * A + m * A + dd];
+        Ay[m][dd] = t.Aax[((size_t)q * 3 + 1) * A * A + m * A + dd];
+      }
+  }
+  // this lane's staging copies: the same (row, node, chunk) triples every
+  // step; the cell column jx = step - row moves, linear in the source address
+  const int nchunk_seg = seg * (int)sizeof(T) / chunk;
+  const int per_step = RW * S * nchunk_seg;
+  int crow[UMAX];
+  long long csrc[UMAX];
+  int cdst[UMAX];
+  const long long xstep = (negx ? -1LL : 1LL) * S * nadof * (long long)sizeof(T);
+#pragma unroll
+  for (int u = 0; u < UMAX; ++u) {
+    const int i = lane + u * 32;
+    crow[u] = -1;
+    csrc[u] = 0;
+    cdst[u] = 0;
+    if (i < per_step) {
+      const int row = i / (S * nchunk_seg);
+      const int rem = i - row * S * nchunk_seg;
+      const int l = rem / nchunk_seg, ch = rem - l * nchunk_seg;
+      const int jyc = warp * RW + row;
+      if (jyc < ny) {
+        const int iy = negy ? ny - 1 - jyc : jyc;
+        const int c0 = (negx ? nx - 1 : 0) + nx * iy;
+        crow[u] = row;
+        csrc[u] = (((long long)c0 * S + l) * nadof + q0 * A) * (long long)sizeof(T) + ch * chunk;
+        cdst[u] = (row * RS + l * SEGP) * (int)sizeof(T) + ch * chunk;
+      }
+    }
+  }
+  const char* bbase = reinterpret_cast<const char*>(b);
+  constexpr int kStageElems = RW * RS;
+  T* wstage = stage + (size_t)warp * (NST + 1) * kStageElems;
+  T* wout = wstage + (size_t)NST * kStageElems;  // this warp's outputs of one step
+  char* wbase = reinterpret_cast<char*>(wstage);
+  // outputs leave through the staging buffer as whole 16-byte chunks when
+  // the segments are 16-byte aligned (the copy layout of b)
+  const bool vec_out = chunk == 16;
+  const int nsteps = nx + RW - 1;
+  auto issue = [&](int ts) {
+    if (ts < nsteps) {
+      char* st = wbase + (ts % NST) * kStageElems * (int)sizeof(T);
+#pragma unroll
+      for (int u = 0; u < UMAX; ++u) {
+        if (crow[u] >= 0) {
+          const int jx = ts - crow[u];
+          if (jx >= 0 && jx < nx) cp_async_bytes(st + cdst[u], bbase + csrc[u] + jx * xstep, chunk);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  __syncthreads();
+#pragma unroll
+  for (int ts = 0; ts < NST - 1; ++ts) issue(ts);
+  const int ownx = negx, owny = negy;
+  const T fmx00 = T(g.facemass[0][0][0]), fmx01 = T(g.facemass[0][0][1]);
+  const T fmx10 = T(g.facemass[0][1][0]), fmx11 = T(g.facemass[0][1][1]);
+  const T fmy00 = T(g.facemass[1][0][0]), fmy01 = T(g.facemass[1][0][1]);
+  const T fmy10 = T(g.facemass[1][1][0]), fmy11 = T(g.facemass[1][1][1]);
+  const T nsx = ownx ? T(1) : T(-1), nsy = owny ? T(1) : T(-1);
+  T xf[HS][A], yo[HS][A];
+#pragma unroll
+  for (int j = 0; j < HS; ++j)
+#pragma unroll
+    for (int m = 0; m < A; ++m) {
+      xf[j][m] = T(0);
+      yo[j][m] = T(0);
+    }
+  const int iy = negy ? ny - 1 - jy : jy;
+  int mat_next = 0;
+  if (mine) mat_next = cd.mat[(negx ? nx - 1 : 0) + nx * iy];
+  for (int ts = 0; ts < nsteps; ++ts) {
+    cp_async_wait<NST - 2>();
+    __syncwarp();
+    issue(ts + NST - 1);
+    const int jx = ts - r;
+    const bool act = mine && jx >= 0 && jx < nx;
+    // y-upwind values: row r - 1's outputs of the step before
+    T yv[HS][A];
+#pragma unroll
+    for (int j = 0; j < HS; ++j)
+#pragma unroll
+      for (int m = 0; m < A; ++m) yv[j][m] = __shfl_up_sync(0xffffffffu, yo[j][m], G);
+    // row 0: the previous warp's last row, once that warp has passed step ts + RW - 1
+    if (warp > 0 && ts < nx) {
+      bool ok = true;
+      if (lane == 0) ok = wait_at_least(prog + warp - 1, ts + RW, err);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      __syncwarp();  // lane 0's acquire orders the ring reads of every lane
+      if (r == 0 && p < nq) {
+        const T* rs = ring + (((size_t)(warp - 1) * R + ts % R) * G + p) * HS * A;
+#pragma unroll
+        for (int j = 0; j < HS; ++j)
+#pragma unroll
+          for (int m = 0; m < A; ++m) yv[j][m] = rs[j * A + m];
+      }
+    }
+    if (act) {
+      const int ix = negx ? nx - 1 - jx : jx;
+      const int c = ix + nx * iy;
+      const int mat = mat_next;
+      if (jx + 1 < nx) mat_next = cd.mat[c + (negx ? -1 : 1)];
+      T rhs[SA];
+      const T* st = wstage + (size_t)(ts % NST) * kStageElems + (size_t)r * RS + p * A;
+#pragma unroll
+      for (int l = 0; l < S; ++l)
+#pragma unroll
+        for (int m = 0; m < A; ++m) rhs[l * A + m] = st[l * SEGP + m];
+      // node l is on the x-inflow face when bit 0 of l equals ownx (face index
+      // bit 1 of l), on the y-inflow face when bit 1 equals owny (bit 0)
+      if (jx > 0) {
+        T dv[HS][A];
+#pragma unroll
+        for (int jp = 0; jp < HS; ++jp)
+#pragma unroll
+          for (int m = 0; m < A; ++m) {
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int dd = 0; dd < A; ++dd) {
+              a0 += Ax[m][dd] * xf[0][dd];
+              a1 += Ax[m][dd] * xf[1][dd];
+            }
+            dv[jp][m] = nsx * (jp == 0 ? fmx00 * a0 + fmx01 * a1 : fmx10 * a0 + fmx11 * a1);
+          }
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const bool on = (l & 1) == ownx;
+#pragma unroll
+          for (int m = 0; m < A; ++m) rhs[l * A + m] -= on ? dv[l >> 1][m] : T(0);
+        }
+      }
+      if (jy > 0) {
+        T dv[HS][A];
+#pragma unroll
+        for (int jp = 0; jp < HS; ++jp)
+#pragma unroll
+          for (int m = 0; m < A; ++m) {
+            T a0 = T(0), a1 = T(0);
+#pragma unroll
+            for (int dd = 0; dd < A; ++dd) {
+              a0 += Ay[m][dd] * yv[0][dd];
+              a1 += Ay[m][dd] * yv[1][dd];
+            }
+            dv[jp][m] = nsy * (jp == 0 ? fmy00 * a0 + fmy01 * a1 : fmy10 * a0 + fmy11 * a1);
+          }
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const bool on = ((l >> 1) & 1) == owny;
+#pragma unroll
+          for (int m = 0; m < A; ++m) rhs[l * A + m] -= on ? dv[l & 1][m] : T(0);
+        }
+      }
+      T x[SA];
+      if (mat < nmat_s) {
+        const T* Ki = kin + ((size_t)mat * G + p) * KST;
+#pragma unroll
+        for (int rr = 0; rr < SA; ++rr) {
+          T acc = T(0);
+#pragma unroll
+          for (int cc = 0; cc < SA; cc += 16 / (int)sizeof(T)) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 k4 = *reinterpret_cast<const float4*>(Ki + rr * SA + cc);
+              acc += k4.x * rhs[cc] + k4.y * rhs[cc + 1] + k4.z * rhs[cc + 2] + k4.w * rhs[cc + 3];
+            } else {
+              const double2 k2 = *reinterpret_cast<const double2*>(Ki + rr * SA + cc);
+              acc += k2.x * rhs[cc] + k2.y * rhs[cc + 1];
+            }
+          }
+          x[rr] = acc;
+        }
+      } else {
+        const T* Ki = t.Kinv + ((size_t)mat * g.P + q) * SA * SA;
+#pragma unroll
+        for (int rr = 0; rr < SA; ++rr) {
+          T acc = T(0);
+#pragma unroll
+          for (int cc = 0; cc < SA; ++cc) acc += __ldg(Ki + rr * SA + cc) * rhs[cc];
+          x[rr] = acc;
+        }
+      }
+      if (vec_out) {
+        T* o = wout + (size_t)r * RS + p * A;
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+          for (int m = 0; m < A; ++m) o[l * SEGP + m] = x[l * A + m];
+      } else {
+        T* out = psi + (long long)c * S * nadof + q * A;
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+          for (int m = 0; m < A; ++m) out[(long long)l * nadof + m] = x[l * A + m];
+      }
+      // outflow faces: nodes with bit 0 (x) or bit 1 (y) equal to 1 - own
+#pragma unroll
+      for (int j = 0; j < HS; ++j)
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          xf[j][m] = ownx ? x[(2 * j) * A + m] : x[(2 * j + 1) * A + m];
+          yo[j][m] = owny ? x[j * A + m] : x[(2 + j) * A + m];
+        }
+    }
+    if (vec_out) {
+      // the step's outputs as 16-byte chunks: the same (row, node, chunk)
+      // triples as the copies of b, each to its cell's segment of psi
+      __syncwarp();
+      char* pbase = reinterpret_cast<char*>(psi);
+      const char* obase = reinterpret_cast<const char*>(wout);
+#pragma unroll
+      for (int u = 0; u < UMAX; ++u) {
+        if (crow[u] >= 0) {
+          const int jx2 = ts - crow[u];
+          if (jx2 >= 0 && jx2 < nx)
+            *reinterpret_cast<int4*>(pbase + csrc[u] + jx2 * xstep) =
+                *reinterpret_cast<const int4*>(obase + cdst[u]);
+        }
+      }
+    }
+    // the last row's outputs into the ring for the next warp
+    const int jl = ts - (RW - 1);
+    if (warp + 1 < nwarp && jl >= 0 && jl < nx) {
+      bool ok = true;
+      if (lane == 0 && jl >= R) ok = wait_at_least(prog + warp + 1, jl - R + 1, err);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (r == RW - 1 && p < nq && jy < ny) {
+        T* rs = ring + (((size_t)warp * R + jl % R) * G + p) * HS * A;
+#pragma unroll
+        for (int j = 0; j < HS; ++j)
+#pragma unroll
+          for (int m = 0; m < A; ++m) rs[j * A + m] = yo[j][m];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) st_release_cta(prog + warp, ts + 1);
+  }
+  cp_async_wait<0>();
+}
+
 // Spatial matrices of the Kronecker form of the diagonal block
 //   K0_q + sigma_t kron(N, M_q) = sum_xi kron(G_xi^(sign), A^xi_q) + sigma_t kron(N, M_q),
 //   G_xi^(+) = Fown_{xi,high} - V_xi,   G_xi^(-) = -Fown_{xi,low} - V_xi,
@@ -599,9 +969,39 @@ size_t sweep2d_smem(const Geom& g, int G, int nmat_s, int nst) {
 
 template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst,
-                  cudaStream_t st) {
+                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst, int variant,
+                  int* err, cudaStream_t st) {
   note_launch();
+  // warp-pipelined form (variant 2; auto with at least 4 patches per block):
+  // Lin basis, G dividing 32 with at least two patches per row, at most 512
+  // threads
+  const bool want_warp = variant == 2 || (variant == 0 && G >= 4);
+  if (g.dim == 2 && want_warp && g.a == 3 && (G == 2 || G == 4 || G == 8) && err) {
+    const int RW = 32 / G, nwarp = (g.ny + RW - 1) / RW;
+    constexpr int NSTW = sizeof(T) == 4 ? 4 : 3;
+    int nmat_s = nmat;
+    while (nmat_s > 0 && sweep2d_warp_smem<T>(g.ny, G, 3, nmat_s, NSTW) > 200 * 1024) --nmat_s;
+    const size_t smem = sweep2d_warp_smem<T>(g.ny, G, 3, nmat_s, NSTW);
+    const int chunk = chunk16 ? 16 : (int)sizeof(T);
+    const int seg_chunks = (G * 3 * (int)sizeof(T)) / chunk;
+    const int need = (RW * 4 * seg_chunks + 31) / 32;
+    if (nwarp * 32 <= 512 && smem <= 200 * 1024 && need <= 12) {
+      auto launch = [&](auto kern) {
+        allow_max_smem(kern);
+        kern<<<sc.ntask, nwarp * 32, smem, st>>>(g, t, cd, sc, b, psi, nmat_s, chunk, err);
+      };
+      auto by_g = [&](auto g_tag) {
+        constexpr int GG = decltype(g_tag)::value;
+        if (need <= 3) launch(sweep2d_warp_kernel<T, 3, GG, NSTW, 3>);
+        else if (need <= 6) launch(sweep2d_warp_kernel<T, 3, GG, NSTW, 6>);
+        else launch(sweep2d_warp_kernel<T, 3, GG, NSTW, 12>);
+      };
+      if (G == 2) by_g(std::integral_constant<int, 2>());
+      else if (G == 4) by_g(std::integral_constant<int, 4>());
+      else by_g(std::integral_constant<int, 8>());
+      return;
+    }
+  }
   if (g.dim == 2 && G > 0 && g.ny * G <= 512) {
     int NST = nst > 0 ? nst : (sizeof(T) == 4 ? 4 : 3);
     NST = NST >= 6 ? 6 : (NST >= 4 ? 4 : (NST >= 3 ? 3 : 2));
@@ -698,8 +1098,8 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 
 #define AMGT_INST(T)                                                                          \
   template void launch_sweep<T>(const Geom&, const LevelDev<T>&, const CellData&,             \
-                                const Schedule&, const T*, T*, int, int, bool, int,           \
-                                cudaStream_t);                                                \
+                                const Schedule&, const T*, T*, int, int, bool, int, int,      \
+                                int*, cudaStream_t);                                          \
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
   template void launch_source<T>(const Geom&, const T*, const T*, const int*, const double*,  \

@@ -59,6 +59,22 @@ def test_fullsize_sweep_sampled_patches(setup):
     assert _rel(_host(y)[:, cols], ref[:, cols]) < TOL32
 
 
+def test_fullsize_warp_pipelined_sweep_sampled_patches(setup):
+    from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
+    prob, ctx, T, _, _ = setup
+    x = W.random_vector((T.nsdof, T.nadof), 83)
+    xd = torch.from_numpy(x).to("cuda", torch.float32)
+    y = torch.empty_like(xd)
+    ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, 2)
+    ctx.amgt_op_sweep(0, xd, y)
+    ctx.amgt_sync()
+    ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, 0)
+    pats = [int(T.patches_of(d)[k]) for d, k in zip(range(4), (3, 64, 100, 127))]
+    ref = T.sweep(x, patches=pats)
+    cols = np.concatenate([np.arange(q * 3, q * 3 + 3) for q in pats])
+    assert _rel(_host(y)[:, cols], ref[:, cols]) < TOL32
+
+
 def test_fullsize_apply_L_and_scatter_sampled_cells(setup):
     prob, ctx, T, _, _ = setup
     x = W.random_vector((T.nsdof, T.nadof), 82)

@@ -377,6 +377,37 @@ def test_row_pipelined_gs_3d_several_rows_per_block():
     ctx.close()
 
 
+@pytest.mark.parametrize("group", [2, 4, 8], ids=["G2", "G4", "G8"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nc", [(37, 29), (5, 21), (70, 24)], ids=["37x29", "5x21", "70x24"])
+def test_warp_pipelined_sweep(group, dtype, nc):
+    """The 2D warp-pipelined sweep (AMGT_TUNE_SWEEP_KERNEL = 2) against the
+    oracle on two patches of every direction, and against the level-
+    synchronous row sweep on all of them: ragged last warps, rows shorter than
+    the hand-over ring and rows that wrap it several times, inflow faces."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
+    prob = W.random_problem(2, nc, 2, 4, 35, inflow=0.3)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(2, group)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    x = _dev(W.random_vector((T.nsdof, T.nadof), 36), td)
+    yw = torch.empty_like(x)
+    yr = torch.empty_like(x)
+    ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, 2)
+    ctx.amgt_op_sweep(0, x, yw)
+    ctx.amgt_sync()
+    ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, 1)
+    ctx.amgt_op_sweep(0, x, yr)
+    assert _rel(_host(yw), _host(yr)) < (1e-14 if dtype == "f64" else 1e-6)
+    pats = [q for d in range(T.ndir) for q in T.patches_of(d)[:2]]
+    ref = T.sweep(_host(x), patches=pats)
+    cols = np.concatenate([np.arange(q * T.a, (q + 1) * T.a) for q in pats])
+    assert _rel(_host(yw)[:, cols], ref[:, cols]) < tol
+    ctx.close()
+
+
 def test_kernel_timers_count_launches():
     """The library's per-kernel event timers: off by default (nothing
     recorded), on: one timed launch per operator call with positive time."""
