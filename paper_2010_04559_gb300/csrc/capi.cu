@@ -766,18 +766,29 @@ int ensure_dense_bf16(amgt_ctx* ctx, int k) {
   return AMGT_OK;
 }
 
-// Slice width and pair groups of the split FP64 contraction for inner
+// Slice width and GEMM passes of the split FP64 contraction for inner
 // dimension K (kernels_split64.cu): `bits` b is the largest (at most 7, so
 // that digits up to 2^7 are exact in BF16) with K 2^(2b) <= 2^24, the range
 // of exact FP32 integers; nsl = ceil(50 / b) slices keep 50 bits of each
-// operand; the pairs (i, j) of slices with i + j = d < nsl are grouped so
-// that the sum of their bounds K D_i D_j (D_0 = 2^b, D_i = 2^(b-1)) stays
-// within 2^24, and each group is accumulated on the tensor cores before one
-// FP64 accumulation.  bits = 0: the split form does not apply.
+// operand, and the products of slices (i, j) with i + j = d < nsl are taken.
+// Leading diagonals d < dt = ceil(26 / b): the pairs are grouped so that the
+// sum of their bounds K D_i D_j (D_0 = 2^b, D_i = 2^(b-1)) stays within 2^24,
+// each group accumulated exactly on the tensor cores (beta = 1) and then in
+// FP64.  Trailing diagonals d >= dt: one Horner pass from d = nsl - 1 down
+// to dt in FP32 (the first product of each diagonal takes beta = 2^-b); its
+// rounding is 2^-24 of a sum 2^(-b dt) <= 2^-26 below the leading term.
+// bits = 0: the split form does not apply.
+struct SplitGemm {
+  int i, j;
+  float beta;
+};
+struct SplitPass {
+  std::vector<SplitGemm> gemms;
+  int d;  // the pass is accumulated into y with the scale 2^(-b (d + 2))
+};
 struct SplitPlan {
   int bits = 0, nsl = 0;
-  std::vector<int> gd;  // diagonal d of each group
-  std::vector<std::vector<std::pair<int, int>>> groups;
+  std::vector<SplitPass> passes;
 };
 
 SplitPlan split_plan(int K) {
@@ -788,23 +799,32 @@ SplitPlan split_plan(int K) {
   if (b < 2) return p;
   p.bits = b;
   p.nsl = (50 + b - 1) / b;
+  const int dt = std::min(p.nsl, (26 + b - 1) / b);
   auto D = [&](int i) { return std::ldexp(1.0, i == 0 ? b : b - 1); };
-  for (int d = 0; d < p.nsl; ++d) {
-    std::vector<std::pair<int, int>> cur;
+  for (int d = 0; d < dt; ++d) {
+    SplitPass cur{{}, d};
     double acc = 0.0;
     for (int i = 0; i <= d; ++i) {
       const double bound = (double)K * D(i) * D(d - i);
-      if (!cur.empty() && acc + bound > lim) {
-        p.groups.push_back(cur);
-        p.gd.push_back(d);
-        cur.clear();
+      if (!cur.gemms.empty() && acc + bound > lim) {
+        p.passes.push_back(cur);
+        cur = SplitPass{{}, d};
         acc = 0.0;
       }
-      cur.push_back({i, d - i});
+      cur.gemms.push_back({i, d - i, cur.gemms.empty() ? 0.0f : 1.0f});
       acc += bound;
     }
-    p.groups.push_back(cur);
-    p.gd.push_back(d);
+    p.passes.push_back(cur);
+  }
+  if (dt < p.nsl) {
+    SplitPass tail{{}, dt};
+    for (int d = p.nsl - 1; d >= dt; --d)
+      for (int i = 0; i <= d; ++i) {
+        const float beta =
+            tail.gemms.empty() ? 0.0f : (i == 0 ? std::ldexp(1.0f, -b) : 1.0f);
+        tail.gemms.push_back({i, d - i, beta});
+      }
+    p.passes.push_back(tail);
   }
   return p;
 }
@@ -888,15 +908,13 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
       launch_split_rows(rows, n, S, true, x + r0 * n, ctx->d_sigs + r0 / S, ctx->geom.Nmass,
                         sp.nsl, sp.bits, mu, xs, rows * n, ctx->stream);
     }
-    for (size_t g = 0; g < sp.groups.size(); ++g) {
-      const auto& grp = sp.groups[g];
-      for (size_t e = 0; e < grp.size(); ++e) {
-        const int i = grp[e].first, j = grp[e].second;
+    for (const SplitPass& pass : sp.passes) {
+      for (const SplitGemm& gm : pass.gemms) {
         int rc;
         {
           KernelTimer kt(ctx, AMGT_KT_SPLIT_TC);
-          rc = launch_tc_gemm((int)rows, n, n, xs + (size_t)i * rows * n,
-                              L.Sf_split + (size_t)j * n * n, P, nullptr, e == 0 ? 0.0f : 1.0f,
+          rc = launch_tc_gemm((int)rows, n, n, xs + (size_t)gm.i * rows * n,
+                              L.Sf_split + (size_t)gm.j * n * n, P, nullptr, gm.beta,
                               ctx->d_status, ctx->stream);
         }
         if (rc != 0)
@@ -904,7 +922,7 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
                       "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
       }
       KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX);
-      launch_split_flush(rows, n, P, mu, L.Sf_nu, alpha * std::ldexp(1.0, -sp.bits * (sp.gd[g] + 2)),
+      launch_split_flush(rows, n, P, mu, L.Sf_nu, alpha * std::ldexp(1.0, -sp.bits * (pass.d + 2)),
                          y + r0 * n, ctx->stream);
     }
   }

@@ -4,17 +4,20 @@
 // multiplication", Numer. Algorithms 59, 2012), restated for tcgen05 BF16
 // MMAs with FP32 accumulation.
 //
-// A row z of an FP64 matrix is scaled by mu = 2^e, the power of two just
-// above max |z|, and cut into digit slices: t_0 = z / mu, then for each slice
-// t <- t 2^b, d = rint(t), t <- t - d.  Every step is exact in FP64, every
-// digit is an integer with |d_0| <= 2^b and |d_i| <= 2^(b-1) for i >= 1, so
-// it is exact in BF16, and z = mu sum_i d_i 2^(-b(i+1)) + mu t 2^(-b nsl).
+// A row z of an FP64 matrix is scaled by mu = 2^e, a power of two above
+// max |z|, and cut into nsl digit slices of b bits: z / mu rounded to a
+// multiple of 2^(-b nsl) is sum_i d_i 2^(-b(i+1)) with integer digits,
+// |d_0| <= 2^b and |d_i| <= 2^(b-1) for i >= 1 (balanced), exact in BF16.
 // For two sliced operands the product of slices i and j is a matrix of
 // integer dot products bounded by K 2^(2b); while the accumulated bound
 // stays at or below 2^24 the FP32 accumulator holds it exactly.  The host
-// picks b and groups the slice pairs of each diagonal i + j = d under that
-// bound; each group's exact integer sums are scaled by mu_r nu_c 2^(-b(d+2))
-// (a power of two) and accumulated in FP64.
+// picks b and groups the slice pairs of each leading diagonal i + j = d under
+// that bound; each group's exact integer sums are scaled by mu_r nu_c
+// 2^(-b(d+2)) (a power of two) and accumulated in FP64.  The trailing
+// diagonals, whose sum lies 2^(-b d_t) below the leading term, are summed on
+// the tensor cores in FP32 by Horner's rule (each diagonal's first product
+// adds 2^(-b) times the sum of the less significant ones) and accumulated in
+// FP64 once.
 #include "kernels.cuh"
 
 namespace amgt {
@@ -48,66 +51,94 @@ __device__ __forceinline__ void row_values(const double* __restrict__ x, long lo
 
 // One block per group of S rows.  mu[r] receives the row scale 2^e,
 // out[i * slice_stride + r K + k] the digit of slice i.
+//
+// The scale comes from a bound rather than the exact maximum: with m_i the
+// largest |x| of input row i (an integer maximum of the bit patterns, no FP64
+// arithmetic), |z_l| <= |sig| sum_i |N_li| m_i, and 2^e is the power of two
+// above that bound (at most a bit is lost where rows cancel).  The digits are
+// then taken in integer arithmetic: T = rint(z 2^(bits nsl - e)) is an exact
+// integer with |T| <= 2^(bits nsl); from the least significant end, the
+// balanced remainder r in [-2^(bits-1), 2^(bits-1)) of T modulo 2^bits is a
+// digit and (T - r) / 2^bits (an exact shift) carries on; what is left after
+// nsl - 1 digits is the leading digit, |d_0| <= 2^bits.  GB300's FP64 rate
+// makes the FP64 form of this (three FP64 operations per digit) the slowest
+// step of the split scatter; here each unknown costs the mixing, two FP64
+// multiplications and one conversion.  A row whose bound is not finite gets
+// mu = NaN, so the product carries it.
 template <int S, bool MIX>
 __global__ void __launch_bounds__(kSplitThreads) split_rows_kernel(
     long long rows, int K, const double* __restrict__ x, const double* __restrict__ sig,
     NmassArg nm, int nsl, int bits, double* __restrict__ mu, __nv_bfloat16* __restrict__ out,
     long long slice_stride) {
-  __shared__ double red[kSplitThreads / 32][S];
+  __shared__ unsigned long long red[kSplitThreads / 32][S];
   __shared__ double inv_s[S];
   __shared__ double Nm[S * S];
   const long long r0 = (long long)blockIdx.x * S;
   if (r0 >= rows) return;
   const int nrow = (int)min((long long)S, rows - r0);
   for (int e = threadIdx.x; e < S * S; e += blockDim.x) Nm[e] = MIX ? nm.v[e] : 0.0;
-  __syncthreads();
   const double sg = MIX ? sig[r0 / S] : 1.0;
-  double m[S];
+  // largest |x| of each input row as bit patterns (monotone for |x|)
+  unsigned long long m[S];
 #pragma unroll
-  for (int l = 0; l < S; ++l) m[l] = 0.0;
+  for (int i = 0; i < S; ++i) m[i] = 0ull;
+  const unsigned long long* xb = reinterpret_cast<const unsigned long long*>(x);
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double z[S];
-    row_values<S, MIX>(x, r0, K, nrow, k, sg, Nm, z);
 #pragma unroll
-    for (int l = 0; l < S; ++l) m[l] = fmax(m[l], fabs(z[l]));
+    for (int i = 0; i < S; ++i)
+      if (i < nrow) {
+        const unsigned long long v = xb[(r0 + i) * (long long)K + k] & 0x7fffffffffffffffull;
+        m[i] = v > m[i] ? v : m[i];
+      }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int l = 0; l < S; ++l) {
-    double v = m[l];
+  for (int i = 0; i < S; ++i) {
+    unsigned long long v = m[i];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) red[warp][l] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
   if (threadIdx.x < S) {
     const int l = threadIdx.x;
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w][l]);
+    double bound = 0.0;
+    for (int i = 0; i < S; ++i) {
+      unsigned long long v = 0ull;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = red[w][i] > v ? red[w][i] : v;
+      const double mi = __longlong_as_double((long long)v);
+      if (MIX) bound += fabs(Nm[l * S + i]) * mi;
+      else if (i == l) bound = mi;
+    }
+    bound *= fabs(sg);
     int e = 0;
-    if (v > 0.0) frexp(v, &e);  // v = f 2^e, f in [0.5, 1): v < 2^e
-    if (l < nrow) mu[r0 + l] = ldexp(1.0, e);
-    inv_s[l] = ldexp(1.0, -e);
+    if (bound > 0.0) frexp(bound, &e);  // bound = f 2^e, f in [0.5, 1)
+    if (l < nrow) mu[r0 + l] = isfinite(bound) ? ldexp(1.0, e) : __longlong_as_double(0x7ff8000000000000ll);
+    inv_s[l] = isfinite(bound) ? ldexp(1.0, -e) : 0.0;
   }
   __syncthreads();
   double inv[S];
 #pragma unroll
   for (int l = 0; l < S; ++l) inv[l] = inv_s[l];
-  const double up = ldexp(1.0, bits);
+  const double p2 = ldexp(1.0, bits * nsl);
+  const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double z[S];
     row_values<S, MIX>(x, r0, K, nrow, k, sg, Nm, z);
 #pragma unroll
     for (int l = 0; l < S; ++l) {
       if (l >= nrow) break;
-      double t = z[l] * inv[l];
+      long long T = __double2ll_rn((z[l] * inv[l]) * p2);
       __nv_bfloat16* o = out + (r0 + l) * (long long)K + k;
-      for (int i = 0; i < nsl; ++i) {
-        t *= up;
-        const double d = rint(t);
-        t -= d;
-        o[i * slice_stride] = __double2bfloat16(d);
+      for (int i = nsl - 1; i > 0; --i) {
+        const long long r = ((T + half) & mask) - half;
+        T = (T - r) >> bits;
+        o[i * slice_stride] = __float2bfloat16_rn((float)r);
       }
+      o[0] = __float2bfloat16_rn((float)T);
     }
   }
 }
