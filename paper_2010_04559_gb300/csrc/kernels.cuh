@@ -71,7 +71,12 @@ inline cudaError_t allow_max_smem(K kern) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  // the opt-in limit covers static and dynamic shared memory together
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              mx - (int)fa.sharedSizeBytes);
 }
 
 // status word written by device-side bounded waits

@@ -40,6 +40,15 @@ namespace {
 constexpr int kRowsMaxThreads = 512;
 constexpr int kRowsMaxU = 2;  // padded cell unknowns per thread
 constexpr int kRowsMaxM = 8;  // cell moments per thread
+// prefetch register shapes (unknowns, moments per thread) of the kernel
+// instantiations: a prefetched value spilled to local memory would make the
+// prefetch wait for its load, so each launch takes the smallest shape that
+// holds its cell
+__host__ __device__ inline int rows_shape(int Ev, int Snm, int nt) {
+  if (Ev <= nt && Snm <= nt) return 0;       // 1, 1
+  if (Ev <= 2 * nt && Snm <= 2 * nt) return 1;  // 2, 2
+  return 2;                                     // 2, 8
+}
 // give up a face wait after this long: the block records code 5 in the
 // status word and goes on; every later wait of every block then returns at once
 constexpr unsigned long long kRowsWaitNs = 2000000000ULL;
@@ -187,8 +196,8 @@ struct RowsArgs {
   int* err;
 };
 
-template <class T, int DIM, int A>
-__global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArgs<T> p) {
+template <class T, int DIM, int A, int UM, int MM>
+__global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(RowsArgs<T> p) {
   constexpr int S = 1 << DIM;
   constexpr int HS = S / 2;
   constexpr int VW = V16<T>::n;
@@ -218,6 +227,10 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
   T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [NF][HS][Jv] y/z inflow
   T* Tg = reinterpret_cast<T*>(smem_raw + Ly.o_Tg);      // [2][Emax (col)][Emax (row)]
+  // first patch of each direction, kept on chip: the prefetch computes its
+  // addresses from it, and a global load there would stall every cell
+  __shared__ int sdb[8];
+  if (tid < ndir) sdb[tid] = p.dir_begin[tid];
   for (int i = tid; i < S * S; i += NT) Ns[i] = (T)g.Nmass[i];
   for (int i = tid; i < 2 * Ev; i += NT) bufs[i] = T(0);
   for (int i = tid; i < 2 * S * NMp; i += NT) phss[i] = T(0);
@@ -242,7 +255,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   __syncthreads();
   long long kc = 0;     // cells solved by this block (buffer parity)
   // prefetch registers for the next cell
-  T pf[kRowsMaxU], px[kRowsMaxU], pm[kRowsMaxM];
+  T pf[UM], px[UM], pm[MM];
   int pmat = 0;
   T psig = T(0);
   long long c_next = -1;
@@ -252,9 +265,9 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
     const int ix = n0 ? nx - 1 - k : k;
     const long long c = ix + (long long)nx * R;
     c_next = c;
-    const int qa = p.dir_begin[d] * A;
+    const int qa = sdb[d] * A;
 #pragma unroll
-    for (int u = 0; u < kRowsMaxU; ++u) {
+    for (int u = 0; u < UM; ++u) {
       const int pe = tid + u * NT;
       pf[u] = T(0);
       px[u] = T(0);
@@ -268,19 +281,25 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
       }
     }
 #pragma unroll
-    for (int u = 0; u < kRowsMaxM; ++u) {
+    for (int u = 0; u < MM; ++u) {
       const int e = tid + u * NT;
       if (e < S * nm) pm[u] = __ldcg(p.mom + c * S * nm + e);
     }
     pmat = p.cd.mat[c];
-    psig = (T)p.cd.sigma_s[c];
-    // the block inverse of an unstaged material into the free buffer
-    if (p.gbuf > 0 && pmat >= p.nmat_s) {
-      const char* src = reinterpret_cast<const char*>(
-          p.TinvT + ((size_t)pmat * ndir + d) * p.Emax * p.Emax);
-      char* dst = reinterpret_cast<char*>(Tg + (size_t)((kc + 1) & 1) * p.gbuf);
-      const int nchunk = p.Emax * p.Emax * (int)sizeof(T) / 16;
-      for (int i = tid; i < nchunk; i += NT) cp_async16(dst + 16 * i, src + 16 * i);
+    // sigma_s in the kernel's precision: a conversion here would wait for the
+    // load and stall the prefetch
+    if constexpr (sizeof(T) == 4) psig = p.cd.sigma_s32[c];
+    else psig = p.cd.sigma_s[c];
+    // the block inverse of an unstaged material into the free buffer (pmat is
+    // only waited for when such materials exist)
+    if (p.gbuf > 0) {
+      if (pmat >= p.nmat_s) {
+        const char* src = reinterpret_cast<const char*>(
+            p.TinvT + ((size_t)pmat * ndir + d) * p.Emax * p.Emax);
+        char* dst = reinterpret_cast<char*>(Tg + (size_t)((kc + 1) & 1) * p.gbuf);
+        const int nchunk = p.Emax * p.Emax * (int)sizeof(T) / 16;
+        for (int i = tid; i < nchunk; i += NT) cp_async16(dst + 16 * i, src + 16 * i);
+      }
     }
   };
   // Phi_c += X_d^T delta for the cell `cp` whose delta is in buffer `slot`;
@@ -386,7 +405,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
           // ---- 1: the cell's data into shared memory; first look at the faces;
           //         the previous cell's moment update
 #pragma unroll
-          for (int u = 0; u < kRowsMaxU; ++u) {
+          for (int u = 0; u < UM; ++u) {
             const int pe = tid + u * NT;
             if (pe < Ev) {
               rhs[pe] = pf[u];
@@ -395,7 +414,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
           }
           if (c != last) {
 #pragma unroll
-            for (int u = 0; u < kRowsMaxM; ++u) {
+            for (int u = 0; u < MM; ++u) {
               const int e = tid + u * NT;
               if (e < S * nm) {
                 const int lk = slk[e];
@@ -569,33 +588,41 @@ __global__ void __launch_bounds__(kRowsMaxThreads) coarse_gs_rows_kernel(RowsArg
   cp_async_wait_all();
 }
 
-template <class T, int DIM, int A>
-cudaError_t rows_launch(const RowsArgs<T>& a, int nblocks, int threads, size_t smem,
-                        cudaStream_t st) {
-  auto kern = coarse_gs_rows_kernel<T, DIM, A>;
-  cudaError_t e = allow_max_smem(kern);
-  if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(threads), args, smem, st);
+template <class T, int DIM, int A, class F>
+auto with_rows_kernel(int shape, F f) {
+  if (shape == 0) return f(coarse_gs_rows_kernel<T, DIM, A, 1, 1>);
+  if (shape == 1) return f(coarse_gs_rows_kernel<T, DIM, A, 2, 2>);
+  return f(coarse_gs_rows_kernel<T, DIM, A, 2, 8>);
 }
 
 template <class T, int DIM, int A>
-int rows_max_blocks(int threads, size_t smem) {
-  auto kern = coarse_gs_rows_kernel<T, DIM, A>;
-  if (allow_max_smem(kern) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int per_sm = 0, dev = 0, nsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return per_sm * nsm;
+cudaError_t rows_launch(const RowsArgs<T>& a, int shape, int nblocks, int threads, size_t smem,
+                        cudaStream_t st) {
+  return with_rows_kernel<T, DIM, A>(shape, [&](auto kern) {
+    cudaError_t e = allow_max_smem(kern);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&a};
+    return cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(threads), args, smem, st);
+  });
+}
+
+template <class T, int DIM, int A>
+int rows_max_blocks(int shape, int threads, size_t smem) {
+  return with_rows_kernel<T, DIM, A>(shape, [&](auto kern) {
+    if (allow_max_smem(kern) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int per_sm = 0, dev = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm * nsm;
+  });
 }
 
 }  // namespace
@@ -626,11 +653,14 @@ int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, i
   const size_t bytes = bytes_for(ns);
   if (bytes > 200 * 1024) return 0;
   *gbuf = ns < nmat ? gb : 0;
+  const int shape = rows_shape(l0.Ev, S * nmom, nt);
   int nb;
   if (g.dim == 2)
-    nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(nt, bytes) : rows_max_blocks<T, 2, 1>(nt, bytes);
+    nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(shape, nt, bytes)
+                  : rows_max_blocks<T, 2, 1>(shape, nt, bytes);
   else
-    nb = g.a == 3 ? rows_max_blocks<T, 3, 3>(nt, bytes) : rows_max_blocks<T, 3, 1>(nt, bytes);
+    nb = g.a == 3 ? rows_max_blocks<T, 3, 3>(shape, nt, bytes)
+                  : rows_max_blocks<T, 3, 1>(shape, nt, bytes);
   nb = std::min(nb, g.ny * g.nz);
   *nmat_s = ns;
   *threads = nt;
@@ -647,13 +677,15 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
                           unsigned tag0, int* err, cudaStream_t st) {
   RowsArgs<T> a{g, t, cd, ndir, dir_begin, dir_end, sweeps, f, phi, mom, TinvT, SLD,
                 Emax, Jmax, nmat, nmat_s, gbuf, rows, rpb, faces, tag0, err};
+  const RowsLayout<T> l0(0, Jmax, t.nmom, g.s, g.dim, g.a, ndir, 0);
+  const int shape = rows_shape(l0.Ev, g.s * t.nmom, threads);
   cudaError_t e;
   if (g.dim == 2)
-    e = g.a == 3 ? rows_launch<T, 2, 3>(a, nblocks, threads, smem, st)
-                 : rows_launch<T, 2, 1>(a, nblocks, threads, smem, st);
+    e = g.a == 3 ? rows_launch<T, 2, 3>(a, shape, nblocks, threads, smem, st)
+                 : rows_launch<T, 2, 1>(a, shape, nblocks, threads, smem, st);
   else
-    e = g.a == 3 ? rows_launch<T, 3, 3>(a, nblocks, threads, smem, st)
-                 : rows_launch<T, 3, 1>(a, nblocks, threads, smem, st);
+    e = g.a == 3 ? rows_launch<T, 3, 3>(a, shape, nblocks, threads, smem, st)
+                 : rows_launch<T, 3, 1>(a, shape, nblocks, threads, smem, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -1;
