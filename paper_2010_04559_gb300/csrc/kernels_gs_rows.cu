@@ -469,7 +469,16 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
               const int l = lj >> 16, j = lj & 0xffff;
               const T* xr = XFr + j * NMp;
               const T* ph = phs + l * NMp;
-              for (int ch = l4 * VW; ch < NMp; ch += 4 * VW) a += V16<T>::dot(xr + ch, ph + ch);
+              // two partial sums and an unrolled loop: the loads of several
+              // chunks are in flight together
+              T a1 = T(0);
+#pragma unroll 4
+              for (int ch = l4 * VW, it = 0; ch < NMp; ch += 4 * VW, ++it) {
+                const T v = V16<T>::dot(xr + ch, ph + ch);
+                if (it & 1) a1 += v;
+                else a += v;
+              }
+              a += a1;
               const T* sl = SLr + j * Jp;
               const T* xo = xold + l * Jv;
               for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a -= V16<T>::dot(sl + ch, xo + ch);
@@ -535,7 +544,14 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
             if (lj >= 0) {
               if (mat < p.nmat_s) {
                 const T* row = Tin + ((size_t)mat * Ev + pe) * Evp;
-                for (int ch = l4 * VW; ch < Ev; ch += 4 * VW) a += V16<T>::dot(row + ch, rhs + ch);
+                T a1 = T(0);
+#pragma unroll 4
+                for (int ch = l4 * VW, it = 0; ch < Ev; ch += 4 * VW, ++it) {
+                  const T v = V16<T>::dot(row + ch, rhs + ch);
+                  if (it & 1) a1 += v;
+                  else a += v;
+                }
+                a += a1;
               } else if (p.gbuf > 0) {
                 const int r = (lj >> 16) * J + (lj & 0xffff);
                 const T* col = Tg + (size_t)(kc & 1) * p.gbuf + r;
