@@ -70,9 +70,9 @@ __host__ __device__ inline int qpad(int n) {
 // Shared-memory layout of one block (byte offsets, 16-byte aligned).
 template <class T>
 struct RowsLayout {
-  int Jv, Ev, Evp, NMp, Jp;
+  int Jv, Ev, Evp, NMp, Jp, Eyl, Wp;
   size_t o_Tin, o_XFr, o_Xk, o_SLr, o_Ns, o_Ad, o_lj, o_lk, o_rhs, o_xold, o_buf, o_phs, o_xfc,
-      o_yup, o_Tg, bytes;
+      o_yup, o_Tg, o_W, o_y0, bytes;
   // gbuf: elements of one prefetch buffer for a block inverse that is not
   // staged (0: read those from global memory)
   __host__ __device__ RowsLayout(int nmat_s, int Jmax, int nm, int S, int dim, int A, int ndir,
@@ -83,6 +83,8 @@ struct RowsLayout {
     Evp = qpad<T>(Ev);
     NMp = qpad<T>(nm);
     Jp = qpad<T>(Jv);
+    Eyl = (dim - 1) * (S / 2) * Jv;  // inflow unknowns from the other rows' blocks
+    Wp = qpad<T>(Eyl);
     size_t o = 0;
     auto take = [&](size_t nbytes) {
       const size_t at = o;
@@ -105,6 +107,8 @@ struct RowsLayout {
     o_xfc = take((size_t)(S / 2) * Jv * t);
     o_yup = take((size_t)(dim - 1) * (S / 2) * Jv * t);
     o_Tg = take((size_t)2 * gbuf * t);
+    o_W = take((size_t)nmat_s * Ev * Wp * t);
+    o_y0 = take((size_t)Ev * t);
     bytes = o;
   }
 };
@@ -227,6 +231,12 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
   T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
   T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [NF][HS][Jv] y/z inflow
   T* Tg = reinterpret_cast<T*>(smem_raw + Ly.o_Tg);      // [2][Emax (col)][Emax (row)]
+  // Tinv U for the y/z inflow of staged materials: x = Tinv rhs0 + W yup, so
+  // the block solve runs before the other rows' face values arrive
+  T* Wl = reinterpret_cast<T*>(smem_raw + Ly.o_W);       // [nmat_s][Ev][Wp]
+  T* y0 = reinterpret_cast<T*>(smem_raw + Ly.o_y0);      // [Ev] Tinv rhs0
+  const int Eyl = Ly.Eyl, Wp = Ly.Wp;
+  for (int i = tid; i < Eyl; i += NT) yup[i] = T(0);  // padding stays zero
   // first patch of each direction, kept on chip: the prefetch computes its
   // addresses from it, and a global load there would stall every cell
   __shared__ int sdb[8];
@@ -389,6 +399,34 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
         pj = rem - pjn * J;
       }
       __syncthreads();
+      // W[(lr, jr)][(axis, jn, jq A + dd)] = sum over the inflow-face nodes l
+      // and m of Tinv[(lr, jr)][(l, jq A + m)] U, with U the coupling of the
+      // rhs of (l, jq A + m) to the upwind face value (jn, jq A + dd) as in
+      // the rhs assembly below
+      for (int i = tid; i < p.nmat_s * Ev * Eyl; i += NT) {
+        const int mt = i / (Ev * Eyl);
+        const int rem = i - mt * Ev * Eyl;
+        const int pe = rem / Eyl, ey = rem - pe * Eyl;
+        const int xi = 1 + ey / (HS * Jv);
+        const int jn = (ey / Jv) % HS, jc = ey % Jv;
+        T w = T(0);
+        if (lj_d[pe] >= 0 && jc < J) {
+          const int own = xi == 1 ? n1 : n2;
+          const int jq = jc / A, dd = jc - jq * A;
+          const T sg = own ? T(-1) : T(1);
+          const T* trow = Tin + ((size_t)mt * Ev + pe) * Evp;
+#pragma unroll
+          for (int l = 0; l < S; ++l) {
+            if (((l >> xi) & 1) != own) continue;
+            const T fm = sg * T(g.facemass[xi][fcompress(l, xi)][jn]);
+#pragma unroll
+            for (int m = 0; m < A; ++m)
+              w += trow[l * Jv + jq * A + m] * fm * Ad[((size_t)jq * DIM + xi) * A * A + m * A + dd];
+          }
+        }
+        Wl[((size_t)mt * Ev + pe) * Wp + ey] = w;
+      }
+      __syncthreads();
       for (int ri = 0;; ++ri) {
         const int R = row_of(d, ri);
         if (R < 0) break;
@@ -487,24 +525,33 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
             a += __shfl_xor_sync(0xffffffffu, a, 2);
             if (pe < Ev && l4 == 0) buf[pe] = a;
           }
-          // the upwind rows' face words
-          if (need) {
-            if (!FaceWords<T>::ready(fw, tag)) {
-              const unsigned long long t0 = gsx::now_ns();
-              unsigned it = 0;
-              do {
-                FaceWords<T>::load(wp, fw);
-                if ((++it & 63u) == 0) {
-                  // after any block gave up, the others stop waiting too
-                  if (gsx::now_ns() - t0 > kRowsWaitNs) atomicExch(p.err, 5);
-                  if (*reinterpret_cast<volatile int*>(p.err) != 0) break;
-                }
-              } while (!FaceWords<T>::ready(fw, tag));
+          // staged materials take the y/z inflow after the block solve:
+          // rhs0 leaves it out, y0 = Tinv rhs0, then x = y0 + W yup
+          // (rows on the inflow boundary have nothing to wait for)
+          const bool late = mat < p.nmat_s && (jy > 0 || (DIM == 3 && jz > 0));
+          auto wait_faces = [&]() {
+            if (need) {
+              if (!FaceWords<T>::ready(fw, tag)) {
+                const unsigned long long t0 = gsx::now_ns();
+                unsigned it = 0;
+                do {
+                  FaceWords<T>::load(wp, fw);
+                  if ((++it & 63u) == 0) {
+                    // after any block gave up, the others stop waiting too
+                    if (gsx::now_ns() - t0 > kRowsWaitNs) atomicExch(p.err, 5);
+                    if (*reinterpret_cast<volatile int*>(p.err) != 0) break;
+                  }
+                } while (!FaceWords<T>::ready(fw, tag));
+              }
+              yup[(pa * HS + pjn) * Jv + pj] = FaceWords<T>::value(fw);
+            } else if (tid < npoll) {
+              yup[(pa * HS + pjn) * Jv + pj] = T(0);  // a boundary face: no inflow here
             }
-            yup[(pa * HS + pjn) * Jv + pj] = FaceWords<T>::value(fw);
-          }
+          };
+          // the upwind rows' face words
+          if (!late) wait_faces();
           __syncthreads();
-          // ---- 3: rhs = f - upwind + sigma_s N buf
+          // ---- 3: rhs = f - upwind + sigma_s N buf (x only when late)
           for (int pe = tid; pe < Ev; pe += NT) {
             const int lj = lj_d[pe];
             if (lj < 0) continue;
@@ -513,6 +560,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
             T val = rhs[pe];
 #pragma unroll
             for (int xi = 0; xi < DIM; ++xi) {
+              if (late && xi > 0) continue;
               const int own = xi == 0 ? n0 : (xi == 1 ? n1 : n2);
               const int jr = xi == 0 ? k : (xi == 1 ? jy : jz);
               if (jr == 0 || ((l >> xi) & 1) != own) continue;
@@ -537,6 +585,27 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
           cp_async_wait_prior();  // this cell's inverse (the next cell's may still fly)
           __syncthreads();
           // ---- 4: x_new = Tinv rhs (four lanes per row); outputs
+          auto emit = [&](int pe, int lj, T a) {
+            if (lj >= 0) {
+              const int l = lj >> 16, j = lj & 0xffff;
+              p.psi[(c * S + l) * nadof + qb * A + j] = a;
+              buf[pe] = a - xold[pe];
+              if (((l & 1) ^ n0) == 1) xfc[fcompress(l, 0) * Jv + j] = a;
+#pragma unroll
+              for (int xi = 1; xi < DIM; ++xi) {
+                const int own = xi == 1 ? n1 : n2;
+                const int jr = xi == 1 ? jy : jz;
+                const int nn = xi == 1 ? g.ny : g.nz;
+                if (((l >> xi) & 1) == own || jr == nn - 1) continue;
+                unsigned long long* wq =
+                    p.faces + ((((size_t)(xi - 1) * ndir + d) * g.C + c) * HS * p.Jmax +
+                               (size_t)fcompress(l, xi) * J + j) * W;
+                FaceWords<T>::put(wq, a, tag);
+              }
+            } else {
+              buf[pe] = T(0);
+            }
+          };
           for (int base = 0; base < Ev; base += NQ) {
             const int pe = base + qd;
             const int lj = pe < Ev ? lj_d[pe] : -1;
@@ -571,25 +640,25 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
             a += __shfl_xor_sync(0xffffffffu, a, 1);
             a += __shfl_xor_sync(0xffffffffu, a, 2);
             if (pe < Ev && l4 == 0) {
-              if (lj >= 0) {
-                const int l = lj >> 16, j = lj & 0xffff;
-                p.psi[(c * S + l) * nadof + qb * A + j] = a;
-                buf[pe] = a - xold[pe];
-                if (((l & 1) ^ n0) == 1) xfc[fcompress(l, 0) * Jv + j] = a;
-#pragma unroll
-                for (int xi = 1; xi < DIM; ++xi) {
-                  const int own = xi == 1 ? n1 : n2;
-                  const int jr = xi == 1 ? jy : jz;
-                  const int nn = xi == 1 ? g.ny : g.nz;
-                  if (((l >> xi) & 1) == own || jr == nn - 1) continue;
-                  unsigned long long* wq =
-                      p.faces + ((((size_t)(xi - 1) * ndir + d) * g.C + c) * HS * p.Jmax +
-                                 (size_t)fcompress(l, xi) * J + j) * W;
-                  FaceWords<T>::put(wq, a, tag);
-                }
-              } else {
-                buf[pe] = T(0);
+              if (late) y0[pe] = a;
+              else emit(pe, lj, a);
+            }
+          }
+          if (late) {
+            // ---- 5: the other rows' face values, then x = y0 + W yup
+            wait_faces();
+            __syncthreads();
+            for (int base = 0; base < Ev; base += NQ) {
+              const int pe = base + qd;
+              const int lj = pe < Ev ? lj_d[pe] : -1;
+              T a = T(0);
+              if (lj >= 0 && NF > 0) {
+                const T* wr = Wl + ((size_t)mat * Ev + pe) * Wp;
+                for (int ch = l4 * VW; ch < Eyl; ch += 4 * VW) a += V16<T>::dot(wr + ch, yup + ch);
               }
+              a += __shfl_xor_sync(0xffffffffu, a, 1);
+              a += __shfl_xor_sync(0xffffffffu, a, 2);
+              if (pe < Ev && l4 == 0) emit(pe, lj, y0[pe] + a);
             }
           }
           __syncthreads();
