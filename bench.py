@@ -52,8 +52,8 @@ KERNEL_NAMES = {
 # DRAM bytes (read + write) per launch on this workload from the ncu captures
 # summarised under profiles/; a kernel changed since its capture has no entry
 TRAFFIC = {
-    "sweep": 769.9e6,       # profiles/ncu_sweep_warp_config2.md
-    "scatter_tc": 554.3e6,  # profiles/ncu_top_kernels_config2.md
+    "sweep": 773.4e6,       # profiles/ncu_sweep_warp_config2.md
+    "scatter_tc": 554.7e6,  # profiles/ncu_top_kernels_config2.md
 }
 NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate

@@ -353,12 +353,23 @@ int make_sweep_tasks(amgt_ctx* ctx, Level& Lv, const Geom& g, int Gwant) {
       Lv.task_nq.push_back(std::min(G, Lv.dir_end[d] - q0));
     }
   // 16-byte staging copies need 16-byte aligned segment starts and lengths
-  Lv.chunk16_f32 = Lv.chunk16_f64 = (dim == 2);
-  for (size_t i = 0; i < Lv.task_q0.size(); ++i) {
+  // copy chunk of the 2D sweep's staging: 16 bytes when every segment start
+  // and length is 16-byte aligned, else 8, else one element
+  Lv.chunk_f32 = Lv.chunk_f64 = 0;
+  if (dim == 2) {
     for (int bytes : {4, 8}) {
-      bool ok = ((size_t)nadof * bytes) % 16 == 0 && ((size_t)Lv.task_q0[i] * a * bytes) % 16 == 0 &&
-                ((size_t)Lv.task_nq[i] * a * bytes) % 16 == 0 && ((size_t)G * a * bytes) % 16 == 0;
-      if (!ok) (bytes == 4 ? Lv.chunk16_f32 : Lv.chunk16_f64) = false;
+      int best = 0;
+      for (int ch : {16, 8}) {
+        bool ok = true;
+        for (size_t i = 0; i < Lv.task_q0.size() && ok; ++i)
+          ok = ((size_t)nadof * bytes) % ch == 0 && ((size_t)Lv.task_q0[i] * a * bytes) % ch == 0 &&
+               ((size_t)Lv.task_nq[i] * a * bytes) % ch == 0 && ((size_t)G * a * bytes) % ch == 0;
+        if (ok) {
+          best = ch;
+          break;
+        }
+      }
+      (bytes == 4 ? Lv.chunk_f32 : Lv.chunk_f64) = best > 0 ? best : bytes;
     }
   }
   TRY(upload(ctx, Lv.task_dir, &Lv.d_task_dir));
@@ -1004,10 +1015,10 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
 template <class T>
 int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   const Level& L = ctx->lv[k];
-  const bool c16 = sizeof(T) == 4 ? L.chunk16_f32 : L.chunk16_f64;
+  const int chunk = sizeof(T) == 4 ? L.chunk_f32 : L.chunk_f64;
   KernelTimer kt(ctx, AMGT_KT_SWEEP);
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
-                  schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, c16, ctx->sweep_stages,
+                  schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, chunk, ctx->sweep_stages,
                   ctx->sweep_kernel, ctx->d_status, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;

@@ -51,7 +51,7 @@ struct Level {
   unsigned long long* d_faces = nullptr;      // tagged face words between rows
   size_t faces_bytes = 0;
   int sweep_G = 0;         // patches per block of the 2D row-pipelined sweep (0: level kernel)
-  bool chunk16_f32 = false, chunk16_f64 = false;
+  int chunk_f32 = 0, chunk_f64 = 0;  // 2D sweep staging copy size in bytes (0: no row sweep)
   LevelDevStore<double> d64;
   LevelDevStore<float> d32;
   __nv_bfloat16* Sf_bf16 = nullptr;  // dense S_f^T in BF16 for the tensor-core path

@@ -91,7 +91,7 @@ template <class T>
 // variant: 0 auto, 1 level-synchronous row kernel, 2 warp-pipelined (2D, Lin);
 // err: status word for the bounded waits of the warp-pipelined form
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst, int variant,
+                  const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
                   int* err, cudaStream_t st);
 template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,

@@ -527,9 +527,9 @@ __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t
   T* wstage = stage + (size_t)warp * (NST + 1) * kStageElems;
   T* wout = wstage + (size_t)NST * kStageElems;  // this warp's outputs of one step
   char* wbase = reinterpret_cast<char*>(wstage);
-  // outputs leave through the staging buffer as whole 16-byte chunks when
-  // the segments are 16-byte aligned (the copy layout of b)
-  const bool vec_out = chunk == 16;
+  // outputs leave through the staging buffer as whole 16- or 8-byte chunks
+  // when the segments are so aligned (the copy layout of b)
+  const bool vec_out = chunk >= 8;
   const int nsteps = nx + RW - 1;
   auto issue = [&](int ts) {
     if (ts < nsteps) {
@@ -706,9 +706,14 @@ __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t
       for (int u = 0; u < UMAX; ++u) {
         if (crow[u] >= 0) {
           const int jx2 = ts - crow[u];
-          if (jx2 >= 0 && jx2 < nx)
-            *reinterpret_cast<int4*>(pbase + csrc[u] + jx2 * xstep) =
-                *reinterpret_cast<const int4*>(obase + cdst[u]);
+          if (jx2 >= 0 && jx2 < nx) {
+            if (chunk == 16)
+              *reinterpret_cast<int4*>(pbase + csrc[u] + jx2 * xstep) =
+                  *reinterpret_cast<const int4*>(obase + cdst[u]);
+            else
+              *reinterpret_cast<int2*>(pbase + csrc[u] + jx2 * xstep) =
+                  *reinterpret_cast<const int2*>(obase + cdst[u]);
+          }
         }
       }
     }
@@ -969,20 +974,21 @@ size_t sweep2d_smem(const Geom& g, int G, int nmat_s, int nst) {
 
 template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
-                  const T* b, T* psi, int G, int nmat, bool chunk16, int nst, int variant,
+                  const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
                   int* err, cudaStream_t st) {
   note_launch();
-  // warp-pipelined form (variant 2; auto with at least 4 patches per block):
+  // warp-pipelined form (variant 2; auto with at least 2 (FP32) or 4 (FP64)
+  // patches per block, where it measured faster):
   // Lin basis, G dividing 32 with at least two patches per row, at most 512
   // threads
-  const bool want_warp = variant == 2 || (variant == 0 && G >= 4);
+  const bool want_warp = variant == 2 || (variant == 0 && G >= (sizeof(T) == 4 ? 2 : 4));
   if (g.dim == 2 && want_warp && g.a == 3 && (G == 2 || G == 4 || G == 8) && err) {
     const int RW = 32 / G, nwarp = (g.ny + RW - 1) / RW;
     constexpr int NSTW = sizeof(T) == 4 ? 4 : 3;
     int nmat_s = nmat;
     while (nmat_s > 0 && sweep2d_warp_smem<T>(g.ny, G, 3, nmat_s, NSTW) > 200 * 1024) --nmat_s;
     const size_t smem = sweep2d_warp_smem<T>(g.ny, G, 3, nmat_s, NSTW);
-    const int chunk = chunk16 ? 16 : (int)sizeof(T);
+    const int chunk = chunk_bytes > 0 ? chunk_bytes : (int)sizeof(T);
     const int seg_chunks = (G * 3 * (int)sizeof(T)) / chunk;
     const int need = (RW * 4 * seg_chunks + 31) / 32;
     if (nwarp * 32 <= 512 && smem <= 200 * 1024 && need <= 12) {
@@ -1010,7 +1016,7 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
     while (nmat_s > 0 && sweep2d_smem<T>(g, G, nmat_s, NST) > 200 * 1024) --nmat_s;
     const size_t smem = sweep2d_smem<T>(g, G, nmat_s, NST);
     // 16-byte copies when every segment start and length is 16-byte aligned
-    const int chunk = chunk16 ? 16 : (int)sizeof(T);
+    const int chunk = chunk_bytes > 0 ? chunk_bytes : (int)sizeof(T);
     const int threads = ((g.ny * G + 31) / 32) * 32;
     const int seg_chunks = (G * g.a * (int)sizeof(T) + chunk - 1) / chunk;
     const bool slots_ok = (long long)g.ny * 4 * seg_chunks <= 12LL * threads;
@@ -1098,7 +1104,7 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 
 #define AMGT_INST(T)                                                                          \
   template void launch_sweep<T>(const Geom&, const LevelDev<T>&, const CellData&,             \
-                                const Schedule&, const T*, T*, int, int, bool, int, int,      \
+                                const Schedule&, const T*, T*, int, int, int, int, int,       \
                                 int*, cudaStream_t);                                          \
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
