@@ -50,6 +50,7 @@ AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
 AMGT_KT_SPLIT_TC, AMGT_KT_SPLIT_AUX = 7, 8
+AMGT_KT_COUNT = 9
 
 # every exported symbol of include/amgt.h
 EXPORTS = [

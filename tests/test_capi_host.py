@@ -45,3 +45,27 @@ def test_null_context_is_rejected(lib):
     lib.amgt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     lib.amgt_create.restype = ctypes.c_int
     assert lib.amgt_create(None, 0, None) == -1
+
+
+def _header_constants():
+    src = open(os.path.join(ROOT, "include", "amgt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {name: int(val) for name, val in re.findall(r"#define\s+(AMGT_[A-Z_0-9]+)\s+(-?\d+)", src)}
+    for name, val in re.findall(r"\b(AMGT_[A-Z_0-9]+)\s*=\s*(-?\d+)", src):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The tuning keys, kernel-timer classes, dtypes, modes and error codes
+    the header defines are exported by the package with the same values."""
+    import paper_2010_04559_gb300 as pkg
+    from paper_2010_04559_gb300 import _capi
+    consts = _header_constants()
+    assert len(consts) > 30
+    for name, val in consts.items():
+        assert hasattr(_capi, name), name
+        assert getattr(_capi, name) == val, name
+        if name.startswith(("AMGT_TUNE_", "AMGT_KT_", "AMGT_F", "AMGT_MODE_", "AMGT_PREC_",
+                            "AMGT_KRYLOV_")) and name != "AMGT_KT_COUNT":
+            assert getattr(pkg, name) == val, name
