@@ -125,53 +125,61 @@ __global__ void __launch_bounds__(kSplitThreads) split_rows_kernel(
   for (int l = 0; l < S; ++l) inv[l] = inv_s[l];
   const double p2 = ldexp(1.0, bits * nsl);
   const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double z[S];
-    row_values<S, MIX>(x, r0, K, nrow, k, sg, Nm, z);
+  // two adjacent columns per thread, stored as BF16 pairs (K and the slice
+  // stride are even)
+  const long long ss2 = slice_stride / 2;
+  for (int k = 2 * threadIdx.x; k < K; k += 2 * blockDim.x) {
+    double z0[S], z1[S];
+    row_values<S, MIX>(x, r0, K, nrow, k, sg, Nm, z0);
+    row_values<S, MIX>(x, r0, K, nrow, k + 1, sg, Nm, z1);
 #pragma unroll
     for (int l = 0; l < S; ++l) {
       if (l >= nrow) break;
-      long long T = __double2ll_rn((z[l] * inv[l]) * p2);
-      __nv_bfloat16* o = out + (r0 + l) * (long long)K + k;
+      long long T0 = __double2ll_rn((z0[l] * inv[l]) * p2);
+      long long T1 = __double2ll_rn((z1[l] * inv[l]) * p2);
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (r0 + l) * (long long)K + k);
       for (int i = nsl - 1; i > 0; --i) {
-        const long long r = ((T + half) & mask) - half;
-        T = (T - r) >> bits;
-        o[i * slice_stride] = __float2bfloat16_rn((float)r);
+        const long long d0 = ((T0 + half) & mask) - half;
+        const long long d1 = ((T1 + half) & mask) - half;
+        T0 = (T0 - d0) >> bits;
+        T1 = (T1 - d1) >> bits;
+        o[i * ss2] = __floats2bfloat162_rn((float)d0, (float)d1);
       }
-      o[0] = __float2bfloat16_rn((float)T);
+      o[0] = __floats2bfloat162_rn((float)T0, (float)T1);
     }
   }
 }
 
-// y[r][c] += sc mu[r] nu[c] P[r][c]  (sc mu nu is a power of two times sc)
+// y[r][c] += sc mu[r] nu[c] P[r][c]  (sc mu nu is a power of two times sc,
+// so each product is exact and only the sum rounds).  A block per row at a
+// time: no index division, one row scale per row.
 __global__ void split_flush_kernel(long long M, int N, const float* __restrict__ P,
                                    const double* __restrict__ mu, const double* __restrict__ nu,
                                    double sc, double* __restrict__ y) {
   if ((N & 3) == 0) {
     const int n4 = N >> 2;
-    const long long total = M * n4;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-      const long long r = idx / n4;
-      const int c = (int)(idx - r * n4) * 4;
-      const float4 p = __ldcs(reinterpret_cast<const float4*>(P + r * N + c));
+    const double2* nu2 = reinterpret_cast<const double2*>(nu);
+    for (long long r = blockIdx.x; r < M; r += gridDim.x) {
       const double s = sc * mu[r];
-      double2* yp = reinterpret_cast<double2*>(y + r * N + c);
-      double2 a = yp[0], b = yp[1];
-      a.x += (s * nu[c]) * (double)p.x;
-      a.y += (s * nu[c + 1]) * (double)p.y;
-      b.x += (s * nu[c + 2]) * (double)p.z;
-      b.y += (s * nu[c + 3]) * (double)p.w;
-      yp[0] = a;
-      yp[1] = b;
+      const float4* pr = reinterpret_cast<const float4*>(P + r * N);
+      double2* yr = reinterpret_cast<double2*>(y + r * N);
+      for (int c4 = threadIdx.x; c4 < n4; c4 += blockDim.x) {
+        const float4 p = __ldcs(pr + c4);
+        const double2 na = nu2[2 * c4], nb = nu2[2 * c4 + 1];
+        double2 a = yr[2 * c4], b = yr[2 * c4 + 1];
+        a.x = fma(s * na.x, (double)p.x, a.x);
+        a.y = fma(s * na.y, (double)p.y, a.y);
+        b.x = fma(s * nb.x, (double)p.z, b.x);
+        b.y = fma(s * nb.y, (double)p.w, b.y);
+        yr[2 * c4] = a;
+        yr[2 * c4 + 1] = b;
+      }
     }
   } else {
-    const long long total = M * N;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-      const long long r = idx / N;
-      const int c = (int)(idx - r * N);
-      y[idx] += (sc * mu[r] * nu[c]) * (double)P[idx];
+    for (long long r = blockIdx.x; r < M; r += gridDim.x) {
+      const double s = sc * mu[r];
+      for (int c = threadIdx.x; c < N; c += blockDim.x)
+        y[r * N + c] = fma(s * nu[c], (double)P[r * N + c], y[r * N + c]);
     }
   }
 }
@@ -200,8 +208,7 @@ void launch_split_rows(long long rows, int K, int S, bool mix, const double* x,
 void launch_split_flush(long long M, int N, const float* P, const double* mu, const double* nu,
                         double sc, double* y, cudaStream_t st) {
   note_launch();
-  const long long work = (N & 3) == 0 ? M * (N >> 2) : M * N;
-  long long grid = (work + 255) / 256;
+  long long grid = M;
   if (grid > 152LL * 16) grid = 152LL * 16;
   if (grid < 1) grid = 1;
   split_flush_kernel<<<(unsigned)grid, 256, 0, st>>>(M, N, P, mu, nu, sc, y);
