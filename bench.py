@@ -54,6 +54,7 @@ KERNEL_NAMES = {
 TRAFFIC = {
     "sweep": 773.4e6,       # profiles/ncu_sweep_warp_config2.md
     "scatter_tc": 554.7e6,  # profiles/ncu_top_kernels_config2.md
+    "coarse_gs": 243.8e6,   # profiles/ncu_coarse_gs_rows_config2.md (10-sweep launch)
 }
 NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
@@ -185,7 +186,17 @@ def run_profile(args):
     prob = W.config2_checkerboard(n=args.n)
     ctx = context_from_problem(prob, device=0)
     ns, na = ctx.amgt_query_sizes(0)
-    if args.profile == "sweeps":
+    if args.profile == "gs":
+        # the coarse Gauss-Seidel launch of one V-cycle (10 sweeps), once to
+        # warm up and once more
+        nsc, nac = ctx.amgt_query_sizes(2)
+        fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
+        pc = torch.zeros_like(fc)
+        for _ in range(2):
+            ctx.amgt_op_coarse_gs(10, fc, pc)
+        ctx.amgt_sync()
+        print("kernels: coarse Gauss-Seidel, 10 sweeps (x2)")
+    elif args.profile == "sweeps":
         from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
         x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
         y = torch.empty_like(x)
@@ -235,7 +246,7 @@ def main():
                     help="problems of the uneven 2D batch solved concurrently (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="tolerance of each inner FP32 solve (0: adaptive)")
-    ap.add_argument("--profile", choices=["solve", "kernels", "sweeps"], default=None,
+    ap.add_argument("--profile", choices=["solve", "kernels", "sweeps", "gs"], default=None,
                     help="run one solve, or one launch of each hot kernel, and exit (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
