@@ -7,7 +7,7 @@
  * discontinuous Galerkin in space (Q1 on axis-aligned quads/hexes) and in
  * angle (spherical patches, Const or Lin basis; Sec. 2.1-2.3), with the
  * Legendre-expanded scatter source of Sec. 4.2 and the angular multigrid
- * preconditioner of Sec. 4 (Fig. lmg) inside restarted GMRES.
+ * preconditioner of Sec. 4 (Fig. lmg) inside restarted GMRES or BiCGStab.
  *
  * Conventions shared by every call
  * --------------------------------
