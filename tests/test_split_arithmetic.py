@@ -6,7 +6,6 @@ and the FP64 result against the FP64 product.  The same rules are what the
 library's host planner and kernels implement for the tensor cores (Ozaki,
 Ogita, Oishi and Rump 2012, error-free splitting); here an FP32 matrix
 product stands in for the tensor-core MMAs with FP32 accumulation."""
-import math
 
 import numpy as np
 import pytest
