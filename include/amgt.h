@@ -219,7 +219,9 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *   AMGT_TUNE_SPLIT_ROWS  rows of psi per pass of the split form (0 = auto:
  *                         as many as keep its digit slices within ~8 GB;
  *                         else rounded up to a multiple of 128)
- *   AMGT_TUNE_SWEEP_KERNEL the 2D sweep: 0 auto, 1 level-synchronous row
+ *   AMGT_TUNE_SWEEP_KERNEL the 2D sweep: 0 auto (2 where a block holds at
+ *                         least two patches in FP32 or four in FP64, else
+ *                         1), 1 level-synchronous row
  *                         kernel (one block barrier per wavefront level),
  *                         2 warp-pipelined kernel (Lin basis, 2, 4 or 8
  *                         patches per block: each warp runs its own skewed
