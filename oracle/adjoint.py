@@ -17,7 +17,8 @@ Definitions
       dR/dsigma_t[c] = -sum_q lam_cq^T kron(N, M_q) psi_cq
       dR/dsigma_s[c] = +lam_c^T kron(N, S_f) psi_c
       dR/df_n        = +sum_c sigma_s(c) lam_c^T kron(N, X_n X_n^T) psi_c
-  where X_n are the 2n+1 columns of X of degree n.
+  where X_n are the 2n+1 columns of X of degree n; with several materials
+  (moment shapes) the sum over c runs over the cells of each material.
 
 Reading (pinned in tests/test_oracle_adjoint.py against the plain transpose)
 -------------------------------------------------------------------------
@@ -87,9 +88,9 @@ def dense_solve(T, rhs):
 
 
 def gradients(T, psi, lam):
-    """(dR/dsigma_t [C], dR/dsigma_s [C], dR/df_n [N+1]) from the forward
-    solution psi and the adjoint solution lam (definitions in the module
-    docstring), cell by cell."""
+    """(dR/dsigma_t [C], dR/dsigma_s [C], dR/df_n [N+1], or [materials][N+1]
+    with several moment shapes) from the forward solution psi and the adjoint
+    solution lam (definitions in the module docstring), cell by cell."""
     s = T.s
     N = T.cell.N
     pb = T.to_blocks(psi)
@@ -98,16 +99,16 @@ def gradients(T, psi, lam):
     for c in range(T.C):
         for q in range(T.P):
             dsigt[c] -= lb[c, q] @ T.B[q] @ pb[c, q]
-    Sf = T.angular_scatter_matrix()
+    Sfs = [T.angular_scatter_matrix(m) for m in range(T.nshape)]
     deg = harmonics.degree_of_index(T.Nscat)
     dsigs = np.zeros(T.C)
-    dfn = np.zeros(T.Nscat + 1)
+    dfn = np.zeros((T.nshape, T.Nscat + 1))
     for c in range(T.C):
         psi_c = psi[c * s:(c + 1) * s]
         lam_c = lam[c * s:(c + 1) * s]
         # kron(N, S_f) acting on the cell block with index (l, j): N psi_c S_f^T
-        dsigs[c] = np.sum(lam_c * (N @ psi_c @ Sf.T))
+        dsigs[c] = np.sum(lam_c * (N @ psi_c @ Sfs[T.fid[c]].T))
         for n in range(T.Nscat + 1):
             Xn = T.X[:, deg == n]
-            dfn[n] += T.sigma_s[c] * np.sum(lam_c * (N @ psi_c @ (Xn @ Xn.T)))
-    return dsigt, dsigs, dfn
+            dfn[T.fid[c], n] += T.sigma_s[c] * np.sum(lam_c * (N @ psi_c @ (Xn @ Xn.T)))
+    return dsigt, dsigs, (dfn[0] if T.nshape == 1 else dfn)

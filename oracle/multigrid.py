@@ -86,7 +86,7 @@ def coarse_gs(T, f, phi, nsweeps):
     s, a = T.s, T.a
     fb = T.to_blocks(f)
     xb = T.to_blocks(phi).copy()
-    Sf = T.angular_scatter_matrix()
+    Sfs = [T.angular_scatter_matrix(m) for m in range(T.nshape)]
     N = T.cell.N
     for _ in range(nsweeps):
         for d in range(T.ndir):
@@ -100,6 +100,7 @@ def coarse_gs(T, f, phi, nsweeps):
                             rhs -= T.U[fc, q] @ xb[nb, q]
                     # scatter from all other patches of the cell (latest values)
                     xc = xb[c].reshape(T.P, s, a)
+                    Sf = Sfs[T.fid[c]]
                     src = np.zeros((s, a))
                     for p in range(T.P):
                         if p == q:

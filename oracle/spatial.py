@@ -61,6 +61,24 @@ class Q1Cell:
                 self.Fnb[f] = np.einsum("k,kl,ki->li", Wf, own, nb)
                 self.mf[f] = Wf @ own
 
+    def face_integral(self, f, a, b):
+        """int over the part of face f whose tangential coordinates lie in
+        [a_e, b_e] (cell-local, one interval per tangential axis e in
+        increasing order, already clipped to [0, h_e]) of Phi_l; [s].  The
+        same tensor Gauss rule, mapped onto the sub-rectangle."""
+        d, s = self.dim, self.s
+        xi, side = divmod(f, 2)
+        others = [e for e in range(d) if e != xi]
+        t, wt = _gauss01(3)
+        fp = np.array(list(itertools.product(range(3), repeat=d - 1))).reshape(-1, d - 1)
+        Xf = np.zeros((fp.shape[0], d))
+        Wf = np.ones(fp.shape[0])
+        for j, e in enumerate(others):
+            Xf[:, e] = a[j] + t[fp[:, j]] * (b[j] - a[j])
+            Wf = Wf * wt[fp[:, j]] * (b[j] - a[j])
+        Xf[:, xi] = side * self.h[xi]
+        return Wf @ self.basis(Xf)
+
     def _l(self, a, t, h):
         return (1.0 - t / h) if a == 0 else (t / h)
 

@@ -16,7 +16,9 @@ Paper passages followed
 Readings
 --------
 * The collision coefficient of L is sigma_t (Eq. LBE); S carries the whole
-  Legendre in-scatter including n = 0, sigma_{s,n} = sigma_s(cell) * f_n.
+  Legendre in-scatter including n = 0, sigma_{s,n} = sigma_s(cell) * f_n,
+  with one moment shape f_n per material (`mat_id` maps cells to materials;
+  one shape for every cell without it).
 * Faces of an axis-aligned box are normal to a coordinate axis and a patch
   never crosses a coordinate plane, so Omega.n has one sign on a patch and the
   face flux is the exact upwind value: the own trace on outflow faces, the
@@ -36,6 +38,12 @@ Readings
   level), and the Dirac mass is split equally, 1/k to each; this is the limit
   of a uniform inflow over a shrinking cap around Omega_b, each of whose
   quarters lies in one of those patches.
+* A beam of general direction over part of a face (Sec. 5.4's cube with a
+  boundary source on a square of its face): psi_b = S delta(Omega - Omega_b)
+  on the range, zero on the rest of the face; its inflow term is
+  -S (Omega_b.n) int_{face & range} Phi_l Psi_m(Omega_b) share_q, with the
+  share of patch q the fraction of an infinitesimal cap around Omega_b that
+  lies in it (1 inside, 1/2 on an edge, interior angle / 2 pi at a vertex).
 """
 import itertools
 
@@ -45,17 +53,38 @@ from . import angular, harmonics
 from .spatial import Q1Cell
 
 
+def _vertex_angle(A, B, C):
+    """Interior angle at vertex A of the spherical triangle ABC: the angle
+    between the great circles AB and AC at A."""
+    tb = B - (B @ A) * A
+    tc = C - (C @ A) * A
+    return np.arctan2(np.linalg.norm(np.cross(tb, tc)), tb @ tc)
+
+
 def beam_weights(amesh, omega_b):
-    """wb[P, a]: Psi_[q]m(omega_b) / k on the k patches whose closed spherical
-    triangle holds omega_b, zero elsewhere (the Dirac mass split equally
-    among them).  A patch holds omega_b iff omega_b is a non-negative
-    combination of its vertices."""
+    """wb[P, a]: Psi_[q]m(omega_b) times the share of the Dirac mass that
+    patch q receives, zero elsewhere.  A patch holds omega_b iff omega_b is a
+    non-negative combination of its vertices.  The share is the fraction of an
+    infinitesimal cap around omega_b that lies in the patch: 1 inside it, 1/2
+    on an edge (a great circle halves the cap), and at a vertex the patch's
+    interior angle there over 2 pi (1/4 at a vertex of the octahedron, where
+    four right angles meet)."""
     wb = np.zeros((amesh.P, amesh.a))
-    hits = [q for q in range(amesh.P)
-            if np.linalg.solve(amesh.verts[q].T, omega_b).min() > -1e-12]
-    for q in hits:
-        wb[q] = angular.basis_eval(amesh.verts[q], amesh.octant[q], amesh.basis,
-                                   omega_b) / len(hits)
+    for q in range(amesh.P):
+        V = amesh.verts[q]
+        lam = np.linalg.solve(V.T, omega_b)
+        if lam.min() < -1e-12:
+            continue
+        zero = np.abs(lam) <= 1e-12 * np.abs(lam).max()
+        nz = int(zero.sum())
+        if nz == 0:
+            share = 1.0
+        elif nz == 1:
+            share = 0.5
+        else:
+            i = int(np.argmax(~zero))            # omega_b is vertex i
+            share = _vertex_angle(V[i], V[(i + 1) % 3], V[(i + 2) % 3]) / (2.0 * np.pi)
+        wb[q] = share * angular.basis_eval(V, amesh.octant[q], amesh.basis, omega_b)
     return wb
 
 
@@ -83,13 +112,22 @@ class Transport:
         self.sigma_s = np.asarray(prob["sigma_s"], dtype=np.float64)
         N = prob["N"] if Nscat is None else Nscat
         self.Nscat = N
-        fm = np.zeros(N + 1)
+        # moment shapes: one row f_n per material of mat_id (one for all
+        # cells without it); sigma_{s,n}(c) = sigma_s(c) f_{mat_id(c), n}
+        ftab = np.atleast_2d(np.asarray(prob["fmom"], dtype=np.float64))
         nkeep = min(N, prob["N"]) + 1
-        fm[:nkeep] = prob["fmom"][:nkeep]
-        self.fmom = fm
-        # --- angular scatter matrix S_f = X diag(f_n) X^T (Sec. 4.2) ---
+        fm = np.zeros((ftab.shape[0], N + 1))
+        fm[:, :nkeep] = ftab[:, :nkeep]
+        mid = prob.get("mat_id")
+        self.fid = (np.zeros(self.C, dtype=np.int64) if mid is None
+                    else np.asarray(mid, dtype=np.int64))
+        self.nshape = fm.shape[0]
+        self.fmom_tab = fm
+        self.fmom = fm[0]
+        # --- angular scatter matrices S_f = X diag(f_n) X^T (Sec. 4.2) ---
         self.X = amesh.X(N).reshape(self.nadof, harmonics.nmoments(N))
-        self.Fdiag = fm[harmonics.degree_of_index(N)]
+        self.Ftab = fm[:, harmonics.degree_of_index(N)]   # [shapes, nmom]
+        self.Fdiag = self.Ftab[0]
         # --- per-patch blocks of L ---
         s, a = self.s, self.a
         nf = 2 * d
@@ -184,12 +222,23 @@ class Transport:
                 yb[c] += np.einsum("qij,qj->qi", self.U[f], xb[nb])
         return self.from_blocks(yb)
 
-    def scatter(self, x):
-        """y = S x through the flux moments of Sec. 4.2."""
-        Phi = x @ self.X                       # [Nsdof, Nmom] moments
-        Yang = (Phi * self.Fdiag) @ self.X.T   # sum_{n,o} f_n X_q Phi
-        y = np.empty_like(x)
+    def scatter(self, x, cells=None):
+        """y = S x through the flux moments of Sec. 4.2.  S couples only the
+        rows of one cell, so with `cells` only those cells' rows are computed
+        (x may then hold just those rows, cell by cell, [len(cells)*s, Nadof])."""
         N = self.cell.N
+        if cells is not None:
+            y = np.empty_like(x)
+            for i, c in enumerate(cells):
+                rows = slice(i * self.s, (i + 1) * self.s)
+                Phi = x[rows] @ self.X
+                y[rows] = self.sigma_s[c] * (N @ ((Phi * self.Ftab[self.fid[c]]) @ self.X.T))
+            return y
+        Phi = x @ self.X                       # [Nsdof, Nmom] moments
+        # sum_{n,o} f_n X_q Phi with each cell's moment shape
+        Frow = np.repeat(self.Ftab[self.fid], self.s, axis=0)
+        Yang = (Phi * Frow) @ self.X.T
+        y = np.empty_like(x)
         for c in range(self.C):
             rows = slice(c * self.s, (c + 1) * self.s)
             y[rows] = self.sigma_s[c] * (N @ Yang[rows])
@@ -232,11 +281,14 @@ class Transport:
         for f, (kind, val) in enumerate(self.prob["boundary"]):
             if kind == 0:
                 continue
-            if kind not in (1, 2):
-                raise ValueError("oracle supports vacuum, isotropic inflow and the beam")
+            if kind not in (1, 2, 3):
+                raise ValueError("oracle supports vacuum, isotropic inflow and the beams")
             xi, side = divmod(f, 2)
             sgn = 2.0 * side - 1.0
             inflow = ~self.outflow[f]
+            if kind == 3:
+                self._general_beam(fb, f, val)
+                continue
             if kind == 2:
                 n = np.zeros(3)
                 n[xi] = sgn
@@ -255,6 +307,40 @@ class Transport:
                 term = -val * self.cell.mf[f][None, :, None] * ndotpsi[:, None, :]
                 fb[c][inflow] += term[inflow]
         return fb.transpose(0, 2, 1, 3).reshape(self.nsdof, self.nadof)
+
+    def _general_beam(self, fb, f, val):
+        """Beam psi_b = S delta(Omega - Omega_b) over the part of face f whose
+        tangential coordinates (axes in increasing order) lie in
+        [u0, u1] (x [v0, v1] in 3D), val = (S, Omega_b[3], u0, u1, v0, v1):
+        the inflow term -S (Omega_b.n) int_{face cell & range} Phi_l
+        Psi_m(Omega_b) share_q (beam_weights), Omega_b normalised and
+        pointing into the domain."""
+        S = float(val[0])
+        om = np.asarray(val[1:4], dtype=np.float64)
+        om = om / np.linalg.norm(om)
+        rng = [(float(val[4]), float(val[5])), (float(val[6]), float(val[7]))]
+        xi, side = divmod(f, 2)
+        n = np.zeros(3)
+        n[xi] = 2.0 * side - 1.0
+        if om @ n >= 0.0:
+            raise ValueError("the beam must point into the domain")
+        wb = beam_weights(self.am, om)
+        others = [e for e in range(self.dim) if e != xi]
+        h = self.cell.h
+        for c in range(self.C):
+            if self.neighbour(c, f) >= 0:
+                continue
+            ic = self.cell_coords(c)
+            a, b = [], []
+            for j, e in enumerate(others):
+                x0 = self.prob["lo"][e] + ic[e] * h[e]
+                lo_, hi_ = max(x0, rng[j][0]), min(x0 + h[e], rng[j][1])
+                a.append(lo_ - x0)
+                b.append(max(hi_, lo_) - x0)
+            if any(bb <= aa for aa, bb in zip(a, b)):
+                continue
+            I = self.cell.face_integral(f, a, b)
+            fb[c] += -S * (om @ n) * I[None, :, None] * wb[:, None, :]
 
     def scalar_flux(self, psi):
         """phi_s[Nsdof] = sum_{q,d} psi * int Psi_{[q]d} (n = 0 moment)."""
@@ -282,10 +368,10 @@ class Transport:
         return Ld
 
     def dense_S(self):
-        Sf = (self.X * self.Fdiag) @ self.X.T
+        Sfs = [self.angular_scatter_matrix(m) for m in range(self.nshape)]
         blocks = []
         for c in range(self.C):
-            blocks.append(self.sigma_s[c] * np.kron(self.cell.N, Sf))
+            blocks.append(self.sigma_s[c] * np.kron(self.cell.N, Sfs[self.fid[c]]))
         n = self.nsdof * self.nadof
         Sd = np.zeros((n, n))
         m = self.s * self.nadof
@@ -293,6 +379,7 @@ class Transport:
             Sd[c * m:(c + 1) * m, c * m:(c + 1) * m] = blocks[c]
         return Sd
 
-    def angular_scatter_matrix(self):
-        """S_f = X diag(f_n) X^T over the angular DOFs (unit sigma_s)."""
-        return (self.X * self.Fdiag) @ self.X.T
+    def angular_scatter_matrix(self, shape=0):
+        """S_f = X diag(f_n) X^T over the angular DOFs (unit sigma_s) for the
+        moment shape of material `shape`."""
+        return (self.X * self.Ftab[shape]) @ self.X.T

@@ -233,3 +233,14 @@ def test_coarse_gs_block_equation_holds():
             mix[g] = v1[g]
         res = fv[r] - A[r] @ mix
         assert np.abs(res).max() < 1e-12 * (1 + np.abs(fv).max())
+
+
+def test_scatter_on_a_subset_of_cells_equals_the_full_scatter():
+    prob = W.random_problem(2, (3, 2), 1, 5, 27)
+    T = _T(prob)
+    x = W.random_vector((T.nsdof, T.nadof), 28)
+    full = T.scatter(x)
+    cells = [4, 1]
+    rows = np.concatenate([np.arange(c * T.s, (c + 1) * T.s) for c in cells])
+    part = T.scatter(x[rows], cells=cells)
+    assert np.abs(part - full[rows]).max() < 1e-13 * np.abs(full).max()

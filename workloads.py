@@ -12,7 +12,9 @@ A problem is a dict with keys
   sigma_t        float64[C]  total cross section per cell
   sigma_s        float64[C]  scatter cross section sigma_{s,0} per cell
   N              Legendre order of the scatter expansion
-  fmom           float64[N+1] moment shape f_n (sigma_{s,n} = sigma_s * f_n), f_0 = 1
+  fmom           float64[N+1] moment shape f_n (sigma_{s,n} = sigma_s * f_n), f_0 = 1,
+                 or float64[nmat][N+1], one shape per material of mat_id
+  mat_id         optional int[C]: material of each cell (index into fmom's rows)
   q              float64[C]  isotropic volumetric source (scalar emission density)
   boundary       list of 2*dim (kind, value): kind 0 vacuum, 1 isotropic inflow
                  of angular flux `value`, 2 normally incident pencil beam of
@@ -74,15 +76,28 @@ def _central_source(dim, ncell, lo, hi, width, strength=1.0):
 
 def problem(dim, ncell, sigma_t, sigma_s, N, fmom, q, level, basis="lin",
             boundary=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), mg=None,
-            tol=1e-8, restart=20):
+            tol=1e-8, restart=20, mat_id=None):
     if boundary is None:
         boundary = [(0, 0.0)] * (2 * dim)
-    return dict(dim=dim, ncell=tuple(int(n) for n in ncell), lo=tuple(lo),
-                hi=tuple(hi), sigma_t=np.asarray(sigma_t, dtype=np.float64),
-                sigma_s=np.asarray(sigma_s, dtype=np.float64), N=int(N),
-                fmom=np.asarray(fmom, dtype=np.float64),
-                q=np.asarray(q, dtype=np.float64), boundary=list(boundary),
-                basis=basis, level=int(level), mg=mg, tol=tol, restart=restart)
+    out = dict(dim=dim, ncell=tuple(int(n) for n in ncell), lo=tuple(lo),
+               hi=tuple(hi), sigma_t=np.asarray(sigma_t, dtype=np.float64),
+               sigma_s=np.asarray(sigma_s, dtype=np.float64), N=int(N),
+               fmom=np.asarray(fmom, dtype=np.float64),
+               q=np.asarray(q, dtype=np.float64), boundary=list(boundary),
+               basis=basis, level=int(level), mg=mg, tol=tol, restart=restart)
+    if mat_id is not None:
+        out["mat_id"] = np.asarray(mat_id, dtype=np.int32)
+    return out
+
+
+def two_shape_problem(dim, ncell, level, N, seed_k, g=(0.9, 0.4), basis="lin"):
+    """Small random problem whose cells carry one of two HG moment shapes
+    (g per material), material per cell Bernoulli(0.5) from the seed."""
+    prob = random_problem(dim, ncell, level, N, seed_k, basis=basis)
+    rng = _rng(2000 + seed_k)
+    prob["mat_id"] = rng.integers(0, 2, size=int(np.prod(ncell))).astype(np.int32)
+    prob["fmom"] = np.stack([hg_moments(gg, N) for gg in g])
+    return prob
 
 
 def config1_square16(level=1):
