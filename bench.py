@@ -1,19 +1,28 @@
 """Benchmark of the transport hot path on GB300.
 
-Workload: 2D 128x128 DG-Q1 quads, two-material checkerboard (sigma_t 1/10,
-scatter ratio 0.5/0.99, seeded 16x16-cell tiles), angular level 3 (512 Lin
-patches, 1536 angular DOF), HG g = 0.9 at Legendre order 16, centred unit
-source, vacuum; 3-level angular multigrid V(1,1), coarse order 4, 10 coarse
-Gauss-Seidel sweeps; 1.01e8 unknowns.
+Headline workload (the largest configuration that fits one GPU): 2D 256x256
+DG-Q1 quads, sigma_t = 5, sigma_s = 4.95, Henyey-Greenstein g = 0.98 at
+Legendre order 64, a normally incident pencil beam of unit strength on the
+low-x edge, vacuum elsewhere, uniform angular level 4 (2048 Lin patches, 6144
+angular DOF), 4-level angular multigrid V(1,1) with coarse scatter order 12
+and 10 coarse Gauss-Seidel sweeps: 1.61e9 unknowns.
 
-One step = one complete solve to ||b - A x|| / ||b|| < 1e-8 (mixed mode:
-FP64 GMRES refinement around an FP32 flexible GMRES(20) whose V-cycle and
-operator run the FP32 sweeps/transfers and the scatter contraction on BF16
-tensor cores), i.e. every hot-path operator: sweep, scatter, operator apply,
-restriction/prolongation, smoother, coarse Gauss-Seidel, GMRES and the scalar
-flux.  value = unknowns x Krylov iterations / step time (GDOF/s of
-preconditioned transport-operator applications); ms_per_step is the time to
-residual 1e-8.
+One step = one complete mixed-precision solve to ||b - A x|| / ||b|| < 1e-8:
+FP64 GMRES refinement around an FP32 flexible GMRES(8) whose operator takes
+the FP32-accurate FP16 three-product scatter and whose V-cycle runs FP32
+sweeps/transfers, the BF16 tensor-core scatter and the coarse Gauss-Seidel;
+the refinement residuals take the FP64-accurate split scatter.  Every
+hot-path operator runs in it: sweep, scatter, operator apply, restriction /
+prolongation, smoother, coarse Gauss-Seidel, GMRES and the scalar flux.
+value = unknowns x Krylov iterations / step time (GDOF/s of preconditioned
+transport-operator applications); ms_per_step is the time to residual 1e-8.
+The timed steps run with the library's kernel timers off and the V-cycle
+replayed from a captured CUDA graph; a separate instrumented solve gives the
+per-kernel shares and the rooflines.  fp64_gpu times the plain FP64 GPU solve
+of the same inputs (BiCGStab, the paper's Krylov method, whose FP64 basis
+fits in memory at this size; every FP64 scatter in the split form).  The
+128x128 two-material checkerboard workload (1.01e8 unknowns) is timed the
+same way under extra.config2.
 
 --impl reference times the CPU FP64 oracle instead (bounded sample, see
 cpu_baseline.sample).  Multi-GPU: replicas only (the method has no data-path
@@ -21,6 +30,7 @@ exchange on one problem); each rank solves its own copy.
 """
 import argparse
 import json
+import multiprocessing
 import os
 import subprocess
 import sys
@@ -35,35 +45,52 @@ if ROOT not in sys.path:
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = "2D 128x128 Q1, checkerboard sigma_t 1/10 c 0.5/0.99, level-3 Lin (512 patches), HG g=0.9 N=16, 3-level MG Nr=4"
+WORKLOAD = ("2D 256x256 Q1, sigma_t 5 sigma_s 4.95, HG g=0.98 N=64, normally incident pencil "
+            "beam on the low-x edge, uniform level-4 Lin (2048 patches), 4-level MG Nr=12")
+WORKLOAD2 = ("2D 128x128 Q1, checkerboard sigma_t 1/10 c 0.5/0.99, level-3 Lin (512 patches), "
+             "HG g=0.9 N=16, 3-level MG Nr=4")
 METRIC = "transport-operator GDOF/s; time-to-residual 1e-8, mixed/batched vs FP64 GPU"
+HEAD_RESTART = 8   # FGMRES(8): 17 FP32 basis vectors of 6.4 GB each at 1.61e9 unknowns
 
-KERNEL_NAMES = {
-    "sweep": "sweep2d_warp_kernel<float,3,4,4,3>",
-    "apply_L": "apply_L_kernel<float,2,3>",
-    "scatter_prep": "tc_prep_kernel<4>",
-    "scatter_tc": "tc_gemm_kernel (tcgen05, persistent)",
-    "scatter_f32": "gemm_kernel<float>",
-    "scatter_f64": "gemm_kernel<double>",
-    "coarse_gs": "coarse_gs_rows_kernel<float,2,3>",
-    "split_tc": "tc_gemm_kernel (tcgen05, slice products of the split FP64 scatter)",
-    "split_aux": "split_rows_kernel + split_flush_kernel (digit slicing, FP64 accumulation)",
+# kernel class -> (kernel, bound, work unit); the work per launch is counted by
+# the library (amgt_query_kernel_stats) from each launch's shapes
+CLASSES = {
+    "sweep": ("sweep2d_warp_kernel", "hbm", "B"),
+    "apply_L": ("apply_L_kernel", "hbm", "B"),
+    "scatter_prep": ("tc_prep_kernel", "hbm", "B"),
+    "scatter_tc": ("tc_gemm_kernel<bf16> (tcgen05, V-cycle scatter)", "tensor", "flop"),
+    "scatter_f32": ("gemm_kernel<float> (SIMT)", "alu", "flop"),
+    "scatter_f64": ("gemm_kernel<double> (SIMT)", "alu64", "flop"),
+    "coarse_gs": ("coarse_gs_rows_kernel", "alu", "flop"),
+    "split_tc": ("tc_gemm_kernel<bf16> (tcgen05, slice products of the split FP64 scatter)",
+                 "tensor", "flop"),
+    "split_aux": ("split_rows_kernel + split_flush_kernel", "hbm", "B"),
+    "tc3": ("tc_gemm_kernel<f16> (tcgen05, FP32-accurate three-product scatter)", "tensor", "flop"),
+    "tc3_prep": ("tc3_prep_kernel", "hbm", "B"),
 }
-# DRAM bytes (read + write) per launch on this workload from the ncu captures
-# summarised under profiles/; a kernel changed since its capture has no entry
+# DRAM bytes (read + write) per launch from the ncu captures summarised under
+# profiles/, per workload; a kernel changed since its capture has no entry
 TRAFFIC = {
-    "sweep": 773.4e6,       # profiles/ncu_sweep_warp_config2.md
-    "scatter_tc": 554.7e6,  # profiles/ncu_top_kernels_config2.md
-    "coarse_gs": 243.8e6,   # profiles/ncu_coarse_gs_rows_config2.md (10-sweep launch)
+    "config5": {},
+    "config2": {"sweep": 773.4e6, "coarse_gs": 243.8e6},
 }
-NMOM_FINE = 289           # (N + 1)^2 Legendre moments at order 16
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
+ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
 PEAK_KINDS = {
     "alu": "FP32 FMA units x clock (152 x 128 x 2 x 2.07 GHz)",
     "alu64": "nominal GB300 FP64 rate, 1.25 TFLOP/s",
     "hbm": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-    "tensor": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)",
+    "tensor": "measured BF16 GEMM burst (MEASURED_PEAKS.json bf16_tflops; FP16 runs at the "
+              "same dense rate)",
 }
+
+
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def _peaks():
@@ -75,11 +102,24 @@ def _peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+def gpu_identity(local):
+    """The CUDA device's UUID in nvidia-smi's form (GPU-xxxxxxxx-...), which
+    names the same GPU whatever CUDA_VISIBLE_DEVICES renumbers; None if
+    unavailable."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
 
-    def __init__(self, gpu):
-        self.gpu = gpu
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons of one GPU, named by its UUID,
+    sampled during the timed region."""
+
+    def __init__(self, gpu_id):
+        self.gpu = gpu_id
         self.rows = []
         self.proc = None
 
@@ -87,10 +127,13 @@ class ClockSampler:
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
+        if self.gpu is None:
+            return self
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -122,20 +165,21 @@ class ClockSampler:
             except Exception:
                 continue
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                    "gpu": self.gpu}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu": self.gpu}
 
 
+# ------------------------------------------------------------------ CPU oracle
 def oracle_sampler():
-    """The oracle on a bounded sample of the workload: a 16x16-cell window
-    (same angular mesh, order, materials and multigrid).  Returns a function
-    timing one preconditioned GMRES iteration (one V-cycle plus one operator
-    apply, FP64) and returning the cpu_baseline record; the set-up (tables,
-    hierarchy) is done once, outside the timing."""
+    """The oracle on a bounded sample of the headline workload: a 4x4-cell
+    window of it (same angular mesh, order, materials, beam and multigrid).
+    Returns a function timing one preconditioned Krylov iteration (one
+    V-cycle plus one operator apply, FP64) and returning the cpu_baseline
+    record; the set-up (tables, hierarchy) is done once, outside the timing."""
     from oracle import multigrid
-    import multiprocessing
-    prob = W.config2_checkerboard(n=16, block=16)
+    prob = W.config5_beam(n=4)
     H = multigrid.Hierarchy(prob)
     T = H.levels[0]
     f = T.source()
@@ -151,10 +195,50 @@ def oracle_sampler():
         _ = T.apply_A(z)
         dt = time.perf_counter() - t0
         return {"value": dof / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
-                "sample": (f"16x16-cell window of the 128x128 workload ({dof} unknowns, all 512 "
-                           f"patches, N=16, 3-level MG): one V-cycle + one operator apply "
-                           f"(= one preconditioned GMRES iteration) in {dt:.1f} s, NumPy FP64")}
+                "sample": (f"4x4-cell window of the 256x256 beam workload ({dof} unknowns, all "
+                           f"2048 patches, N=64, 4-level MG): one V-cycle + one operator apply "
+                           f"(= one preconditioned Krylov iteration) in {dt:.2f} s, NumPy FP64")}
     return step
+
+
+def _oracle_child(conn):
+    """Spawned process: builds the oracle sample, then times one sample per
+    request (so the set-up overlaps the GPU work of the parent)."""
+    try:
+        step = oracle_sampler()
+        conn.send(("ready", None))
+        while True:
+            msg = conn.recv()
+            if msg != "go":
+                break
+            conn.send(("sample", step()))
+    except Exception as ex:  # reported in the bench line
+        conn.send(("error", str(ex)[:200]))
+
+
+class OracleBaseline:
+    """The CPU baseline in a spawned process started before any CUDA call."""
+
+    def __init__(self):
+        ctx = multiprocessing.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_oracle_child, args=(child,), daemon=True)
+        self.proc.start()
+
+    def sample(self):
+        try:
+            kind, val = self.conn.recv()
+            if kind != "ready":
+                return {"error": val}
+            self.conn.send("go")
+            kind, val = self.conn.recv()
+            return val if kind == "sample" else {"error": val}
+        finally:
+            try:
+                self.conn.send("stop")
+            except Exception:
+                pass
+            self.proc.join(timeout=10)
 
 
 def cpu_baseline():
@@ -179,6 +263,14 @@ def job_gdofs(world, unknowns, iterations, seconds):
     return world * unknowns * float(iterations) / seconds / 1e9
 
 
+def head_config(world):
+    return {"workload": WORKLOAD, "unknowns": 4 * 256 * 256 * 6144, "mode": "mixed",
+            "krylov": f"FP64 refinement around FP32 FGMRES({HEAD_RESTART})",
+            "precond": "MG V(1,1)", "tol": 1e-8, "inner_tol": "adaptive",
+            "l2": "inputs larger than L2 (6.4-12.9 GB per vector)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, baseline=None):
     """The oracle (the method restated from the paper, NumPy FP64) on the
     host cores: W untimed warm-up samples, then K timed ones.  Under torchrun
@@ -201,7 +293,7 @@ def run_reference(args, baseline=None):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle sample: 16x16-cell window)"},
+            "config": head_config(args.gpus),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -209,57 +301,376 @@ def run_reference(args, baseline=None):
     return 0
 
 
-def run_profile(args):
-    """One mixed-precision solve, or one launch each of the sweep, the tensor-
-    core scatter and one coarse Gauss-Seidel sweep, on the benchmark workload."""
-    import torch
+# ------------------------------------------------------------------ GPU parts
+def _kt_ids(pkg):
+    return {"sweep": pkg.AMGT_KT_SWEEP, "apply_L": pkg.AMGT_KT_APPLY_L,
+            "scatter_prep": pkg.AMGT_KT_SCATTER_PREP, "scatter_tc": pkg.AMGT_KT_SCATTER_TC,
+            "scatter_f32": pkg.AMGT_KT_SCATTER_F32, "scatter_f64": pkg.AMGT_KT_SCATTER_F64,
+            "coarse_gs": pkg.AMGT_KT_COARSE_GS, "split_tc": pkg.AMGT_KT_SPLIT_TC,
+            "split_aux": pkg.AMGT_KT_SPLIT_AUX, "tc3": pkg.AMGT_KT_TC3,
+            "tc3_prep": pkg.AMGT_KT_TC3_PREP}
+
+
+def kt_read(ctx, pkg):
+    return {k: ctx.amgt_query_kernel_stats(i, reset=True) for k, i in _kt_ids(pkg).items()}
+
+
+def class_roofline(name, ms, n, work, peaks, traffic):
+    """Achieved rate of one kernel class over its timed launches: summed
+    algorithmic work / summed launch time, against the class's peak."""
+    hbm, bf16, peak_src = peaks
+    kernel, bound, unit = CLASSES[name]
+    sec = ms / 1e3
+    if unit == "B":
+        achieved, peak, u = work / sec / 1e9, hbm, "GB/s"
+    else:
+        achieved, u = work / sec / 1e12, "TFLOP/s"
+        peak = {"tensor": bf16, "alu": ALU_PEAK, "alu64": FP64_PEAK}[bound]
+    return {"kernel": kernel, "bound": "alu" if bound == "alu64" else bound,
+            "achieved": achieved, "peak": peak, "unit": u, "frac": achieved / peak,
+            "launches": n, "mean_launch_s": sec / max(n, 1),
+            "work_per_launch": work / max(n, 1), "work_unit": unit,
+            "traffic": traffic.get(name),
+            "peak_kind": PEAK_KINDS[bound] + ("" if bound in ("alu", "alu64") else
+                                              f" ({peak_src})")}
+
+
+def solve_timed(ctx, solve, steps, stream, torch):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    its, outer, relres = [], [], []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        st = solve()
+        its.append(st.iterations)
+        outer.append(st.outer_iterations)
+        relres.append(st.relres)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, its, outer, relres
+
+
+def coarse_f64_variant(ctx, solve, stream, torch, steps):
+    """The same mixed solve with the coarsest Gauss-Seidel solve of the FP32
+    V-cycle in FP64 (AMGT_TUNE_COARSE_F64): one warm-up solve, `steps` timed."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_COARSE_F64
+    ctx.amgt_set_tuning(AMGT_TUNE_COARSE_F64, 1)
+    with torch.cuda.stream(stream):
+        solve()
+        el, its, outer, rel = solve_timed(ctx, solve, steps, stream, torch)
+    ctx.amgt_set_tuning(AMGT_TUNE_COARSE_F64, 0)
+    return {"time_to_tol_s": el / steps, "krylov_iterations": its, "refinement_steps": outer,
+            "relres": rel}
+
+
+def instrumented(ctx, solve, pkg, peaks, traffic, torch):
+    """One solve with the library's per-launch event timers on: per kernel
+    class its device time, launches, share of the solve and roofline."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_KERNEL_TIMERS
+    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
+    kt_read(ctx, pkg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = solve()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    k = kt_read(ctx, pkg)
+    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
+    out = {}
+    for name, (ms, n, work) in k.items():
+        if n > 0:
+            r = class_roofline(name, ms, n, work, peaks, traffic)
+            r["ms"] = ms
+            r["share"] = ms / 1e3 / wall
+            out[name] = r
+    return out, wall, st
+
+
+def operators_alone(ctx, nsdof, nadof, nmom, peaks, torch, stream, pkg):
+    """One call of each operator on the finest level (FP32 unless stated),
+    timed with events on the library's stream: GDOF/s per operator, and for
+    the scatter the method's own work, 2 min(Nadof, 2 nmom) flop per unknown
+    (dense S_f or the moment form, whichever is cheaper)."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_KERNEL_TIMERS
+    dof = nsdof * nadof
+    x32 = torch.randn((nsdof, nadof), device="cuda", dtype=torch.float32)
+    y32 = torch.empty_like(x32)
+    method_flop = 2.0 * dof * min(nadof, 2 * nmom)
+    out = {}
+
+    def timeit(fn, reps):
+        fn()
+        ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
+        kt_read(ctx, pkg)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        k = kt_read(ctx, pkg)
+        ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
+        return a.elapsed_time(b) / reps / 1e3, {n: v for n, v in k.items() if v[1] > 0}
+
+    with torch.cuda.stream(stream):
+        t, _ = timeit(lambda: ctx.amgt_op_sweep(0, x32, y32), 5)
+        out["sweep_f32"] = {"s": t, "GDOF/s": dof / t / 1e9, "GB/s": 8.0 * dof / t / 1e9}
+        t, _ = timeit(lambda: ctx.amgt_op_apply_L(0, x32, y32), 5)
+        out["apply_L_f32"] = {"s": t, "GDOF/s": dof / t / 1e9, "GB/s": 8.0 * dof / t / 1e9}
+        t, k = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32, tc=True), 5)
+        out["scatter_bf16tc"] = {"s": t, "GDOF/s": dof / t / 1e9,
+                                 "method_TFLOP/s": method_flop / t / 1e12,
+                                 "gemm_TFLOP/s": k["scatter_tc"][2] / k["scatter_tc"][0] / 1e9}
+        t, k = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32, tc="tc3"), 3)
+        if "tc3" in k:
+            out["scatter_f32_tc3"] = {"s": t, "GDOF/s": dof / t / 1e9,
+                                      "method_TFLOP/s": method_flop / t / 1e12,
+                                      "gemm_TFLOP/s": k["tc3"][2] / k["tc3"][0] / 1e9}
+        t, _ = timeit(lambda: ctx.amgt_op_vcycle(x32, y32, tc=True), 2)
+        out["vcycle_bf16tc"] = {"s": t, "GDOF/s": dof / t / 1e9}
+        del x32, y32
+        x64 = torch.randn((nsdof, nadof), device="cuda", dtype=torch.float64)
+        y64 = torch.empty_like(x64)
+        t, k = timeit(lambda: ctx.amgt_op_scatter(0, x64, y64, tc=True), 1)
+        if "split_tc" in k:
+            out["scatter_f64_split"] = {"s": t, "GDOF/s": dof / t / 1e9,
+                                        "method_TFLOP/s": method_flop / t / 1e12,
+                                        "gemm_TFLOP/s": k["split_tc"][2] / k["split_tc"][0] / 1e9,
+                                        "gemm_launches": k["split_tc"][1]}
+        del x64, y64
+    return out
+
+
+def fp64_solve(prob, local, krylov, restart, torch, maxit=400):
+    """Time to relres 1e-8 of the plain FP64 GPU solve on its own context
+    (every FP64 scatter in the split form on the tensor cores), after one
+    warm-up operator apply and V-cycle that build the lazily made tables."""
+    from paper_2010_04559_gb300 import (AMGT_MODE_F64, AMGT_PREC_MG, AMGT_TUNE_FP64_SCATTER,
+                                        context_from_problem)
+    stream = torch.cuda.Stream()
+    ctx = context_from_problem(prob, device=local, stream=stream.cuda_stream)
+    ctx.amgt_set_tuning(AMGT_TUNE_FP64_SCATTER, 2)
+    ns, na = ctx.amgt_query_sizes(0)
+    psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+    phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+    with torch.cuda.stream(stream):
+        tmp = torch.empty_like(psi)
+        ctx.amgt_op_apply_A(0, psi.zero_(), tmp, tc=True)
+        ctx.amgt_op_vcycle(psi, tmp, tc=True)
+        del tmp
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=restart, maxit=maxit,
+                                     precond=AMGT_PREC_MG, mode=AMGT_MODE_F64, psi=psi, phi=phi,
+                                     device_ptrs=True, allow_not_converged=True, krylov=krylov)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    ctx.close()
+    del psi, phi
+    torch.cuda.empty_cache()
+    return {"time_to_tol_s": t, "iterations": st.iterations, "restarts": st.outer_iterations,
+            "relres": st.relres,
+            "krylov": "BiCGStab" if krylov == 1 else f"GMRES({restart})",
+            "scatter": "FP64-accurate split form on BF16 tensor cores (AMGT_F64_SPLIT)",
+            "warmup": "one operator apply and one V-cycle (lazy tables and workspaces)"}
+
+
+def config2_extra(local, torch, pkg, peaks, steps=3, warmup=3):
+    """The 128x128 checkerboard workload: mixed solve time (events, timers
+    off), its kernel shares, and the FP64 GPU solve of the same inputs."""
+    from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_GRAPHS,
+                                        context_from_problem)
+    prob = W.config2_checkerboard()
+    stream = torch.cuda.Stream()
+    ctx = context_from_problem(prob, device=local, stream=stream.cuda_stream)
+    ctx.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
+    ns, na = ctx.amgt_query_sizes(0)
+    psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+    phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+
+    def solve():
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
+                                     mode=AMGT_MODE_MIXED, psi=psi, phi=phi, device_ptrs=True)
+        return st
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            solve()
+        el, its, outer, rel = solve_timed(ctx, solve, steps, stream, torch)
+        kin, wall, _ = instrumented(ctx, solve, pkg, peaks, TRAFFIC["config2"], torch)
+    cf64 = coarse_f64_variant(ctx, solve, stream, torch, steps)
+    ctx.close()
+    del psi, phi
+    torch.cuda.empty_cache()
+    t_mixed = el / steps
+    f64 = fp64_solve(prob, local, 0, 20, torch)
+    dof = ns * na
+    dom = max(kin, key=lambda n: kin[n]["share"])
+    return {"workload": WORKLOAD2, "unknowns": dof,
+            "mixed": {"time_to_tol_s": t_mixed, "GDOF/s": dof * np.mean(its) / t_mixed / 1e9,
+                      "krylov_iterations": its, "refinement_steps": outer, "relres": rel,
+                      "krylov": "FP64 refinement around FP32 FGMRES(20)"},
+            "fp64_gpu": f64, "mixed_speedup_vs_fp64": f64["time_to_tol_s"] / t_mixed,
+            "mixed_coarse_f64": cf64,
+            "solve_kernels": {n: {"ms": v["ms"], "share": v["share"], "launches": v["launches"]}
+                              for n, v in kin.items()},
+            "dominant": dict(kin[dom], name=dom)}
+
+
+def adjoint_extra(local, torch):
+    """Adjoint solve (mixed, 1e-8) for the flux integral over a 16x16-cell
+    corner block of the 128x128 workload, then the response and all its
+    gradients."""
     from paper_2010_04559_gb300 import AMGT_MODE_MIXED, AMGT_PREC_MG, context_from_problem
+    from paper_2010_04559_gb300.adjoint import response_problem
+    prob = W.config2_checkerboard()
+    nx = 128
+    weight = np.zeros(nx * nx)
+    for iy in range(16):
+        weight[iy * nx:iy * nx + 16] = 1.0
+    stream = torch.cuda.Stream()
+    ctx = context_from_problem(prob, device=local, stream=stream.cuda_stream)
+    actx = context_from_problem(response_problem(prob, weight), device=local,
+                                stream=stream.cuda_stream)
+    actx.amgt_set_adjoint(1)
+    ns, na = ctx.amgt_query_sizes(0)
+    psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+    lam = torch.empty_like(psi)
+    phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+    C = nx * nx
+    dt = torch.empty(C, device="cuda", dtype=torch.float64)
+    ds = torch.empty_like(dt)
+    df = torch.empty(prob["N"] + 1, device="cuda", dtype=torch.float64)
+    with torch.cuda.stream(stream):
+        ctx.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=psi, phi=phi,
+                       device_ptrs=True)
+
+        def step():
+            _, _, sta, _ = actx.amgt_solve(tol=1e-8, restart=20, maxit=400,
+                                           precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=lam,
+                                           phi=phi, device_ptrs=True)
+            R = actx.amgt_response(psi)
+            ctx.amgt_response_gradients(psi, lam, dt, ds, df)
+            return sta, R
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sta, R = step()
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ctx.amgt_response_gradients(psi, lam, dt, ds, df)
+        t_grad = time.perf_counter() - t0
+    actx.close()
+    ctx.close()
+    return {"workload": "128x128 checkerboard workload: flux integral over the 16x16-cell corner "
+                        "block; dR/dsigma_t, dR/dsigma_s per cell and dR/df_n (N=16)",
+            "adjoint_solve_and_gradients_s": t_adj, "gradients_s": t_grad,
+            "iterations": sta.iterations, "relres": sta.relres, "response": R}
+
+
+def batch_extra(local, torch, nprob):
+    """The first problems of the 256-problem batch of uneven 2D problems, each
+    on its own context and stream, autotuned, V-cycles replayed from captured
+    graphs, solved concurrently (mixed, 1e-8), and one after another."""
+    from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_GRAPHS,
+                                        amgt_solve_batch, context_from_problem)
+    probs = W.config4_batch()[:nprob]
+    bstreams = [torch.cuda.Stream() for _ in probs]
+    bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
+            for p, s in zip(probs, bstreams)]
+    t0 = time.perf_counter()
+    tunes = [c.amgt_autotune(3) for c in bctx]
+    t_tune = time.perf_counter() - t0
+    for c in bctx:
+        c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
+    bpsi = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64) for c in bctx]
+    bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
+    amgt_solve_batch(bctx, bpsi, tol=1e-8)  # warm-up: captures the graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bst = amgt_solve_batch(bctx, bpsi, tol=1e-8)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c, p in zip(bctx, bpsi):
+        c.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=p, phi=None,
+                     device_ptrs=True)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    dof_its = sum(d * st.iterations for d, st in zip(bdof, bst))
+    for c in bctx:
+        c.close()
+    return {"workload": f"first {len(probs)} problems of the 256-problem batch (2D, n in 16..96, "
+                        f"level 1..3, per-cell lognormal sigma_t, N = 2 level + 4)",
+            "problems": len(probs), "unknowns": sum(bdof), "value": dof_its / t_batch / 1e9,
+            "unit": "GDOF/s", "time_to_tol_s": t_batch, "sequential_time_to_tol_s": t_seq,
+            "max_relres": max(st.relres for st in bst),
+            "iterations": [st.iterations for st in bst], "autotune_s": t_tune,
+            "tuned": [list(t[:3]) for t in tunes]}
+
+
+def run_profile(args):
+    """Small launches for ncu: one launch of a chosen kernel on a chosen
+    workload, warm-up launch first."""
+    import torch
+    from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_SWEEP_KERNEL,
+                                        context_from_problem)
     from paper_2010_04559_gb300 import build as _b
     _b.build()
-    prob = W.config2_checkerboard(n=args.n)
+    if args.profile in ("gemm5", "tc3_5", "split5"):
+        # the headline's contraction shape on a 64x64-cell slab of its rows:
+        # K = N = 6144, 65536 rows (a few GB on the device, larger than L2)
+        prob = W.config5_beam(n=64)
+    elif args.profile in ("solve5", "gs5"):
+        prob = W.config5_beam()
+    else:
+        prob = W.config2_checkerboard(n=args.n)
     ctx = context_from_problem(prob, device=0)
     ns, na = ctx.amgt_query_sizes(0)
-    if args.profile == "gs":
-        # the coarse Gauss-Seidel launch of one V-cycle (10 sweeps), once to
-        # warm up and once more
+    if args.profile == "gs5":
+        # the headline's coarse Gauss-Seidel launch (level 1: 32 patches, 10 sweeps)
+        nsc, nac = ctx.amgt_query_sizes(3)
+        fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
+        pc = torch.zeros_like(fc)
+        for _ in range(2):
+            ctx.amgt_op_coarse_gs(10, fc, pc)
+        print("kernels: coarse Gauss-Seidel of the beam workload, 10 sweeps (x2)")
+    elif args.profile == "gs":
         nsc, nac = ctx.amgt_query_sizes(2)
         fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
         pc = torch.zeros_like(fc)
         for _ in range(2):
             ctx.amgt_op_coarse_gs(10, fc, pc)
-        ctx.amgt_sync()
         print("kernels: coarse Gauss-Seidel, 10 sweeps (x2)")
     elif args.profile == "sweeps":
-        from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
         x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
         y = torch.empty_like(x)
-        for _ in range(2):  # one warm-up launch of each variant, then one each
+        for _ in range(2):
             for k in (1, 2):
                 ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, k)
                 ctx.amgt_op_sweep(0, x, y)
-        ctx.amgt_sync()
         print("kernels: level-synchronous row sweep, warp-pipelined sweep (x2)")
-    elif args.profile == "solve":
-        psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
-        phi = torch.empty(ns, device="cuda", dtype=torch.float64)
-        _, _, st, _ = ctx.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED,
-                                     psi=psi, phi=phi, device_ptrs=True)
-        print(f"solve: {st.iterations} iterations, relres {st.relres:.3e}")
-    else:
+    elif args.profile in ("gemm5", "tc3_5"):
         x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
         y = torch.empty_like(x)
-        nsc, nac = ctx.amgt_query_sizes(2)
-        fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
-        pc = torch.zeros_like(fc)
-        ctx.amgt_op_sweep(0, x, y)
+        for _ in range(2):
+            ctx.amgt_op_scatter(0, x, y, tc=True if args.profile == "gemm5" else "tc3")
+        print("kernels: scatter contraction at K = N = 6144 (x2)")
+    elif args.profile == "split5":
+        x = torch.randn((ns, na), device="cuda", dtype=torch.float64)
+        y = torch.empty_like(x)
         ctx.amgt_op_scatter(0, x, y, tc=True)
-        ctx.amgt_op_coarse_gs(1, fc, pc)
-        x64 = x.double()
-        ctx.amgt_op_scatter(0, x64, torch.empty_like(x64))
-        ctx.amgt_op_scatter(0, x64, torch.empty_like(x64), tc=True)
-        ctx.amgt_sync()
-        print("kernels: sweep, tensor-core scatter, coarse Gauss-Seidel (1 sweep), FP64 scatter "
-              "(SIMT, then split form)")
+        print("kernels: split FP64 scatter at K = N = 6144")
+    elif args.profile in ("solve", "solve5"):
+        psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+        phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=HEAD_RESTART if args.profile == "solve5"
+                                     else 20, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED,
+                                     psi=psi, phi=phi, device_ptrs=True)
+        print(f"solve: {st.iterations} iterations, relres {st.relres:.3e}")
+    ctx.amgt_sync()
     torch.cuda.synchronize()
     ctx.close()
     return 0
@@ -268,29 +679,32 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=128, help="cells per axis")
-    ap.add_argument("--fp64-ref", action="store_true", help="also time one FP64 GPU solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the FP64 arm, the 128x128 workload, the adjoint and the batch")
+    ap.add_argument("--graphs", type=int, default=1, help="V-cycle graph replay (1) or not (0)")
     ap.add_argument("--batch", type=int, default=32,
                     help="problems of the uneven 2D batch solved concurrently (0: skip)")
-    ap.add_argument("--inner-tol", type=float, default=0.0,
-                    help="tolerance of each inner FP32 solve (0: adaptive)")
-    ap.add_argument("--profile", choices=["solve", "kernels", "sweeps", "gs"], default=None,
-                    help="run one solve, or one launch of each hot kernel, and exit (for ncu)")
+    ap.add_argument("--n", type=int, default=128, help="cells per axis of --profile's workload")
+    ap.add_argument("--profile", choices=["solve", "solve5", "sweeps", "gs", "gs5", "gemm5",
+                                          "tc3_5", "split5"],
+                    default=None, help="one launch of a hot kernel, and exit (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile(args)
 
-    import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the oracle's set-up starts before any CUDA call, in a spawned process
+    oracle = OracleBaseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+
+    import torch
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -301,319 +715,119 @@ def main():
         return 2
 
     import paper_2010_04559_gb300 as pkg
-    from paper_2010_04559_gb300 import (AMGT_F32, AMGT_F32_BF16TC, AMGT_MODE_F64,
-                                        AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_KERNEL_TIMERS,
+    from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_GRAPHS,
                                         amgt_query_launches, context_from_problem)
-    kt_ids = {"sweep": pkg.AMGT_KT_SWEEP, "apply_L": pkg.AMGT_KT_APPLY_L,
-              "scatter_prep": pkg.AMGT_KT_SCATTER_PREP, "scatter_tc": pkg.AMGT_KT_SCATTER_TC,
-              "scatter_f32": pkg.AMGT_KT_SCATTER_F32, "scatter_f64": pkg.AMGT_KT_SCATTER_F64,
-              "coarse_gs": pkg.AMGT_KT_COARSE_GS, "split_tc": pkg.AMGT_KT_SPLIT_TC,
-              "split_aux": pkg.AMGT_KT_SPLIT_AUX}
-
-    def kt_read(reset=True):
-        return {k: ctx.amgt_query_kernel_time(i, reset=reset) for k, i in kt_ids.items()}
     from paper_2010_04559_gb300 import build as _b
     _b.build()
+    peaks = _peaks()
     stream = torch.cuda.Stream()
-    prob = W.config2_checkerboard(n=args.n)
+    prob = W.config5_beam()
+    t0 = time.perf_counter()
     ctx = context_from_problem(prob, device=local, stream=stream.cuda_stream)
     nsdof, nadof = ctx.amgt_query_sizes(0)
+    t_setup = time.perf_counter() - t0
+    ctx.amgt_set_tuning(AMGT_TUNE_GRAPHS, args.graphs)
     dof = nsdof * nadof
     psi = torch.empty((nsdof, nadof), device="cuda", dtype=torch.float64)
     phi = torch.empty(nsdof, device="cuda", dtype=torch.float64)
 
     def solve():
-        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
-                                     mode=AMGT_MODE_MIXED, psi=psi, phi=phi, device_ptrs=True,
-                                     inner_tol=args.inner_tol, inner_maxit=200)
+        _, _, st, _ = ctx.amgt_solve(tol=1e-8, restart=HEAD_RESTART, maxit=400,
+                                     precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=psi,
+                                     phi=phi, device_ptrs=True, inner_maxit=200)
         return st
 
-    for _ in range(args.warmup):
-        st = solve()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    its = []
-    outer = []
-    relres = []
-    l0 = amgt_query_launches()
-    # the library records CUDA events on its stream around each launch of its
-    # main kernels while the timers are on: per-kernel device time in the solve
-    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
-    kt_read()
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
+    log(f"headline context ready ({t_setup:.1f} s)")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
             st = solve()
-            its.append(st.iterations)
-            outer.append(st.outer_iterations)
-            relres.append(st.relres)
-        e1.record(stream)
+            log(f"warm-up solve: {st.iterations} iterations, relres {st.relres:.2e}")
         torch.cuda.synchronize()
-    launches = amgt_query_launches() - l0
-    elapsed = e0.elapsed_time(e1) / 1e3
-    kt_solve = kt_read()
-    ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
+        if dist:
+            dist.barrier()
+        l0 = amgt_query_launches()
+        with ClockSampler(gpu_identity(local)) as clk:
+            elapsed, its, outer, relres = solve_timed(ctx, solve, args.steps, stream, torch)
+        launches = amgt_query_launches() - l0
     elapsed = max_over_ranks(elapsed, dist, "cuda")
     ms = elapsed / args.steps * 1e3
     value = job_gdofs(world, dof, np.sum(its), elapsed)
 
-    # ---- end to end through the public API with host buffers
+    log(f"timed: {ms:.1f} ms per solve")
+    # ---- end to end through the public API with host buffers: the source
+    # upload and the psi/phi download inside the timed region
+    e2e_steps = min(args.steps, 2)
     qsrc = np.ascontiguousarray(prob["q"])
     psi_h = torch.empty((nsdof, nadof), dtype=torch.float64, pin_memory=True).numpy()
     phi_h = torch.empty(nsdof, dtype=torch.float64, pin_memory=True).numpy()
     e2e_its = 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         ctx.amgt_set_source_iso(qsrc)
-        _, _, st2, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
-                                      mode=AMGT_MODE_MIXED, psi=psi_h, phi=phi_h,
-                                      inner_tol=args.inner_tol, inner_maxit=200)
+        _, _, st2, _ = ctx.amgt_solve(tol=1e-8, restart=HEAD_RESTART, maxit=400,
+                                      precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=psi_h,
+                                      phi=phi_h, inner_maxit=200)
         e2e_its += st2.iterations
     e2e_t = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": job_gdofs(world, dof, e2e_its, e2e_t), "unit": "GDOF/s",
            "h2d_bytes_per_step": int(qsrc.nbytes),
-           "d2h_bytes_per_step": int(psi_h.nbytes + phi_h.nbytes)}
+           "d2h_bytes_per_step": int(psi_h.nbytes + phi_h.nbytes), "steps": e2e_steps,
+           "time_to_tol_s": e2e_t / e2e_steps}
+    del psi_h, phi_h
 
-    # ---- per-kernel roofline, timed with events on the library's stream
-    hbm, bf16, peak_kind = _peaks()
-    kern = {}
-    x32 = torch.randn((nsdof, nadof), device="cuda", dtype=torch.float32)
-    y32 = torch.empty_like(x32)
-    nsc, nac = ctx.amgt_query_sizes(2)
-    fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
-    pc = torch.zeros_like(fc)
+    log(f"e2e: {e2e['time_to_tol_s']:.2f} s per solve")
+    # ---- one instrumented solve: kernel shares and rooflines
     with torch.cuda.stream(stream):
-        def timeit(fn, reps=10):
-            for _ in range(2):
-                fn()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 1)
-            kt_read()
-            a.record(stream)
-            for _ in range(reps):
-                fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            k = kt_read()
-            ctx.amgt_set_tuning(AMGT_TUNE_KERNEL_TIMERS, 0)
-            # seconds per call, and per kernel class: seconds per launch
-            per = {n: (v[0] / 1e3 / v[1]) for n, v in k.items() if v[1] > 0}
-            return a.elapsed_time(b) / reps / 1e3, per
-        t_sweep, k_sw = timeit(lambda: ctx.amgt_op_sweep(0, x32, y32))
-        kern["sweep_f32"] = {"s": t_sweep, "GB/s": 8.0 * dof / k_sw["sweep"] / 1e9}
-        use_tc = True
-        try:
-            t_sc, k_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32, tc=True))
-            kern["scatter_bf16tc"] = {"s": t_sc, "gemm_s": k_sc["scatter_tc"],
-                                      "prep_s": k_sc["scatter_prep"],
-                                      "gemm_TFLOP/s": 2.0 * nsdof * nadof * nadof / k_sc["scatter_tc"] / 1e12}
-        except Exception as ex:
-            use_tc = False
-            t_sc, k_sc = timeit(lambda: ctx.amgt_op_scatter(0, x32, y32))
-            kern["scatter_f32"] = {"s": t_sc, "note": str(ex)[:80]}
-        x64 = x32.double()
-        y64 = torch.empty_like(x64)
-        t_sp, k_sp = timeit(lambda: ctx.amgt_op_scatter(0, x64, y64, tc=True), reps=3)
-        if k_sp.get("split_tc"):
-            kern["scatter_f64_split"] = {"s": t_sp, "gemm_s_per_launch": k_sp["split_tc"],
-                                         "gemm_TFLOP/s": 2.0 * nsdof * nadof * nadof / k_sp["split_tc"] / 1e12}
-        t_64, k_64 = timeit(lambda: ctx.amgt_op_scatter(0, x64, y64), reps=2)
-        kern["scatter_f64_simt"] = {"s": t_64}
-        del x64, y64
-        t_L, k_L = timeit(lambda: ctx.amgt_op_apply_L(0, x32, y32))
-        kern["apply_L_f32"] = {"s": t_L, "GB/s": 8.0 * dof / k_L["apply_L"] / 1e9}
-        t_gs, k_gs = timeit(lambda: ctx.amgt_op_coarse_gs(10, fc, pc), reps=3)
-        kern["coarse_gs_f32_10sweeps"] = {"s": t_gs, "kernel_s": k_gs["coarse_gs"]}
-        t_v, _ = timeit(lambda: ctx.amgt_op_vcycle(x32, y32, tc=use_tc), reps=3)
-        kern["vcycle_bf16tc" if use_tc else "vcycle_f32"] = {"s": t_v}
-    # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    # coarse Gauss-Seidel algorithmic work: per cell, per sweep direction and
-    # per sweep, the sequential per-patch form of the block solves
-    # (moments source s*a*nm, self-scatter s*a*a, mass mix s*a*s, block solve
-    # (s*a)^2, moment update s*nm*a per patch) -> 2 flop per FMA
-    nsc_cells = nsc // 4
-    npd = nac // 3 // 4
-    nm = 25
-    per_patch = 4 * 3 * nm + 4 * 3 * 3 + 4 * 3 * 4 + (4 * 3) ** 2 + 4 * nm * 3
-    gs_flop = 2.0 * per_patch * npd * 4 * nsc_cells * 10
-    gs_alg = f"{gs_flop/1e9:.2f} GFLOP per launch of 10 sweeps (sequential per-patch form)"
-    tc_flop = 2.0 * nsdof * nadof * nadof
-    # work per launch of each kernel class on the benchmark workload
-    work = {
-        "sweep": ("hbm", 8.0 * dof / 1e9, hbm, "GB/s", "8 B per unknown (read b, write psi, FP32)"),
-        "apply_L": ("hbm", 8.0 * dof / 1e9, hbm, "GB/s", "8 B per unknown (read x, write y, FP32)"),
-        "scatter_prep": ("hbm", 6.0 * dof / 1e9, hbm, "GB/s",
-                         "6 B per unknown (read FP32 x, write BF16 operand)"),
-        "scatter_tc": ("tensor", tc_flop / 1e12, bf16, "TFLOP/s", "2 Nsdof Nadof^2 flop (dense S_f, BF16)"),
-        "coarse_gs": ("alu", gs_flop / 1e12, alu_peak, "TFLOP/s", gs_alg),
-        # FP64 moment form of the scatter in each refinement residual:
-        # Phi = psi X and Y = Phi (F X^T), 2 Nsdof Nadof nmom flop each
-        "scatter_f64": ("alu", 4.0 * nsdof * nadof * NMOM_FINE / 1e12, FP64_PEAK, "TFLOP/s",
-                        "4 Nsdof Nadof nmom flop per residual (two FP64 GEMMs, nmom = 289)"),
-        "scatter_f32": ("alu", 4.0 * nsdof * nadof * NMOM_FINE / 1e12, alu_peak, "TFLOP/s",
-                        "4 Nsdof Nadof nmom flop per apply (two FP32 GEMMs, nmom = 289)"),
-        # one slice-pair product of the split FP64 scatter per launch
-        "split_tc": ("tensor", tc_flop / 1e12, bf16, "TFLOP/s",
-                     "2 Nsdof Nadof^2 flop per slice-pair GEMM (BF16 digits, dense S_f)"),
-    }
-    rl = {}
-    for name, per_launch in (("sweep", k_sw.get("sweep")), ("apply_L", k_L.get("apply_L")),
-                             ("scatter_prep", k_sc.get("scatter_prep")),
-                             ("scatter_tc", k_sc.get("scatter_tc")),
-                             ("split_tc", k_sp.get("split_tc")),
-                             ("coarse_gs", k_gs.get("coarse_gs"))):
-        if not per_launch:
-            continue
-        bound, w, peak, unit, alg = work[name]
-        rl[name] = {"kernel": KERNEL_NAMES[name], "bound": bound, "achieved": w / per_launch,
-                    "peak": peak, "unit": unit, "frac": w / per_launch / peak,
-                    "launch_s": per_launch, "traffic": TRAFFIC.get(name), "algorithmic": alg}
-    # in-solve device time per kernel class (timed region, library events)
-    solve_k = {}
-    for name, (msum, n) in kt_solve.items():
-        if n > 0:
-            solve_k[name] = {"ms_per_step": msum / args.steps, "launches_per_step": n / args.steps,
-                             "share": msum / 1e3 / elapsed}
-    dom_name = max(solve_k, key=lambda k: solve_k[k]["share"]) if solve_k else "coarse_gs"
-    if dom_name in work:
-        bound, w, peak, unit, alg = work[dom_name]
-        msum, n = kt_solve[dom_name]
-        per_launch = msum / 1e3 / n
-        roof = {"kernel": KERNEL_NAMES[dom_name], "bound": bound, "achieved": w / per_launch,
-                "peak": peak, "unit": unit, "frac": w / per_launch / peak,
-                "traffic": TRAFFIC.get(dom_name), "share_of_solve": solve_k[dom_name]["share"],
-                "peak_kind": PEAK_KINDS["alu64"] if dom_name == "scatter_f64"
-                else PEAK_KINDS.get(bound, peak_kind), "algorithmic": alg}
-    else:
-        roof = {"kernel": dom_name, "bound": None, "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None,
-                "share_of_solve": solve_k[dom_name]["share"]}
+        kin, wall, _ = instrumented(ctx, solve, pkg, peaks, TRAFFIC["config5"], torch)
+    dom = max(kin, key=lambda n: kin[n]["share"])
+    roof = dict(kin[dom])
+    roof["class"] = dom
+    tc_classes = [n for n in kin if CLASSES[n][0].startswith("tc_gemm_kernel")]
+    tc_gemm = {"classes": tc_classes,
+               "share": sum(kin[n]["share"] for n in tc_classes),
+               "TFLOP/s": (sum(kin[n]["work_per_launch"] * kin[n]["launches"] for n in tc_classes)
+                           / max(1e-9, sum(kin[n]["ms"] for n in tc_classes) / 1e3) / 1e12)}
+    tc_gemm["frac"] = tc_gemm["TFLOP/s"] / peaks[1]
+    log(f"instrumented solve {wall:.2f} s, dominant {dom}")
+    ops = operators_alone(ctx, nsdof, nadof, (prob["N"] + 1) ** 2, peaks, torch, stream, pkg)
+    cf64 = coarse_f64_variant(ctx, solve, stream, torch, 1)
+    log(f"coarse FP64 variant: {cf64['time_to_tol_s']:.2f} s")
+    ctx.close()
+    del psi, phi
+    torch.cuda.empty_cache()
 
-    # ---- adjoint: lambda = A^-T g for the flux integral over a 16x16-cell
-    # corner block, then the response and its gradients (mixed solve to 1e-8)
-    adj = None
-    if not args.no_adjoint:
-        from paper_2010_04559_gb300.adjoint import response_problem
-        nx = args.n
-        weight = np.zeros(nx * nx)
-        for iy in range(16):
-            weight[iy * nx:iy * nx + 16] = 1.0
-        actx = context_from_problem(response_problem(prob, weight), device=local,
-                                    stream=stream.cuda_stream)
-        actx.amgt_set_adjoint(1)
-        lam = torch.empty_like(psi)
-        C = nx * nx
-        dt = torch.empty(C, device="cuda", dtype=torch.float64)
-        ds = torch.empty_like(dt)
-        df = torch.empty(prob["N"] + 1, device="cuda", dtype=torch.float64)
-
-        def adjoint_step():
-            _, _, sta, _ = actx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
-                                           mode=AMGT_MODE_MIXED, psi=lam, phi=phi,
-                                           device_ptrs=True, inner_tol=args.inner_tol)
-            R = actx.amgt_response(psi)
-            ctx.amgt_response_gradients(psi, lam, dt, ds, df)
-            return sta, R
-        solve()                     # psi of the forward problem
-        adjoint_step()              # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sta, R = adjoint_step()
-        torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        ctx.amgt_response_gradients(psi, lam, dt, ds, df)
-        t_grad = time.perf_counter() - t0
-        adj = {"workload": "flux integral over the 16x16-cell corner block; dR/dsigma_t, "
-                           "dR/dsigma_s per cell and dR/df_n (N=16)",
-               "adjoint_solve_and_gradients_s": t_adj, "gradients_s": t_grad,
-               "iterations": sta.iterations, "relres": sta.relres, "response": R}
-        actx.close()
-
-    # ---- batched: the first problems of the 256-problem batch of uneven 2D
-    # problems, each on its own context and stream, autotuned, V-cycles
-    # replayed from captured graphs, solved concurrently (mixed, 1e-8)
-    batch = None
-    if args.batch > 0:
-        from paper_2010_04559_gb300 import AMGT_TUNE_GRAPHS, amgt_solve_batch
-        probs = W.config4_batch()[:args.batch]
-        bstreams = [torch.cuda.Stream() for _ in probs]
-        bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
-                for p, s in zip(probs, bstreams)]
-        t0 = time.perf_counter()
-        tunes = [c.amgt_autotune(3) for c in bctx]
-        t_tune = time.perf_counter() - t0
-        for c in bctx:
-            c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
-        bpsi = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64)
-                for c in bctx]
-        bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
-        amgt_solve_batch(bctx, bpsi, tol=1e-8)  # warm-up: captures the graphs
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bst = amgt_solve_batch(bctx, bpsi, tol=1e-8)
-        torch.cuda.synchronize()
-        t_batch = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        for c, p in zip(bctx, bpsi):
-            c.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=p,
-                         phi=None, device_ptrs=True)
-        torch.cuda.synchronize()
-        t_seq = time.perf_counter() - t0
-        dof_its = sum(d * st.iterations for d, st in zip(bdof, bst))
-        batch = {"workload": f"first {len(probs)} problems of the 256-problem batch (2D, n in "
-                             f"16..96, level 1..3, per-cell lognormal sigma_t, N = 2 level + 4)",
-                 "problems": len(probs), "unknowns": sum(bdof),
-                 "value": dof_its / t_batch / 1e9, "unit": "GDOF/s",
-                 "time_to_tol_s": t_batch, "sequential_time_to_tol_s": t_seq,
-                 "max_relres": max(st.relres for st in bst),
-                 "iterations": [st.iterations for st in bst], "autotune_s": t_tune,
-                 "tuned": [list(t[:3]) for t in tunes]}
-        for c in bctx:
-            c.close()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            cpu = cpu_baseline()
-        except Exception as ex:
-            cpu = {"error": str(ex)[:200]}
+    extra = {}
     fp64 = None
-    if args.fp64_ref:
-        t0 = time.perf_counter()
-        _, _, st3, _ = ctx.amgt_solve(tol=1e-8, restart=20, maxit=400, precond=AMGT_PREC_MG,
-                                      mode=AMGT_MODE_F64, psi=psi, phi=phi, device_ptrs=True,
-                                      allow_not_converged=True)
-        fp64 = {"time_to_tol_s": time.perf_counter() - t0, "iterations": st3.iterations,
-                "relres": st3.relres}
+    if not args.no_extra:
+        log("operators timed; FP64 arm")
+        fp64 = fp64_solve(prob, local, 1, 20, torch, maxit=200)
+        log(f"FP64 arm: {fp64['time_to_tol_s']:.1f} s, {fp64['iterations']} iterations")
+        extra["config2"] = config2_extra(local, torch, pkg, peaks)
+        log("128x128 workload done")
+        extra["adjoint"] = adjoint_extra(local, torch)
+        if args.batch > 0:
+            extra["batched"] = batch_extra(local, torch, args.batch)
+
+    log("GPU parts done; CPU oracle sample")
+    cpu = oracle.sample() if oracle else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32/bf16 (f64 refinement)", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.n == 128 else WORKLOAD.replace("128x128", f"{args.n}x{args.n}"),
-                           "unknowns": dof, "mode": "mixed", "precond": "MG V(1,1)",
-                           "tol": 1e-8, "inner_tol": args.inner_tol if args.inner_tol > 0 else "adaptive",
-                           "l2": "inputs larger than L2 (0.4-0.8 GB per vector)",
-                           "parallelism": f"replicas x{world}"},
-                "time_to_tol_s": ms / 1e3, "krylov_iterations": its, "refinement_steps": outer, "relres": relres,
-                "gpu_launches": int(launches), "roofline": roof, "rooflines": rl,
-                "solve_kernels": solve_k, "kernels": kern,
+                "dtype": "f32/bf16/f16 (f64 refinement)", "data": "synthetic",
+                "config": head_config(world),
+                "time_to_tol_s": ms / 1e3, "krylov_iterations": its,
+                "refinement_steps": outer, "relres": relres,
+                "gpu_launches": int(launches), "graphs": bool(args.graphs),
+                "setup_s": t_setup, "roofline": roof, "tensor_core_gemm": tc_gemm,
+                "solve_kernels": kin, "instrumented_solve_s": wall, "operators": ops,
                 "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu}
+        line["mixed_coarse_f64"] = cf64
         if fp64:
             line["fp64_gpu"] = fp64
-        if adj:
-            line["adjoint"] = adj
-        if batch:
-            line["batched"] = batch
+            line["mixed_speedup_vs_fp64"] = fp64["time_to_tol_s"] / (ms / 1e3)
+        line["extra"] = extra
         print(json.dumps(line))
-    ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0

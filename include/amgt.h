@@ -66,6 +66,15 @@ typedef enum {
                              summed in FP64; falls back to the FP64 SIMT
                              contraction where the angular size is below 64,
                              not a multiple of 8, or tcgen05 is absent       */
+#define AMGT_F32_TC3 4    /* float in/out, scatter contraction to FP32 accuracy
+                             on FP16 tensor cores: each row of sigma_s N x is
+                             scaled by a power of two and cut into a high and
+                             a low FP16 part (S_f likewise), and the three
+                             products hi S_hi + lo S_hi + hi S_lo run as one
+                             GEMM over the concatenated inner dimension with
+                             FP32 accumulation (relative error ~2^-21); same
+                             fallback as AMGT_F64_SPLIT, to the FP32 SIMT
+                             contraction                                      */
 
 /* preconditioners and precision modes of amgt_solve */
 #define AMGT_PREC_NONE 0
@@ -73,7 +82,8 @@ typedef enum {
 #define AMGT_PREC_MG 2        /* linear V-cycle of Fig. lmg (Sec. 4)              */
 #define AMGT_MODE_F64 0       /* everything in FP64                               */
 #define AMGT_MODE_MIXED 1     /* FP64 GMRES as iterative refinement around an FP32
-                                 flexible GMRES (FP32 operator) whose multigrid
+                                 flexible GMRES (FP32-accurate operator, its
+                                 scatter as AMGT_F32_TC3) whose multigrid
                                  preconditioner runs FP32 sweeps/transfers and the
                                  BF16 tensor-core scatter (FP32 accumulation)     */
 
@@ -133,8 +143,23 @@ int amgt_query_launches(int64_t* count);
 #define AMGT_KT_SCATTER_F64 6  /* FP64 scatter contractions (SIMT)             */
 #define AMGT_KT_SPLIT_TC 7     /* tcgen05 GEMMs of the split FP64 scatter      */
 #define AMGT_KT_SPLIT_AUX 8    /* digit slicing and FP64 accumulation of it    */
-#define AMGT_KT_COUNT 9
+#define AMGT_KT_TC3 9          /* tcgen05 FP16 GEMM of the AMGT_F32_TC3 scatter */
+#define AMGT_KT_TC3_PREP 10    /* its FP32 -> FP16 hi/lo operand pass          */
+#define AMGT_KT_COUNT 11
 int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches);
+/* As amgt_query_kernel_time, and *work (may be NULL) receives the summed
+ * algorithmic work of the timed launches, counted by the library from each
+ * launch's shapes: bytes for the memory-bound classes (SWEEP: read b and
+ * write psi; APPLY_L: read x, write y, and read y when it accumulates;
+ * SCATTER_PREP: 4 B read + 2 B written per unknown; TC3_PREP: 4 + 6 B;
+ * SPLIT_AUX: the digit slicing's and the FP64 accumulation's reads and
+ * writes), flop for the contractions (SCATTER_TC, SPLIT_TC: 2 M N K of the
+ * GEMM; TC3: 2 M N (3K); SCATTER_F32/F64: 2 M N^2 dense or 4 M N nmom in
+ * moment form; COARSE_GS: 2 flop per multiply-add of the sequential
+ * per-patch block solves, (2 s a nm + s a^2 + s^2 a + (s a)^2) per cell,
+ * patch and sweep).  reset clears all three counters. */
+int amgt_query_kernel_stats(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches,
+                            double* work);
 /* Blocks until all work issued on the context's stream has finished; returns
  * AMGT_ERR_DEVICE_TIMEOUT if a device-side bounded wait gave up since the
  * last check. */
@@ -146,11 +171,18 @@ int amgt_sync(amgt_ctx* ctx);
 int amgt_set_mesh_cartesian(amgt_ctx* ctx, int dim, const int64_t ncell[3],
                             const double lo[3], const double hi[3]);
 /* Per-cell sigma_t[C] and sigma_s[C] (= sigma_{s,0}) on host memory, and the
- * Legendre moment shape fmom[N+1] with sigma_{s,n} = sigma_s * fmom[n]
- * (fmom[0] = 1; Sec. 4.2, Eq. for Q).  The scatter kernel is
- * sum_n (2n+1)/(4 pi) sigma_{s,n} P_n(Omega.Omega').  Requires the mesh. */
+ * Legendre moment shapes f[nmat][N+1] (row-major) of nmat materials, the
+ * material of cell c being mat_id[c]: sigma_{s,n}(c) = sigma_s[c] *
+ * f[mat_id[c]][n] (f[m][0] = 1; Sec. 4.2, Eq. for Q).  mat_id may be NULL
+ * when nmat = 1 (one shape for every cell).  The scatter kernel is
+ * sum_n (2n+1)/(4 pi) sigma_{s,n} P_n(Omega.Omega').  With several shapes the
+ * scatter runs in moment form (each cell's moments scaled by its shape) on
+ * the SIMT GEMM and the coarse Gauss-Seidel in its per-patch form; the dense,
+ * tensor-core and split forms need one shape.  Requires the mesh.
+ * AMGT_ERR_ARG for sigma_t <= 0, sigma_s < 0, non-finite values, mat_id out
+ * of [0, nmat) or f[m][0] != 1. */
 int amgt_set_materials(amgt_ctx* ctx, const double* sigma_t, const double* sigma_s,
-                       int N, const double* fmom);
+                       const int32_t* mat_id, int nmat, int N, const double* f);
 /* Uniform angular mesh of the given level (8*4^level patches; Sec. 2.1).
  * basis: 0 Const, 1 Lin (Sec. 2.2). */
 int amgt_set_angular_uniform(amgt_ctx* ctx, int basis, int level);
@@ -169,12 +201,22 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q);
 /* Boundary face f = 2*axis + side (side 1 = high): kind 0 vacuum, kind 1
  * isotropic inflow of angular flux params[0], kind 2 a normally incident
  * pencil beam of strength S = params[0] (particles per unit face area),
- * uniform over the face (Sec. 5.4): psi_b = S delta(Omega - Omega_b) with
- * Omega_b the inward normal, taken in the DG weak form.  Omega_b is a vertex
- * of k = 4 patches; each receives S Psi_m(Omega_b) / k times the face
- * integral of the spatial basis function.  params is read at the call
- * (needs params[0] for kinds 1 and 2); AMGT_ERR_ARG for a face or kind out of
- * range. */
+ * uniform over the face, kind 3 a pencil beam of any inward direction over a
+ * rectangle of the face: params = {S, Omega_b[3], u0, u1, v0, v1}, Omega_b
+ * (normalised by the library) with Omega_b . n < 0, the beam covering the
+ * face points whose tangential coordinates (the face's other axes in
+ * increasing order) lie in [u0, u1] x [v0, v1] (in 2D [u0, u1]; v0, v1 are
+ * read but unused), clipped to the face (Sec. 5.4: the cube with a boundary
+ * source on a square of its face).  A beam psi_b = S delta(Omega - Omega_b)
+ * is taken in the DG weak form: the patches whose closed spherical triangle
+ * holds Omega_b share the Dirac mass by the fraction of an infinitesimal cap
+ * around Omega_b lying in each (1 inside, 1/2 on an edge, interior angle /
+ * 2 pi at a vertex: 1/4 each at the octahedron vertex of kind 2), and patch
+ * q receives S |Omega_b . n| share_q Psi_m(Omega_b) times the integral of the
+ * spatial basis function over the beam's part of the face.  params is read
+ * at the call (1 value for kinds 1 and 2, 8 for kind 3); AMGT_ERR_ARG for a
+ * face or kind out of range, a non-finite value, a zero or outward beam
+ * direction or an empty range. */
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 /* Kernel tuning knobs (results do not depend on them beyond rounding):
  *   AMGT_TUNE_GS_KERNEL   0 auto, 1 per-patch coarse Gauss-Seidel kernel,
@@ -229,7 +271,22 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         row to the next warp through a shared ring with a
  *                         step counter; a wait gives up after 2 s and
  *                         reports AMGT_ERR_DEVICE_TIMEOUT at the next
- *                         amgt_sync); cases outside 2's scope run 1. */
+ *                         amgt_sync); cases outside 2's scope run 1.
+ *   AMGT_TUNE_F32_SCATTER the FP32 scatter of the mixed solve's inner
+ *                         operator: 0 auto (the FP16 three-product tensor-
+ *                         core form of AMGT_F32_TC3 where it applies), 1 the
+ *                         FP32 SIMT contraction
+ *   AMGT_TUNE_COARSE_F64  the coarsest-level Gauss-Seidel solve of the FP32
+ *                         V-cycle (mixed solves, AMGT_F32 cycles): 0 in FP32
+ *                         (default), 1 in FP64 (the right-hand side converted
+ *                         to FP64, the FP64 sweeps, the result rounded back)
+ *   AMGT_TUNE_TEST_SWEEP_HOLD for tests of the failure path only: 1 makes
+ *                         the warp-pipelined 2D sweep's first warp of each
+ *                         block withhold its progress counter and every wait
+ *                         of that kernel give up after 10 ms instead of 2 s,
+ *                         so the launch ends early with psi undefined and the
+ *                         next amgt_sync returns AMGT_ERR_DEVICE_TIMEOUT (the
+ *                         context stays usable); 0 (default) normal */
 #define AMGT_TUNE_GS_KERNEL 1
 #define AMGT_TUNE_SWEEP_GROUP 2
 #define AMGT_TUNE_SWEEP_STAGES 3
@@ -240,6 +297,9 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 #define AMGT_TUNE_FP64_SCATTER 8
 #define AMGT_TUNE_SPLIT_ROWS 9
 #define AMGT_TUNE_SWEEP_KERNEL 10
+#define AMGT_TUNE_F32_SCATTER 11
+#define AMGT_TUNE_TEST_SWEEP_HOLD 12
+#define AMGT_TUNE_COARSE_F64 13
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Times the sweep's patches per block and copy depth (what bit 0) and the
  * coarse Gauss-Seidel kernel (what bit 1) on this context's own hierarchy
@@ -316,7 +376,11 @@ int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void*
  * amgt_query_sizes completes it).  Every call, from every context, uses the
  * same array and leaves its contents behind; each call overwrites it before
  * reading, so no clearing is needed, but calls that overlap on the GPU (other
- * streams, other contexts) race on it and must be serialised by the caller. */
+ * streams, other contexts) race on it and must be serialised by the caller.
+ * The library's kernel timers (AMGT_TUNE_KERNEL_TIMERS) never time this call
+ * (recording them would create CUDA events), and the moment contraction's and
+ * the default row Gauss-Seidel's kernels are resolved at set-up, so a first
+ * call does not load their code onto the GPU either. */
 int amgt_op_coarse_gs_noalloc(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi);
 /* phi = LMG(0, f, finest) (Fig. lmg).  dtype AMGT_F32_BF16TC runs the FP32
  * cycle with the BF16 tensor-core scatter. */
@@ -345,7 +409,8 @@ int amgt_response(amgt_ctx* ctx, int device, const double* psi, double* R);
  * Sec. 4.2):
  *   dsigma_t[c] = -sum_q lambda_cq^T (N (x) M_q) psi_cq          [C]
  *   dsigma_s[c] =  lambda_c^T (N (x) S_f) psi_c                   [C]
- *   dfmom[n]    =  sum_c sigma_s[c] lambda_c^T (N (x) X_n X_n^T) psi_c   [N+1]
+ *   dfmom[m][n] =  sum_{c of material m} sigma_s[c] lambda_c^T (N (x) X_n X_n^T)
+ *                  psi_c                                              [nmat][N+1]
  * (S_f = X diag(f_n) X^T, X_n the degree-n harmonics moments; sigma_s[c] the
  * cell's n = 0 scatter cross section).  Outputs in the same memory space as
  * the inputs; the call returns after they are written. */

@@ -27,6 +27,7 @@ AMGT_F64 = 0
 AMGT_F32 = 1
 AMGT_F32_BF16TC = 2
 AMGT_F64_SPLIT = 3
+AMGT_F32_TC3 = 4
 
 AMGT_PREC_NONE = 0
 AMGT_PREC_SWEEP = 1
@@ -46,16 +47,20 @@ AMGT_TUNE_GRAPHS = 7
 AMGT_TUNE_FP64_SCATTER = 8
 AMGT_TUNE_SPLIT_ROWS = 9
 AMGT_TUNE_SWEEP_KERNEL = 10
+AMGT_TUNE_F32_SCATTER = 11
+AMGT_TUNE_TEST_SWEEP_HOLD = 12
+AMGT_TUNE_COARSE_F64 = 13
 AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6
 AMGT_KT_SPLIT_TC, AMGT_KT_SPLIT_AUX = 7, 8
-AMGT_KT_COUNT = 9
+AMGT_KT_TC3, AMGT_KT_TC3_PREP = 9, 10
+AMGT_KT_COUNT = 11
 
 # every exported symbol of include/amgt.h
 EXPORTS = [
     "amgt_create", "amgt_destroy", "amgt_last_error", "amgt_set_stream", "amgt_sync",
-    "amgt_query_launches", "amgt_query_kernel_time",
+    "amgt_query_launches", "amgt_query_kernel_time", "amgt_query_kernel_stats",
     "amgt_set_mesh_cartesian", "amgt_set_materials", "amgt_set_angular_uniform",
     "amgt_set_angular_aniso", "amgt_set_multigrid", "amgt_set_source_iso",
     "amgt_set_boundary", "amgt_set_tuning", "amgt_query_sizes", "amgt_solve", "amgt_op_source",
@@ -96,8 +101,9 @@ _SIGS = {
     "amgt_sync": ([_P], _I),
     "amgt_query_launches": ([_PI64], _I),
     "amgt_query_kernel_time": ([_P, _I, _I, _PD, _PI64], _I),
+    "amgt_query_kernel_stats": ([_P, _I, _I, _PD, _PI64, _PD], _I),
     "amgt_set_mesh_cartesian": ([_P, _I, _PI64, _PD, _PD], _I),
-    "amgt_set_materials": ([_P, _PD, _PD, _I, _PD], _I),
+    "amgt_set_materials": ([_P, _PD, _PD, ctypes.POINTER(ctypes.c_int32), _I, _I, _PD], _I),
     "amgt_set_angular_uniform": ([_P, _I, _I], _I),
     "amgt_set_angular_aniso": ([_P, _I, _PD, _I], _I),
     "amgt_set_multigrid": ([_P, _I, _PI, _I, _I, _I], _I),
@@ -219,12 +225,17 @@ class Context:
             self.h, int(dim), nc.ctypes.data_as(_PI64), lo.ctypes.data_as(_PD),
             hi.ctypes.data_as(_PD)))
 
-    def amgt_set_materials(self, sigma_t, sigma_s, N, fmom):
+    def amgt_set_materials(self, sigma_t, sigma_s, N, fmom, mat_id=None):
+        """fmom: f[N+1] (one shape) or f[nmat][N+1] with mat_id[C]."""
         st = _np(sigma_t, np.float64)
         ss = _np(sigma_s, np.float64)
-        fm = _np(fmom, np.float64)
+        fm = _np(np.atleast_2d(np.asarray(fmom, dtype=np.float64)), np.float64)
+        nmat = fm.shape[0]
+        mid = None if mat_id is None else _np(mat_id, np.int32)
+        pm = (ctypes.POINTER(ctypes.c_int32)() if mid is None
+              else mid.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         return self._check(self.lib.amgt_set_materials(
-            self.h, st.ctypes.data_as(_PD), ss.ctypes.data_as(_PD), int(N),
+            self.h, st.ctypes.data_as(_PD), ss.ctypes.data_as(_PD), pm, int(nmat), int(N),
             fm.ctypes.data_as(_PD)))
 
     def amgt_set_angular_uniform(self, basis, level):
@@ -246,7 +257,9 @@ class Context:
         return self._check(self.lib.amgt_set_source_iso(self.h, qq.ctypes.data_as(_PD)))
 
     def amgt_set_boundary(self, face, kind, value=0.0):
-        p = _np([value], np.float64)
+        """value: a number (kinds 0-2), or for kind 3 the eight numbers
+        (S, Omega_b[3], u0, u1, v0, v1)."""
+        p = _np(np.atleast_1d(np.asarray(value, dtype=np.float64)).ravel(), np.float64)
         return self._check(self.lib.amgt_set_boundary(self.h, int(face), int(kind),
                                                       p.ctypes.data_as(_PD)))
 
@@ -260,6 +273,17 @@ class Context:
         self._check(self.lib.amgt_query_kernel_time(self.h, int(kernel), 1 if reset else 0,
                                                     ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def amgt_query_kernel_stats(self, kernel, reset=False):
+        """(milliseconds, launches, algorithmic work in bytes or flop) timed
+        for one AMGT_KT_* kernel class."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        w = ctypes.c_double(0.0)
+        self._check(self.lib.amgt_query_kernel_stats(self.h, int(kernel), 1 if reset else 0,
+                                                     ctypes.byref(ms), ctypes.byref(n),
+                                                     ctypes.byref(w)))
+        return ms.value, n.value, w.value
 
     def amgt_query_sizes(self, level=0):
         a = ctypes.c_int64()
@@ -300,10 +324,14 @@ class Context:
     # ---- operators on torch CUDA tensors
     @staticmethod
     def _dtype_code(t, tc=False):
+        """tc: False (plain), True (BF16 tensor cores for FP32, split form for
+        FP64) or "tc3" (FP32: the FP16 three-product tensor-core form)."""
         import torch
         if t.dtype == torch.float64:
             return AMGT_F64_SPLIT if tc else AMGT_F64
         if t.dtype == torch.float32:
+            if tc == "tc3":
+                return AMGT_F32_TC3
             return AMGT_F32_BF16TC if tc else AMGT_F32
         raise TypeError("buffers must be float64 or float32 CUDA tensors")
 
@@ -400,7 +428,8 @@ class Context:
         return R.value
 
     def amgt_response_gradients(self, psi, lam, dsigt, dsigs, dfmom):
-        """Fill dsigt [C], dsigs [C], dfmom [N+1] (same memory space as psi)."""
+        """Fill dsigt [C], dsigs [C], dfmom [N+1] or [nmat][N+1] (same memory
+        space as psi)."""
         dev, p = self._mem(psi)
         dev2, l = self._mem(lam)
         assert dev == dev2
@@ -436,7 +465,8 @@ def context_from_problem(prob, device=0, stream=None, aniso=None):
     ctx = Context(device, stream)
     dim = prob["dim"]
     ctx.amgt_set_mesh_cartesian(dim, prob["ncell"], prob["lo"], prob["hi"])
-    ctx.amgt_set_materials(prob["sigma_t"], prob["sigma_s"], prob["N"], prob["fmom"])
+    ctx.amgt_set_materials(prob["sigma_t"], prob["sigma_s"], prob["N"], prob["fmom"],
+                           prob.get("mat_id"))
     basis = 1 if prob["basis"] == "lin" else 0
     if aniso is None:
         ctx.amgt_set_angular_uniform(basis, prob["level"])

@@ -40,7 +40,8 @@ def solve_response(prob, weight, device=0, tol=1e-12, mode=AMGT_MODE_F64, precon
         C = int(np.prod(prob["ncell"]))
         dt = torch.empty(C, device=dev, dtype=torch.float64)
         ds = torch.empty(C, device=dev, dtype=torch.float64)
-        df = torch.empty(int(prob["N"]) + 1, device=dev, dtype=torch.float64)
+        # one row of f_n per material (one row without mat_id)
+        df = torch.empty(np.asarray(prob["fmom"]).shape, device=dev, dtype=torch.float64)
         fwd.amgt_response_gradients(psi, lam, dt, ds, df)
     finally:
         fwd.close()
@@ -51,7 +52,8 @@ def solve_response(prob, weight, device=0, tol=1e-12, mode=AMGT_MODE_F64, precon
 class DetectorResponse:
     """R = DetectorResponse.apply(sigma_t, sigma_s, fmom, prob, weight) for
     torch tensors sigma_t [C], sigma_s [C] (n = 0 scatter per cell) and
-    fmom [N+1] (f_n, f_0 = 1); backward returns the adjoint gradients."""
+    fmom [N+1] (f_n, f_0 = 1), or [nmat][N+1] with prob["mat_id"]; backward
+    returns the adjoint gradients."""
 
     _fn = None
 

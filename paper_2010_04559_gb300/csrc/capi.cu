@@ -9,6 +9,7 @@
 #include <atomic>
 #include <initializer_list>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <stdexcept>
 #include <string>
@@ -157,10 +158,12 @@ Geom level_geom(const amgt_ctx* ctx, int k) {
 }
 
 // CUDA events around one launch on the context's stream while the kernel
-// timers are on (RAII: the stop event is recorded when the scope ends)
+// timers are on (RAII: the stop event is recorded when the scope ends), with
+// the launch's algorithmic work (bytes or flop, per kernel class)
 struct KernelTimer {
   amgt_ctx* ctx;
   int id;
+  double work;
   cudaEvent_t a = nullptr, b = nullptr;
   static cudaEvent_t take(amgt_ctx* c) {
     if (!c->kt_free.empty()) {
@@ -175,8 +178,11 @@ struct KernelTimer {
     }
     return e;
   }
-  KernelTimer(amgt_ctx* c, int kid) : ctx(c), id(kid) {
-    if (!ctx->ktimers) return;
+  // enabled = false: never records (the allocation-free entry point, which
+  // must not create events)
+  KernelTimer(amgt_ctx* c, int kid, double w = 0.0, bool enabled = true)
+      : ctx(c), id(kid), work(w) {
+    if (!ctx->ktimers || !enabled) return;
     a = take(ctx);
     b = take(ctx);
     if (!a || !b) {
@@ -190,13 +196,14 @@ struct KernelTimer {
   ~KernelTimer() {
     if (!a) return;
     cudaEventRecord(b, ctx->stream);
-    ctx->kt_pending.push_back({id, a, b});
+    ctx->kt_pending.push_back({id, a, b, work});
   }
 };
 
 CellData cell_data(const amgt_ctx* ctx) {
   CellData cd;
   cd.mat = ctx->d_mat;
+  cd.fid = ctx->nf > 1 ? ctx->d_fid : nullptr;
   cd.sigma_t = ctx->d_sigt;
   cd.sigma_s = ctx->d_sigs;
   cd.sigma_t32 = ctx->d_sigt32;
@@ -223,7 +230,8 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
                  const std::vector<double>& B, const std::vector<double>& Kinv,
                  const std::vector<double>& Ginv, const std::vector<double>& X,
                  const std::vector<double>& XFt, const std::vector<double>& Sqq,
-                 const std::vector<double>& tblk, LevelDevStore<T>& s) {
+                 const std::vector<double>& tblk, LevelDevStore<T>& s,
+                 const std::vector<double>& Xt = {}, const std::vector<double>& fdeg = {}) {
   TRY(upload(ctx, K0, &s.K0));
   TRY(upload(ctx, B, &s.B));
   TRY(upload(ctx, Kinv, &s.Kinv));
@@ -236,6 +244,8 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
   TRY(upload(ctx, L.mesh.Aw, &s.Aw));
   TRY(upload(ctx, L.mesh.M, &s.Mang));
   if (!tblk.empty()) TRY(upload(ctx, tblk, &s.tblk));
+  if (!Xt.empty()) TRY(upload(ctx, Xt, &s.Xt));
+  if (!fdeg.empty()) TRY(upload(ctx, fdeg, &s.fdeg));
   return AMGT_OK;
 }
 
@@ -434,33 +444,78 @@ int build_gs_rows(amgt_ctx* ctx) {
 // patches.  Table: beam[f][q a + m] = S Psi_[q]m(Omega_b) / k.  Adjoint
 // contexts hold reversed directions, so their patch q covers -D_q: the table
 // is built from the forward mesh (before the reversal) at -Omega_b.
+// Pencil-beam inflow weights per beam face (kinds 2 and 3): the Dirac mass
+// at the beam direction goes to the patches whose closed spherical triangle
+// holds it, each with the fraction of an infinitesimal cap around it that
+// lies in the patch (1 inside, 1/2 on an edge, interior angle / 2 pi at a
+// vertex: 1/4 at an octahedron vertex), times Psi_m there; kind 3 also
+// carries the incidence factor |Omega_b . n|.
 int build_beam(amgt_ctx* ctx, Level& Lv, int dim) {
   bool any = false;
-  for (int f = 0; f < 2 * dim; ++f) any |= ctx->bkind[f] == 2;
+  for (int f = 0; f < 2 * dim; ++f) any |= ctx->bkind[f] >= 2;
   if (!any) return AMGT_OK;
   const int a = Lv.mesh.a, nadof = Lv.mesh.nadof();
+  // on an adjoint context patch q stands for -D_q: the same physical beam is
+  // found at -Omega_b among the forward patches
   const double sg = ctx->adjoint ? -1.0 : 1.0;
   std::vector<double> beam((size_t)2 * dim * nadof, 0.0);
   for (int f = 0; f < 2 * dim; ++f) {
-    if (ctx->bkind[f] != 2) continue;
-    double ob[3] = {0.0, 0.0, 0.0};
-    ob[f / 2] = (f & 1) ? -1.0 : 1.0;
-    std::vector<int> hits;
-    for (int q = 0; q < Lv.mesh.P; ++q)
-      for (int v = 0; v < 3; ++v) {
-        const double* x = Lv.mesh.patch[q].v[v];
-        if (std::fabs(sg * x[0] - ob[0]) + std::fabs(sg * x[1] - ob[1]) +
-                std::fabs(sg * x[2] - ob[2]) < 1e-12)
-          hits.push_back(q);
+    if (ctx->bkind[f] < 2) continue;
+    double ob[3] = {0.0, 0.0, 0.0}, fac = ctx->bval[f];
+    if (ctx->bkind[f] == 2) {
+      ob[f / 2] = (f & 1) ? -1.0 : 1.0;
+    } else {
+      for (int e = 0; e < 3; ++e) ob[e] = ctx->bdir[f][e];
+      fac *= std::fabs(ob[f / 2]);  // |Omega_b . n|
+    }
+    const double om[3] = {sg * ob[0], sg * ob[1], sg * ob[2]};
+    double total = 0.0;
+    for (int q = 0; q < Lv.mesh.P; ++q) {
+      const auto& V = Lv.mesh.patch[q].v;
+      // om = sum_i lam_i V_i (Cramer's rule)
+      auto det = [](const double* c0, const double* c1, const double* c2) {
+        return c0[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (c0[1] * c2[2] - c0[2] * c2[1]) +
+               c2[0] * (c0[1] * c1[2] - c0[2] * c1[1]);
+      };
+      const double D = det(V[0], V[1], V[2]);
+      const double lam[3] = {det(om, V[1], V[2]) / D, det(V[0], om, V[2]) / D,
+                             det(V[0], V[1], om) / D};
+      const double lmax = std::max({std::fabs(lam[0]), std::fabs(lam[1]), std::fabs(lam[2])});
+      if (std::min({lam[0], lam[1], lam[2]}) < -1e-12 * lmax) continue;
+      int nz = 0, vi = -1;
+      for (int i = 0; i < 3; ++i) {
+        if (std::fabs(lam[i]) <= 1e-12 * lmax) ++nz;
+        else vi = i;
       }
-    if (hits.empty()) return fail(ctx, AMGT_ERR_UNSUPPORTED, "beam direction is no patch vertex");
-    for (int q : hits) {
-      const double om[3] = {sg * ob[0], sg * ob[1], sg * ob[2]};
+      double share = 1.0;
+      if (nz == 1) {
+        share = 0.5;
+      } else if (nz == 2) {
+        // interior angle at vertex vi between the great circles to the others
+        const double* A = V[vi];
+        const double* B = V[(vi + 1) % 3];
+        const double* C = V[(vi + 2) % 3];
+        double tb[3], tc[3];
+        const double ab = A[0] * B[0] + A[1] * B[1] + A[2] * B[2];
+        const double ac = A[0] * C[0] + A[1] * C[1] + A[2] * C[2];
+        for (int e = 0; e < 3; ++e) {
+          tb[e] = B[e] - ab * A[e];
+          tc[e] = C[e] - ac * A[e];
+        }
+        const double cr[3] = {tb[1] * tc[2] - tb[2] * tc[1], tb[2] * tc[0] - tb[0] * tc[2],
+                              tb[0] * tc[1] - tb[1] * tc[0]};
+        const double dt = tb[0] * tc[0] + tb[1] * tc[1] + tb[2] * tc[2];
+        share = std::atan2(std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), dt) /
+                (2.0 * M_PI);
+      }
       double psi[3];
       basis_values(Lv.mesh, q, om, psi);
-      for (int m = 0; m < a; ++m)
-        beam[(size_t)f * nadof + q * a + m] = ctx->bval[f] * psi[m] / (double)hits.size();
+      for (int m = 0; m < a; ++m) beam[(size_t)f * nadof + q * a + m] = fac * share * psi[m];
+      total += share;
     }
+    if (std::fabs(total - 1.0) > 1e-9)
+      return fail(ctx, AMGT_ERR_UNSUPPORTED,
+                  "beam direction: the patch shares around it do not sum to 1");
   }
   return upload(ctx, beam, &Lv.d_beam);
 }
@@ -482,6 +537,13 @@ int build(amgt_ctx* ctx) {
   ctx->moments_bytes = 0;
   ctx->d_bf16 = nullptr;
   ctx->bf16_bytes = 0;
+  // every scratch buffer went with ctx->mem
+  ctx->d_split = nullptr;
+  ctx->split_bytes = 0;
+  ctx->d_tc3 = nullptr;
+  ctx->tc3_bytes = 0;
+  ctx->d_grad = nullptr;
+  ctx->grad_bytes = 0;
 
   const int dim = ctx->dim;
   double h[3] = {1, 1, 1};
@@ -496,6 +558,10 @@ int build(amgt_ctx* ctx) {
   g.nx = (int)ctx->ncell[0];
   g.ny = (int)ctx->ncell[1];
   g.nz = dim == 3 ? (int)ctx->ncell[2] : 1;
+  for (int e = 0; e < 3; ++e) {
+    g.lo[e] = ctx->lo[e];
+    g.h[e] = h[e];
+  }
   g.C = g.nx * g.ny * g.nz;
   g.nsdof = (long long)g.C * s;
   const int hs = s / 2;
@@ -519,18 +585,22 @@ int build(amgt_ctx* ctx) {
   const int C = g.C;
   ctx->C = C;
 
-  // materials: distinct (sigma_t, sigma_s) pairs
-  std::map<std::pair<double, double>, int> mm;
+  // materials: distinct (sigma_t, sigma_s, moment shape) triples
+  std::map<std::tuple<double, double, int>, int> mm;
   ctx->mat.assign(C, 0);
   ctx->mat_st.clear();
   ctx->mat_ss.clear();
+  ctx->mat_f.clear();
+  const int nf = ctx->nf;
   for (int c = 0; c < C; ++c) {
-    auto key = std::make_pair(ctx->sigma_t[c], ctx->sigma_s[c]);
+    const int sh = nf > 1 ? ctx->fid[c] : 0;
+    auto key = std::make_tuple(ctx->sigma_t[c], ctx->sigma_s[c], sh);
     auto it = mm.find(key);
     if (it == mm.end()) {
       it = mm.emplace(key, (int)ctx->mat_st.size()).first;
-      ctx->mat_st.push_back(key.first);
-      ctx->mat_ss.push_back(key.second);
+      ctx->mat_st.push_back(ctx->sigma_t[c]);
+      ctx->mat_ss.push_back(ctx->sigma_s[c]);
+      ctx->mat_f.push_back(sh);
     }
     ctx->mat[c] = it->second;
   }
@@ -560,24 +630,39 @@ int build(amgt_ctx* ctx) {
     const int nadof = Lv.mesh.nadof();
     Lv.Nr = k < (int)ctx->Nr.size() ? std::min(ctx->Nr[k], ctx->N) : ctx->N;
     Lv.nmom = nmoments(Lv.Nr);
-    Lv.dense = nadof < 2 * Lv.nmom;
+    // dense S_f needs one moment shape for every cell
+    Lv.dense = nadof < 2 * Lv.nmom && nf == 1;
     const int nm = Lv.nmom;
     std::vector<double> X = x_table(Lv.mesh, Lv.Nr);
-    std::vector<double> F(nm);
-    for (int n = 0; n <= Lv.Nr; ++n)
-      for (int o = -n; o <= n; ++o) F[n * n + n + o] = ctx->fmom[n];
-    std::vector<double> XFt((size_t)nm * nadof);
-    for (int j = 0; j < nadof; ++j)
-      for (int kk = 0; kk < nm; ++kk) XFt[(size_t)kk * nadof + j] = F[kk] * X[(size_t)j * nm + kk];
-    std::vector<double> Sqq((size_t)P * a * a, 0.0);
-    for (int q = 0; q < P; ++q)
-      for (int m = 0; m < a; ++m)
-        for (int d = 0; d < a; ++d) {
-          double acc = 0.0;
-          for (int kk = 0; kk < nm; ++kk)
-            acc += X[(size_t)(q * a + m) * nm + kk] * F[kk] * X[(size_t)(q * a + d) * nm + kk];
-          Sqq[(q * a + m) * a + d] = acc;
-        }
+    // f of each shape per moment index (degree n of index k: n^2 <= k < (n+1)^2)
+    std::vector<double> Fall((size_t)nf * nm);
+    for (int sh = 0; sh < nf; ++sh)
+      for (int n = 0; n <= Lv.Nr; ++n)
+        for (int o = -n; o <= n; ++o)
+          Fall[(size_t)sh * nm + n * n + n + o] = ctx->ftab[(size_t)sh * (ctx->N + 1) + n];
+    const std::vector<double> F(Fall.begin(), Fall.begin() + nm);  // shape 0
+    std::vector<double> XFt((size_t)nf * nm * nadof);
+    for (int sh = 0; sh < nf; ++sh)
+      for (int j = 0; j < nadof; ++j)
+        for (int kk = 0; kk < nm; ++kk)
+          XFt[((size_t)sh * nm + kk) * nadof + j] = Fall[(size_t)sh * nm + kk] * X[(size_t)j * nm + kk];
+    std::vector<double> Sqq((size_t)nf * P * a * a, 0.0);
+    for (int sh = 0; sh < nf; ++sh)
+      for (int q = 0; q < P; ++q)
+        for (int m = 0; m < a; ++m)
+          for (int d = 0; d < a; ++d) {
+            double acc = 0.0;
+            for (int kk = 0; kk < nm; ++kk)
+              acc += X[(size_t)(q * a + m) * nm + kk] * Fall[(size_t)sh * nm + kk] *
+                     X[(size_t)(q * a + d) * nm + kk];
+            Sqq[(((size_t)sh * P + q) * a + m) * a + d] = acc;
+          }
+    std::vector<double> Xt;
+    if (nf > 1) {
+      Xt.resize((size_t)nm * nadof);
+      for (int j = 0; j < nadof; ++j)
+        for (int kk = 0; kk < nm; ++kk) Xt[(size_t)kk * nadof + j] = X[(size_t)j * nm + kk];
+    }
     // per-patch blocks
     std::vector<double> K0((size_t)P * sa * sa, 0.0), B((size_t)P * sa * sa, 0.0);
     Lv.pdir.resize(P);
@@ -616,15 +701,17 @@ int build(amgt_ctx* ctx) {
     if (singular) return fail(ctx, AMGT_ERR_ARG, "singular transport block (sigma_t <= 0?)");
     if (k == nl - 1) {
       Ginv.resize(nblk);
-      std::vector<double> NSq((size_t)P * sa * sa, 0.0);  // kron(N, S_qq) per patch
-      for (int q = 0; q < P; ++q)
-        kron_add(s, a, q1.N.data(), &Sqq[(size_t)q * a * a], 1.0, &NSq[(size_t)q * sa * sa]);
+      // kron(N, S_qq) per shape and patch
+      std::vector<double> NSq((size_t)nf * P * sa * sa, 0.0);
+      for (int sq = 0; sq < nf * P; ++sq)
+        kron_add(s, a, q1.N.data(), &Sqq[(size_t)sq * a * a], 1.0, &NSq[(size_t)sq * sa * sa]);
       parallel_for((long long)ctx->nmat * P, [&](long long i) {
         const int mt = (int)(i / P), q = (int)(i % P);
+        const double* nsq = &NSq[((size_t)ctx->mat_f[mt] * P + q) * sa * sa];
         std::vector<double> blk(sa * sa);
         for (int e = 0; e < sa * sa; ++e)
           blk[e] = K0[(size_t)q * sa * sa + e] + ctx->mat_st[mt] * B[(size_t)q * sa * sa + e] -
-                   ctx->mat_ss[mt] * NSq[(size_t)q * sa * sa + e];
+                   ctx->mat_ss[mt] * nsq[e];
         if (!invert(sa, blk.data(), &Ginv[((size_t)mt * P + q) * sa * sa])) singular = 1;
       });
       if (singular) return fail(ctx, AMGT_ERR_ARG, "singular Gauss-Seidel block");
@@ -649,9 +736,12 @@ int build(amgt_ctx* ctx) {
     TRY(upload(ctx, Lv.octant, &Lv.d_octant));
     TRY(upload(ctx, Lv.dir_begin, &Lv.d_dbeg));
     TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
-    TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64));
-    TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32));
-    if (k == nl - 1) TRY(build_gs_blocks(ctx, Lv, K0, B, X, F));
+    const std::vector<double> fdeg = nf > 1 ? Fall : std::vector<double>{};
+    TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64, Xt, fdeg));
+    TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32, Xt, fdeg));
+    // the direction-blocked Gauss-Seidel tables assume one moment shape; with
+    // several, the per-patch kernel (shape-indexed tables) runs
+    if (k == nl - 1 && nf == 1) TRY(build_gs_blocks(ctx, Lv, K0, B, X, F));
   }
   for (int k = 0; k + 1 < nl; ++k) {
     Level& F = ctx->lv[k];
@@ -686,6 +776,7 @@ int build(amgt_ctx* ctx) {
   }
   // cell data and source
   TRY(upload(ctx, ctx->mat, &ctx->d_mat));
+  if (nf > 1) TRY(upload(ctx, ctx->fid, &ctx->d_fid));
   TRY(upload(ctx, ctx->sigma_t, &ctx->d_sigt));
   TRY(upload(ctx, ctx->sigma_s, &ctx->d_sigs));
   TRY(upload(ctx, ctx->sigma_t, &ctx->d_sigt32));
@@ -695,6 +786,8 @@ int build(amgt_ctx* ctx) {
   TRY(upload(ctx, q, &ctx->d_q));
   TRY(upload(ctx, std::vector<int>(ctx->bkind, ctx->bkind + 6), &ctx->d_bkind));
   TRY(upload(ctx, std::vector<double>(ctx->bval, ctx->bval + 6), &ctx->d_bval));
+  TRY(upload(ctx, std::vector<double>(&ctx->brange[0][0], &ctx->brange[0][0] + 24),
+             &ctx->d_brange));
   TRY(upload(ctx, q1.N, &ctx->d_Nm32));
   TRY(upload(ctx, q1.mu, &ctx->d_mu));
   TRY(upload(ctx, q1.mf, &ctx->d_mf));
@@ -707,6 +800,10 @@ int build(amgt_ctx* ctx) {
   ctx->ws64.assign(nl, {});
   ctx->ws32.assign(nl, {});
   CK(noalloc_moment_address(ctx->device, &ctx->noalloc_moments));
+  // the moment contraction's kernels loaded now, not at a first launch inside
+  // the allocation-free entry point (the row Gauss-Seidel kernel is resolved
+  // by its occupancy query in build_gs_rows)
+  CK(preload_gemm());
   TRY(build_gs_rows(ctx));
   ctx->dirty = false;
   return AMGT_OK;
@@ -842,7 +939,7 @@ SplitPlan split_plan(int K) {
 
 bool split_applies(amgt_ctx* ctx, int k) {
   const int n = ctx->lv[k].nadof();
-  return tc_available() && n >= 64 && n % 8 == 0 && split_plan(n).bits > 0 &&
+  return ctx->nf == 1 && tc_available() && n >= 64 && n % 8 == 0 && split_plan(n).bits > 0 &&
          (ctx->geom.s == 4 || ctx->geom.s == 8);
 }
 
@@ -915,7 +1012,8 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
   for (long long r0 = 0; r0 < M; r0 += Mc) {
     const long long rows = std::min(Mc, M - r0);
     {
-      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX);
+      // read x (twice: row maximum, digits), write nsl BF16 digit slices
+      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX, (16.0 + 2.0 * sp.nsl) * rows * n);
       launch_split_rows(rows, n, S, true, x + r0 * n, ctx->d_sigs + r0 / S, ctx->geom.Nmass,
                         sp.nsl, sp.bits, mu, xs, rows * n, ctx->stream);
     }
@@ -923,7 +1021,7 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
       for (const SplitGemm& gm : pass.gemms) {
         int rc;
         {
-          KernelTimer kt(ctx, AMGT_KT_SPLIT_TC);
+          KernelTimer kt(ctx, AMGT_KT_SPLIT_TC, 2.0 * rows * n * n);
           rc = launch_tc_gemm((int)rows, n, n, xs + (size_t)gm.i * rows * n,
                               L.Sf_split + (size_t)gm.j * n * n, P, nullptr, gm.beta,
                               ctx->d_status, ctx->stream);
@@ -932,7 +1030,8 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
           return fail(ctx, AMGT_ERR_UNSUPPORTED,
                       "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
       }
-      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX);
+      // read the FP32 products, read and write the FP64 result
+      KernelTimer kt(ctx, AMGT_KT_SPLIT_AUX, 20.0 * rows * n);
       launch_split_flush(rows, n, P, mu, L.Sf_nu, alpha * std::ldexp(1.0, -sp.bits * (pass.d + 2)),
                          y + r0 * n, ctx->stream);
     }
@@ -941,11 +1040,93 @@ int scatter_split64(amgt_ctx* ctx, int k, const double* x, double* y, double alp
   return AMGT_OK;
 }
 
-// y = alpha * S x + beta * y + add  (add may be null).  For T = double, `tc`
-// selects the split form (where it applies; else the FP64 SIMT contraction).
+// the FP16 three-product form applies on level k (tensor cores present,
+// K = Nadof >= 64 and a multiple of 8, Q1 cells)
+bool tc3_applies(amgt_ctx* ctx, int k) {
+  const int n = ctx->lv[k].nadof();
+  return ctx->nf == 1 && tc_available() && n >= 64 && n % 8 == 0 &&
+         (ctx->geom.s == 4 || ctx->geom.s == 8);
+}
+
+// the rows of S_f cut into FP16 [hi | hi | lo] (kernels_tc3.cu)
+int ensure_tc3(amgt_ctx* ctx, int k) {
+  Level& L = ctx->lv[k];
+  if (L.Sf_tc3) return AMGT_OK;
+  TRY(ensure_dense(ctx, k));
+  const int n = L.nadof();
+  __half* bt;
+  TRY(dalloc(ctx, (size_t)n * 3 * n, &bt));
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(ctx->d_status + 8);
+  double sinv = 0.0;
+  CK(tc3_split_sf(n, L.d64.Sf, mx, bt, &sinv, ctx->stream));
+  L.Sf_tc3 = bt;
+  L.tc3_sinv = sinv;
+  return AMGT_OK;
+}
+
+// y = alpha S x + beta y + add in FP32 from FP16 tensor-core products: each
+// row of alpha sig_s N x is scaled by a power of two and cut into hi + lo
+// FP16 parts, and hi S_hi + lo S_hi + hi S_lo run as one GEMM over the
+// concatenated inner dimension 3 Nadof, the epilogue undoing the row scales.
+// Rows are processed in passes that keep the FP16 operand within ~4 GB.
+int scatter_tc3(amgt_ctx* ctx, int k, const float* x, float* y, double alpha, double beta,
+                const float* add) {
+  Level& L = ctx->lv[k];
+  const long long M = L.nsdof;
+  const int n = L.nadof();
+  const int S = ctx->geom.s;
+  TRY(ensure_tc3(ctx, k));
+  long long Mc = (long long)(((size_t)4 << 30) / ((size_t)6 * n)) / 128 * 128;
+  if (Mc < 128) Mc = 128;
+  if (Mc > M) Mc = M;
+  const size_t a_bytes = ((size_t)Mc * 3 * n * 2 + 255) / 256 * 256;
+  const size_t need = a_bytes + (size_t)Mc * 4;
+  if (ctx->tc3_bytes < need) {
+    unsigned char* p;
+    TRY(dalloc(ctx, need, &p));
+    ctx->d_tc3 = p;
+    ctx->tc3_bytes = need;
+  }
+  auto* base = static_cast<unsigned char*>(ctx->d_tc3);
+  auto* A = reinterpret_cast<__half*>(base);
+  auto* rs = reinterpret_cast<float*>(base + a_bytes);
+  for (long long r0 = 0; r0 < M; r0 += Mc) {
+    const long long rows = std::min(Mc, M - r0);
+    {
+      // read FP32 x, write three FP16 operand parts
+      KernelTimer kt(ctx, AMGT_KT_TC3_PREP, 10.0 * rows * n);
+      launch_tc3_prep(rows / S, S, n, x + r0 * n, ctx->d_sigs32 + r0 / S, ctx->d_Nm32,
+                      (float)alpha, (float)L.tc3_sinv, A, rs, ctx->stream);
+    }
+    int rc;
+    {
+      KernelTimer kt(ctx, AMGT_KT_TC3, 2.0 * rows * n * 3.0 * n);
+      rc = launch_tc_gemm_ex((int)rows, n, 3 * n, A, L.Sf_tc3, true, y + r0 * n,
+                             add ? add + r0 * n : nullptr, (float)beta, rs, ctx->d_status,
+                             ctx->stream);
+    }
+    if (rc != 0)
+      return fail(ctx, AMGT_ERR_UNSUPPORTED,
+                  "tensor-core GEMM launch failed (code " + std::to_string(rc) + ")");
+  }
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// y = alpha * S x + beta * y + add  (add may be null).  path: 0 the SIMT
+// contraction in T; 1 for T = float the BF16 tensor-core form, for T = double
+// the split form (where it applies; else the FP64 SIMT contraction); 2 (T =
+// float) the FP32-accurate FP16 three-product form where it applies.
 template <class T>
-int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, double beta,
+int scatter_impl(amgt_ctx* ctx, int k, int path, const T* x, T* y, double alpha, double beta,
                  const T* add) {
+  // several moment shapes: the moment form, each cell's moments scaled by its
+  // shape (the dense and tensor-core forms assume one S_f)
+  if (ctx->nf > 1) path = 0;
+  bool tc = path == 1;
+  if constexpr (sizeof(T) == 4) {
+    if (path == 2 && tc3_applies(ctx, k)) return scatter_tc3(ctx, k, x, y, alpha, beta, add);
+  }
   Level& L = ctx->lv[k];
   const long long M = L.nsdof;
   const int n = L.nadof();
@@ -958,8 +1139,9 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
   for (int i = 0; i < epi.s * epi.s; ++i) epi.Nm[i] = ctx->geom.Nmass[i];
   epi.sig = ctx->d_sigs;
   epi.sig32 = ctx->d_sigs32;
-  // the tensor-core path needs K = Nadof >= 64 (one K step of the tile)
-  if (tc && n < 64) tc = false;
+  // the tensor-core path needs K = Nadof >= 64 (one K step of the tile) and a
+  // multiple of 8 (16-byte TMA rows); other levels take the SIMT contraction
+  if (tc && (n < 64 || n % 8 != 0)) tc = false;
   if (tc) {
     if constexpr (sizeof(T) == 4) {
       if (!tc_available()) return fail(ctx, AMGT_ERR_UNSUPPORTED, "tensor-core path unavailable");
@@ -974,13 +1156,13 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
       auto* xb = static_cast<__nv_bfloat16*>(ctx->d_bf16);
       // sigma_s and the spatial mass commute with S: applied while rounding to BF16
       {
-        KernelTimer kt(ctx, AMGT_KT_SCATTER_PREP);
+        KernelTimer kt(ctx, AMGT_KT_SCATTER_PREP, 6.0 * M * n);
         launch_tc_prep(M / ctx->geom.s, ctx->geom.s, n, x, ctx->d_sigs32, ctx->d_Nm32,
                        (float)alpha, xb, ctx->stream);
       }
       int rc;
       {
-        KernelTimer kt(ctx, AMGT_KT_SCATTER_TC);
+        KernelTimer kt(ctx, AMGT_KT_SCATTER_TC, 2.0 * M * n * n);
         rc = launch_tc_gemm((int)M, n, n, xb, L.Sf_bf16, y, add, (float)beta, ctx->d_status,
                             ctx->stream);
       }
@@ -996,7 +1178,8 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
   if (L.dense) {
     TRY(ensure_dense(ctx, k));
     const T* Sf = store<T>(L).Sf;
-    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32);
+    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32,
+                   2.0 * M * n * n);
     launch_gemm<T>((int)M, n, n, x, n, Sf, n, y, n, epi, ctx->stream);
   } else {
     void* mp;
@@ -1004,9 +1187,16 @@ int scatter_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y, double alpha, 
     T* Phi = static_cast<T*>(mp);
     GemmEpi e0{};
     e0.mode = 0;
-    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32);
+    KernelTimer kt(ctx, sizeof(T) == 8 ? AMGT_KT_SCATTER_F64 : AMGT_KT_SCATTER_F32,
+                   4.0 * M * n * L.nmom);
     launch_gemm<T>((int)M, L.nmom, n, x, n, store<T>(L).X, L.nmom, Phi, L.nmom, e0, ctx->stream);
-    launch_gemm<T>((int)M, n, L.nmom, Phi, L.nmom, store<T>(L).XFt, n, y, n, epi, ctx->stream);
+    if (ctx->nf > 1) {
+      launch_scale_moments<T>(M, ctx->geom.s, L.nmom, ctx->d_fid, store<T>(L).fdeg, Phi,
+                              ctx->stream);
+      launch_gemm<T>((int)M, n, L.nmom, Phi, L.nmom, store<T>(L).Xt, n, y, n, epi, ctx->stream);
+    } else {
+      launch_gemm<T>((int)M, n, L.nmom, Phi, L.nmom, store<T>(L).XFt, n, y, n, epi, ctx->stream);
+    }
   }
   CK(cudaGetLastError());
   return AMGT_OK;
@@ -1016,10 +1206,11 @@ template <class T>
 int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   const Level& L = ctx->lv[k];
   const int chunk = sizeof(T) == 4 ? L.chunk_f32 : L.chunk_f64;
-  KernelTimer kt(ctx, AMGT_KT_SWEEP);
+  // read b, write psi
+  KernelTimer kt(ctx, AMGT_KT_SWEEP, 2.0 * sizeof(T) * L.nsdof * L.nadof());
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                   schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, chunk, ctx->sweep_stages,
-                  ctx->sweep_kernel, ctx->d_status, ctx->stream);
+                  ctx->sweep_kernel, ctx->d_status, ctx->test_sweep_hold, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1027,7 +1218,9 @@ int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
 template <class T>
 int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
   const Level& L = ctx->lv[k];
-  KernelTimer kt(ctx, AMGT_KT_APPLY_L);
+  // read x, write y (and read y when it accumulates)
+  KernelTimer kt(ctx, AMGT_KT_APPLY_L,
+                 (beta != T(0) ? 3.0 : 2.0) * sizeof(T) * L.nsdof * L.nadof());
   launch_apply_L<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx), alpha,
                     beta, x, y, ctx->stream);
   CK(cudaGetLastError());
@@ -1036,8 +1229,8 @@ int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
 
 // y = (L - S) x
 template <class T>
-int applyA_impl(amgt_ctx* ctx, int k, bool tc, const T* x, T* y) {
-  TRY(scatter_impl<T>(ctx, k, tc, x, y, -1.0, 0.0, nullptr));
+int applyA_impl(amgt_ctx* ctx, int k, int path, const T* x, T* y) {
+  TRY(scatter_impl<T>(ctx, k, path, x, y, -1.0, 0.0, nullptr));
   return applyL_impl<T>(ctx, k, T(1), T(1), x, y);
 }
 
@@ -1045,7 +1238,8 @@ template <class T>
 int source_impl(amgt_ctx* ctx, int k, T* f) {
   const Level& L = ctx->lv[k];
   launch_source<T>(level_geom(ctx, k), store<T>(L).w, store<T>(L).Aw, L.d_octant, ctx->d_q,
-                   ctx->d_bval, ctx->d_bkind, L.d_beam, ctx->d_mu, ctx->d_mf, f, ctx->stream);
+                   ctx->d_bval, ctx->d_bkind, L.d_beam, ctx->d_brange, ctx->d_mu, ctx->d_mf, f,
+                   ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1087,7 +1281,7 @@ int smooth_impl(amgt_ctx* ctx, int k, bool tc, int nu, const T* f, T* phi, bool 
 }
 
 template <class T>
-int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom);
+int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool timed = true);
 
 template <class T>
 int coarse_gs_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
@@ -1109,18 +1303,26 @@ int coarse_gs_noalloc_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
                 "allocation-free entry point holds at most " +
                     std::to_string(noalloc_moment_bytes()) + " bytes");
   if (!ctx->noalloc_moments) return fail(ctx, AMGT_ERR_STATE, "fixed scratch not set up");
-  return coarse_gs_run<T>(ctx, sweeps, f, phi, static_cast<T*>(ctx->noalloc_moments));
+  return coarse_gs_run<T>(ctx, sweeps, f, phi, static_cast<T*>(ctx->noalloc_moments), false);
 }
 
 template <class T>
-int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom) {
+int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool timed) {
   const int k = (int)ctx->lv.size() - 1;
   const Level& L = ctx->lv[k];
   GemmEpi e0{};
   e0.mode = 0;
   launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
                  L.nmom, e0, ctx->stream);
-  KernelTimer kt(ctx, AMGT_KT_COARSE_GS);
+  // sequential per-patch form of the block solves, per (cell, patch, sweep):
+  // moment source s a nm, self-scatter s a a, mass mixing s a s, block solve
+  // (s a)^2, moment update s nm a multiply-adds
+  const double gs_fma = (double)L.nsdof / ctx->geom.s * L.mesh.P * sweeps *
+                        (2.0 * ctx->geom.s * L.mesh.a * L.nmom +
+                         (double)ctx->geom.s * L.mesh.a * L.mesh.a +
+                         (double)ctx->geom.s * L.mesh.a * ctx->geom.s +
+                         (double)ctx->geom.s * L.mesh.a * ctx->geom.s * L.mesh.a);
+  KernelTimer kt(ctx, AMGT_KT_COARSE_GS, 2.0 * gs_fma, timed);
   // row-pipelined kernel: the default where available
   if (store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6)) {
     const int pi = sizeof(T) == 4 ? 0 : 1;
@@ -1187,6 +1389,21 @@ int vcycle_impl(amgt_ctx* ctx, int k, bool tc, const T* f, T* phi) {
   const Level& L = ctx->lv[k];
   const size_t bytes = (size_t)L.nsdof * L.nadof() * sizeof(T);
   if (k == (int)ctx->lv.size() - 1) {
+    if constexpr (sizeof(T) == 4) {
+      if (ctx->coarse_f64) {
+        // the coarsest solve in FP64 inside the FP32 cycle
+        const long long n = L.nsdof * L.nadof();
+        double *f64, *phi64;
+        TRY(wsvec<double>(ctx, k, 1, &f64));
+        TRY(wsvec<double>(ctx, k, 2, &phi64));
+        launch_convert<float, double>(n, f, f64, ctx->stream);
+        CK(cudaMemsetAsync(phi64, 0, (size_t)n * sizeof(double), ctx->stream));
+        TRY(coarse_gs_impl<double>(ctx, ctx->coarse_sweeps, f64, phi64));
+        launch_convert<double, float>(n, phi64, phi, ctx->stream);
+        CK(cudaGetLastError());
+        return AMGT_OK;
+      }
+    }
     CK(cudaMemsetAsync(phi, 0, bytes, ctx->stream));
     return coarse_gs_impl<T>(ctx, ctx->coarse_sweeps, f, phi);
   }
@@ -1611,7 +1828,8 @@ int amgt_query_launches(int64_t* count) {
   return AMGT_OK;
 }
 
-int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches) {
+int amgt_query_kernel_stats(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches,
+                            double* work) {
   if (!ctx) return AMGT_ERR_ARG;
   if (kernel < 0 || kernel >= AMGT_KT_COUNT) return fail(ctx, AMGT_ERR_ARG, "unknown kernel id");
   for (auto& p : ctx->kt_pending) {
@@ -1620,17 +1838,24 @@ int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int
     CK(cudaEventElapsedTime(&t, p.a, p.b));
     ctx->kt_ms[p.id] += t;
     ctx->kt_n[p.id] += 1;
+    ctx->kt_work[p.id] += p.work;
     ctx->kt_free.push_back(p.a);
     ctx->kt_free.push_back(p.b);
   }
   ctx->kt_pending.clear();
   if (ms) *ms = ctx->kt_ms[kernel];
   if (launches) *launches = ctx->kt_n[kernel];
+  if (work) *work = ctx->kt_work[kernel];
   if (reset) {
     ctx->kt_ms[kernel] = 0.0;
     ctx->kt_n[kernel] = 0;
+    ctx->kt_work[kernel] = 0.0;
   }
   return AMGT_OK;
+}
+
+int amgt_query_kernel_time(amgt_ctx* ctx, int kernel, int reset, double* ms, int64_t* launches) {
+  return amgt_query_kernel_stats(ctx, kernel, reset, ms, launches, nullptr);
 }
 
 int amgt_sync(amgt_ctx* ctx) {
@@ -1670,19 +1895,34 @@ int amgt_set_mesh_cartesian(amgt_ctx* ctx, int dim, const int64_t ncell[3], cons
   return AMGT_OK;
 }
 
-int amgt_set_materials(amgt_ctx* ctx, const double* st, const double* ss, int N,
-                       const double* fmom) {
+int amgt_set_materials(amgt_ctx* ctx, const double* st, const double* ss, const int32_t* mat_id,
+                       int nmat, int N, const double* f) {
   if (!ctx) return AMGT_ERR_ARG;
   if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "set the mesh first");
-  if (!st || !ss || !fmom || N < 0 || N > 128) return fail(ctx, AMGT_ERR_ARG, "bad materials");
+  if (!st || !ss || !f || N < 0 || N > 128 || nmat < 1 || (!mat_id && nmat != 1))
+    return fail(ctx, AMGT_ERR_ARG,
+                "bad materials: need sigma_t, sigma_s, f, 0 <= N <= 128, nmat >= 1 (1 without "
+                "mat_id)");
   const int64_t C = ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2];
   for (int64_t c = 0; c < C; ++c) {
     if (!(st[c] > 0.0) || !(ss[c] >= 0.0) || !std::isfinite(st[c]) || !std::isfinite(ss[c]))
       return fail(ctx, AMGT_ERR_ARG, "need sigma_t > 0 and sigma_s >= 0, finite");
+    if (mat_id && (mat_id[c] < 0 || mat_id[c] >= nmat))
+      return fail(ctx, AMGT_ERR_ARG, "mat_id out of range");
   }
+  for (int64_t i = 0; i < (int64_t)nmat * (N + 1); ++i)
+    if (!std::isfinite(f[i])) return fail(ctx, AMGT_ERR_ARG, "moments are not finite");
+  for (int m = 0; m < nmat; ++m)
+    if (std::fabs(f[(size_t)m * (N + 1)] - 1.0) > 1e-12)
+      return fail(ctx, AMGT_ERR_ARG, "f[m][0] must be 1 (sigma_s is the n = 0 moment)");
   ctx->sigma_t.assign(st, st + C);
   ctx->sigma_s.assign(ss, ss + C);
-  ctx->fmom.assign(fmom, fmom + N + 1);
+  ctx->ftab.assign(f, f + (size_t)nmat * (N + 1));
+  ctx->nf = nmat;
+  if (nmat > 1)
+    ctx->fid.assign(mat_id, mat_id + C);
+  else
+    ctx->fid.clear();
   ctx->N = N;
   ctx->dirty = true;
   return AMGT_OK;
@@ -1733,9 +1973,13 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q) {
   if (ctx->dim == 0) return fail(ctx, AMGT_ERR_STATE, "set the mesh first");
   if (!q) return fail(ctx, AMGT_ERR_ARG, "null source");
   const int64_t C = ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2];
+  for (int64_t c = 0; c < C; ++c)
+    if (!std::isfinite(q[c])) return fail(ctx, AMGT_ERR_ARG, "source is not finite");
   ctx->qsrc.assign(q, q + C);
   if (!ctx->dirty && ctx->d_q) {
-    CK(cudaMemcpy(ctx->d_q, ctx->qsrc.data(), sizeof(double) * C, cudaMemcpyHostToDevice));
+    // ordered on the context's stream; returns once the host data is staged
+    CK(cudaMemcpyAsync(ctx->d_q, ctx->qsrc.data(), sizeof(double) * C, cudaMemcpyHostToDevice,
+                       ctx->stream));
   } else {
     ctx->dirty = true;
   }
@@ -1744,10 +1988,26 @@ int amgt_set_source_iso(amgt_ctx* ctx, const double* q) {
 
 int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params) {
   if (!ctx) return AMGT_ERR_ARG;
-  if (face < 0 || face >= 6 || kind < 0 || kind > 2)
+  if (face < 0 || face >= 6 || kind < 0 || kind > 3)
     return fail(ctx, AMGT_ERR_ARG,
-                "face 0..5, kind 0 (vacuum), 1 (isotropic inflow) or 2 (pencil beam)");
-  if (kind != 0 && !params) return fail(ctx, AMGT_ERR_ARG, "inflow needs params[0]");
+                "face 0..5, kind 0 (vacuum), 1 (isotropic inflow), 2 (normal pencil beam) or 3 "
+                "(pencil beam of any inward direction over part of the face)");
+  if (kind != 0 && !params) return fail(ctx, AMGT_ERR_ARG, "inflow needs params");
+  const int np = kind == 3 ? 8 : (kind != 0 ? 1 : 0);
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, AMGT_ERR_ARG, "boundary value is not finite");
+  if (kind == 3) {
+    const double* d = params + 1;
+    const double nrm = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (!(nrm > 0.0)) return fail(ctx, AMGT_ERR_ARG, "beam direction is zero");
+    const double nsgn = (face & 1) ? 1.0 : -1.0;  // outward normal along axis face / 2
+    if (!(d[face / 2] / nrm * nsgn < -1e-12))
+      return fail(ctx, AMGT_ERR_ARG, "beam direction must point into the domain");
+    if (!(params[4] < params[5]) || (ctx->dim == 3 && !(params[6] < params[7])))
+      return fail(ctx, AMGT_ERR_ARG, "beam range needs u0 < u1 (and v0 < v1 in 3D)");
+    for (int e = 0; e < 3; ++e) ctx->bdir[face][e] = d[e] / nrm;
+    for (int e = 0; e < 4; ++e) ctx->brange[face][e] = params[4 + e];
+  }
   ctx->bkind[face] = kind;
   ctx->bval[face] = kind != 0 ? params[0] : 0.0;
   ctx->dirty = true;
@@ -1794,7 +2054,9 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
   const Level& L0 = ctx->lv[0];
   const long long n = L0.nsdof * L0.nadof();
   const int C = ctx->geom.C, nm = L0.nmom, N = L0.Nr;
-  if ((int)ctx->fmom.size() < N + 1) return fail(ctx, AMGT_ERR_STATE, "Legendre moments not set");
+  const int nf = ctx->nf;
+  if ((int)ctx->ftab.size() < nf * (ctx->N + 1))
+    return fail(ctx, AMGT_ERR_STATE, "Legendre moments not set");
   const double *p, *l;
   if (device) {
     p = psi;
@@ -1809,7 +2071,7 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
     l = ll;
   }
   // scratch: both moment sets, the outputs, f_n
-  const size_t need = ((size_t)2 * L0.nsdof * nm + 2 * (size_t)C + 2 * (size_t)(N + 1)) * 8;
+  const size_t need = ((size_t)2 * L0.nsdof * nm + 2 * (size_t)C + 2 * (size_t)nf * (N + 1)) * 8;
   if (ctx->grad_bytes < need) {
     double* q;
     TRY(dalloc<double>(ctx, need / 8, &q));
@@ -1821,9 +2083,13 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
   double* dt = PhiL + (size_t)L0.nsdof * nm;
   double* ds = dt + C;
   double* df = ds + C;
-  double* fm = df + (N + 1);
-  CK(cudaMemcpyAsync(fm, ctx->fmom.data(), (size_t)(N + 1) * 8, cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaMemsetAsync(df, 0, (size_t)(N + 1) * 8, ctx->stream));
+  double* fm = df + (size_t)nf * (N + 1);
+  // the shapes at the finest level's order N (= the problem's order)
+  std::vector<double> fl((size_t)nf * (N + 1));
+  for (int m = 0; m < nf; ++m)
+    for (int n2 = 0; n2 <= N; ++n2) fl[(size_t)m * (N + 1) + n2] = ctx->ftab[(size_t)m * (ctx->N + 1) + n2];
+  CK(cudaMemcpyAsync(fm, fl.data(), fl.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemsetAsync(df, 0, (size_t)nf * (N + 1) * 8, ctx->stream));
   GemmEpi e0{};
   e0.mode = 0;
   launch_gemm<double>((int)L0.nsdof, nm, L0.nadof(), p, L0.nadof(), L0.d64.X, nm, PhiP, nm, e0,
@@ -1832,12 +2098,13 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
                       ctx->stream);
   const Geom g = level_geom(ctx, 0);
   launch_grad_sigma_t(g, L0.d64.Mang, p, l, dt, ctx->stream);
-  launch_grad_moments(g, nm, N, PhiP, PhiL, fm, ctx->d_sigs, ds, df, ctx->stream);
+  launch_grad_moments(g, nm, N, PhiP, PhiL, fm, nf > 1 ? ctx->d_fid : nullptr, ctx->d_sigs, ds,
+                      df, ctx->stream);
   CK(cudaGetLastError());
   const cudaMemcpyKind kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CK(cudaMemcpyAsync(dsigma_t, dt, (size_t)C * 8, kind, ctx->stream));
   CK(cudaMemcpyAsync(dsigma_s, ds, (size_t)C * 8, kind, ctx->stream));
-  CK(cudaMemcpyAsync(dfmom, df, (size_t)(N + 1) * 8, kind, ctx->stream));
+  CK(cudaMemcpyAsync(dfmom, df, (size_t)nf * (N + 1) * 8, kind, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return AMGT_OK;
 }
@@ -1882,7 +2149,7 @@ int amgt_autotune(amgt_ctx* ctx, int what, int* choice) {
                     std::to_string(g0.ny) + "x" + std::to_string(g0.nz) + "/" +
                     std::to_string(ctx->basis);
   for (int k = 0; k < nl; ++k) key += "/" + std::to_string(ctx->lv[k].mesh.P) + ":" + std::to_string(ctx->lv[k].nmom);
-  key += "/" + std::to_string(std::min(ctx->nmat, 64));
+  key += "/" + std::to_string(std::min(ctx->nmat, 64)) + "/" + std::to_string(ctx->nf);
   TuneChoice best;
   bool cached = false;
   {
@@ -1987,6 +2254,21 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
     drop_graphs(ctx);
     return AMGT_OK;
   }
+  if (key == AMGT_TUNE_COARSE_F64) {
+    if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "coarse FP64 0 or 1");
+    ctx->coarse_f64 = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_TEST_SWEEP_HOLD) {
+    if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "test sweep hold 0 or 1");
+    ctx->test_sweep_hold = value;
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_F32_SCATTER) {
+    if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "FP32 scatter 0 or 1");
+    ctx->f32_scatter = value;
+    return AMGT_OK;
+  }
   if (key == AMGT_TUNE_FP64_SCATTER) {
     if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "FP64 scatter 0, 1 or 2");
     ctx->fp64_scatter = value;
@@ -2033,10 +2315,19 @@ int amgt_query_sizes(const amgt_ctx* cctx, int level, int64_t* nsdof, int64_t* n
 #define DISPATCH(dtype, CALL64, CALL32)                                            \
   do {                                                                            \
     if ((dtype) == AMGT_F64 || (dtype) == AMGT_F64_SPLIT) return CALL64;          \
-    if ((dtype) == AMGT_F32 || (dtype) == AMGT_F32_BF16TC) return CALL32;         \
+    if ((dtype) == AMGT_F32 || (dtype) == AMGT_F32_BF16TC || (dtype) == AMGT_F32_TC3) \
+      return CALL32;                                                              \
     return fail(ctx, AMGT_ERR_ARG,                                                \
-                "dtype must be AMGT_F64, AMGT_F64_SPLIT, AMGT_F32 or AMGT_F32_BF16TC"); \
+                "dtype must be AMGT_F64, AMGT_F64_SPLIT, AMGT_F32, AMGT_F32_BF16TC or " \
+                "AMGT_F32_TC3");                                                  \
   } while (0)
+
+namespace {
+// scatter path of an FP32 dtype (see scatter_impl)
+int f32_path(int dtype) {
+  return dtype == AMGT_F32_BF16TC ? 1 : dtype == AMGT_F32_TC3 ? 2 : 0;
+}
+}  // namespace
 
 int amgt_op_source(amgt_ctx* ctx, int level, int dtype, void* f) {
   if (!ctx) return AMGT_ERR_ARG;
@@ -2065,7 +2356,7 @@ int amgt_op_scatter(amgt_ctx* ctx, int level, int dtype, const void* x, void* y)
   TRY(check_level(ctx, level));
   DISPATCH(dtype,
            scatter_impl<double>(ctx, level, dtype == AMGT_F64_SPLIT, (const double*)x, (double*)y, 1.0, 0.0, nullptr),
-           scatter_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y,
+           scatter_impl<float>(ctx, level, f32_path(dtype), (const float*)x, (float*)y,
                                1.0, 0.0, nullptr));
 }
 
@@ -2073,7 +2364,7 @@ int amgt_op_apply_A(amgt_ctx* ctx, int level, int dtype, const void* x, void* y)
   if (!ctx) return AMGT_ERR_ARG;
   TRY(check_level(ctx, level));
   DISPATCH(dtype, applyA_impl<double>(ctx, level, dtype == AMGT_F64_SPLIT, (const double*)x, (double*)y),
-           applyA_impl<float>(ctx, level, dtype == AMGT_F32_BF16TC, (const float*)x, (float*)y));
+           applyA_impl<float>(ctx, level, f32_path(dtype), (const float*)x, (float*)y));
 }
 
 int amgt_op_restrict(amgt_ctx* ctx, int level, int dtype, const void* rf, void* rc) {
@@ -2206,9 +2497,11 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     if (bnorm == 0.0) {
       CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
     }
-    // the inner operator keeps the FP32 contraction (its rounding sets how far
-    // each inner solve can go); the preconditioner's scatters use BF16 tensor cores
-    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, false, xx, yy); };
+    // the inner operator keeps FP32 accuracy (its rounding sets how far each
+    // inner solve can go): the FP16 three-product tensor-core form, or the SIMT
+    // FP32 contraction; the preconditioner's scatters use BF16 tensor cores
+    const int a32_path = ctx->f32_scatter == 1 ? 0 : 2;
+    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, a32_path, xx, yy); };
     auto M32 = [&](const float* v, float* z) -> int {
       if (prec == AMGT_PREC_SWEEP) return sweep_impl<float>(ctx, 0, v, z);
       if (prec == AMGT_PREC_MG)

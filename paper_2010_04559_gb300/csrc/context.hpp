@@ -31,6 +31,8 @@ struct LevelDevStore {
   T *K0 = nullptr, *B = nullptr, *Kinv = nullptr, *Aax = nullptr, *Ginv = nullptr, *X = nullptr,
     *XFt = nullptr, *Sqq = nullptr, *w = nullptr, *Aw = nullptr, *Sf = nullptr, *tblk = nullptr,
     *TinvT = nullptr, *SLD = nullptr, *Mang = nullptr;
+  // several moment shapes: X^T without f, and f of each shape per moment index
+  T *Xt = nullptr, *fdeg = nullptr;
 };
 
 struct Level {
@@ -58,6 +60,10 @@ struct Level {
   // FP64 scatter in split form: the rows of S_f cut into BF16 digit slices
   __nv_bfloat16* Sf_split = nullptr;  // [nsl][n][n]
   double* Sf_nu = nullptr;            // [n] row scales (powers of two)
+  // FP32-accurate scatter on FP16 tensor cores: [S_hi | S_hi | S_lo] rows of
+  // S_f scaled by 2^e, and the inverse scale 2^-e
+  __half* Sf_tc3 = nullptr;  // [n][3n]
+  double tc3_sinv = 0.0;
   int *d_pdir = nullptr, *d_octant = nullptr, *d_dbeg = nullptr, *d_dend = nullptr;
   // pencil-beam inflow weights [2 dim][nadof] (null without a beam face)
   double* d_beam = nullptr;
@@ -85,11 +91,18 @@ struct amgt_ctx {
   int dim = 0;
   int64_t ncell[3] = {1, 1, 1};
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-  std::vector<double> sigma_t, sigma_s, fmom;
+  std::vector<double> sigma_t, sigma_s;
   int N = -1;
+  // Legendre moment shapes: nf rows f[m][0..N] (row-major), the shape of each
+  // cell (empty when nf == 1)
+  int nf = 1;
+  std::vector<double> ftab;
+  std::vector<int> fid;
   std::vector<double> qsrc;
   int bkind[6] = {0, 0, 0, 0, 0, 0};
   double bval[6] = {0, 0, 0, 0, 0, 0};
+  double bdir[6][3] = {};    // kind 3: unit beam direction
+  double brange[6][4] = {};  // kind 3: u0, u1, v0, v1 on the face's tangential axes
   int basis = 1;
   std::vector<std::vector<uint8_t>> paths;
   int nlevels = 1;
@@ -103,12 +116,14 @@ struct amgt_ctx {
   int C = 0, nmat = 0;
   std::vector<int> mat;
   std::vector<double> mat_st, mat_ss;
+  std::vector<int> mat_f;  // moment shape of each material
   std::vector<amgt::Level> lv;
   std::vector<amgt::Transfer> tr;
   std::vector<std::unique_ptr<amgt::DevMem>> mem;  // every device allocation
-  int *d_mat = nullptr, *d_cells = nullptr, *d_level_off = nullptr, *d_bkind = nullptr;
+  int *d_mat = nullptr, *d_cells = nullptr, *d_level_off = nullptr, *d_bkind = nullptr,
+      *d_fid = nullptr;
   double *d_sigt = nullptr, *d_sigs = nullptr, *d_q = nullptr, *d_bval = nullptr, *d_mu = nullptr,
-         *d_mf = nullptr;
+         *d_mf = nullptr, *d_brange = nullptr;
   float *d_sigt32 = nullptr, *d_sigs32 = nullptr, *d_Nm32 = nullptr;
   int nlev_wave = 0;
   // scratch
@@ -123,6 +138,11 @@ struct amgt_ctx {
   size_t bf16_bytes = 0;
   void* d_split = nullptr;                     // split-form slices, products, row scales
   size_t split_bytes = 0;
+  void* d_tc3 = nullptr;                       // FP16 operand rows and row scales
+  size_t tc3_bytes = 0;
+  int f32_scatter = 0;                         // AMGT_TUNE_F32_SCATTER
+  int test_sweep_hold = 0;                     // AMGT_TUNE_TEST_SWEEP_HOLD
+  int coarse_f64 = 0;                          // AMGT_TUNE_COARSE_F64
   int fp64_scatter = 0;                        // AMGT_TUNE_FP64_SCATTER
   int split_rows = 0;                          // AMGT_TUNE_SPLIT_ROWS
   int sweep_kernel = 0;                        // AMGT_TUNE_SWEEP_KERNEL
@@ -154,11 +174,13 @@ struct amgt_ctx {
   struct KtPending {
     int id;
     cudaEvent_t a, b;
+    double work;  // algorithmic bytes or flop of the launch
   };
   std::vector<KtPending> kt_pending;
   std::vector<cudaEvent_t> kt_free;
   double kt_ms[AMGT_KT_COUNT] = {};
   long long kt_n[AMGT_KT_COUNT] = {};
+  double kt_work[AMGT_KT_COUNT] = {};
   ~amgt_ctx() {
     for (auto& row : vgraph)
       for (auto& v : row)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 namespace amgt {
@@ -16,6 +17,7 @@ struct Geom {
   int C;
   long long nsdof;
   int nadof, P;
+  double lo[3], h[3];        // box corner and cell widths
   double facemass[3][4][4];  // [axis][own face node][neighbour face node]
   double Nmass[64];          // spatial mass matrix N (s x s)
   float NmassF[64];
@@ -34,8 +36,8 @@ struct LevelDev {
   const T* Aax;    // [P][3][a][a] A^xi_q
   const T* Ginv;   // [nmat][P][sa][sa] Gauss-Seidel block inverses (coarsest)
   const T* X;      // [nadof][nmom]
-  const T* XFt;    // [nmom][nadof] diag(f_n) X^T
-  const T* Sqq;    // [P][a][a] self-scatter blocks X_q F X_q^T
+  const T* XFt;    // [nf][nmom][nadof] diag(f_n) X^T per moment shape
+  const T* Sqq;    // [nf][P][a][a] self-scatter blocks X_q F X_q^T per shape
   const T* w;      // [nadof] int Psi
   const T* Mang;   // [P][a][a] angular mass M_q
   const int* pdir; // [P] sweep direction of each patch
@@ -44,6 +46,7 @@ struct LevelDev {
 
 struct CellData {
   const int* mat;         // [C] material index
+  const int* fid;         // [C] moment shape of the cell (null: one shape)
   const double* sigma_t;  // [C]
   const double* sigma_s;  // [C]
   const float* sigma_t32;
@@ -89,10 +92,13 @@ struct DevStatus {
 // schedule's tasks must then hold G-patch groups); otherwise the level kernel.
 template <class T>
 // variant: 0 auto, 1 level-synchronous row kernel, 2 warp-pipelined (2D, Lin);
-// err: status word for the bounded waits of the warp-pipelined form
+// err: status word for the bounded waits of the warp-pipelined form;
+// test_hold != 0 (tests of the failure path only): in the warp-pipelined form
+// the first warp of each block never publishes its progress and every wait
+// gives up after 10 ms, so the launch ends with status code 7
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
                   const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
-                  int* err, cudaStream_t st);
+                  int* err, int test_hold, cudaStream_t st);
 template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
                     const T* x, T* y, cudaStream_t st);
@@ -109,6 +115,7 @@ struct GemmEpi {
 template <class T>
 void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc,
                  const GemmEpi& epi, cudaStream_t st);
+cudaError_t preload_gemm();
 
 template <class T>
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
@@ -119,8 +126,8 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 template <class T>
 void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant,
                    const double* q, const double* bnd_val, const int* bnd_kind,
-                   const double* beam, const double* mu, const double* mf, T* f,
-                   cudaStream_t st);
+                   const double* beam, const double* brange, const double* mu,
+                   const double* mf, T* f, cudaStream_t st);
 template <class T>
 void launch_scalar_flux(long long nsdof, int nadof, const T* w, const T* psi, T* phi,
                         cudaStream_t st);
@@ -171,9 +178,11 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
 // (dfn must be zeroed first)
 void launch_grad_sigma_t(const Geom& g, const double* Mang, const double* psi, const double* lam,
                          double* dsigt, cudaStream_t st);
+// ftab [nf][N+1] moment shapes, fid [C] the cell's shape (null: shape 0);
+// dfn [nf][N+1]
 void launch_grad_moments(const Geom& g, int nmom, int N, const double* PhiP, const double* PhiL,
-                         const double* fmom, const double* sig_s, double* dsigs, double* dfn,
-                         cudaStream_t st);
+                         const double* ftab, const int* fid, const double* sig_s, double* dsigs,
+                         double* dfn, cudaStream_t st);
 
 // fixed moment scratch of the allocation-free coarse Gauss-Seidel entry point
 size_t noalloc_moment_bytes();
@@ -193,6 +202,11 @@ template <class T>
 void launch_scale_copy(long long n, double alpha, const T* x, T* y, cudaStream_t st);
 template <class Tin, class Tout>
 void launch_convert(long long n, const Tin* x, Tout* y, cudaStream_t st);
+// Phi[r][k] *= fdeg[fid[r / s]][k] for r < rows (moments scaled by each
+// cell's moment shape)
+template <class T>
+void launch_scale_moments(long long rows, int s, int nmom, const int* fid, const T* fdeg, T* Phi,
+                          cudaStream_t st);
 template <class T>
 void launch_lincomb(long long n, int nvec, const T* const* Z, const double* y, T* x,
                     cudaStream_t st);
@@ -210,6 +224,21 @@ void launch_tc_prep(long long ncell, int s, int n, const float* x, const float* 
 // C = A Bt^T (+ beta C + add); returns 0 on a successful launch
 int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
                    const float* add, float beta, int* err, cudaStream_t st);
+// C = rs (A Bt^T) (+ beta C + add) with A, Bt both BF16 (f16 = false) or both
+// FP16 (f16 = true); rs [M] per-row scales or null
+int launch_tc_gemm_ex(int M, int N, int K, const void* A, const void* Bt, bool f16, float* C,
+                      const float* add, float beta, const float* rs, int* err, cudaStream_t st);
+// FP32-accurate scatter on FP16 tensor cores (kernels_tc3.cu): rows r = c s + l
+// of z = alpha sig[c] (N x_c)[l] scaled per row by a power of two and cut into
+// hi + lo FP16 parts, out[r] = [hi | lo | hi] (3n halves), rs[r] = inverse row
+// scale times sinv
+void launch_tc3_prep(long long ncell, int s, int n, const float* x, const float* sig,
+                     const float* Nm, float alpha, float sinv, __half* out, float* rs,
+                     cudaStream_t st);
+// Bt[n][3n] = [S_hi | S_hi | S_lo] of S scaled by one power of two (largest
+// entry in [2^14, 2^15)); *sinv receives the inverse scale (synchronises st)
+cudaError_t tc3_split_sf(int n, const double* Sf, unsigned long long* dmax, __half* Bt,
+                         double* sinv, cudaStream_t st);
 
 // Error-free splitting of FP64 rows into BF16 digit slices (kernels_split64.cu):
 // per row r of z (x itself, or with mix the per-cell rows sig[c] N x of S

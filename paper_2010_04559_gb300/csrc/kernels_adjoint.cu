@@ -78,13 +78,16 @@ template <int S>
 __global__ void __launch_bounds__(kGradThreads) grad_moments_kernel(Geom g, int nmom, int N,
                                                                     const double* __restrict__ PhiP,
                                                                     const double* __restrict__ PhiL,
-                                                                    const double* __restrict__ fmom,
+                                                                    const double* __restrict__ ftab,
+                                                                    const int* __restrict__ fid,
                                                                     const double* __restrict__ sig_s,
                                                                     double* __restrict__ dsigs,
                                                                     double* __restrict__ dfn) {
   __shared__ double red[kGradThreads / 32];
   extern __shared__ double part[];  // [N+1] per-degree sums of this cell
   const long long c = blockIdx.x;
+  const int sh = fid ? fid[c] : 0;
+  const double* fmom = ftab + (size_t)sh * (N + 1);
   for (int n = threadIdx.x; n <= N; n += blockDim.x) part[n] = 0.0;
   __syncthreads();
   double vs = 0.0;
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_moments_kernel(Geom g, int 
   if (threadIdx.x == 0) dsigs[c] = ts;
   __syncthreads();
   const double ss = sig_s[c];
-  for (int n = threadIdx.x; n <= N; n += blockDim.x) atomicAdd(&dfn[n], ss * part[n]);
+  for (int n = threadIdx.x; n <= N; n += blockDim.x)
+    atomicAdd(&dfn[(size_t)sh * (N + 1) + n], ss * part[n]);
 }
 
 }  // namespace
@@ -127,16 +131,16 @@ void launch_grad_sigma_t(const Geom& g, const double* Mang, const double* psi, c
 }
 
 void launch_grad_moments(const Geom& g, int nmom, int N, const double* PhiP, const double* PhiL,
-                         const double* fmom, const double* sig_s, double* dsigs, double* dfn,
-                         cudaStream_t st) {
+                         const double* ftab, const int* fid, const double* sig_s, double* dsigs,
+                         double* dfn, cudaStream_t st) {
   note_launch();
   const size_t smem = (size_t)(N + 1) * sizeof(double);
   if (g.s == 4)
-    grad_moments_kernel<4><<<g.C, kGradThreads, smem, st>>>(g, nmom, N, PhiP, PhiL, fmom, sig_s,
-                                                           dsigs, dfn);
+    grad_moments_kernel<4><<<g.C, kGradThreads, smem, st>>>(g, nmom, N, PhiP, PhiL, ftab, fid,
+                                                           sig_s, dsigs, dfn);
   else
-    grad_moments_kernel<8><<<g.C, kGradThreads, smem, st>>>(g, nmom, N, PhiP, PhiL, fmom, sig_s,
-                                                           dsigs, dfn);
+    grad_moments_kernel<8><<<g.C, kGradThreads, smem, st>>>(g, nmom, N, PhiP, PhiL, ftab, fid,
+                                                           sig_s, dsigs, dfn);
 }
 
 }  // namespace amgt

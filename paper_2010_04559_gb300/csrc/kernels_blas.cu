@@ -235,6 +235,27 @@ void launch_convert(long long n, const Tin* x, Tout* y, cudaStream_t st) {
   convert_kernel<Tin, Tout><<<grid_1d(n), kThreads, 0, st>>>(n, x, y);
 }
 
+// Phi[r][k] *= fdeg[fid[r / s]][k]: moments scaled by each cell's moment shape
+template <class T>
+__global__ void scale_moments_kernel(long long rows, int s, int nmom, const int* __restrict__ fid,
+                                     const T* __restrict__ fdeg, T* __restrict__ Phi) {
+  const long long total = rows * nmom;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / nmom;
+    const int k = (int)(i - r * nmom);
+    Phi[i] *= fdeg[(size_t)fid[r / s] * nmom + k];
+  }
+}
+
+template <class T>
+void launch_scale_moments(long long rows, int s, int nmom, const int* fid, const T* fdeg, T* Phi,
+                          cudaStream_t st) {
+  note_launch();
+  scale_moments_kernel<T><<<grid_1d(rows * nmom), kThreads, 0, st>>>(rows, s, nmom, fid, fdeg,
+                                                                      Phi);
+}
+
 template <class T>
 void launch_lincomb(long long n, int nvec, const T* const* Z, const double* y, T* x,
                     cudaStream_t st) {
@@ -253,7 +274,9 @@ void launch_lincomb(long long n, int nvec, const T* const* Z, const double* y, T
   template void launch_axpby<T>(long long, double, const T*, double, T*, cudaStream_t);      \
   template void launch_scale_copy<T>(long long, double, const T*, T*, cudaStream_t);         \
   template void launch_lincomb<T>(long long, int, const T* const*, const double*, T*,        \
-                                  cudaStream_t);
+                                  cudaStream_t);                                             \
+  template void launch_scale_moments<T>(long long, int, int, const int*, const T*, T*,       \
+                                        cudaStream_t);
 AMGT_INST(double)
 AMGT_INST(float)
 #undef AMGT_INST

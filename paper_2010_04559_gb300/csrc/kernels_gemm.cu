@@ -118,6 +118,15 @@ void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, 
   gemm_kernel<T><<<grid, block, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi);
 }
 
+// Resolves both GEMM kernels on the current device (under CUDA's lazy module
+// loading a kernel's code is otherwise loaded at its first launch).
+cudaError_t preload_gemm() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, gemm_kernel<double>);
+  if (e != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&a, gemm_kernel<float>);
+}
+
 template void launch_gemm<double>(int, int, int, const double*, int, const double*, int,
                                   double*, int, const GemmEpi&, cudaStream_t);
 template void launch_gemm<float>(int, int, int, const float*, int, const float*, int, float*,

@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(512) coarse_gs_kernel(Geom g, LevelDev<T> t, C
           T* Phi = mom + (long long)c * S * nm;
           const int mat = cd.mat[c];
           const T sig_s = (T)cd.sigma_s[c];
+          const int sh = cd.fid ? cd.fid[c] : 0;  // the cell's moment shape
+          const T* xfs = t.XFt + (size_t)sh * nm * nadof;
+          const T* sqs = t.Sqq + (size_t)sh * g.P * A * A;
           for (int q = qb; q < qe; ++q) {
             const long long off = ((long long)c * S + l) * nadof + q * A + m;
             T rhs = act ? f[off] : T(0);
@@ -148,10 +151,10 @@ __global__ void __launch_bounds__(512) coarse_gs_kernel(Geom g, LevelDev<T> t, C
             // G[l][m] = (X_q F Phi_c)[m][l] - (S_qq x_old)[l][m]
             T G = T(0);
             if (act) {
-              const T* xf = t.XFt;  // [nm][nadof]
+              const T* xf = xfs;  // [nm][nadof]
               for (int kk = 0; kk < nm; ++kk) G += xf[(long long)kk * nadof + q * A + m] * __ldcg(Phi + l * nm + kk);
             }
-            const T* Sq = t.Sqq + (size_t)q * A * A;
+            const T* Sq = sqs + (size_t)q * A * A;
 #pragma unroll
             for (int dd = 0; dd < A; ++dd) {
               const T od = __shfl_sync(0xffffffffu, old, l * A + dd);

@@ -38,15 +38,20 @@ constexpr uint32_t TMEM_COLS = 2 * BN;            // two accumulators
 constexpr unsigned long long kWaitNs = 2000000000ULL;
 constexpr size_t kSmemBytes = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 
-// instruction descriptor: D f32, A/B bf16, both K-major, N >> 3, M >> 4
-constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor: D f32, A/B bf16 (F16 = false) or f16 (F16 = true),
+// both K-major, N >> 3, M >> 4
+template <bool F16>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (F16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
 
 struct TcArgs {
   int M, N, K;
   float* C;
   const float* add;
   float beta;
+  const float* rs;  // optional per-row scale of the product (null: 1)
   int* err;
 };
 
@@ -106,13 +111,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;              // 128-byte swizzle
   return d;
 }
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t accumulate) {
+__device__ __forceinline__ void umma_16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t id, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(id), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -148,13 +153,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // one accumulator chunk (32 columns of this thread's row) to global memory
 __device__ __forceinline__ void store_chunk(float* out, const float* ad, const float4 (&a4)[8],
-                                            const uint32_t (&v)[32], float beta, bool vec,
-                                            int ncols) {
+                                            const uint32_t (&v)[32], float beta, float rsc,
+                                            bool vec, int ncols) {
   if (vec) {
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
-      float4 o = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                             __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+      float4 o = make_float4(rsc * __uint_as_float(v[j]), rsc * __uint_as_float(v[j + 1]),
+                             rsc * __uint_as_float(v[j + 2]), rsc * __uint_as_float(v[j + 3]));
       if (beta != 0.0f) {
         const float4 b = *reinterpret_cast<const float4*>(out + j);
         o.x += beta * b.x;
@@ -174,7 +179,7 @@ __device__ __forceinline__ void store_chunk(float* out, const float* ad, const f
 #pragma unroll
     for (int j = 0; j < 32; ++j) {  // static register indices
       if (j < ncols) {
-        float o = __uint_as_float(v[j]);
+        float o = rsc * __uint_as_float(v[j]);
         if (beta != 0.0f) o += beta * out[j];
         if (ad) o += ad[j];
         out[j] = o;
@@ -183,6 +188,7 @@ __device__ __forceinline__ void store_chunk(float* out, const float* ad, const f
   }
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                  const __grid_constant__ CUtensorMap tmB,
                                                                  TcArgs args) {
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           const uint64_t bdesc = sw128_desc(sa + A_BYTES);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
-            umma_bf16(dt, adesc + 2ull * kk, bdesc + 2ull * kk, (k | kk) != 0 ? 1u : 0u);
+            umma_16(dt, adesc + 2ull * kk, bdesc + 2ull * kk, idesc<F16>(), (k | kk) != 0 ? 1u : 0u);
           umma_commit(&empty[s]);
         }
         if (!ok) break;
@@ -319,6 +325,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       const bool rowok = row < args.M;
       const int cbase = n0 + h * (BN / 2);
       const float* adrow = args.add ? args.add + (long long)row * args.N : nullptr;
+      // the scale is exactly 1 without a row-scale vector
+      const float rsc = (args.rs && rowok) ? args.rs[row] : 1.0f;
       // add for chunk c+1 is loaded while chunk c is stored (two register sets)
       float4 aA[8], aB[8];
       auto load_add = [&](int c, float4(&dst)[8]) {
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         if (rowok && col0 < args.N) {
           const int ncols = min(32, args.N - col0);
           store_chunk(args.C + (long long)row * args.N + col0, adrow ? adrow + col0 : nullptr, cur,
-                      v, args.beta, vec && ncols == 32, ncols);
+                      v, args.beta, rsc, vec && ncols == 32, ncols);
         }
       };
       static_assert(BN / 64 == 4, "four 32-column chunks per epilogue warp");
@@ -401,14 +409,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool encode_kmajor(CUtensorMap* m, const void* ptr, int rows, int K, int box_rows) {
+bool encode_kmajor(CUtensorMap* m, const void* ptr, int rows, int K, int box_rows, bool f16) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
   const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+  return fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(ptr), dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -417,7 +426,8 @@ bool encode_kmajor(CUtensorMap* m, const void* ptr, int rows, int K, int box_row
 
 bool tc_available() {
   cudaFuncAttributes a;
-  return cudaFuncGetAttributes(&a, tc_gemm_kernel) == cudaSuccess && encode_fn() != nullptr;
+  return cudaFuncGetAttributes(&a, tc_gemm_kernel<false>) == cudaSuccess &&
+         cudaFuncGetAttributes(&a, tc_gemm_kernel<true>) == cudaSuccess && encode_fn() != nullptr;
 }
 
 void launch_tc_prep(long long ncell, int s, int n, const float* x, const float* sig,
@@ -432,17 +442,18 @@ void launch_tc_prep(long long ncell, int s, int n, const float* x, const float* 
     tc_prep_kernel<8><<<(int)grid, 256, 0, st>>>(ncell, n, x, sig, Nm, alpha, xb);
 }
 
-// C = A B (+ beta C + add): A [M][K] bf16, Bt [N][K] bf16 (B^T), C/add [M][N] f32
-int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
-                   const float* add, float beta, int* err, cudaStream_t st) {
+// C = rs (A B) (+ beta C + add): A [M][K] and Bt [N][K] (B^T) both bf16 or
+// both f16, C/add [M][N] f32, rs [M] f32 or null
+int launch_tc_gemm_ex(int M, int N, int K, const void* A, const void* Bt, bool f16, float* C,
+                      const float* add, float beta, const float* rs, int* err, cudaStream_t st) {
   if (M <= 0 || N < 16 || K < BK || (K % 8) != 0) return -1;
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Bt)) & 15) return -1;
   CUtensorMap ta, tb;
-  if (!encode_kmajor(&ta, A, M, K, BM) || !encode_kmajor(&tb, Bt, N, K, BN)) return -2;
+  if (!encode_kmajor(&ta, A, M, K, BM, f16) || !encode_kmajor(&tb, Bt, N, K, BN, f16)) return -2;
   // per launch: the attribute and the SM count belong to the current device
-  if (allow_max_smem(tc_gemm_kernel) != cudaSuccess)
+  if (allow_max_smem(f16 ? tc_gemm_kernel<true> : tc_gemm_kernel<false>) != cudaSuccess)
     return -3;
-  TcArgs args{M, N, K, C, add, beta, err};
+  TcArgs args{M, N, K, C, add, beta, rs, err};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -450,8 +461,16 @@ int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
   const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
   const int grid = tiles < nsm ? tiles : nsm;
   note_launch();
-  tc_gemm_kernel<<<grid, TC_THREADS, kSmemBytes, st>>>(ta, tb, args);
+  if (f16)
+    tc_gemm_kernel<true><<<grid, TC_THREADS, kSmemBytes, st>>>(ta, tb, args);
+  else
+    tc_gemm_kernel<false><<<grid, TC_THREADS, kSmemBytes, st>>>(ta, tb, args);
   return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+int launch_tc_gemm(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Bt, float* C,
+                   const float* add, float beta, int* err, cudaStream_t st) {
+  return launch_tc_gemm_ex(M, N, K, A, Bt, false, C, add, beta, nullptr, err, st);
 }
 
 }  // namespace amgt

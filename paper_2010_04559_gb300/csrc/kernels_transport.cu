@@ -394,15 +394,18 @@ __device__ __forceinline__ void st_release_cta(int* p, int v) {
                : "memory");
 }
 constexpr unsigned long long kSweepWaitNs = 2000000000ULL;
-// lane 0 waits until *p >= target; false once it gave up
-__device__ __forceinline__ bool wait_at_least(const int* p, int target, int* err) {
+constexpr unsigned long long kSweepTestWaitNs = 10000000ULL;  // failure-path tests
+// lane 0 waits until *p >= target; false once it gave up (after wait_ns, or
+// as soon as another wait gave up)
+__device__ __forceinline__ bool wait_at_least(const int* p, int target, int* err,
+                                              unsigned long long wait_ns) {
   if (ld_acquire_cta(p) >= target) return true;
   const unsigned long long t0 = gsx::now_ns();
   unsigned it = 0;
   while (ld_acquire_cta(p) < target) {
     if ((++it & 63u) == 0) {
       if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-      if (gsx::now_ns() - t0 > kSweepWaitNs) {
+      if (gsx::now_ns() - t0 > wait_ns) {
         atomicExch(err, 7);
         return false;
       }
@@ -453,7 +456,9 @@ template <class T, int A, int G, int NST, int UMAX>
 __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t, CellData cd,
                                                             Schedule sc, const T* __restrict__ b,
                                                             T* __restrict__ psi, int nmat_s,
-                                                            int chunk, int* err) {
+                                                            int chunk, int* err,
+                                                            unsigned long long wait_ns,
+                                                            int hold) {
   constexpr int S = 4, HS = 2;
   constexpr int SA = S * A;
   constexpr int RW = 32 / G;
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t
     // row 0: the previous warp's last row, once that warp has passed step ts + RW - 1
     if (warp > 0 && ts < nx) {
       bool ok = true;
-      if (lane == 0) ok = wait_at_least(prog + warp - 1, ts + RW, err);
+      if (lane == 0) ok = wait_at_least(prog + warp - 1, ts + RW, err, wait_ns);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       __syncwarp();  // lane 0's acquire orders the ring reads of every lane
@@ -721,7 +726,7 @@ __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t
     const int jl = ts - (RW - 1);
     if (warp + 1 < nwarp && jl >= 0 && jl < nx) {
       bool ok = true;
-      if (lane == 0 && jl >= R) ok = wait_at_least(prog + warp + 1, jl - R + 1, err);
+      if (lane == 0 && jl >= R) ok = wait_at_least(prog + warp + 1, jl - R + 1, err, wait_ns);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       if (r == RW - 1 && p < nq && jy < ny) {
@@ -733,7 +738,8 @@ __global__ void __launch_bounds__(512) sweep2d_warp_kernel(Geom g, LevelDev<T> t
       }
     }
     __syncwarp();
-    if (lane == 0) st_release_cta(prog + warp, ts + 1);
+    // (hold: the failure-path test keeps warp 0's progress unpublished)
+    if (lane == 0 && !(hold && warp == 0)) st_release_cta(prog + warp, ts + 1);
   }
   cp_async_wait<0>();
 }
@@ -856,8 +862,10 @@ template <class T>
 __global__ void source_kernel(Geom g, const T* __restrict__ w, const T* __restrict__ Aw,
                               const int* __restrict__ octant, const double* __restrict__ qsrc,
                               const double* __restrict__ bval, const int* __restrict__ bkind,
-                              const double* __restrict__ beam, const double* __restrict__ mu,
-                              const double* __restrict__ mf, T* __restrict__ f) {
+                              const double* __restrict__ beam,
+                              const double* __restrict__ brange,
+                              const double* __restrict__ mu, const double* __restrict__ mf,
+                              T* __restrict__ f) {
   const long long total = g.nsdof * g.nadof;
   const int a = g.a, s = g.s;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -876,8 +884,33 @@ __global__ void source_kernel(Geom g, const T* __restrict__ w, const T* __restri
         const int face = 2 * xi + side;
         if (bkind[face] == 0) continue;
         if (side == 0 ? ic[xi] != 0 : ic[xi] != n[xi] - 1) continue;
-        if (bkind[face] == 2) {  // pencil beam: S mf_l Psi_m(Omega_b) / k
+        if (bkind[face] == 2) {  // pencil beam: S mf_l Psi_m(Omega_b) share_q
           v += beam[(size_t)face * g.nadof + j] * mf[face * s + l];
+          continue;
+        }
+        if (bkind[face] == 3) {
+          // beam over part of the face: S |Omega_b.n| Psi_m(Omega_b) share_q times
+          // the integral of Phi_l over the cell face and the range, a product
+          // over the tangential axes of integrals of the linear nodal functions
+          // l_0 = 1 - t/h, l_1 = t/h over the overlap [ta, tb] of the cell
+          if (((l >> xi) & 1) != side) continue;
+          double I = 1.0;
+          int k = 0;
+          for (int e = 0; e < g.dim; ++e) {
+            if (e == xi) continue;
+            const double x0 = g.lo[e] + ic[e] * g.h[e];
+            const double lo_ = fmax(x0, brange[face * 4 + 2 * k]);
+            const double hi_ = fmin(x0 + g.h[e], brange[face * 4 + 2 * k + 1]);
+            ++k;
+            if (!(hi_ > lo_)) {
+              I = 0.0;
+              break;
+            }
+            const double ta = lo_ - x0, tb = hi_ - x0, he = g.h[e];
+            const double i1 = (tb * tb - ta * ta) / (2.0 * he);
+            I *= ((l >> e) & 1) ? i1 : (tb - ta) - i1;
+          }
+          v += beam[(size_t)face * g.nadof + j] * I;
           continue;
         }
         // inflow iff the patch moves into the domain through this face
@@ -975,7 +1008,7 @@ size_t sweep2d_smem(const Geom& g, int G, int nmat_s, int nst) {
 template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
                   const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
-                  int* err, cudaStream_t st) {
+                  int* err, int test_hold, cudaStream_t st) {
   note_launch();
   // warp-pipelined form (variant 2; auto with at least 2 (FP32) or 4 (FP64)
   // patches per block, where it measured faster):
@@ -994,7 +1027,9 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
     if (nwarp * 32 <= 512 && smem <= 200 * 1024 && need <= 12) {
       auto launch = [&](auto kern) {
         allow_max_smem(kern);
-        kern<<<sc.ntask, nwarp * 32, smem, st>>>(g, t, cd, sc, b, psi, nmat_s, chunk, err);
+        kern<<<sc.ntask, nwarp * 32, smem, st>>>(g, t, cd, sc, b, psi, nmat_s, chunk, err,
+                                                 test_hold ? kSweepTestWaitNs : kSweepWaitNs,
+                                                 test_hold ? 1 : 0);
       };
       auto by_g = [&](auto g_tag) {
         constexpr int GG = decltype(g_tag)::value;
@@ -1070,11 +1105,13 @@ void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T a
 
 template <class T>
 void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant, const double* q,
-                   const double* bval, const int* bkind, const double* beam, const double* mu,
-                   const double* mf, T* f, cudaStream_t st) {
+                   const double* bval, const int* bkind, const double* beam,
+                   const double* brange, const double* mu, const double* mf, T* f,
+                   cudaStream_t st) {
   note_launch();
   const int grid = grid_for(g.nsdof * g.nadof, 256);
-  source_kernel<T><<<grid, 256, 0, st>>>(g, w, Aw, octant, q, bval, bkind, beam, mu, mf, f);
+  source_kernel<T><<<grid, 256, 0, st>>>(g, w, Aw, octant, q, bval, bkind, beam, brange, mu, mf,
+                                         f);
 }
 
 template <class T>
@@ -1105,12 +1142,12 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 #define AMGT_INST(T)                                                                          \
   template void launch_sweep<T>(const Geom&, const LevelDev<T>&, const CellData&,             \
                                 const Schedule&, const T*, T*, int, int, int, int, int,       \
-                                int*, cudaStream_t);                                          \
+                                int*, int, cudaStream_t);                                     \
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
   template void launch_source<T>(const Geom&, const T*, const T*, const int*, const double*,  \
                                  const double*, const int*, const double*, const double*,     \
-                                 const double*, T*, cudaStream_t);                            \
+                                 const double*, const double*, T*, cudaStream_t);             \
   template void launch_scalar_flux<T>(long long, int, const T*, const T*, T*, cudaStream_t);  \
   template void launch_restrict<T>(long long, int, int, int, int, const int*, const int*,     \
                                    const T*, const T*, T*, cudaStream_t);                     \

@@ -12,10 +12,13 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
 #include <stdexcept>
+#include <thread>
+#include <vector>
 
 namespace amgt {
 
@@ -320,21 +323,36 @@ std::vector<double> x_table(const AngMesh& m, int N) {
   const int nm = (N + 1) * (N + 1);
   const int a = m.a;
   std::vector<double> X((size_t)m.P * a * nm, 0.0);
-  std::vector<double> nodes, wts, Y(nm);
-  double psi[3];
-  for (int p = 0; p < m.P; ++p) {
-    patch_quadrature(m.patch[p], quadrature_order(m.patch[p].level, N), nodes, wts);
-    for (size_t k = 0; k < wts.size(); ++k) {
-      const double* om = &nodes[3 * k];
-      basis_values(m, p, om, psi);
-      real_harmonics(N, om, Y.data());
-      for (int i = 0; i < a; ++i) {
-        double wp = wts[k] * psi[i];
-        double* row = &X[((size_t)p * a + i) * nm];
-        for (int j = 0; j < nm; ++j) row[j] += wp * Y[j];
+  // patches are independent: spread them over the host's cores
+  std::atomic<int> next{0};
+  auto work = [&] {
+    std::vector<double> nodes, wts, Y(nm);
+    double psi[3];
+    for (int p; (p = next.fetch_add(1)) < m.P;) {
+      patch_quadrature(m.patch[p], quadrature_order(m.patch[p].level, N), nodes, wts);
+      for (size_t k = 0; k < wts.size(); ++k) {
+        const double* om = &nodes[3 * k];
+        basis_values(m, p, om, psi);
+        real_harmonics(N, om, Y.data());
+        for (int i = 0; i < a; ++i) {
+          double wp = wts[k] * psi[i];
+          double* row = &X[((size_t)p * a + i) * nm];
+          for (int j = 0; j < nm; ++j) row[j] += wp * Y[j];
+        }
       }
     }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 64) nt = 64;
+  if ((int)nt > m.P) nt = (unsigned)m.P;
+  if (nt <= 1) {
+    work();
+    return X;
   }
+  std::vector<std::thread> ts;
+  for (unsigned t = 0; t < nt; ++t) ts.emplace_back(work);
+  for (auto& t : ts) t.join();
   return X;
 }
 

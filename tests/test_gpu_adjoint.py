@@ -129,3 +129,25 @@ def test_autograd_gradients_match_central_differences():
             h = 1e-4 * max(1.0, abs(prob[key][i]))
             fd = (resp(key, i, h) - resp(key, i, -h)) / (2 * h)
             assert abs(fd - grad[i]) < 1e-5 * np.abs(grad).max(), (key, i, fd, grad[i])
+
+
+def test_per_material_shape_gradients_match_the_oracle():
+    """dR/df for two materials with different moment shapes: the library's
+    [nmat][N+1] gradient against the oracle's adjoint gradients."""
+    from oracle import adjoint as oadj
+    from paper_2010_04559_gb300.adjoint import solve_response
+    prob = W.two_shape_problem(2, (4, 3), 1, 4, 95)
+    weight = np.zeros(12)
+    weight[[0, 5, 7]] = 1.0
+    am = angular.AngularMesh(angular.uniform_paths(1), "lin")
+    T = transport.Transport(prob, am)
+    psi = oadj.dense_solve(T, T.source())
+    Ta = oadj.adjoint_transport(prob, am, weight)
+    lam = oadj.dense_solve(Ta, Ta.source())
+    dt_o, ds_o, df_o = oadj.gradients(T, psi, lam)
+    R, _, _, dt, ds, df = solve_response(prob, weight, tol=1e-13)
+    assert abs(R - oadj.response(T, psi, weight)) < 1e-10 * abs(R)
+    assert df.shape == (2, 5)
+    for a, b in ((dt, dt_o), (ds, ds_o), (df, df_o)):
+        a = a.cpu().numpy()
+        assert np.abs(a - b).max() < 1e-9 * np.abs(b).max()

@@ -170,3 +170,90 @@ def test_forward_peaked_beam_workload_full_size_mixed():
     avg = phi.cpu().numpy().reshape(n * n, 4).sum(axis=1).reshape(n, n)
     assert np.abs(avg - avg[::-1]).max() < 1e-7 * np.abs(avg).max()
     assert avg[:, 0].mean() > avg[:, -1].mean() > 0
+
+
+# ------------------------------------------------ beams of any direction, part of a face
+def _gbeam(dim, nc, level, faces, N=4, g=0.8, basis="lin", ss=0.8, q=0.0, seed=73):
+    """faces: (face, (S, Omega_b[3], u0, u1, v0, v1)) for kind-3 beams."""
+    rng = np.random.default_rng(seed)
+    C = int(np.prod(nc))
+    st = 1.0 + rng.random(C)
+    bnd = [(0, 0.0)] * (2 * dim)
+    for f, val in faces:
+        bnd[f] = (3, tuple(val))
+    return W.problem(dim, nc, st, ss * st, N, W.hg_moments(g, N), np.full(C, q), level,
+                     basis=basis, boundary=bnd)
+
+
+GSRC = [
+    # inside a patch, cutting cells at both ends of the range
+    (2, (5, 7), 1, "lin", [(0, (1.0, 0.8, 0.35, 0.2, 0.23, 0.61, 0, 0))], None),
+    # on an edge of the patches (the x-y great circle), high-y face
+    (2, (6, 4), 2, "const", [(3, (0.7, 0.3, -1.0, 0.0, 0.1, 0.95, 0, 0))], None),
+    # at a level-1 vertex (six patches, unequal angles), 3D, two beams
+    (3, (4, 3, 3), 2, "lin", [(4, (1.0, 0.0, 1.0, 1.0, 0.3, 0.7, 0.15, 0.52)),
+                              (1, (0.5, -1.0, 0.2, 0.3, 0.0, 1.0, 0.0, 1.0))], None),
+    # the cube's boundary source of Sec. 5.4: along +z on a central square of
+    # the low-z face, z-pole band-refined mesh
+    (3, (4, 4, 3), None, "lin", [(4, (1.0, 0.0, 0.0, 1.0, 0.375, 0.625, 0.375, 0.625))],
+     ((0.0, 0.0, 1.0), 3)),
+]
+
+
+@pytest.mark.parametrize("dim,nc,level,basis,faces,aniso", GSRC,
+                         ids=["inside", "edge", "vertex3d", "zpole-square"])
+def test_general_beam_source_matches_oracle(dim, nc, level, basis, faces, aniso):
+    from paper_2010_04559_gb300 import context_from_problem
+    prob = _gbeam(dim, nc, level if level is not None else 0, faces, basis=basis, q=0.2)
+    paths = (angular.uniform_paths(level) if aniso is None
+             else angular.aniso_paths(aniso[1], aniso[0]))
+    T = transport.Transport(prob, angular.AngularMesh(paths, basis))
+    ctx = context_from_problem(prob, device=0, aniso=aniso)
+    assert ctx.amgt_query_sizes(0) == (T.nsdof, T.nadof)
+    ref = T.source()
+    for td, tol in ((torch.float64, 1e-13), (torch.float32, 1e-6)):
+        f = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=td)
+        ctx.amgt_op_source(0, f)
+        torch.cuda.synchronize()
+        assert _rel(f.double().cpu().numpy(), ref) < tol
+    ctx.close()
+
+
+def test_general_beam_arguments_are_checked():
+    from paper_2010_04559_gb300 import AMGT_ERR_ARG, AmgtError, context_from_problem
+    prob = _beam(2, (3, 3), 1, [(0, 1.0)])
+    ctx = context_from_problem(prob, device=0)
+    for val in ((1.0, -1.0, 0.0, 0.0, 0.0, 1.0, 0, 0),     # outward on the low-x face
+                (1.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0, 0),      # zero direction
+                (1.0, 1.0, 0.0, 0.0, 0.6, 0.4, 0, 0),      # empty range
+                (1.0, 1.0, np.nan, 0.0, 0.0, 1.0, 0, 0)):  # not finite
+        with pytest.raises(AmgtError) as e:
+            ctx.amgt_set_boundary(0, 3, val)
+        assert e.value.code == AMGT_ERR_ARG
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_cube_partial_face_beam_solve_on_a_zpole_mesh_matches_oracle(mode):
+    """Sec. 5.4's second test problem, reduced: a cube with a pencil beam
+    along +z entering through the square 0.375 < x, y < 0.625 of its low-z
+    face, the angular mesh refined about the z pole (l_max = 3, bands of
+    Sec. 5.4), 3-level multigrid over its coarsened meshes; FP64 and mixed
+    solves against the oracle's."""
+    from paper_2010_04559_gb300 import (AMGT_MODE_F64, AMGT_MODE_MIXED, AMGT_PREC_MG,
+                                        context_from_problem)
+    beam = (1.0, 0.0, 0.0, 1.0, 0.375, 0.625, 0.375, 0.625)
+    prob = _mg(_gbeam(3, (4, 4, 4), 0, [(4, beam)], N=6, g=0.9, ss=0.9), 3, [6, 3, 3])
+    paths = angular.aniso_paths(3, (0.0, 0.0, 1.0))
+    H = multigrid.Hierarchy(prob, paths)
+    T = H.levels[0]
+    xo, _, _, rel = gmres.gmres(T.apply_A, T.source(), lambda v: H.vcycle(v), 1e-13, 20, 1000)
+    assert rel < 1e-13
+    ctx = context_from_problem(prob, device=0, aniso=((0.0, 0.0, 1.0), 3))
+    md = AMGT_MODE_F64 if mode == "f64" else AMGT_MODE_MIXED
+    tol = 1e-13 if mode == "f64" else 1e-11
+    psi, phi, st, _ = ctx.amgt_solve(tol=tol, precond=AMGT_PREC_MG, mode=md)
+    assert st.relres < tol
+    assert _rel(psi, xo) < (1e-10 if mode == "f64" else 1e-6)
+    assert _rel(phi, T.scalar_flux(xo)) < (1e-10 if mode == "f64" else 1e-6)
+    ctx.close()

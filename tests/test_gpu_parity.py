@@ -6,6 +6,7 @@ Tolerances (relative L2 over the compared entries):
   FP64 solves               1e-10  (both sides solved to relres 1e-13)
   FP32 operators            2e-5   (unit roundoff 6e-8 times sum lengths <= a few 1e3)
   BF16 tensor-core scatter  1e-2   (inputs rounded to 8-bit mantissas, FP32 sums)
+  FP16 three-product scatter 2e-5 (hi + lo parts keep ~22 bits, FP32 sums)
   mixed-precision solve     1e-6   (after FP64 iterative refinement to relres 1e-12)
 """
 import numpy as np
@@ -204,6 +205,28 @@ def test_mixed_solve_matches_oracle():
     ctx.close()
 
 
+def test_fp64_coarse_solve_in_the_fp32_cycle():
+    """AMGT_TUNE_COARSE_F64: the FP32 V-cycle with its coarsest Gauss-Seidel
+    solve in FP64 against the oracle's cycle, and the mixed solve with it
+    against the oracle's solution."""
+    from paper_2010_04559_gb300 import AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_COARSE_F64
+    prob = _mg_problem(2, (8, 8), 2, "lin", 3, [8, 4, 4], sweeps=10, seed=53)
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(AMGT_TUNE_COARSE_F64, 1)
+    f = W.random_vector((T.nsdof, T.nadof), 54)
+    out = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=torch.float32)
+    ctx.amgt_op_vcycle(_dev(f, torch.float32), out)
+    assert _rel(_host(out), H.vcycle(f)) < 2e-4
+    xo, *_ = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+    psi, phi, st, rc = ctx.amgt_solve(tol=1e-12, restart=20, maxit=1000, precond=AMGT_PREC_MG,
+                                      mode=AMGT_MODE_MIXED, inner_tol=1e-4)
+    assert st.relres < 1e-12
+    assert _rel(psi, xo) < 1e-6
+    ctx.close()
+
+
 def test_config1_square16_fp64_gmres20():
     """The 16x16 / level-1 / HG g = 0.8 order-8 problem, FP64 GMRES(20) to 1e-8,
     sweep preconditioner; compared with the oracle solved to 1e-12."""
@@ -327,6 +350,34 @@ def test_bf16_tensor_core_scatter(dim, nc, level, basis):
     ctx.amgt_op_apply_A(0, xd, y, tc=True)
     assert _rel(_host(y), T.apply_A(x)) < 1e-2
     ctx.amgt_sync()        # no bounded device wait gave up
+    ctx.close()
+
+
+@pytest.mark.parametrize("dim,nc,level,basis", TC_CASES,
+                         ids=[f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}" for d, n, l, b in TC_CASES])
+def test_fp16_three_product_scatter(dim, nc, level, basis):
+    """FP32-accurate scatter on FP16 tensor cores (AMGT_F32_TC3: per-row power-
+    of-two scales, hi/lo FP16 parts, three products in one GEMM) against the
+    FP64 oracle at the FP32 operator tolerance, with rows whose magnitudes
+    span 20 decades; also inside (L - S) x."""
+    prob = W.random_problem(dim, nc, level, 6, 37, basis=basis)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    x = W.random_vector((T.nsdof, T.nadof), 38)
+    x *= 10.0 ** np.linspace(-10, 10, T.nsdof)[:, None]
+    xd = _dev(x, torch.float32)
+    x32 = _host(xd)                # the FP32 input both sides see
+    y = torch.empty_like(xd)
+    ctx.amgt_op_scatter(0, xd, y, tc="tc3")
+    ref = T.scatter(x32)
+    # relative per spatial row: the rows' scales differ by 1e20
+    rows = np.linalg.norm(_host(y) - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+    assert rows.max() < 2e-5
+    x2 = W.random_vector((T.nsdof, T.nadof), 39)
+    xd2 = _dev(x2, torch.float32)
+    ctx.amgt_op_apply_A(0, xd2, y, tc="tc3")
+    assert _rel(_host(y), T.apply_A(_host(xd2))) < 2e-5
+    ctx.amgt_sync()
     ctx.close()
 
 
@@ -501,4 +552,41 @@ def test_bicgstab_solve_matches_oracle(precond, mode):
                                      krylov=AMGT_KRYLOV_BICGSTAB)
     assert st.relres < tol
     assert _rel(psi, xo) < (1e-10 if mode == "f64" else 1e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dim,nc,level", [(2, (7, 6), 2), (3, (3, 4, 3), 1)])
+def test_per_material_moment_shapes(dim, nc, level):
+    """Two materials with different HG shapes (amgt_set_materials with mat_id,
+    f[2][N+1]): the scatter (moment form with each cell's shape), the coarse
+    Gauss-Seidel (per-patch form, shape-indexed tables), a V-cycle and the
+    FP64 and mixed solves against the oracle."""
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_MODE_MIXED, AMGT_PREC_MG
+    prob = W.two_shape_problem(dim, nc, level, 6, 91)
+    prob["mg"] = dict(nlevels=2, Nr=[6, 3], nu_pre=1, nu_post=1, coarse_sweeps=10)
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    ctx = _ctx(prob)
+    for td, tol in ((torch.float64, 1e-12), (torch.float32, 2e-5)):
+        x = W.random_vector((T.nsdof, T.nadof), 92)
+        y = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=td)
+        for tc in (False, True):           # the tensor-core flags fall back
+            ctx.amgt_op_scatter(0, _dev(x, td), y, tc=tc)
+            assert _rel(_host(y), T.scatter(x)) < tol
+        ctx.amgt_op_apply_A(0, _dev(x, td), y)
+        assert _rel(_host(y), T.apply_A(x)) < tol
+        Tc = H.levels[-1]
+        fc = W.random_vector((Tc.nsdof, Tc.nadof), 93)
+        pc0 = W.random_vector((Tc.nsdof, Tc.nadof), 94)
+        pc = _dev(pc0, td)
+        ctx.amgt_op_coarse_gs(3, _dev(fc, td), pc)
+        assert _rel(_host(pc), multigrid.coarse_gs(Tc, fc, pc0, 3)) < tol * 10
+        out = torch.empty_like(y)
+        ctx.amgt_op_vcycle(_dev(x, td), out)
+        assert _rel(_host(out), H.vcycle(x)) < tol * 10
+    xo, *_ = gmres.gmres(T.apply_A, T.source(), lambda v: H.vcycle(v), 1e-13, 20, 1000)
+    psi, phi, st, _ = ctx.amgt_solve(tol=1e-13, precond=AMGT_PREC_MG, mode=AMGT_MODE_F64)
+    assert st.relres < 1e-13 and _rel(psi, xo) < 1e-10
+    psi, phi, st, _ = ctx.amgt_solve(tol=1e-11, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED)
+    assert st.relres < 1e-11 and _rel(psi, xo) < 1e-6
     ctx.close()

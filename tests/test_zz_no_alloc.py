@@ -49,6 +49,34 @@ def test_noalloc_matches_allocating_entry_point(dtype, tol):
     ctx.close()
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)],
+                         ids=["f64", "f32"])
+def test_first_call_on_a_fresh_context_takes_no_device_memory(dtype, tol):
+    """The very first call on a freshly built context (set-up completed by
+    amgt_query_sizes, nothing launched yet) leaves the device's free memory
+    unchanged, then agrees with the allocating entry point."""
+    from paper_2010_04559_gb300 import context_from_problem
+    prob = W.random_problem(2, (8, 9), 2, 8, 73, g=0.8)
+    prob["mg"] = dict(nlevels=2, Nr=[8, 4], nu_pre=1, nu_post=1, coarse_sweeps=4)
+    ctx = context_from_problem(prob, device=0)
+    nsc, nac = ctx.amgt_query_sizes(1)
+    gen = torch.Generator(device="cpu").manual_seed(8)
+    f = torch.randn((nsc, nac), generator=gen, dtype=torch.float64).to("cuda", dtype)
+    phi0 = torch.randn((nsc, nac), generator=gen, dtype=torch.float64).to("cuda", dtype)
+    out = phi0.clone()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx.amgt_op_coarse_gs_noalloc(3, f, out)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    ref = phi0.clone()
+    ctx.amgt_op_coarse_gs(3, f, ref)
+    torch.cuda.synchronize()
+    assert _rel(out, ref) < tol
+    ctx.close()
+
+
 def test_noalloc_rejects_oversized_coarse_level():
     from paper_2010_04559_gb300 import AmgtError, context_from_problem
     # 128 x 128 cells, coarse order 8: 65536 x 81 doubles = 42 MB > 32 MiB
