@@ -71,8 +71,11 @@ CLASSES = {
 # DRAM bytes (read + write) per launch from the ncu captures summarised under
 # profiles/, per workload; a kernel changed since its capture has no entry
 TRAFFIC = {
-    "config5": {},
-    "config2": {"sweep": 773.4e6, "coarse_gs": 243.8e6},
+    # split_tc, tc3: captured at 16384 rows (profiles/ncu_split_gemm_config5shape.md,
+    # ncu_tc3_gemm_config5shape.md), scaled to the mean launch's rows (52428 and
+    # 87381); coarse_gs: one 10-sweep launch (profiles/ncu_coarse_gs_rows_config5.md)
+    "config5": {"split_tc": 6.86e9, "tc3": 31.1e9, "coarse_gs": 19.76e9},
+    "config2": {},
 }
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
 ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
