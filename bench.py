@@ -573,45 +573,116 @@ def adjoint_extra(local, torch):
             "iterations": sta.iterations, "relres": sta.relres, "response": R}
 
 
-def batch_extra(local, torch, nprob):
-    """The first problems of the 256-problem batch of uneven 2D problems, each
-    on its own context and stream, autotuned, V-cycles replayed from captured
-    graphs, solved concurrently (mixed, 1e-8), and one after another."""
+def batch_extra(local, torch, nprob, wave=16):
+    """The 256-problem batch of uneven 2D problems (n = 16..96 cells per axis,
+    levels 1..3, per-cell lognormal sigma_t, own g and order), in waves of
+    `wave` problems: each wave's contexts are set up (block inverses on the
+    GPU), solved concurrently by amgt_solve_batch (each problem on its own
+    stream, V-cycles replayed from captured graphs; a first solve captures
+    them), then solved one after another for comparison.  Times are sums over
+    the waves of the timed solves only."""
     from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_GRAPHS,
                                         amgt_solve_batch, context_from_problem)
     probs = W.config4_batch()[:nprob]
-    bstreams = [torch.cuda.Stream() for _ in probs]
-    bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
-            for p, s in zip(probs, bstreams)]
-    t0 = time.perf_counter()
-    tunes = [c.amgt_autotune(3) for c in bctx]
-    t_tune = time.perf_counter() - t0
-    for c in bctx:
-        c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
-    bpsi = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64) for c in bctx]
-    bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
-    amgt_solve_batch(bctx, bpsi, tol=1e-8)  # warm-up: captures the graphs
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    bst = amgt_solve_batch(bctx, bpsi, tol=1e-8)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    for c, p in zip(bctx, bpsi):
-        c.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=p, phi=None,
-                     device_ptrs=True)
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    dof_its = sum(d * st.iterations for d, st in zip(bdof, bst))
-    for c in bctx:
-        c.close()
-    return {"workload": f"first {len(probs)} problems of the 256-problem batch (2D, n in 16..96, "
-                        f"level 1..3, per-cell lognormal sigma_t, N = 2 level + 4)",
-            "problems": len(probs), "unknowns": sum(bdof), "value": dof_its / t_batch / 1e9,
-            "unit": "GDOF/s", "time_to_tol_s": t_batch, "sequential_time_to_tol_s": t_seq,
-            "max_relres": max(st.relres for st in bst),
-            "iterations": [st.iterations for st in bst], "autotune_s": t_tune,
-            "tuned": [list(t[:3]) for t in tunes]}
+    t_conc = t_seq = t_setup = 0.0
+    dof_its = 0
+    unknowns = 0
+    iters, maxrel = [], 0.0
+    for w0 in range(0, len(probs), wave):
+        part = probs[w0:w0 + wave]
+        bstreams = [torch.cuda.Stream() for _ in part]
+        t0 = time.perf_counter()
+        bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
+                for p, s in zip(part, bstreams)]
+        bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
+        torch.cuda.synchronize()
+        t_setup += time.perf_counter() - t0
+        for c in bctx:
+            c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
+        bpsi = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64)
+                for c in bctx]
+        amgt_solve_batch(bctx, bpsi, tol=1e-8)          # warm-up: captures the graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bst = amgt_solve_batch(bctx, bpsi, tol=1e-8)
+        torch.cuda.synchronize()
+        t_conc += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for c, p in zip(bctx, bpsi):
+            c.amgt_solve(tol=1e-8, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED, psi=p, phi=None,
+                         device_ptrs=True)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+        dof_its += sum(d * st.iterations for d, st in zip(bdof, bst))
+        unknowns += sum(bdof)
+        iters += [st.iterations for st in bst]
+        maxrel = max(maxrel, max(st.relres for st in bst))
+        for c in bctx:
+            c.close()
+        del bpsi
+        torch.cuda.empty_cache()
+    return {"workload": f"{len(probs)} problems of the uneven 2D batch (n in 16..96, level "
+                        f"1..3, per-cell lognormal sigma_t, N = 2 level + 4), waves of {wave}",
+            "problems": len(probs), "unknowns": unknowns, "value": dof_its / t_conc / 1e9,
+            "unit": "GDOF/s", "time_to_tol_s": t_conc, "sequential_time_to_tol_s": t_seq,
+            "concurrency_speedup": t_seq / t_conc, "setup_s": t_setup, "max_relres": maxrel,
+            "iterations": iters}
+
+
+# the paper's Table 1, Lin basis, level 3 (Sec. 5.1): Krylov (BiCGStab)
+# iterations to 1e-8, single grid (SG) and V(1,1) with N_r = 1, 2, 3
+TABLE1 = {4: {"SG": 44, 1: 4, 2: 4}, 8: {"SG": 124, 1: 11, 2: 8, 3: 4},
+          16: {"SG": 284, 1: 31, 2: 22, 3: 22}}
+
+
+def run_table1(args):
+    """Context run of the paper's Table 1 set-up (workloads.table1_cube): FP64
+    BiCGStab to relres 1e-8 on the GPU, single grid (sweep preconditioner)
+    and V(1,1) multigrid with the reduced coarse orders, iteration counts
+    beside the paper's.  Context only: the coarse solve and the absorption
+    are readings (see workloads.table1_cube)."""
+    import torch
+    from paper_2010_04559_gb300 import (AMGT_MODE_F64, AMGT_PREC_MG, AMGT_PREC_SWEEP,
+                                        AMGT_TUNE_FP64_SCATTER, context_from_problem)
+    from paper_2010_04559_gb300 import build as _b
+    _b.build()
+    out = []
+    for N in args.table1_orders:
+        runs = [("SG", 2)] + [(nr, nr) for nr in (1, 2, 3) if nr in TABLE1.get(N, {})]
+        for label, nr in runs:
+            prob = W.table1_cube(N, Nr=nr)
+            if label == "SG":
+                prob["mg"] = None
+            stream = torch.cuda.Stream()
+            t0 = time.perf_counter()
+            ctx = context_from_problem(prob, device=0, stream=stream.cuda_stream)
+            ctx.amgt_set_tuning(AMGT_TUNE_FP64_SCATTER, 2)
+            ns, na = ctx.amgt_query_sizes(0)
+            t_set = time.perf_counter() - t0
+            psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+            phi = torch.empty(ns, device="cuda", dtype=torch.float64)
+            with torch.cuda.stream(stream):
+                t0 = time.perf_counter()
+                _, _, st, _ = ctx.amgt_solve(
+                    tol=1e-8, maxit=2000, precond=AMGT_PREC_SWEEP if label == "SG" else AMGT_PREC_MG,
+                    mode=AMGT_MODE_F64, psi=psi, phi=phi, device_ptrs=True,
+                    allow_not_converged=True, krylov=1)
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+            ctx.close()
+            del psi, phi
+            torch.cuda.empty_cache()
+            rec = {"N": N, "run": "SG" if label == "SG" else f"V(1,1) N_r={nr}",
+                   "iterations": st.iterations, "paper_iterations": TABLE1[N][label],
+                   "relres": st.relres, "solve_s": t, "setup_s": t_set}
+            log(json.dumps(rec))
+            out.append(rec)
+    line = {"table1": out, "workload": "5 cm cube, 30^3 Q1 hexes, uniform isotropic unit "
+            "source, vacuum, FP-equivalent moments alpha = 1 (sigma_t = sigma_s0 = N(N+1)/2, "
+            "no absorption), Lin level 3 (512 patches), BiCGStab FP64 to 1e-8, multigrid down "
+            "to level 0 with 30 coarse Gauss-Seidel sweeps", "context_only": True}
+    print(json.dumps(line))
+    return 0
 
 
 def run_profile(args):
@@ -689,13 +760,18 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the FP64 arm, the 128x128 workload, the adjoint and the batch")
     ap.add_argument("--graphs", type=int, default=1, help="V-cycle graph replay (1) or not (0)")
-    ap.add_argument("--batch", type=int, default=32,
-                    help="problems of the uneven 2D batch solved concurrently (0: skip)")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="problems of the uneven 2D batch, solved in concurrent waves (0: skip)")
     ap.add_argument("--n", type=int, default=128, help="cells per axis of --profile's workload")
     ap.add_argument("--profile", choices=["solve", "solve5", "sweeps", "gs", "gs5", "gemm5",
                                           "tc3_5", "split5"],
                     default=None, help="one launch of a hot kernel, and exit (for ncu)")
+    ap.add_argument("--table1", action="store_true",
+                    help="context run of the paper's Table 1 set-up (iteration counts), and exit")
+    ap.add_argument("--table1-orders", type=int, nargs="*", default=[4, 8, 16])
     args = ap.parse_args()
+    if args.table1:
+        return run_table1(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:

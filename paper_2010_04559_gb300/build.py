@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU = ["capi.cu", "kernels_transport.cu", "kernels_gemm.cu", "kernels_blas.cu",
       "kernels_gs.cu", "kernels_gs_rows.cu", "kernels_gs_tc.cu", "kernels_tc.cu", "kernels_adjoint.cu",
-      "kernels_split64.cu", "kernels_tc3.cu"]
+      "kernels_split64.cu", "kernels_tc3.cu", "kernels_setup.cu"]
 CPP = ["setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

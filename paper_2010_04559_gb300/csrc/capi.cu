@@ -234,7 +234,7 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
                  const std::vector<double>& Xt = {}, const std::vector<double>& fdeg = {}) {
   TRY(upload(ctx, K0, &s.K0));
   TRY(upload(ctx, B, &s.B));
-  TRY(upload(ctx, Kinv, &s.Kinv));
+  if (!Kinv.empty()) TRY(upload(ctx, Kinv, &s.Kinv));
   TRY(upload(ctx, L.mesh.A, &s.Aax));
   if (!Ginv.empty()) TRY(upload(ctx, Ginv, &s.Ginv));
   TRY(upload(ctx, X, &s.X));
@@ -246,6 +246,43 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
   if (!tblk.empty()) TRY(upload(ctx, tblk, &s.tblk));
   if (!Xt.empty()) TRY(upload(ctx, Xt, &s.Xt));
   if (!fdeg.empty()) TRY(upload(ctx, fdeg, &s.fdeg));
+  return AMGT_OK;
+}
+
+// Block inverses of level Lv on the GPU from its uploaded K0, B and S_qq:
+// Kinv = (K0_q + sigma_t B_q)^-1 per material and patch, and on the coarsest
+// level Ginv = (K0_q + sigma_t B_q - sigma_s N (x) S_qq)^-1; FP32 copies.
+int device_block_inverses(amgt_ctx* ctx, Level& Lv, bool coarsest) {
+  const int s = ctx->q1.s, a = Lv.mesh.a, P = Lv.mesh.P, sa = s * a;
+  const size_t nblk = (size_t)ctx->nmat * P * sa * sa;
+  int* sing = ctx->d_setup_flag;
+  if (!sing) {
+    TRY(dalloc(ctx, 1, &sing));
+    ctx->d_setup_flag = sing;
+  }
+  CK(cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream));
+  for (int kind = 0; kind < (coarsest ? 2 : 1); ++kind) {
+    double* out64;
+    float* out32;
+    TRY(dalloc(ctx, nblk, &out64));
+    TRY(dalloc(ctx, nblk, &out32));
+    CK(launch_invert_blocks(ctx->geom, kind, ctx->nmat, P, s, a, Lv.d64.K0, Lv.d64.B,
+                            Lv.d64.Sqq, nullptr, 0, nullptr, nullptr, 0, 0, ctx->d_mat_st,
+                            ctx->d_mat_ss, ctx->d_mat_f, out64, sing, ctx->stream));
+    launch_convert<double, float>((long long)nblk, out64, out32, ctx->stream);
+    CK(cudaGetLastError());
+    if (kind == 0) {
+      Lv.d64.Kinv = out64;
+      Lv.d32.Kinv = out32;
+    } else {
+      Lv.d64.Ginv = out64;
+      Lv.d32.Ginv = out32;
+    }
+  }
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h) return fail(ctx, AMGT_ERR_ARG, "singular transport or Gauss-Seidel block");
   return AMGT_OK;
 }
 
@@ -273,7 +310,8 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
   if (Emax > 384 || (size_t)ctx->nmat * Lv.ndir * Emax * Emax * sizeof(double) > ((size_t)8 << 30))
     return AMGT_OK;
   std::vector<double> SLD((size_t)Lv.ndir * Jmax * Jmax, 0.0);
-  std::vector<double> TinvT((size_t)ctx->nmat * Lv.ndir * Emax * Emax, 0.0);
+  const bool dev_inv = Emax <= invert_blocks_max();
+  std::vector<double> TinvT(dev_inv ? 0 : (size_t)ctx->nmat * Lv.ndir * Emax * Emax, 0.0);
   for (int d = 0; d < Lv.ndir; ++d) {
     const int qb = Lv.dir_begin[d], J = (Lv.dir_end[d] - qb) * a, E = s * J;
     double* sl = &SLD[(size_t)d * Jmax * Jmax];
@@ -287,7 +325,7 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
         for (int kk = 0; kk < nm; ++kk) acc += xa[kk] * F[kk] * xb[kk];
         sl[j * Jmax + j2] = acc;
       }
-    if (E == 0) continue;
+    if (E == 0 || dev_inv) continue;
     std::atomic<int> singular{0};
     parallel_for(ctx->nmat, [&](long long mi) {
       const int mt = (int)mi;
@@ -317,10 +355,36 @@ int build_gs_blocks(amgt_ctx* ctx, Level& Lv, const std::vector<double>& K0,
     });
     if (singular) return fail(ctx, AMGT_ERR_ARG, "singular direction-blocked Gauss-Seidel matrix");
   }
-  TRY(upload(ctx, TinvT, &Lv.d64.TinvT));
-  TRY(upload(ctx, TinvT, &Lv.d32.TinvT));
   TRY(upload(ctx, SLD, &Lv.d64.SLD));
   TRY(upload(ctx, SLD, &Lv.d32.SLD));
+  if (!dev_inv) {
+    TRY(upload(ctx, TinvT, &Lv.d64.TinvT));
+    TRY(upload(ctx, TinvT, &Lv.d32.TinvT));
+    return AMGT_OK;
+  }
+  // on the GPU: one block per (material, direction)
+  const size_t n = (size_t)ctx->nmat * Lv.ndir * Emax * Emax;
+  double* t64;
+  float* t32;
+  TRY(dalloc(ctx, n, &t64));
+  TRY(dalloc(ctx, n, &t32));
+  int* sing = ctx->d_setup_flag;
+  if (!sing) {
+    TRY(dalloc(ctx, 1, &sing));
+    ctx->d_setup_flag = sing;
+  }
+  CK(cudaMemsetAsync(sing, 0, sizeof(int), ctx->stream));
+  CK(launch_invert_blocks(ctx->geom, 2, ctx->nmat, Lv.mesh.P, s, a, Lv.d64.K0, Lv.d64.B,
+                          Lv.d64.Sqq, Lv.d64.SLD, Lv.ndir, Lv.d_dbeg, Lv.d_dend, Jmax, Emax,
+                          ctx->d_mat_st, ctx->d_mat_ss, ctx->d_mat_f, t64, sing, ctx->stream));
+  launch_convert<double, float>((long long)n, t64, t32, ctx->stream);
+  CK(cudaGetLastError());
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, sing, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h) return fail(ctx, AMGT_ERR_ARG, "singular direction-blocked Gauss-Seidel matrix");
+  Lv.d64.TinvT = t64;
+  Lv.d32.TinvT = t32;
   return AMGT_OK;
 }
 
@@ -544,6 +608,8 @@ int build(amgt_ctx* ctx) {
   ctx->tc3_bytes = 0;
   ctx->d_grad = nullptr;
   ctx->grad_bytes = 0;
+  ctx->d_setup_flag = nullptr;
+  ctx->d_fid = nullptr;
 
   const int dim = ctx->dim;
   double h[3] = {1, 1, 1};
@@ -606,6 +672,9 @@ int build(amgt_ctx* ctx) {
   }
   ctx->nmat = (int)ctx->mat_st.size();
 
+  TRY(upload(ctx, ctx->mat_st, &ctx->d_mat_st));
+  TRY(upload(ctx, ctx->mat_ss, &ctx->d_mat_ss));
+  TRY(upload(ctx, ctx->mat_f, &ctx->d_mat_f));
   // angular hierarchy
   const int L = max_level(ctx->paths);
   const int nl = ctx->nlevels;
@@ -689,9 +758,13 @@ int build(amgt_ctx* ctx) {
     if (nblk * sizeof(double) > (size_t)48 << 30)
       return fail(ctx, AMGT_ERR_UNSUPPORTED,
                   "too many distinct (sigma_t, sigma_s) pairs for per-material block inverses");
-    std::vector<double> Kinv(nblk), Ginv;
+    std::vector<double> Kinv, Ginv;
     std::atomic<int> singular{0};
-    parallel_for((long long)ctx->nmat * P, [&](long long i) {
+    // the block inverses are built on the GPU (kernels_setup.cu) unless the
+    // blocks are larger than it takes
+    const bool dev_inv = sa <= invert_blocks_max();
+    if (!dev_inv) Kinv.resize(nblk);
+    if (!dev_inv) parallel_for((long long)ctx->nmat * P, [&](long long i) {
       const int mt = (int)(i / P), q = (int)(i % P);
       std::vector<double> blk(sa * sa);
       for (int e = 0; e < sa * sa; ++e)
@@ -699,7 +772,7 @@ int build(amgt_ctx* ctx) {
       if (!invert(sa, blk.data(), &Kinv[((size_t)mt * P + q) * sa * sa])) singular = 1;
     });
     if (singular) return fail(ctx, AMGT_ERR_ARG, "singular transport block (sigma_t <= 0?)");
-    if (k == nl - 1) {
+    if (k == nl - 1 && !dev_inv) {
       Ginv.resize(nblk);
       // kron(N, S_qq) per shape and patch
       std::vector<double> NSq((size_t)nf * P * sa * sa, 0.0);
@@ -739,6 +812,7 @@ int build(amgt_ctx* ctx) {
     const std::vector<double> fdeg = nf > 1 ? Fall : std::vector<double>{};
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64, Xt, fdeg));
     TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32, Xt, fdeg));
+    if (dev_inv) TRY(device_block_inverses(ctx, Lv, k == nl - 1));
     // the direction-blocked Gauss-Seidel tables assume one moment shape; with
     // several, the per-patch kernel (shape-indexed tables) runs
     if (k == nl - 1 && nf == 1) TRY(build_gs_blocks(ctx, Lv, K0, B, X, F));

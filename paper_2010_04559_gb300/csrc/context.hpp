@@ -123,7 +123,9 @@ struct amgt_ctx {
   int *d_mat = nullptr, *d_cells = nullptr, *d_level_off = nullptr, *d_bkind = nullptr,
       *d_fid = nullptr;
   double *d_sigt = nullptr, *d_sigs = nullptr, *d_q = nullptr, *d_bval = nullptr, *d_mu = nullptr,
-         *d_mf = nullptr, *d_brange = nullptr;
+         *d_mf = nullptr, *d_brange = nullptr, *d_mat_st = nullptr, *d_mat_ss = nullptr;
+  int* d_mat_f = nullptr;
+  int* d_setup_flag = nullptr;  // set-up kernels' error flag
   float *d_sigt32 = nullptr, *d_sigs32 = nullptr, *d_Nm32 = nullptr;
   int nlev_wave = 0;
   // scratch

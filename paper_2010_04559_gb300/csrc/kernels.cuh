@@ -117,6 +117,19 @@ void launch_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, 
                  const GemmEpi& epi, cudaStream_t st);
 cudaError_t preload_gemm();
 
+// Set-up block inverses on the GPU (kernels_setup.cu), FP64: kind 0
+// (K0_q + sigma_t B_q)^-1 and kind 1 (... - sigma_s N (x) S_qq)^-1 per material
+// and patch into out[nmat][P][sa][sa]; kind 2 the direction-blocked Gauss-
+// Seidel inverses per material and direction, transposed and zero-padded
+// into out[nmat][ndir][Emax][Emax].  Matrices up to invert_blocks_max().
+int invert_blocks_max();
+cudaError_t launch_invert_blocks(const Geom& g, int kind, int nmat, int P, int s, int a,
+                                 const double* K0, const double* B, const double* Sqq,
+                                 const double* SLD, int ndir, const int* dir_begin,
+                                 const int* dir_end, int Jmax, int Emax, const double* mat_st,
+                                 const double* mat_ss, const int* mat_f, double* out,
+                                 int* singular, cudaStream_t st);
+
 template <class T>
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
                      const int* cend, const T* blk, const T* rf, T* rc, cudaStream_t st);

@@ -77,3 +77,36 @@ def test_autotune_keeps_the_answer_and_caches():
     assert ctx2.amgt_autotune(3) == (G, stages, gs, 1)
     ctx.close()
     ctx2.close()
+
+
+def test_batch_members_match_the_oracle():
+    """Members of the 256-problem batch (n = 16..22 cells per axis, angular
+    levels 1-3, per-cell sigma_t, their own g and order) solved together by
+    amgt_solve_batch (mixed precision, autotuned, graph-replayed V-cycles),
+    each against the oracle's solution of the same problem (GMRES with the
+    sweep preconditioner to 1e-12: the solution does not depend on the
+    preconditioner)."""
+    from oracle import angular, gmres, transport
+    from paper_2010_04559_gb300 import (AMGT_TUNE_GRAPHS, amgt_solve_batch,
+                                        context_from_problem)
+    allp = W.config4_batch()
+    picks = [75, 95, 141, 18]                  # levels 1, 1, 3, 3; n = 19, 22, 16, 19
+    probs = [allp[i] for i in picks]
+    streams = [torch.cuda.Stream() for _ in probs]
+    ctxs = [context_from_problem(p, device=0, stream=s.cuda_stream)
+            for p, s in zip(probs, streams)]
+    for c in ctxs:
+        c.amgt_autotune(3)
+        c.amgt_set_tuning(AMGT_TUNE_GRAPHS, 1)
+    psis = [torch.empty(c.amgt_query_sizes(0), device="cuda", dtype=torch.float64) for c in ctxs]
+    for _ in range(2):                         # the first solve captures the graphs
+        stats = amgt_solve_batch(ctxs, psis, tol=1e-11)
+    torch.cuda.synchronize()
+    for p, psi, st in zip(probs, psis, stats):
+        assert st.relres < 1e-11
+        T = transport.Transport(p, angular.AngularMesh(angular.uniform_paths(p["level"]), "lin"))
+        xo, _, _, rel = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-12, 30, 3000)
+        assert rel < 1e-12
+        assert np.linalg.norm(psi.cpu().numpy() - xo) / np.linalg.norm(xo) < 1e-6
+    for c in ctxs:
+        c.close()

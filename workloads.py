@@ -200,6 +200,24 @@ def random_vector(shape, seed_k, dtype=np.float64):
     return _rng(5000 + seed_k).standard_normal(shape).astype(dtype)
 
 
+def table1_cube(N, level=3, n=30, basis="lin", nlevels=None, Nr=2, coarse_sweeps=30):
+    """The paper's preliminary test problem (Sec. 5.1, Table 1): a 5 x 5 x 5 cm
+    cube of n^3 cells, uniform isotropic unit source, vacuum on all sides,
+    Fokker-Planck-equivalent moments sigma_{s,n} = alpha/2 (N(N+1) - n(n+1))
+    with alpha = 1.  Reading: the transport cross section sigma_t - sigma_{s,1}
+    = 1 with no absorption, so sigma_t = sigma_{s,0} = N(N+1)/2 and
+    sigma_t - sigma_{s,1} = alpha = 1.  Multigrid down to angular level 0 with
+    order Nr below the finest level; the paper solves its coarsest level to
+    1e-5, here `coarse_sweeps` block Gauss-Seidel sweeps stand in for that."""
+    s0, f = fp_moments(1.0, N)
+    C = n ** 3
+    nl = level + 1 if nlevels is None else nlevels
+    mg = dict(nlevels=nl, Nr=[N] + [min(N, Nr)] * (nl - 1), nu_pre=1, nu_post=1,
+              coarse_sweeps=coarse_sweeps)
+    return problem(3, (n, n, n), np.full(C, s0), np.full(C, s0), N, f, np.ones(C), level,
+                   basis=basis, hi=(5.0, 5.0, 5.0), mg=mg)
+
+
 def config5_beam(n=256, level=4, N=64, nlevels=4, Nr=12, g=0.98):
     """2D unit square, n x n cells, sigma_t = 5, sigma_s = 4.95, HG g at order
     N, a normally incident pencil beam of unit strength over the whole low-x
