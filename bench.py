@@ -74,7 +74,7 @@ TRAFFIC = {
     # split_tc, tc3: captured at 16384 rows (profiles/ncu_split_gemm_config5shape.md,
     # ncu_tc3_gemm_config5shape.md), scaled to the mean launch's rows (52428 and
     # 87381); coarse_gs: one 10-sweep launch (profiles/ncu_coarse_gs_rows_config5.md)
-    "config5": {"split_tc": 6.86e9, "tc3": 31.1e9, "coarse_gs": 19.76e9},
+    "config5": {"split_tc": 3.72e9, "tc3": 21.1e9, "coarse_gs": 19.76e9},
     "config2": {},
 }
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate

@@ -147,6 +147,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Output tile t -> (row, column) tile origin.  Tiles run in groups of kGroupN
+// column tiles, the column tile fastest within a group: the CTAs working at
+// the same time share the k-chunks of ~152 / kGroupN row tiles of A and of
+// kGroupN column tiles of B, so both stay in L2 while they are read
+// (with every column tile in one group, all of B streams past each wave of
+// row tiles and is re-read from DRAM).
+constexpr int kGroupN = 8;
+__device__ __forceinline__ void tile_origin(int t, int m_tiles, int n_tiles, int& m0, int& n0) {
+  const int gsz = kGroupN * m_tiles;
+  const int grp = t / gsz, r = t - grp * gsz;
+  const int gw = min(kGroupN, n_tiles - grp * kGroupN);
+  m0 = (r / gw) * BM;
+  n0 = (grp * kGroupN + r % gw) * BN;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -239,7 +254,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       // TMA producer: the ring runs continuously across this CTA's tiles
       int g = 0;
       for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
-        const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+        int m0, n0;
+        tile_origin(t, m_tiles, n_tiles, m0, n0);
         for (int k = 0; k < kiters; ++k, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -310,7 +326,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const bool vec = (args.N & 3) == 0;
     int i = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-      const int m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+      int m0, n0;
+      tile_origin(t, m_tiles, n_tiles, m0, n0);
       const int buf = i & 1;
       const uint32_t use = (uint32_t)(i >> 1) & 1u;
       bool ok = mbar_wait(&accf[buf], use, abort_flag);
