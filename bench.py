@@ -699,11 +699,29 @@ def run_profile(args):
         prob = W.config5_beam(n=64)
     elif args.profile in ("solve5", "gs5"):
         prob = W.config5_beam()
+    elif args.profile == "sweep3d":
+        prob = W.config3_cube(n=args.n if args.n != 128 else 32)
     else:
         prob = W.config2_checkerboard(n=args.n)
+    t0 = time.perf_counter()
     ctx = context_from_problem(prob, device=0)
     ns, na = ctx.amgt_query_sizes(0)
-    if args.profile == "gs5":
+    print(f"set-up {time.perf_counter() - t0:.2f} s")
+    if args.profile == "sweep3d":
+        # the 32^3 cube (32768 materials, level 2): FP32 then FP64 sweeps, twice
+        for td in (torch.float32, torch.float64):
+            x = torch.randn((ns, na), device="cuda", dtype=td)
+            y = torch.empty_like(x)
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ctx.amgt_op_sweep(0, x, y)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            print(f"3D sweep {td}: {dt * 1e3:.2f} ms, {2 * x.element_size() * ns * na / dt / 1e9:.0f} "
+                  f"GB/s algorithmic")
+            del x, y
+    elif args.profile == "gs5":
         # the headline's coarse Gauss-Seidel launch (level 1: 32 patches, 10 sweeps)
         nsc, nac = ctx.amgt_query_sizes(3)
         fc = torch.randn((nsc, nac), device="cuda", dtype=torch.float32)
@@ -764,7 +782,7 @@ def main():
                     help="problems of the uneven 2D batch, solved in concurrent waves (0: skip)")
     ap.add_argument("--n", type=int, default=128, help="cells per axis of --profile's workload")
     ap.add_argument("--profile", choices=["solve", "solve5", "sweeps", "gs", "gs5", "gemm5",
-                                          "tc3_5", "split5"],
+                                          "tc3_5", "split5", "sweep3d"],
                     default=None, help="one launch of a hot kernel, and exit (for ncu)")
     ap.add_argument("--table1", action="store_true",
                     help="context run of the paper's Table 1 set-up (iteration counts), and exit")

@@ -271,7 +271,13 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         row to the next warp through a shared ring with a
  *                         step counter; a wait gives up after 2 s and
  *                         reports AMGT_ERR_DEVICE_TIMEOUT at the next
- *                         amgt_sync); cases outside 2's scope run 1.
+ *                         amgt_sync); cases outside 2's scope run 1.  In
+ *                         3D, 0 and 2 run every direction and patch in one
+ *                         cooperative launch, level by level with a grid
+ *                         barrier between wavefront levels (a barrier that
+ *                         waits 2 s reports AMGT_ERR_DEVICE_TIMEOUT at the
+ *                         next amgt_sync), and 1 the level kernel with one
+ *                         block per direction and patch group.
  *   AMGT_TUNE_F32_SCATTER the FP32 scatter of the mixed solve's inner
  *                         operator: 0 auto (the FP16 three-product tensor-
  *                         core form of AMGT_F32_TC3 where it applies), 1 the
@@ -339,7 +345,11 @@ int amgt_op_source(amgt_ctx* ctx, int level, int dtype, void* f);
 /* psi = L^-1 b: upwind sweep over the cells per sweep direction, one block
  * solve per (cell, patch) (Sec. 3).  Exact on these meshes. */
 int amgt_op_sweep(amgt_ctx* ctx, int level, int dtype, const void* b, void* psi);
-/* y = L x (Eq. complete, left-hand side with upwind face fluxes). */
+/* y = L x (Eq. complete, left-hand side with upwind face fluxes).  dtype
+ * AMGT_F64_SPLIT: double buffers, L x in double-float arithmetic on the FP32
+ * units (hi + lo FP32 parts, error-free sums and products; relative error
+ * ~1e-13 of the terms), the form the mixed solve's refinement residuals use
+ * with the split-form scatter. */
 int amgt_op_apply_L(amgt_ctx* ctx, int level, int dtype, const void* x, void* y);
 /* y = S x: Q_[j,q]lm = sum N_li sum_n sigma_{s,n} X X phi (Sec. 4.2), with the
  * level's scatter order.  dtype AMGT_F32_BF16TC: float buffers, contraction

@@ -350,9 +350,10 @@ class Context:
         return self._check(self.lib.amgt_op_sweep(self.h, level, self._dtype_code(b),
                                                   _dptr(b), _dptr(psi)))
 
-    def amgt_op_apply_L(self, level, x, y):
+    def amgt_op_apply_L(self, level, x, y, tc=False):
+        """tc=True with float64 buffers: double-float arithmetic (AMGT_F64_SPLIT)."""
         self._req(x, y)
-        return self._check(self.lib.amgt_op_apply_L(self.h, level, self._dtype_code(x),
+        return self._check(self.lib.amgt_op_apply_L(self.h, level, self._dtype_code(x, tc),
                                                     _dptr(x), _dptr(y)))
 
     def amgt_op_scatter(self, level, x, y, tc=False):

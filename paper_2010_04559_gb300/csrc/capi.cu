@@ -1284,7 +1284,8 @@ int sweep_impl(amgt_ctx* ctx, int k, const T* b, T* psi) {
   KernelTimer kt(ctx, AMGT_KT_SWEEP, 2.0 * sizeof(T) * L.nsdof * L.nadof());
   launch_sweep<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx),
                   schedule(ctx, k), b, psi, L.sweep_G, ctx->nmat, chunk, ctx->sweep_stages,
-                  ctx->sweep_kernel, ctx->d_status, ctx->test_sweep_hold, ctx->stream);
+                  ctx->sweep_kernel, ctx->d_status, ctx->test_sweep_hold,
+                  reinterpret_cast<unsigned*>(ctx->d_status + 12), ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1297,6 +1298,17 @@ int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
                  (beta != T(0) ? 3.0 : 2.0) * sizeof(T) * L.nsdof * L.nadof());
   launch_apply_L<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)), cell_data(ctx), alpha,
                     beta, x, y, ctx->stream);
+  CK(cudaGetLastError());
+  return AMGT_OK;
+}
+
+// y = alpha L x + beta y in FP64 from double-float arithmetic on the FP32
+// units (relative error ~1e-13 of the terms; kernels_transport.cu)
+int applyL_df(amgt_ctx* ctx, int k, double alpha, double beta, const double* x, double* y) {
+  const Level& L = ctx->lv[k];
+  KernelTimer kt(ctx, AMGT_KT_APPLY_L, (beta != 0.0 ? 3.0 : 2.0) * 8.0 * L.nsdof * L.nadof());
+  launch_apply_L_df(level_geom(ctx, k), level_view<double>(L, L.d64), cell_data(ctx), alpha, beta,
+                    x, y, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -2421,6 +2433,8 @@ int amgt_op_sweep(amgt_ctx* ctx, int level, int dtype, const void* b, void* psi)
 int amgt_op_apply_L(amgt_ctx* ctx, int level, int dtype, const void* x, void* y) {
   if (!ctx) return AMGT_ERR_ARG;
   TRY(check_level(ctx, level));
+  if (dtype == AMGT_F64_SPLIT)
+    return applyL_df(ctx, level, 1.0, 0.0, (const double*)x, (double*)y);
   DISPATCH(dtype, applyL_impl<double>(ctx, level, 1.0, 0.0, (const double*)x, (double*)y),
            applyL_impl<float>(ctx, level, 1.0f, 0.0f, (const float*)x, (float*)y));
 }
@@ -2598,7 +2612,14 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       if (x_zero) {
         CK(cudaMemcpyAsync(r64, b, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
       } else {
-        TRY(applyA_impl<double>(ctx, 0, use_split64(ctx, true), x, r64));
+        // the refinement residual's operator: with the split-form scatter, L x
+        // in double-float arithmetic (both ~1e-13, far below what 1e-8 needs)
+        if (use_split64(ctx, true) && split_applies(ctx, 0)) {
+          TRY(scatter_impl<double>(ctx, 0, 1, x, r64, -1.0, 0.0, nullptr));
+          TRY(applyL_df(ctx, 0, 1.0, 1.0, x, r64));
+        } else {
+          TRY(applyA_impl<double>(ctx, 0, 0, x, r64));
+        }
         launch_axpby<double>(n, 1.0, b, -1.0, r64, ctx->stream);
       }
       double rn;

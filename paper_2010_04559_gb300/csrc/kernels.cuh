@@ -96,12 +96,19 @@ template <class T>
 // test_hold != 0 (tests of the failure path only): in the warp-pipelined form
 // the first warp of each block never publishes its progress and every wait
 // gives up after 10 ms, so the launch ends with status code 7
+// 3D (variant 0 or 2): the grid-wide level form when a cooperative launch fits
+// (gbar: two words for its grid barrier; a barrier that waits 2 s records
+// status code 8), else the per-task level kernel
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
                   const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
-                  int* err, int test_hold, cudaStream_t st);
+                  int* err, int test_hold, unsigned* gbar, cudaStream_t st);
 template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
                     const T* x, T* y, cudaStream_t st);
+// the same FP64 L x in double-float arithmetic (hi + lo FP32 parts, ~44 bits;
+// relative error ~1e-13 of the terms) on the FP32 units
+void launch_apply_L_df(const Geom& g, const LevelDev<double>& t, const CellData& cd, double alpha,
+                       double beta, const double* x, double* y, cudaStream_t st);
 // C[M][N] = A[M][K] B[K][N] with epilogue (see kernels_gemm.cu)
 struct GemmEpi {
   int mode;            // 0 store, 1 cell mix: out = alpha*sig_s*Nmix(acc) + beta*out + add

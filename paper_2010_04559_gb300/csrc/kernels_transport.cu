@@ -38,11 +38,66 @@ __device__ __forceinline__ void dir_bits(int d, int neg[3]) {
   }
 }
 
+// Double-float numbers: a value is hi + lo with two FP32 parts (about 44
+// significant bits), added and multiplied with error-free transformations --
+// Knuth's two-sum, the fast two-sum for |a| >= |b|, and the exact product of
+// two floats from one FMA (Dekker's product written with fmaf) -- following
+// the double-float arithmetic of Dekker (1971).  Used where an FP64 result is
+// needed to ~1e-13 and GB300's FP32 rate (64x its FP64 rate) pays for the
+// ~10 FP32 operations per multiply-add.
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ DF(int v) : hi((float)v), lo(0.f) {}
+  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit DF(double v) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  }
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return DF(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ DF operator+(const DF& a, const DF& b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  const float t = __fadd_rn(a.lo, b.lo);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t));
+}
+__device__ __forceinline__ DF operator-(const DF& a) { return DF(-a.hi, -a.lo); }
+__device__ __forceinline__ DF operator*(const DF& a, const DF& b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF& operator+=(DF& a, const DF& b) {
+  a = a + b;
+  return a;
+}
+
+// R: the arithmetic (T itself, or DF for T = double); loads and the result
+// convert between T and R
+template <class R, class T>
+__device__ __forceinline__ R to_r(T v) {
+  return R(v);
+}
+template <class T, class R>
+__device__ __forceinline__ T from_r(R v) {
+  return (T)v;
+}
+
 // Adds sign * sum over inflow faces of kron(Fnb_f, A_{f,q}) psi_nb to acc.
-template <class T, int DIM, int A>
+template <class T, int DIM, int A, class R = T>
 __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__ Aax, int q,
                                             const T* __restrict__ psi, int c, const int jj[3],
-                                            const int neg[3], T sign, T* acc) {
+                                            const int neg[3], R sign, R* acc) {
   constexpr int S = 1 << DIM;
   const int nadof = g.nadof;
   const int stride[3] = {1, g.nx, g.nx * g.ny};
@@ -52,20 +107,20 @@ __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__
     const int own = neg[xi];    // side bit of this cell's inflow face
     const int cn = c + (own ? stride[xi] : -stride[xi]);
     const T* An = Aax + ((size_t)q * 3 + xi) * A * A;
-    const T nsgn = own ? T(1) : T(-1);  // outward normal component
+    const R nsgn = own ? R(1) : R(-1);  // outward normal component
     const T* pn = psi + (long long)cn * S * nadof + q * A;
-    T tv[S / 2][A];
+    R tv[S / 2][A];
 #pragma unroll
     for (int j = 0; j < S / 2; ++j) {
       const int i = fnode(j, xi, 1 - own);
-      T v[A];
+      R v[A];
 #pragma unroll
-      for (int d = 0; d < A; ++d) v[d] = pn[(long long)i * nadof + d];
+      for (int d = 0; d < A; ++d) v[d] = to_r<R>(pn[(long long)i * nadof + d]);
 #pragma unroll
       for (int m = 0; m < A; ++m) {
-        T sacc = T(0);
+        R sacc = R(0);
 #pragma unroll
-        for (int d = 0; d < A; ++d) sacc += An[m * A + d] * v[d];
+        for (int d = 0; d < A; ++d) sacc += to_r<R>(An[m * A + d]) * v[d];
         tv[j][m] = nsgn * sacc;
       }
     }
@@ -74,9 +129,9 @@ __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__
       const int l = fnode(jp, xi, own);
 #pragma unroll
       for (int m = 0; m < A; ++m) {
-        T sacc = T(0);
+        R sacc = R(0);
 #pragma unroll
-        for (int j = 0; j < S / 2; ++j) sacc += T(g.facemass[xi][jp][j]) * tv[j][m];
+        for (int j = 0; j < S / 2; ++j) sacc += to_r<R>((T)g.facemass[xi][jp][j]) * tv[j][m];
         acc[l * A + m] += sign * sacc;
       }
     }
@@ -124,6 +179,133 @@ __global__ void __launch_bounds__(256) sweep_kernel(Geom g, LevelDev<T> t, CellD
       }
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3D sweep over every direction and patch at once.  In rotated coordinates
+// (each direction's axes flipped so that it sweeps from the origin) the
+// wavefront levels w = jx + jy + jz are the same for all directions, so one
+// cooperative launch walks the levels with a bounded grid barrier between
+// them and, within a level, hands out the (cell, patch) items of every
+// direction to warps: the patch fixes the direction and so the cell's flips.
+// A warp solves one item: lane r = l A + m (r < S A) forms its entry of the
+// right-hand side (b minus the upwind faces' coupling) and then its entry of
+// the block solve, row r of the block inverse (read as 16-byte chunks) times
+// the right-hand side gathered by shuffles.  The level kernel below runs one
+// block per (direction, patch group) and leaves most of the GPU idle.
+constexpr int kSweep3Threads = 512;
+
+__device__ __forceinline__ void grid_sync_bounded(unsigned* bar, unsigned nblocks, unsigned& gen,
+                                                  int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicExch(bar + 1, gen + 1u);
+    } else {
+      const unsigned long long t0 = gsx::now_ns();
+      unsigned it = 0;
+      while (*vgen == gen) {
+        if ((++it & 255u) == 0) {
+          if (*reinterpret_cast<volatile int*>(err) != 0) break;
+          if (gsx::now_ns() - t0 > 2000000000ULL) {
+            atomicExch(err, 8);  // a grid barrier of the 3D sweep gave up
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+  }
+  gen += 1u;
+  __syncthreads();
+}
+
+template <class T, int A>
+__global__ void __launch_bounds__(kSweep3Threads) sweep3d_grid_kernel(
+    Geom g, LevelDev<T> t, CellData cd, Schedule sc, const T* __restrict__ b,
+    T* __restrict__ psi, unsigned* __restrict__ gbar, int* __restrict__ err) {
+  constexpr int S = 8;
+  constexpr int SA = S * A;
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int P = g.P, nadof = g.nadof;
+  const bool act = lane < SA;
+  const int r = act ? lane : 0;
+  const int l = r / A, m = r - (r / A) * A;
+  const int stride[3] = {1, g.nx, g.nx * g.ny};
+  unsigned gen = 0;
+  for (int w = 0; w < sc.nlev; ++w) {
+    const int beg = sc.level_off[w];
+    const long long items = (long long)(sc.level_off[w + 1] - beg) * P;
+    for (long long it = wid; it < items; it += nwarp) {
+      const int k = (int)(it / P);
+      const int q = (int)(it - (long long)k * P);
+      int neg[3];
+      dir_bits<3>(t.pdir[q], neg);
+      const int packed = sc.cells[beg + k];
+      const int jj[3] = {packed & 2047, (packed >> 11) & 2047, packed >> 22};
+      const int ix = neg[0] ? g.nx - 1 - jj[0] : jj[0];
+      const int iy = neg[1] ? g.ny - 1 - jj[1] : jj[1];
+      const int iz = neg[2] ? g.nz - 1 - jj[2] : jj[2];
+      const int c = ix + g.nx * (iy + g.ny * iz);
+      T rhs = T(0);
+      if (act) {
+        rhs = b[((long long)c * S + l) * nadof + q * A + m];
+        // upwind faces: the neighbour's trace on the shared face
+#pragma unroll
+        for (int xi = 0; xi < 3; ++xi) {
+          const int own = neg[xi];
+          if (jj[xi] == 0 || ((l >> xi) & 1) != own) continue;
+          const int cn = c + (own ? stride[xi] : -stride[xi]);
+          const T* An = t.Aax + ((size_t)q * 3 + xi) * A * A + m * A;
+          const T* pn = psi + (long long)cn * S * nadof + q * A;
+          const int jp = gsx::fcompress(l, xi);
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < S / 2; ++j) {
+            const int i = gsx::fnode(j, xi, 1 - own);
+            T sacc = T(0);
+#pragma unroll
+            for (int d = 0; d < A; ++d) sacc += An[d] * __ldcg(pn + (long long)i * nadof + d);
+            acc += T(g.facemass[xi][jp][j]) * sacc;
+          }
+          rhs -= (own ? T(1) : T(-1)) * acc;
+        }
+      }
+      // x_r = sum_cc Kinv[r][cc] rhs_cc
+      const T* Ki = t.Kinv + ((size_t)cd.mat[c] * P + q) * SA * SA + (size_t)r * SA;
+      T x = T(0);
+      constexpr int VW = 16 / (int)sizeof(T);
+#pragma unroll
+      for (int cc = 0; cc < SA; cc += VW) {
+        T kv[VW];
+        if constexpr (sizeof(T) == 4 && SA % 4 == 0) {
+          const float4 v = *reinterpret_cast<const float4*>(Ki + cc);
+          kv[0] = v.x; kv[1] = v.y; kv[2] = v.z; kv[3] = v.w;
+        } else if constexpr (sizeof(T) == 8 && SA % 2 == 0) {
+          const double2 v = *reinterpret_cast<const double2*>(Ki + cc);
+          kv[0] = v.x; kv[1] = v.y;
+        } else {
+#pragma unroll
+          for (int u = 0; u < VW; ++u) kv[u] = cc + u < SA ? Ki[cc + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          const T ru = __shfl_sync(0xffffffffu, rhs, (cc + u) < SA ? cc + u : 0);
+          if (cc + u < SA) x += kv[u] * ru;
+        }
+      }
+      if (act) psi[((long long)c * S + l) * nadof + q * A + m] = x;
+    }
+    // the next level reads this level's outputs (other warps, other blocks)
+    if (w + 1 < sc.nlev) grid_sync_bounded(gbar, gridDim.x, gen, err);
   }
 }
 
@@ -765,8 +947,10 @@ __device__ __forceinline__ double nsp<double>(const Geom& g, int e) { return g.N
 template <>
 __device__ __forceinline__ float nsp<float>(const Geom& g, int e) { return g.NmassF[e]; }
 
-template <class T, int DIM, int A>
-__global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
+// three blocks per SM for the 2D FP32 form; two (up to 128 registers, no
+// spills of the wider FP64 / double-float working set) otherwise
+template <class T, int DIM, int A, class R = T>
+__global__ void __launch_bounds__(256, DIM == 2 && sizeof(R) == 4 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
                                                       T alpha, T beta, const T* __restrict__ x,
                                                       T* __restrict__ y) {
   constexpr int S = 1 << DIM;
@@ -783,29 +967,29 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, 
     const int jj[3] = {neg[0] ? g.nx - 1 - ix : ix, neg[1] ? g.ny - 1 - iy : iy,
                        neg[2] ? g.nz - 1 - iz : iz};
     const T* xp = x + (long long)c * S * nadof + q * A;
-    T xv[S][A];
+    R xv[S][A];
 #pragma unroll
     for (int l = 0; l < S; ++l)
 #pragma unroll
-      for (int m = 0; m < A; ++m) xv[l][m] = xp[(long long)l * nadof + m];
-    T acc[SA];
+      for (int m = 0; m < A; ++m) xv[l][m] = to_r<R>(xp[(long long)l * nadof + m]);
+    R acc[SA];
 #pragma unroll
-    for (int r = 0; r < SA; ++r) acc[r] = T(0);
+    for (int r = 0; r < SA; ++r) acc[r] = R(0);
     // streaming: sum_xi G_xi X (A^xi)^T
 #pragma unroll
     for (int xi = 0; xi < DIM; ++xi) {
       const T* Aq = t.Aax + ((size_t)q * 3 + xi) * A * A;
-      T a[A][A];
+      R a[A][A];
 #pragma unroll
       for (int m = 0; m < A; ++m)
 #pragma unroll
-        for (int d = 0; d < A; ++d) a[m][d] = Aq[m * A + d];
-      T t1[S][A];
+        for (int d = 0; d < A; ++d) a[m][d] = to_r<R>(Aq[m * A + d]);
+      R t1[S][A];
 #pragma unroll
       for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int m = 0; m < A; ++m) {
-          T v = T(0);
+          R v = R(0);
 #pragma unroll
           for (int d = 0; d < A; ++d) v += xv[i][d] * a[m][d];
           t1[i][m] = v;
@@ -815,40 +999,40 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) apply_L_kernel(Geom g, 
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const T gli = gax<T>(g, xi, sg, l * S + i);
+          const R gli = to_r<R>(gax<T>(g, xi, sg, l * S + i));
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += gli * t1[i][m];
         }
     }
     // collision: sigma_t N X M^T
     {
-      const T st = (T)cd.sigma_t[c];
+      const R st = to_r<R>((T)cd.sigma_t[c]);
       const T* Mm = t.Mang + (size_t)q * A * A;
-      T t1[S][A];
+      R t1[S][A];
 #pragma unroll
       for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int m = 0; m < A; ++m) {
-          T v = T(0);
+          R v = R(0);
 #pragma unroll
-          for (int d = 0; d < A; ++d) v += xv[i][d] * Mm[m * A + d];
+          for (int d = 0; d < A; ++d) v += xv[i][d] * to_r<R>(Mm[m * A + d]);
           t1[i][m] = st * v;
         }
 #pragma unroll
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const T nli = nsp<T>(g, l * S + i);
+          const R nli = to_r<R>(nsp<T>(g, l * S + i));
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += nli * t1[i][m];
         }
     }
-    upwind_term<T, DIM, A>(g, t.Aax, q, x, c, jj, neg, T(1), acc);
+    upwind_term<T, DIM, A, R>(g, t.Aax, q, x, c, jj, neg, R(1), acc);
     T* out = y + (long long)c * S * nadof + q * A;
 #pragma unroll
     for (int r = 0; r < SA; ++r) {
       T* o = out + (long long)(r / A) * nadof + (r % A);
-      T v = alpha * acc[r];
+      T v = alpha * from_r<T>(acc[r]);
       if (beta != T(0)) v += beta * (*o);
       *o = v;
     }
@@ -866,61 +1050,67 @@ __global__ void source_kernel(Geom g, const T* __restrict__ w, const T* __restri
                               const double* __restrict__ brange,
                               const double* __restrict__ mu, const double* __restrict__ mf,
                               T* __restrict__ f) {
-  const long long total = g.nsdof * g.nadof;
+  // one thread per (cell, patch): the cell's position, emission and boundary
+  // faces once, then its s x a entries
+  const long long total = (long long)g.C * g.P;
   const int a = g.a, s = g.s;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / g.nadof;
-    const int j = (int)(idx - r * g.nadof);
-    const int c = (int)(r / s), l = (int)(r - (long long)c * s);
-    const int q = j / a, m = j - q * a;
-    double v = qsrc[c] / (4.0 * M_PI) * mu[l] * (double)w[j];
+    const int c = (int)(idx / g.P);
+    const int q = (int)(idx - (long long)c * g.P);
+    const double qc = qsrc[c] / (4.0 * M_PI);
     const int ic[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
     const int n[3] = {g.nx, g.ny, g.nz};
     const int o = octant[q];
     const int negb[3] = {(o >> 2) & 1, (o >> 1) & 1, o & 1};
-    for (int xi = 0; xi < g.dim; ++xi) {
-      for (int side = 0; side < 2; ++side) {
-        const int face = 2 * xi + side;
-        if (bkind[face] == 0) continue;
-        if (side == 0 ? ic[xi] != 0 : ic[xi] != n[xi] - 1) continue;
-        if (bkind[face] == 2) {  // pencil beam: S mf_l Psi_m(Omega_b) share_q
-          v += beam[(size_t)face * g.nadof + j] * mf[face * s + l];
-          continue;
-        }
-        if (bkind[face] == 3) {
-          // beam over part of the face: S |Omega_b.n| Psi_m(Omega_b) share_q times
-          // the integral of Phi_l over the cell face and the range, a product
-          // over the tangential axes of integrals of the linear nodal functions
-          // l_0 = 1 - t/h, l_1 = t/h over the overlap [ta, tb] of the cell
-          if (((l >> xi) & 1) != side) continue;
-          double I = 1.0;
-          int k = 0;
-          for (int e = 0; e < g.dim; ++e) {
-            if (e == xi) continue;
-            const double x0 = g.lo[e] + ic[e] * g.h[e];
-            const double lo_ = fmax(x0, brange[face * 4 + 2 * k]);
-            const double hi_ = fmin(x0 + g.h[e], brange[face * 4 + 2 * k + 1]);
-            ++k;
-            if (!(hi_ > lo_)) {
-              I = 0.0;
-              break;
+    for (int l = 0; l < s; ++l) {
+      for (int m = 0; m < a; ++m) {
+        const int j = q * a + m;
+        double v = qc * mu[l] * (double)w[j];
+        for (int xi = 0; xi < g.dim; ++xi) {
+          for (int side = 0; side < 2; ++side) {
+            const int face = 2 * xi + side;
+            if (bkind[face] == 0) continue;
+            if (side == 0 ? ic[xi] != 0 : ic[xi] != n[xi] - 1) continue;
+            if (bkind[face] == 2) {  // pencil beam: S mf_l Psi_m(Omega_b) share_q
+              v += beam[(size_t)face * g.nadof + j] * mf[face * s + l];
+              continue;
             }
-            const double ta = lo_ - x0, tb = hi_ - x0, he = g.h[e];
-            const double i1 = (tb * tb - ta * ta) / (2.0 * he);
-            I *= ((l >> e) & 1) ? i1 : (tb - ta) - i1;
+            if (bkind[face] == 3) {
+              // beam over part of the face: S |Omega_b.n| Psi_m(Omega_b) share_q times
+              // the integral of Phi_l over the cell face and the range, a product
+              // over the tangential axes of integrals of the linear nodal functions
+              // l_0 = 1 - t/h, l_1 = t/h over the overlap [ta, tb] of the cell
+              if (((l >> xi) & 1) != side) continue;
+              double I = 1.0;
+              int k = 0;
+              for (int e = 0; e < g.dim; ++e) {
+                if (e == xi) continue;
+                const double x0 = g.lo[e] + ic[e] * g.h[e];
+                const double lo_ = fmax(x0, brange[face * 4 + 2 * k]);
+                const double hi_ = fmin(x0 + g.h[e], brange[face * 4 + 2 * k + 1]);
+                ++k;
+                if (!(hi_ > lo_)) {
+                  I = 0.0;
+                  break;
+                }
+                const double ta = lo_ - x0, tb = hi_ - x0, he = g.h[e];
+                const double i1 = (tb * tb - ta * ta) / (2.0 * he);
+                I *= ((l >> e) & 1) ? i1 : (tb - ta) - i1;
+              }
+              v += beam[(size_t)face * g.nadof + j] * I;
+              continue;
+            }
+            // inflow iff the patch moves into the domain through this face
+            const bool inflow = side == 0 ? (negb[xi] == 0) : (negb[xi] == 1);
+            if (!inflow) continue;
+            const double nsgn = side ? 1.0 : -1.0;
+            v += -bval[face] * mf[face * s + l] * nsgn * (double)Aw[((size_t)q * 3 + xi) * a + m];
           }
-          v += beam[(size_t)face * g.nadof + j] * I;
-          continue;
         }
-        // inflow iff the patch moves into the domain through this face
-        const bool inflow = side == 0 ? (negb[xi] == 0) : (negb[xi] == 1);
-        if (!inflow) continue;
-        const double nsgn = side ? 1.0 : -1.0;
-        v += -bval[face] * mf[face * s + l] * nsgn * (double)Aw[((size_t)q * 3 + xi) * a + m];
+        f[((long long)c * s + l) * g.nadof + j] = (T)v;
       }
     }
-    f[idx] = (T)v;
   }
 }
 
@@ -1008,7 +1198,7 @@ size_t sweep2d_smem(const Geom& g, int G, int nmat_s, int nst) {
 template <class T>
 void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const Schedule& sc,
                   const T* b, T* psi, int G, int nmat, int chunk_bytes, int nst, int variant,
-                  int* err, int test_hold, cudaStream_t st) {
+                  int* err, int test_hold, unsigned* gbar, cudaStream_t st) {
   note_launch();
   // warp-pipelined form (variant 2; auto with at least 2 (FP32) or 4 (FP64)
   // patches per block, where it measured faster):
@@ -1081,11 +1271,49 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
       return;
     }
   }
+  if (g.dim == 3 && variant != 1 && err && gbar) {
+    // every direction and patch at once, a grid barrier per wavefront level
+    auto launch3 = [&](auto kern) -> bool {
+      int per_sm = 0, dev = 0, nsm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweep3Threads, 0) !=
+              cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return false;
+      }
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      int nblocks = per_sm * nsm;
+      if (cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return false;
+      void* args[] = {(void*)&g, (void*)&t, (void*)&cd, (void*)&sc, (void*)&b, (void*)&psi,
+                      (void*)&gbar, (void*)&err};
+      if (cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(kSweep3Threads), args, 0,
+                                      st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      return true;
+    };
+    if (g.a == 3 ? launch3(sweep3d_grid_kernel<T, 3>) : launch3(sweep3d_grid_kernel<T, 1>)) return;
+  }
   dim3 grid(sc.ntask), block(256);
   if (g.dim == 2 && g.a == 3) sweep_kernel<T, 2, 3><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
   else if (g.dim == 2) sweep_kernel<T, 2, 1><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
   else if (g.a == 3) sweep_kernel<T, 3, 3><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
   else sweep_kernel<T, 3, 1><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
+}
+
+void launch_apply_L_df(const Geom& g, const LevelDev<double>& t, const CellData& cd, double alpha,
+                       double beta, const double* x, double* y, cudaStream_t st) {
+  note_launch();
+  const int grid = grid_for((long long)g.C * g.P, 256);
+  if (g.dim == 2 && g.a == 3)
+    apply_L_kernel<double, 2, 3, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+  else if (g.dim == 2)
+    apply_L_kernel<double, 2, 1, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+  else if (g.a == 3)
+    apply_L_kernel<double, 3, 3, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+  else
+    apply_L_kernel<double, 3, 1, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
 }
 
 template <class T>
@@ -1109,7 +1337,7 @@ void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant, co
                    const double* brange, const double* mu, const double* mf, T* f,
                    cudaStream_t st) {
   note_launch();
-  const int grid = grid_for(g.nsdof * g.nadof, 256);
+  const int grid = grid_for((long long)g.C * g.P, 256);
   source_kernel<T><<<grid, 256, 0, st>>>(g, w, Aw, octant, q, bval, bkind, beam, brange, mu, mf,
                                          f);
 }
@@ -1142,7 +1370,7 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
 #define AMGT_INST(T)                                                                          \
   template void launch_sweep<T>(const Geom&, const LevelDev<T>&, const CellData&,             \
                                 const Schedule&, const T*, T*, int, int, int, int, int,       \
-                                int*, int, cudaStream_t);                                     \
+                                int*, int, unsigned*, cudaStream_t);                          \
   template void launch_apply_L<T>(const Geom&, const LevelDev<T>&, const CellData&, T, T,     \
                                   const T*, T*, cudaStream_t);                                \
   template void launch_source<T>(const Geom&, const T*, const T*, const int*, const double*,  \

@@ -590,3 +590,47 @@ def test_per_material_moment_shapes(dim, nc, level):
     psi, phi, st, _ = ctx.amgt_solve(tol=1e-11, precond=AMGT_PREC_MG, mode=AMGT_MODE_MIXED)
     assert st.relres < 1e-11 and _rel(psi, xo) < 1e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("dim,nc,level,basis", CASES, ids=IDS)
+def test_double_float_L_apply(dim, nc, level, basis):
+    """L x in double-float arithmetic (AMGT_F64_SPLIT; the refinement
+    residual's L) against the oracle at 1e-12 per row, rows of very
+    different magnitudes included (the mixed-solve tests above exercise it
+    inside the refinement, where the split-form scatter applies)."""
+    prob = W.random_problem(dim, nc, level, 4, 96, basis=basis, inflow=0.2)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    x = W.random_vector((T.nsdof, T.nadof), 97)
+    x *= 10.0 ** np.linspace(-6, 6, T.nsdof)[:, None]
+    y = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=torch.float64)
+    ctx.amgt_op_apply_L(0, _dev(x), y, tc=True)
+    ref = T.apply_L(x)
+    rows = np.linalg.norm(_host(y) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rows.max() < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("nc,level,basis,dtype", [((5, 4, 6), 1, "lin", "f64"),
+                                                  ((5, 4, 6), 1, "lin", "f32"),
+                                                  ((3, 7, 2), 2, "const", "f64")])
+def test_3d_grid_sweep(nc, level, basis, dtype):
+    """The 3D sweep over every direction and patch at once (default) against
+    the oracle's sweep and against the per-task level kernel
+    (AMGT_TUNE_SWEEP_KERNEL = 1), with per-cell materials and inflow."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_SWEEP_KERNEL
+    prob = W.random_problem(3, nc, level, 4, 98, basis=basis, inflow=0.3)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    x = _dev(W.random_vector((T.nsdof, T.nadof), 99), td)
+    yg = torch.empty_like(x)
+    yl = torch.empty_like(x)
+    ctx.amgt_op_sweep(0, x, yg)
+    ctx.amgt_sync()
+    ctx.amgt_set_tuning(AMGT_TUNE_SWEEP_KERNEL, 1)
+    ctx.amgt_op_sweep(0, x, yl)
+    ctx.amgt_sync()
+    assert _rel(_host(yg), _host(yl)) < (1e-14 if dtype == "f64" else 1e-6)
+    assert _rel(_host(yg), T.sweep(_host(x))) < (1e-12 if dtype == "f64" else 2e-5)
+    ctx.close()
