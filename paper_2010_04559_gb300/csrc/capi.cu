@@ -249,6 +249,21 @@ int upload_level(amgt_ctx* ctx, Level& L, const std::vector<double>& K0,
   return AMGT_OK;
 }
 
+// A^xi_q and M_q as (hi, lo) float pairs for the double-float L apply
+int upload_df_tables(amgt_ctx* ctx, Level& L) {
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float h = (float)v[i];
+      o[i] = make_float2(h, (float)(v[i] - (double)h));
+    }
+    return o;
+  };
+  TRY(upload(ctx, split(L.mesh.A), &L.df_aax));
+  TRY(upload(ctx, split(L.mesh.M), &L.df_mang));
+  return AMGT_OK;
+}
+
 // Block inverses of level Lv on the GPU from its uploaded K0, B and S_qq:
 // Kinv = (K0_q + sigma_t B_q)^-1 per material and patch, and on the coarsest
 // level Ginv = (K0_q + sigma_t B_q - sigma_s N (x) S_qq)^-1; FP32 copies.
@@ -811,6 +826,7 @@ int build(amgt_ctx* ctx) {
     TRY(upload(ctx, Lv.dir_end, &Lv.d_dend));
     const std::vector<double> fdeg = nf > 1 ? Fall : std::vector<double>{};
     TRY(upload_level<double>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d64, Xt, fdeg));
+    TRY(upload_df_tables(ctx, Lv));
     TRY(upload_level<float>(ctx, Lv, K0, B, Kinv, Ginv, X, XFt, Sqq, {}, Lv.d32, Xt, fdeg));
     if (dev_inv) TRY(device_block_inverses(ctx, Lv, k == nl - 1));
     // the direction-blocked Gauss-Seidel tables assume one moment shape; with
@@ -1307,8 +1323,8 @@ int applyL_impl(amgt_ctx* ctx, int k, T alpha, T beta, const T* x, T* y) {
 int applyL_df(amgt_ctx* ctx, int k, double alpha, double beta, const double* x, double* y) {
   const Level& L = ctx->lv[k];
   KernelTimer kt(ctx, AMGT_KT_APPLY_L, (beta != 0.0 ? 3.0 : 2.0) * 8.0 * L.nsdof * L.nadof());
-  launch_apply_L_df(level_geom(ctx, k), level_view<double>(L, L.d64), cell_data(ctx), alpha, beta,
-                    x, y, ctx->stream);
+  launch_apply_L_df(level_geom(ctx, k), L.df_aax, L.df_mang, L.d_pdir, ctx->d_sigt, alpha, beta, x,
+                    y, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }

@@ -64,6 +64,8 @@ struct Level {
   // S_f scaled by 2^e, and the inverse scale 2^-e
   __half* Sf_tc3 = nullptr;  // [n][3n]
   double tc3_sinv = 0.0;
+  // A^xi_q [P][3][a][a] and M_q [P][a][a] as double-float (hi, lo) pairs
+  float2 *df_aax = nullptr, *df_mang = nullptr;
   int *d_pdir = nullptr, *d_octant = nullptr, *d_dbeg = nullptr, *d_dend = nullptr;
   // pencil-beam inflow weights [2 dim][nadof] (null without a beam face)
   double* d_beam = nullptr;

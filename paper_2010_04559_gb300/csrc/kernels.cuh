@@ -106,9 +106,11 @@ template <class T>
 void launch_apply_L(const Geom& g, const LevelDev<T>& t, const CellData& cd, T alpha, T beta,
                     const T* x, T* y, cudaStream_t st);
 // the same FP64 L x in double-float arithmetic (hi + lo FP32 parts, ~44 bits;
-// relative error ~1e-13 of the terms) on the FP32 units
-void launch_apply_L_df(const Geom& g, const LevelDev<double>& t, const CellData& cd, double alpha,
-                       double beta, const double* x, double* y, cudaStream_t st);
+// relative error ~1e-13 of the terms) on the FP32 units; aax [P][3][a][a] and
+// mang [P][a][a] are A^xi_q and M_q split into (hi, lo) float pairs
+void launch_apply_L_df(const Geom& g, const float2* aax, const float2* mang, const int* pdir,
+                       const double* sigma_t, double alpha, double beta, const double* x,
+                       double* y, cudaStream_t st);
 // C[M][N] = A[M][K] B[K][N] with epilogue (see kernels_gemm.cu)
 struct GemmEpi {
   int mode;            // 0 store, 1 cell mix: out = alpha*sig_s*Nmix(acc) + beta*out + add

@@ -82,22 +82,62 @@ __device__ __forceinline__ DF& operator+=(DF& a, const DF& b) {
   return a;
 }
 
-// R: the arithmetic (T itself, or DF for T = double); loads and the result
-// convert between T and R
-template <class R, class T>
-__device__ __forceinline__ R to_r(T v) {
-  return R(v);
+// An FP64 value as double-float by integer operations alone (FP64 conversions
+// run at the FP64 rate): hi keeps the leading 24 bits of the significand
+// (truncated), lo the remaining 29 bits rounded to 24, so hi + lo is the
+// value to a relative 2^-47.  Values outside [2^-74, 2^128) and zero take the
+// conversion path.
+__device__ __forceinline__ DF df_split(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((bits >> 52) & 0x7ffULL) - 1023;
+  if (e < -74 || e > 127) {
+    if ((bits << 1) == 0ULL) return DF(0.f, 0.f);
+    const float h = (float)v;
+    return DF(h, (float)(v - (double)h));
+  }
+  const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
+  const float hi =
+      __uint_as_float(sgn | ((unsigned)(e + 127) << 23) | (unsigned)((bits >> 29) & 0x7fffffULL));
+  const float lo = __fmul_rn(__uint2float_rn((unsigned)(bits & 0x1fffffffULL)),
+                             __uint_as_float((unsigned)(e - 52 + 127) << 23));
+  return DF(hi, sgn ? -lo : lo);
 }
-template <class T, class R>
-__device__ __forceinline__ T from_r(R v) {
-  return (T)v;
+// a float as FP64, exactly, by integer operations (zero and normal floats;
+// subnormals, infinities and NaN by conversion)
+__device__ __forceinline__ double df_f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  if ((u & 0x7fffffffu) == 0u) return 0.0;
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
+__device__ __forceinline__ double df_to_double(const DF& v) { return df_f2d(v.hi) + df_f2d(v.lo); }
+
+// A dot-product accumulator in the style of Ogita, Rump and Oishi's Dot2
+// (2005): the running sum s collects the leading products through two-sum,
+// c the exact product errors, the two-sum errors and the cross terms
+// hi lo + lo hi in plain FP32 (all ~2^-24 of the sum or smaller).
+struct DFAcc {
+  float s = 0.f, c = 0.f;
+};
+__device__ __forceinline__ void df_fma(DFAcc& a, const DF& x, const DF& y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float pe = __fmaf_rn(x.hi, y.hi, -p);
+  const float s = __fadd_rn(a.s, p);
+  const float bb = __fsub_rn(s, a.s);
+  const float se = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.s = s;
+  a.c = __fadd_rn(a.c, __fadd_rn(__fadd_rn(se, pe), __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi))));
+}
+__device__ __forceinline__ DF df_val(const DFAcc& a) { return df_two_sum(a.s, a.c); }
 
 // Adds sign * sum over inflow faces of kron(Fnb_f, A_{f,q}) psi_nb to acc.
-template <class T, int DIM, int A, class R = T>
+template <class T, int DIM, int A>
 __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__ Aax, int q,
                                             const T* __restrict__ psi, int c, const int jj[3],
-                                            const int neg[3], R sign, R* acc) {
+                                            const int neg[3], T sign, T* acc) {
   constexpr int S = 1 << DIM;
   const int nadof = g.nadof;
   const int stride[3] = {1, g.nx, g.nx * g.ny};
@@ -107,20 +147,20 @@ __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__
     const int own = neg[xi];    // side bit of this cell's inflow face
     const int cn = c + (own ? stride[xi] : -stride[xi]);
     const T* An = Aax + ((size_t)q * 3 + xi) * A * A;
-    const R nsgn = own ? R(1) : R(-1);  // outward normal component
+    const T nsgn = own ? T(1) : T(-1);  // outward normal component
     const T* pn = psi + (long long)cn * S * nadof + q * A;
-    R tv[S / 2][A];
+    T tv[S / 2][A];
 #pragma unroll
     for (int j = 0; j < S / 2; ++j) {
       const int i = fnode(j, xi, 1 - own);
-      R v[A];
+      T v[A];
 #pragma unroll
-      for (int d = 0; d < A; ++d) v[d] = to_r<R>(pn[(long long)i * nadof + d]);
+      for (int d = 0; d < A; ++d) v[d] = pn[(long long)i * nadof + d];
 #pragma unroll
       for (int m = 0; m < A; ++m) {
-        R sacc = R(0);
+        T sacc = T(0);
 #pragma unroll
-        for (int d = 0; d < A; ++d) sacc += to_r<R>(An[m * A + d]) * v[d];
+        for (int d = 0; d < A; ++d) sacc += An[m * A + d] * v[d];
         tv[j][m] = nsgn * sacc;
       }
     }
@@ -129,9 +169,9 @@ __device__ __forceinline__ void upwind_term(const Geom& g, const T* __restrict__
       const int l = fnode(jp, xi, own);
 #pragma unroll
       for (int m = 0; m < A; ++m) {
-        R sacc = R(0);
+        T sacc = T(0);
 #pragma unroll
-        for (int j = 0; j < S / 2; ++j) sacc += to_r<R>((T)g.facemass[xi][jp][j]) * tv[j][m];
+        for (int j = 0; j < S / 2; ++j) sacc += T(g.facemass[xi][jp][j]) * tv[j][m];
         acc[l * A + m] += sign * sacc;
       }
     }
@@ -948,9 +988,9 @@ template <>
 __device__ __forceinline__ float nsp<float>(const Geom& g, int e) { return g.NmassF[e]; }
 
 // three blocks per SM for the 2D FP32 form; two (up to 128 registers, no
-// spills of the wider FP64 / double-float working set) otherwise
-template <class T, int DIM, int A, class R = T>
-__global__ void __launch_bounds__(256, DIM == 2 && sizeof(R) == 4 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
+// spills of the wider FP64 working set) otherwise
+template <class T, int DIM, int A>
+__global__ void __launch_bounds__(256, DIM == 2 && sizeof(T) == 4 ? 3 : 2) apply_L_kernel(Geom g, LevelDev<T> t, CellData cd,
                                                       T alpha, T beta, const T* __restrict__ x,
                                                       T* __restrict__ y) {
   constexpr int S = 1 << DIM;
@@ -967,29 +1007,29 @@ __global__ void __launch_bounds__(256, DIM == 2 && sizeof(R) == 4 ? 3 : 2) apply
     const int jj[3] = {neg[0] ? g.nx - 1 - ix : ix, neg[1] ? g.ny - 1 - iy : iy,
                        neg[2] ? g.nz - 1 - iz : iz};
     const T* xp = x + (long long)c * S * nadof + q * A;
-    R xv[S][A];
+    T xv[S][A];
 #pragma unroll
     for (int l = 0; l < S; ++l)
 #pragma unroll
-      for (int m = 0; m < A; ++m) xv[l][m] = to_r<R>(xp[(long long)l * nadof + m]);
-    R acc[SA];
+      for (int m = 0; m < A; ++m) xv[l][m] = xp[(long long)l * nadof + m];
+    T acc[SA];
 #pragma unroll
-    for (int r = 0; r < SA; ++r) acc[r] = R(0);
+    for (int r = 0; r < SA; ++r) acc[r] = T(0);
     // streaming: sum_xi G_xi X (A^xi)^T
 #pragma unroll
     for (int xi = 0; xi < DIM; ++xi) {
       const T* Aq = t.Aax + ((size_t)q * 3 + xi) * A * A;
-      R a[A][A];
+      T a[A][A];
 #pragma unroll
       for (int m = 0; m < A; ++m)
 #pragma unroll
-        for (int d = 0; d < A; ++d) a[m][d] = to_r<R>(Aq[m * A + d]);
-      R t1[S][A];
+        for (int d = 0; d < A; ++d) a[m][d] = Aq[m * A + d];
+      T t1[S][A];
 #pragma unroll
       for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int m = 0; m < A; ++m) {
-          R v = R(0);
+          T v = T(0);
 #pragma unroll
           for (int d = 0; d < A; ++d) v += xv[i][d] * a[m][d];
           t1[i][m] = v;
@@ -999,42 +1039,215 @@ __global__ void __launch_bounds__(256, DIM == 2 && sizeof(R) == 4 ? 3 : 2) apply
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const R gli = to_r<R>(gax<T>(g, xi, sg, l * S + i));
+          const T gli = gax<T>(g, xi, sg, l * S + i);
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += gli * t1[i][m];
         }
     }
     // collision: sigma_t N X M^T
     {
-      const R st = to_r<R>((T)cd.sigma_t[c]);
+      const T st = (T)cd.sigma_t[c];
       const T* Mm = t.Mang + (size_t)q * A * A;
-      R t1[S][A];
+      T t1[S][A];
 #pragma unroll
       for (int i = 0; i < S; ++i)
 #pragma unroll
         for (int m = 0; m < A; ++m) {
-          R v = R(0);
+          T v = T(0);
 #pragma unroll
-          for (int d = 0; d < A; ++d) v += xv[i][d] * to_r<R>(Mm[m * A + d]);
+          for (int d = 0; d < A; ++d) v += xv[i][d] * Mm[m * A + d];
           t1[i][m] = st * v;
         }
 #pragma unroll
       for (int l = 0; l < S; ++l)
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const R nli = to_r<R>(nsp<T>(g, l * S + i));
+          const T nli = nsp<T>(g, l * S + i);
 #pragma unroll
           for (int m = 0; m < A; ++m) acc[l * A + m] += nli * t1[i][m];
         }
     }
-    upwind_term<T, DIM, A, R>(g, t.Aax, q, x, c, jj, neg, R(1), acc);
+    upwind_term<T, DIM, A>(g, t.Aax, q, x, c, jj, neg, T(1), acc);
     T* out = y + (long long)c * S * nadof + q * A;
 #pragma unroll
     for (int r = 0; r < SA; ++r) {
       T* o = out + (long long)(r / A) * nadof + (r % A);
-      T v = alpha * from_r<T>(acc[r]);
+      T v = alpha * acc[r];
       if (beta != T(0)) v += beta * (*o);
       *o = v;
+    }
+  }
+}
+
+// y = alpha L x + beta y to FP64 accuracy on the FP32 units: the Kronecker
+// form of apply_L_kernel in double-float arithmetic.  x, y and sigma_t are
+// split by integer operations, the patch tables A^xi_q and M_q come split
+// (hi, lo) from set-up, and the geometric constants are split once per block
+// into shared memory, so the only FP64 instruction is the final hi + lo of
+// each output.  In 2D two blocks per SM (128 registers, a few spilled)
+// measured 13% faster than one block without spills.
+template <int DIM, int A>
+__global__ void __launch_bounds__(256, DIM == 2 ? 2 : 1)
+    apply_L_df_kernel(Geom g, const float2* __restrict__ aax, const float2* __restrict__ mang,
+                      const int* __restrict__ pdir, const double* __restrict__ sigma_t,
+                      double alpha, double beta, const double* __restrict__ x,
+                      double* __restrict__ y) {
+  constexpr int S = 1 << DIM, HS = S / 2, SA = S * A;
+  __shared__ float2 sG[DIM][2][S * S];  // streaming matrices G_xi^(sign)
+  __shared__ float2 sN[S * S];          // spatial mass N
+  __shared__ float2 sF[DIM][HS][HS];    // face masses
+  for (int i = threadIdx.x; i < DIM * 2 * S * S + S * S + DIM * HS * HS; i += blockDim.x) {
+    double v;
+    float2* dst;
+    if (i < DIM * 2 * S * S) {
+      const int xi = i / (2 * S * S), sg = (i / (S * S)) & 1, e = i % (S * S);
+      v = g.Gax[xi][sg][e];
+      dst = &sG[xi][sg][e];
+    } else if (i < DIM * 2 * S * S + S * S) {
+      const int e = i - DIM * 2 * S * S;
+      v = g.Nmass[e];
+      dst = &sN[e];
+    } else {
+      const int e = i - DIM * 2 * S * S - S * S;
+      const int xi = e / (HS * HS), jp = (e / HS) % HS, j = e % HS;
+      v = g.facemass[xi][jp][j];
+      dst = &sF[xi][jp][j];
+    }
+    const float h = (float)v;
+    *dst = make_float2(h, (float)(v - (double)h));
+  }
+  __syncthreads();
+  const DF alpha_df(alpha), beta_df(beta);
+  const bool unit_alpha = alpha == 1.0;
+  const long long total = (long long)g.C * g.P;
+  const int nadof = g.nadof;
+  const int stride[3] = {1, g.nx, g.nx * g.ny};
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / g.P);
+    const int q = (int)(idx - (long long)c * g.P);
+    int neg[3];
+    dir_bits<DIM>(pdir[q], neg);
+    const int ix = c % g.nx, iy = (c / g.nx) % g.ny, iz = c / (g.nx * g.ny);
+    const int jj[3] = {neg[0] ? g.nx - 1 - ix : ix, neg[1] ? g.ny - 1 - iy : iy,
+                       neg[2] ? g.nz - 1 - iz : iz};
+    const double* xp = x + (long long)c * S * nadof + q * A;
+    DF xv[S][A];
+#pragma unroll
+    for (int l = 0; l < S; ++l)
+#pragma unroll
+      for (int m = 0; m < A; ++m) xv[l][m] = df_split(xp[(long long)l * nadof + m]);
+    DFAcc acc[SA];
+    // streaming: sum_xi G_xi X (A^xi)^T
+#pragma unroll
+    for (int xi = 0; xi < DIM; ++xi) {
+      const float2* Aq = aax + ((size_t)q * 3 + xi) * A * A;
+      DF a[A][A];
+#pragma unroll
+      for (int m = 0; m < A; ++m)
+#pragma unroll
+        for (int d = 0; d < A; ++d) {
+          const float2 v = Aq[m * A + d];
+          a[m][d] = DF(v.x, v.y);
+        }
+      const int sg = neg[xi];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        DF t1[A];
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          DFAcc v;
+#pragma unroll
+          for (int d = 0; d < A; ++d) df_fma(v, xv[i][d], a[m][d]);
+          t1[m] = df_val(v);
+        }
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const float2 gv = sG[xi][sg][l * S + i];
+          const DF gli(gv.x, gv.y);
+#pragma unroll
+          for (int m = 0; m < A; ++m) df_fma(acc[l * A + m], gli, t1[m]);
+        }
+      }
+    }
+    // collision: sigma_t N X M^T
+    {
+      const DF st = df_split(sigma_t[c]);
+      const float2* Mm = mang + (size_t)q * A * A;
+      DF mq[A][A];
+#pragma unroll
+      for (int m = 0; m < A; ++m)
+#pragma unroll
+        for (int d = 0; d < A; ++d) {
+          const float2 v = Mm[m * A + d];
+          mq[m][d] = DF(v.x, v.y);
+        }
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        DF t1[A];
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          DFAcc v;
+#pragma unroll
+          for (int d = 0; d < A; ++d) df_fma(v, xv[i][d], mq[m][d]);
+          t1[m] = st * df_val(v);
+        }
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+          const float2 nv = sN[l * S + i];
+          const DF nli(nv.x, nv.y);
+#pragma unroll
+          for (int m = 0; m < A; ++m) df_fma(acc[l * A + m], nli, t1[m]);
+        }
+      }
+    }
+    // inflow faces: sum over f of kron(Fnb_f, A_{f,q}) x_nb, A_{f,q} = n_xi A^xi_q
+#pragma unroll
+    for (int xi = 0; xi < DIM; ++xi) {
+      if (jj[xi] == 0) continue;
+      const int own = neg[xi];
+      const int cn = c + (own ? stride[xi] : -stride[xi]);
+      const float2* An = aax + ((size_t)q * 3 + xi) * A * A;
+      const double* pn = x + (long long)cn * S * nadof + q * A;
+      DF tv[HS][A];
+#pragma unroll
+      for (int j = 0; j < HS; ++j) {
+        const int i = fnode(j, xi, 1 - own);
+        DF v[A];
+#pragma unroll
+        for (int d = 0; d < A; ++d) v[d] = df_split(pn[(long long)i * nadof + d]);
+#pragma unroll
+        for (int m = 0; m < A; ++m) {
+          DFAcc sacc;
+#pragma unroll
+          for (int d = 0; d < A; ++d) {
+            const float2 av = An[m * A + d];
+            df_fma(sacc, DF(av.x, av.y), v[d]);
+          }
+          const DF t = df_val(sacc);
+          tv[j][m] = own ? t : -t;  // outward normal component
+        }
+      }
+#pragma unroll
+      for (int jp = 0; jp < HS; ++jp) {
+        const int l = fnode(jp, xi, own);
+#pragma unroll
+        for (int j = 0; j < HS; ++j) {
+          const float2 fv = sF[xi][jp][j];
+          const DF fm(fv.x, fv.y);
+#pragma unroll
+          for (int m = 0; m < A; ++m) df_fma(acc[l * A + m], fm, tv[j][m]);
+        }
+      }
+    }
+    double* out = y + (long long)c * S * nadof + q * A;
+#pragma unroll
+    for (int r = 0; r < SA; ++r) {
+      double* o = out + (long long)(r / A) * nadof + (r % A);
+      DF v = df_val(acc[r]);
+      if (!unit_alpha) v = alpha_df * v;
+      if (beta != 0.0) v += beta_df * df_split(*o);
+      *o = df_to_double(v);
     }
   }
 }
@@ -1302,18 +1515,19 @@ void launch_sweep(const Geom& g, const LevelDev<T>& t, const CellData& cd, const
   else sweep_kernel<T, 3, 1><<<grid, block, 0, st>>>(g, t, cd, sc, b, psi);
 }
 
-void launch_apply_L_df(const Geom& g, const LevelDev<double>& t, const CellData& cd, double alpha,
-                       double beta, const double* x, double* y, cudaStream_t st) {
+void launch_apply_L_df(const Geom& g, const float2* aax, const float2* mang, const int* pdir,
+                       const double* sigma_t, double alpha, double beta, const double* x,
+                       double* y, cudaStream_t st) {
   note_launch();
   const int grid = grid_for((long long)g.C * g.P, 256);
   if (g.dim == 2 && g.a == 3)
-    apply_L_kernel<double, 2, 3, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+    apply_L_df_kernel<2, 3><<<grid, 256, 0, st>>>(g, aax, mang, pdir, sigma_t, alpha, beta, x, y);
   else if (g.dim == 2)
-    apply_L_kernel<double, 2, 1, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+    apply_L_df_kernel<2, 1><<<grid, 256, 0, st>>>(g, aax, mang, pdir, sigma_t, alpha, beta, x, y);
   else if (g.a == 3)
-    apply_L_kernel<double, 3, 3, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+    apply_L_df_kernel<3, 3><<<grid, 256, 0, st>>>(g, aax, mang, pdir, sigma_t, alpha, beta, x, y);
   else
-    apply_L_kernel<double, 3, 1, DF><<<grid, 256, 0, st>>>(g, t, cd, alpha, beta, x, y);
+    apply_L_df_kernel<3, 1><<<grid, 256, 0, st>>>(g, aax, mang, pdir, sigma_t, alpha, beta, x, y);
 }
 
 template <class T>
