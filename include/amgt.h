@@ -286,6 +286,14 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         V-cycle (mixed solves, AMGT_F32 cycles): 0 in FP32
  *                         (default), 1 in FP64 (the right-hand side converted
  *                         to FP64, the FP64 sweeps, the result rounded back)
+ *   AMGT_TUNE_GS_FORM     the row-pipelined coarse Gauss-Seidel's scattering
+ *                         source: 0 auto (the dense form where the angular
+ *                         unknowns are fewer than twice the moments plus a
+ *                         direction's unknowns and one moment shape is in
+ *                         use), 1 the moment form (flux moments kept per
+ *                         cell), 2 the dense form S_f x_c where it applies;
+ *                         takes effect at the next set-up (the context is
+ *                         rebuilt before its next use)
  *   AMGT_TUNE_TEST_SWEEP_HOLD for tests of the failure path only: 1 makes
  *                         the warp-pipelined 2D sweep's first warp of each
  *                         block withhold its progress counter and every wait
@@ -306,6 +314,7 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
 #define AMGT_TUNE_F32_SCATTER 11
 #define AMGT_TUNE_TEST_SWEEP_HOLD 12
 #define AMGT_TUNE_COARSE_F64 13
+#define AMGT_TUNE_GS_FORM 14
 int amgt_set_tuning(amgt_ctx* ctx, int key, int value);
 /* Times the sweep's patches per block and copy depth (what bit 0) and the
  * coarse Gauss-Seidel kernel (what bit 1) on this context's own hierarchy

@@ -50,6 +50,7 @@ AMGT_TUNE_SWEEP_KERNEL = 10
 AMGT_TUNE_F32_SCATTER = 11
 AMGT_TUNE_TEST_SWEEP_HOLD = 12
 AMGT_TUNE_COARSE_F64 = 13
+AMGT_TUNE_GS_FORM = 14
 AMGT_KRYLOV_GMRES, AMGT_KRYLOV_BICGSTAB = 0, 1
 AMGT_KT_SWEEP, AMGT_KT_APPLY_L, AMGT_KT_SCATTER_PREP, AMGT_KT_SCATTER_TC = 0, 1, 2, 3
 AMGT_KT_SCATTER_F32, AMGT_KT_COARSE_GS, AMGT_KT_SCATTER_F64 = 4, 5, 6

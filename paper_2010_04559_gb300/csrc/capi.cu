@@ -467,6 +467,8 @@ int make_sweep_tasks(amgt_ctx* ctx, Level& Lv, const Geom& g, int Gwant) {
   return AMGT_OK;
 }
 
+int ensure_dense(amgt_ctx* ctx, int k);
+
 // Row tables and face-word buffer of the row-pipelined coarse Gauss-Seidel:
 // block b owns the rows R = b, b + nb, ... (R = iy + ny*iz) in every
 // direction, visited in increasing rotated level jy + jz.
@@ -474,12 +476,21 @@ int build_gs_rows(amgt_ctx* ctx) {
   const int k = (int)ctx->lv.size() - 1;
   Level& L = ctx->lv[k];
   L.rows_nb = 0;
+  L.rows_dense = 0;
   if (!L.d32.TinvT || !L.d64.TinvT || L.ndir == 0 || ctx->geom.dim < 2) return AMGT_OK;
   const Geom g = level_geom(ctx, k);
-  const int n32 = coarse_gs_rows_plan<float>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
+  // the dense form costs J nadof multiply-adds per node and direction, the
+  // moment form J nm (source) + J nm (moment update) + J^2 (S_dd^{L+D})
+  if (ctx->nf == 1 && ctx->gs_form != 1 &&
+      (ctx->gs_form == 2 || L.nadof() < 2 * L.nmom + L.Jmax)) {
+    TRY(ensure_dense(ctx, k));
+    L.rows_dense = 1;
+  }
+  const bool dense = L.rows_dense != 0;
+  const int n32 = coarse_gs_rows_plan<float>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom, dense,
                                              &L.rows_nmat_s[0], &L.rows_threads[0],
                                              &L.rows_smem[0], &L.rows_gbuf[0]);
-  const int n64 = coarse_gs_rows_plan<double>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom,
+  const int n64 = coarse_gs_rows_plan<double>(g, L.ndir, ctx->nmat, L.Jmax, L.nmom, dense,
                                               &L.rows_nmat_s[1], &L.rows_threads[1],
                                               &L.rows_smem[1], &L.rows_gbuf[1]);
   int nb = std::min(n32, n64);
@@ -1412,23 +1423,29 @@ template <class T>
 int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool timed) {
   const int k = (int)ctx->lv.size() - 1;
   const Level& L = ctx->lv[k];
-  GemmEpi e0{};
-  e0.mode = 0;
-  launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
-                 L.nmom, e0, ctx->stream);
+  const bool rows = store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6) &&
+                    L.rows_nb > 0;
+  const bool dense = rows && L.rows_dense;
+  auto moments = [&]() {
+    GemmEpi e0{};
+    e0.mode = 0;
+    launch_gemm<T>((int)L.nsdof, L.nmom, L.nadof(), phi, L.nadof(), store<T>(L).X, L.nmom, mom,
+                   L.nmom, e0, ctx->stream);
+  };
+  if (!dense) moments();
   // sequential per-patch form of the block solves, per (cell, patch, sweep):
   // moment source s a nm, self-scatter s a a, mass mixing s a s, block solve
-  // (s a)^2, moment update s nm a multiply-adds
+  // (s a)^2, moment update s nm a multiply-adds (dense form: the source
+  // s a nadof, no self-scatter or moment update)
+  const double sa = (double)ctx->geom.s * L.mesh.a;
   const double gs_fma = (double)L.nsdof / ctx->geom.s * L.mesh.P * sweeps *
-                        (2.0 * ctx->geom.s * L.mesh.a * L.nmom +
-                         (double)ctx->geom.s * L.mesh.a * L.mesh.a +
-                         (double)ctx->geom.s * L.mesh.a * ctx->geom.s +
-                         (double)ctx->geom.s * L.mesh.a * ctx->geom.s * L.mesh.a);
+                        ((dense ? sa * L.nadof() : 2.0 * sa * L.nmom + sa * L.mesh.a) +
+                         sa * ctx->geom.s + sa * sa);
   KernelTimer kt(ctx, AMGT_KT_COARSE_GS, 2.0 * gs_fma, timed);
   // row-pipelined kernel: the default where available
   if (store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6)) {
     const int pi = sizeof(T) == 4 ? 0 : 1;
-    if (L.rows_nb > 0) {
+    if (rows) {
       // restart the face-word tags: before wrap-around, and inside a captured
       // graph (every replay then starts from cleared words and tag 0)
       if (ctx->gs_tag > 0xf0000000u || ctx->capturing) {
@@ -1437,7 +1454,8 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool ti
       }
       if (launch_coarse_gs_rows<T>(level_geom(ctx, k), level_view<T>(L, store<T>(L)),
                                    cell_data(ctx), L.ndir, L.d_dbeg, L.d_dend, sweeps, f, phi,
-                                   mom, store<T>(L).TinvT, store<T>(L).SLD, L.Emax, L.Jmax,
+                                   mom, store<T>(L).TinvT, store<T>(L).SLD,
+                                   dense ? store<T>(L).Sf : nullptr, L.Emax, L.Jmax,
                                    ctx->nmat, L.rows_nmat_s[pi], L.rows_gbuf[pi],
                                    L.rows_threads[pi], L.rows_smem[pi], L.d_rows,
                                    L.rows_nb, L.rows_rpb, L.d_faces, ctx->gs_tag,
@@ -1450,6 +1468,7 @@ int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool ti
     if (ctx->gs_kernel == 6)
       return fail(ctx, AMGT_ERR_ARG, "row-pipelined Gauss-Seidel not available for this problem");
   }
+  if (dense) moments();  // the launch above failed: the other kernels keep moments
   int cl = 0;
   if constexpr (sizeof(T) == 4) {
     if (store<T>(L).TinvT && ctx->gs_kernel == 5) {
@@ -2354,6 +2373,12 @@ int amgt_set_tuning(amgt_ctx* ctx, int key, int value) {
     if (value != 0 && value != 1) return fail(ctx, AMGT_ERR_ARG, "graphs 0 or 1");
     ctx->use_graphs = value == 1;
     drop_graphs(ctx);
+    return AMGT_OK;
+  }
+  if (key == AMGT_TUNE_GS_FORM) {
+    if (value < 0 || value > 2) return fail(ctx, AMGT_ERR_ARG, "GS form 0, 1 or 2");
+    if (value != ctx->gs_form) ctx->dirty = true;  // the row plan depends on it
+    ctx->gs_form = value;
     return AMGT_OK;
   }
   if (key == AMGT_TUNE_COARSE_F64) {

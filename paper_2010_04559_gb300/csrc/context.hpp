@@ -47,6 +47,7 @@ struct Level {
   // materials whose block inverses fit in shared memory and the shared bytes,
   // per precision (blocks 0: not available)
   int rows_nb = 0, rows_rpb = 0;
+  int rows_dense = 0;  // dense form M_d x_c (S_f of the level built)
   int rows_nmat_s[2] = {0, 0}, rows_threads[2] = {0, 0}, rows_gbuf[2] = {0, 0};
   size_t rows_smem[2] = {0, 0};
   int* d_rows = nullptr;                      // [ndir][rows_nb][rows_rpb]
@@ -170,6 +171,7 @@ struct amgt_ctx {
   int gs_kernel = 0;    // AMGT_TUNE_GS_KERNEL
   unsigned gs_tag = 0;  // sweeps run by the row-pipelined Gauss-Seidel (face-word tags)
   int gs_grid_blocks = 0;  // AMGT_TUNE_GS_GRID_BLOCKS
+  int gs_form = 0;         // AMGT_TUNE_GS_FORM
   int gs_cluster_size = 0; // AMGT_TUNE_GS_CLUSTER
   int sweep_group = 0;  // AMGT_TUNE_SWEEP_GROUP
   int sweep_stages = 0; // AMGT_TUNE_SWEEP_STAGES

@@ -181,16 +181,18 @@ int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData&
 // resident at once (capped by the number of rows ny*nz; 0 if the shapes are
 // not supported) with the materials whose inverses fit in shared memory, the
 // threads, the shared bytes per block and the size of the per-cell prefetch
-// buffers for the other materials' inverses (0: read from global memory).  launch: returns 0 on a successful
-// launch.
+// buffers for the other materials' inverses (0: read from global memory).
+// dense: the dense form (M_d x_c from S_f, no flux moments; Sf must then be
+// given to the launch and mom is not touched).  launch: returns 0 on a
+// successful launch.
 template <class T>
-int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
-                        int* threads, size_t* smem, int* gbuf);
+int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, bool dense,
+                        int* nmat_s, int* threads, size_t* smem, int* gbuf);
 template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
-                          T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, int gbuf, int threads, size_t smem,
+                          T* phi, T* mom, const T* TinvT, const T* SLD, const T* Sf, int Emax,
+                          int Jmax, int nmat, int nmat_s, int gbuf, int threads, size_t smem,
                           const int* rows, int nblocks, int rpb, unsigned long long* faces,
                           unsigned tag0, int* err, cudaStream_t st);
 

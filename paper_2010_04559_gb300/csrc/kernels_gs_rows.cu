@@ -8,6 +8,14 @@
 // where Tinv_d = (D_d - sigma_s N (x) S_dd^{L+D})^{-1} solves the direction's
 // patches of the cell in index order at once (block lower triangular).
 //
+// Dense form.  Where the cell's angular unknowns are fewer than twice its
+// moments, the moments are not kept: with S_f = X F X^T (one moment shape)
+//
+//   X_d F Phi_c - S_dd^{L+D} x_d^old = M_d x_c,   M_d = S_f[d rows] - S_dd^{L+D}
+//
+// (S_dd^{L+D} subtracted in the direction's own columns), a product with the
+// cell's current unknowns x_c over all directions; the moment update goes.
+//
 // Schedule.  A row is the line of cells along x at fixed (y, z).  Each thread
 // block owns a fixed set of rows for the whole launch and visits, per
 // direction, its rows in the direction's wavefront order (increasing rotated
@@ -75,8 +83,10 @@ struct RowsLayout {
       o_yup, o_Tg, o_W, o_y0, bytes;
   // gbuf: elements of one prefetch buffer for a block inverse that is not
   // staged (0: read those from global memory)
+  // nm: moments per node, or in the dense form the angular unknowns (the
+  // cell's x_c takes the moments' place and X_d, S_dd^{L+D} are not staged)
   __host__ __device__ RowsLayout(int nmat_s, int Jmax, int nm, int S, int dim, int A, int ndir,
-                                 int gbuf) {
+                                 int gbuf, bool dense) {
     const int vw = 16 / (int)sizeof(T);
     Jv = ((Jmax + vw - 1) / vw) * vw;
     Ev = S * Jv;
@@ -94,8 +104,8 @@ struct RowsLayout {
     const size_t t = sizeof(T);
     o_Tin = take((size_t)nmat_s * Ev * Evp * t);
     o_XFr = take((size_t)Jv * NMp * t);
-    o_Xk = take((size_t)nm * Jp * t);
-    o_SLr = take((size_t)Jv * Jp * t);
+    o_Xk = take(dense ? 0 : (size_t)Jv * NMp * t);
+    o_SLr = take(dense ? 0 : (size_t)Jv * Jp * t);
     o_Ns = take((size_t)S * S * t);
     o_Ad = take((size_t)Jmax * dim * A * t);   // [patch][axis][A][A]
     o_lj = take((size_t)ndir * Ev * sizeof(int));
@@ -191,6 +201,8 @@ struct RowsArgs {
   T* mom;                // [C*s][nmom] flux moments, consistent with psi on entry
   const T* TinvT;        // [nmat][ndir][Emax (col)][Emax (row)]
   const T* SLD;          // [ndir][Jmax][Jmax]
+  const T* Sf;           // [nadof][nadof] S_f (dense form)
+  int dense;             // 1: dense form (mom unused, x_c read from psi)
   int Emax, Jmax, nmat, nmat_s;
   int gbuf;              // > 0: inverses of unstaged materials prefetched into shared memory
   const int* rows;       // [ndir][nblocks][rpb] rows of each block, -1 padded
@@ -208,17 +220,19 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
   constexpr int NF = DIM - 1;  // faces exchanged between rows: y (and z)
   constexpr int W = FaceWords<T>::W;
   const Geom& g = p.g;
-  const int nm = p.t.nmom, nadof = g.nadof, nx = g.nx, ndir = p.ndir;
+  const int nadof = g.nadof, nx = g.nx, ndir = p.ndir;
+  const bool dense = p.dense != 0;
+  const int nm = dense ? nadof : p.t.nmom;  // values of the cell vector per node
   const int tid = threadIdx.x, NT = blockDim.x;
   const int qd = tid >> 2, l4 = tid & 3, NQ = NT >> 2;
   const int nb = gridDim.x, b = blockIdx.x;
-  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nm, S, DIM, A, ndir, p.gbuf);
+  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nm, S, DIM, A, ndir, p.gbuf, dense);
   // padded shapes: a direction's J unknowns per node are stored Jv apart
   const int Jv = Ly.Jv, Ev = Ly.Ev, Evp = Ly.Evp, NMp = Ly.NMp, Jp = Ly.Jp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Tin = reinterpret_cast<T*>(smem_raw + Ly.o_Tin);    // [nmat_s][Ev][Evp]
-  T* XFr = reinterpret_cast<T*>(smem_raw + Ly.o_XFr);    // [Jv][NMp]  (diag(f) X_d^T)^T
-  T* Xk = reinterpret_cast<T*>(smem_raw + Ly.o_Xk);      // [nm][Jp]   X_d^T
+  T* XFr = reinterpret_cast<T*>(smem_raw + Ly.o_XFr);    // [Jv][NMp]  (diag(f) X_d^T)^T, or M_d
+  T* Xd = reinterpret_cast<T*>(smem_raw + Ly.o_Xk);      // [Jv][NMp]  X_d (row j: unknown j's moments)
   T* SLr = reinterpret_cast<T*>(smem_raw + Ly.o_SLr);    // [Jv][Jp]   S_dd^{L+D}
   T* Ns = reinterpret_cast<T*>(smem_raw + Ly.o_Ns);      // [S][S]
   T* Ad = reinterpret_cast<T*>(smem_raw + Ly.o_Ad);      // [patch][axis][A][A]
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
   T* rhs = reinterpret_cast<T*>(smem_raw + Ly.o_rhs);    // [S][Jv]
   T* xold = reinterpret_cast<T*>(smem_raw + Ly.o_xold);  // [S][Jv]
   T* bufs = reinterpret_cast<T*>(smem_raw + Ly.o_buf);   // [2][S][Jv] by cell parity
-  T* phss = reinterpret_cast<T*>(smem_raw + Ly.o_phs);   // [2][S][NMp] by cell parity
+  T* phss = reinterpret_cast<T*>(smem_raw + Ly.o_phs);   // [2][S][NMp] Phi_c (or x_c) by cell parity
   T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
   T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [NF][HS][Jv] y/z inflow
   T* Tg = reinterpret_cast<T*>(smem_raw + Ly.o_Tg);      // [2][Emax (col)][Emax (row)]
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
 #pragma unroll
     for (int u = 0; u < MM; ++u) {
       const int e = tid + u * NT;
-      if (e < S * nm) pm[u] = __ldcg(p.mom + c * S * nm + e);
+      if (e < S * nm) pm[u] = __ldcg((dense ? p.psi : p.mom) + c * S * nm + e);
     }
     pmat = p.cd.mat[c];
     // sigma_s in the kernel's precision: a conversion here would wait for the
@@ -313,29 +327,49 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
     }
   };
   // Phi_c += X_d^T delta for the cell `cp` whose delta is in buffer `slot`;
-  // also into the other buffer when the next cell is the same cell
-  auto update_moments = [&](long long cp, int slot, bool next_same) {
+  // also into the other buffer when the next cell is the same cell.  One
+  // thread per moment (l, k): it reads column k of X_d (consecutive threads,
+  // consecutive k: no bank conflicts) and the node's delta as 16-byte chunks
+  // (one address per warp: a broadcast); the stores to mom are coalesced.
+  // In the dense form only a next cell equal to this one needs its x_c: the
+  // old one with direction dp's block advanced by delta.
+  auto update_moments = [&](long long cp, int slot, bool next_same, int dp) {
     const T* bf = bufs + (size_t)slot * Ev;
     T* ph = phss + (size_t)slot * S * NMp;
     T* ph2 = phss + (size_t)(slot ^ 1) * S * NMp;
-    for (int base = 0; base < S * nm; base += NQ) {
-      const int e = base + qd;
-      int lk = 0;
-      T a = T(0);
-      if (e < S * nm) {
-        lk = slk[e];
-        const T* xr = Xk + (lk & 0xffff) * Jp;
-        const T* dl = bf + (lk >> 16) * Jv;
-        for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a += V16<T>::dot(xr + ch, dl + ch);
-      }
-      a += __shfl_xor_sync(0xffffffffu, a, 1);
-      a += __shfl_xor_sync(0xffffffffu, a, 2);
-      if (e < S * nm && l4 == 0) {
+    if (dense) {
+      if (!next_same) return;
+      const int q0 = sdb[dp] * A, Jd = (p.dir_end[dp] - sdb[dp]) * A;
+      for (int e = tid; e < S * nm; e += NT) {
+        const int lk = slk[e];
         const int o = (lk >> 16) * NMp + (lk & 0xffff);
-        const T v = ph[o] + a;
-        p.mom[cp * S * nm + e] = v;
-        if (next_same) ph2[o] = v;
+        const int jd = (lk & 0xffff) - q0;
+        ph2[o] = ph[o] + (jd >= 0 && jd < Jd ? bf[(lk >> 16) * Jv + jd] : T(0));
       }
+      return;
+    }
+    for (int e = tid; e < S * nm; e += NT) {
+      const int lk = slk[e];
+      const int o = (lk >> 16) * NMp + (lk & 0xffff);
+      const T* xc = Xd + (lk & 0xffff);
+      const T* dl = bf + (lk >> 16) * Jv;
+      T a0 = T(0), a1 = T(0);
+      for (int j = 0; j < Jv; j += VW) {
+        if constexpr (VW == 4) {
+          const float4 dv = *reinterpret_cast<const float4*>(dl + j);
+          a0 += xc[(size_t)j * NMp] * dv.x;
+          a1 += xc[(size_t)(j + 1) * NMp] * dv.y;
+          a0 += xc[(size_t)(j + 2) * NMp] * dv.z;
+          a1 += xc[(size_t)(j + 3) * NMp] * dv.w;
+        } else {
+          const double2 dv = *reinterpret_cast<const double2*>(dl + j);
+          a0 += xc[(size_t)j * NMp] * dv.x;
+          a1 += xc[(size_t)(j + 1) * NMp] * dv.y;
+        }
+      }
+      const T v = ph[o] + (a0 + a1);
+      p.mom[cp * S * nm + e] = v;
+      if (next_same) ph2[o] = v;
     }
   };
   {
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
       const int* lj_d = slj + d * Ev;
       // the pending moment update uses the previous direction's tables
       __syncthreads();
-      if (pend) update_moments(last, (int)((kc - 1) & 1), c_next == last);
+      if (pend) update_moments(last, (int)((kc - 1) & 1), c_next == last, d > 0 ? d - 1 : ndir - 1);
       pend = false;
       __syncthreads();
       // stage this direction's tables (padded, zero filled)
@@ -372,17 +406,31 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
               (jc < J && jr < J) ? src[(size_t)(lc * J + jc) * p.Emax + lr * J + jr] : T(0);
         }
       }
-      for (int i = tid; i < Jv * NMp; i += NT) {
-        const int j = i / NMp, kk = i - j * NMp;
-        XFr[i] = (j < J && kk < nm) ? p.t.XFt[(long long)kk * nadof + qb * A + j] : T(0);
-      }
-      for (int i = tid; i < nm * Jp; i += NT) {
-        const int kk = i / Jp, j = i - kk * Jp;
-        Xk[i] = j < J ? p.t.X[(long long)(qb * A + j) * nm + kk] : T(0);
-      }
-      for (int i = tid; i < Jv * Jp; i += NT) {
-        const int j = i / Jp, j2 = i - j * Jp;
-        SLr[i] = (j < J && j2 < J) ? p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2] : T(0);
+      if (dense) {
+        // M_d = S_f[d rows] - S_dd^{L+D} in the direction's own columns
+        for (int i = tid; i < Jv * NMp; i += NT) {
+          const int j = i / NMp, kk = i - j * NMp;
+          T v = T(0);
+          if (j < J && kk < nm) {
+            v = p.Sf[(long long)(qb * A + j) * nadof + kk];
+            const int j2 = kk - qb * A;
+            if (j2 >= 0 && j2 < J) v -= p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2];
+          }
+          XFr[i] = v;
+        }
+      } else {
+        for (int i = tid; i < Jv * NMp; i += NT) {
+          const int j = i / NMp, kk = i - j * NMp;
+          XFr[i] = (j < J && kk < nm) ? p.t.XFt[(long long)kk * nadof + qb * A + j] : T(0);
+        }
+        for (int i = tid; i < Jv * NMp; i += NT) {
+          const int j = i / NMp, kk = i - j * NMp;
+          Xd[i] = (j < J && kk < nm) ? p.t.X[(long long)(qb * A + j) * nm + kk] : T(0);
+        }
+        for (int i = tid; i < Jv * Jp; i += NT) {
+          const int j = i / Jp, j2 = i - j * Jp;
+          SLr[i] = (j < J && j2 < J) ? p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2] : T(0);
+        }
       }
       for (int i = tid; i < (J / A) * DIM * A * A; i += NT) {
         const int jq = i / (DIM * A * A), rem = i - jq * DIM * A * A;
@@ -475,7 +523,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
               FaceWords<T>::load(wp, fw);
             }
           }
-          if (pend) update_moments(last, slot ^ 1, c == last);
+          if (pend) update_moments(last, slot ^ 1, c == last, d);
           __syncthreads();
           // ---- 2: the next cell of this block's sequence into registers;
           //         buf = X_d F Phi - S_dd^{L+D} x_old (four lanes per unknown)
@@ -500,7 +548,10 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
             cp_async_commit_group();  // one group per cell, possibly empty
           }
           for (int base = 0; base < Ev; base += NQ) {
-            const int pe = base + qd;
+            // quads in (j, l) order: the S quads of one j share its row of
+            // XFr (one 64-byte read serves them)
+            const int pq = base + qd;
+            const int pe = pq < Ev ? (pq & (S - 1)) * Jv + pq / S : Ev;
             const int lj = pe < Ev ? lj_d[pe] : -1;
             T a = T(0);
             if (lj >= 0) {
@@ -517,9 +568,11 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
                 else a += v;
               }
               a += a1;
-              const T* sl = SLr + j * Jp;
-              const T* xo = xold + l * Jv;
-              for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a -= V16<T>::dot(sl + ch, xo + ch);
+              if (!dense) {
+                const T* sl = SLr + j * Jp;
+                const T* xo = xold + l * Jv;
+                for (int ch = l4 * VW; ch < Jv; ch += 4 * VW) a -= V16<T>::dot(sl + ch, xo + ch);
+              }
             }
             a += __shfl_xor_sync(0xffffffffu, a, 1);
             a += __shfl_xor_sync(0xffffffffu, a, 2);
@@ -669,7 +722,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
       }
     }
   }
-  if (pend) update_moments(last, (int)((kc - 1) & 1), false);
+  if (pend) update_moments(last, (int)((kc - 1) & 1), false, 0);
   cp_async_wait_all();
 }
 
@@ -713,12 +766,13 @@ int rows_max_blocks(int shape, int threads, size_t smem) {
 }  // namespace
 
 template <class T>
-int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, int* nmat_s,
-                        int* threads, size_t* smem, int* gbuf) {
+int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, bool dense,
+                        int* nmat_s, int* threads, size_t* smem, int* gbuf) {
   if (g.a != 1 && g.a != 3) return 0;
   const int S = g.s;
+  if (dense) nmom = g.nadof;  // the cell vector x_c in the moments' place
   // four lanes per padded unknown and per moment, within one block
-  const RowsLayout<T> l0(0, Jmax, nmom, S, g.dim, g.a, ndir, 0);
+  const RowsLayout<T> l0(0, Jmax, nmom, S, g.dim, g.a, ndir, 0, dense);
   int nt = 4 * std::max(l0.Ev, S * nmom);
   nt = std::max(128, std::min(kRowsMaxThreads, (nt + 31) / 32 * 32));
   if (l0.Ev > kRowsMaxU * nt || S * nmom > kRowsMaxM * nt || (g.dim - 1) * (S / 2) * Jmax > nt ||
@@ -729,10 +783,10 @@ int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, i
   const int Emax = S * Jmax;
   int gb = 0;
   auto bytes_for = [&](int ns) {
-    return RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir, ns < nmat ? gb : 0).bytes;
+    return RowsLayout<T>(ns, Jmax, nmom, S, g.dim, g.a, ndir, ns < nmat ? gb : 0, dense).bytes;
   };
   gb = Emax * Emax;
-  if (RowsLayout<T>(0, Jmax, nmom, S, g.dim, g.a, ndir, gb).bytes > 200 * 1024) gb = 0;
+  if (RowsLayout<T>(0, Jmax, nmom, S, g.dim, g.a, ndir, gb, dense).bytes > 200 * 1024) gb = 0;
   int ns = nmat;
   while (ns > 0 && bytes_for(ns) > 200 * 1024) --ns;
   const size_t bytes = bytes_for(ns);
@@ -756,14 +810,16 @@ int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, i
 template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,
-                          T* phi, T* mom, const T* TinvT, const T* SLD, int Emax, int Jmax,
-                          int nmat, int nmat_s, int gbuf, int threads, size_t smem,
+                          T* phi, T* mom, const T* TinvT, const T* SLD, const T* Sf, int Emax,
+                          int Jmax, int nmat, int nmat_s, int gbuf, int threads, size_t smem,
                           const int* rows, int nblocks, int rpb, unsigned long long* faces,
                           unsigned tag0, int* err, cudaStream_t st) {
-  RowsArgs<T> a{g, t, cd, ndir, dir_begin, dir_end, sweeps, f, phi, mom, TinvT, SLD,
+  const int dense = Sf != nullptr ? 1 : 0;
+  RowsArgs<T> a{g, t, cd, ndir, dir_begin, dir_end, sweeps, f, phi, mom, TinvT, SLD, Sf, dense,
                 Emax, Jmax, nmat, nmat_s, gbuf, rows, rpb, faces, tag0, err};
-  const RowsLayout<T> l0(0, Jmax, t.nmom, g.s, g.dim, g.a, ndir, 0);
-  const int shape = rows_shape(l0.Ev, g.s * t.nmom, threads);
+  const int nm = dense ? g.nadof : t.nmom;
+  const RowsLayout<T> l0(0, Jmax, nm, g.s, g.dim, g.a, ndir, 0, dense != 0);
+  const int shape = rows_shape(l0.Ev, g.s * nm, threads);
   cudaError_t e;
   if (g.dim == 2)
     e = g.a == 3 ? rows_launch<T, 2, 3>(a, shape, nblocks, threads, smem, st)
@@ -779,19 +835,20 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
   return 0;
 }
 
-template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, int*, int*, size_t*,
+template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, bool, int*, int*, size_t*,
                                         int*);
-template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, int*, int*, size_t*,
-                                         int*);
+template int coarse_gs_rows_plan<double>(const Geom&, int, int, int, int, bool, int*, int*,
+                                         size_t*, int*);
 template int launch_coarse_gs_rows<float>(const Geom&, const LevelDev<float>&, const CellData&, int,
                                           const int*, const int*, int, const float*, float*,
-                                          float*, const float*, const float*, int, int, int, int,
-                                          int, int, size_t, const int*, int, int,
+                                          float*, const float*, const float*, const float*, int,
+                                          int, int, int, int, int, size_t, const int*, int, int,
                                           unsigned long long*, unsigned, int*, cudaStream_t);
 template int launch_coarse_gs_rows<double>(const Geom&, const LevelDev<double>&, const CellData&,
                                            int, const int*, const int*, int, const double*,
-                                           double*, double*, const double*, const double*, int,
-                                           int, int, int, int, int, size_t, const int*, int, int,
-                                           unsigned long long*, unsigned, int*, cudaStream_t);
+                                           double*, double*, const double*, const double*,
+                                           const double*, int, int, int, int, int, int, size_t,
+                                           const int*, int, int, unsigned long long*, unsigned,
+                                           int*, cudaStream_t);
 
 }  // namespace amgt

@@ -428,6 +428,48 @@ def test_row_pipelined_gs_3d_several_rows_per_block():
     ctx.close()
 
 
+GS_FORM_CASES = [
+    ("2d-12x10-two-materials", 2, (12, 10), 2, 3, [8, 5, 4], 0),
+    ("2d-6x5-per-cell", 2, (6, 5), 2, 3, [8, 4, 3], 0),
+    ("2d-20x40-4-blocks", 2, (20, 40), 1, 1, [3], 4),
+    ("3d-4x3x5-2-blocks", 3, (4, 3, 5), 1, 1, [3], 2),
+]
+
+
+@pytest.mark.parametrize("name,dim,nc,level,nlev,Nr,blocks", GS_FORM_CASES,
+                         ids=[c[0] for c in GS_FORM_CASES])
+@pytest.mark.parametrize("form", [1, 2], ids=["moment-form", "dense-form"])
+def test_row_pipelined_gs_forms(name, dim, nc, level, nlev, Nr, blocks, form):
+    """The row-pipelined coarse Gauss-Seidel with its scattering source in
+    the moment form (flux moments kept per cell) and in the dense form
+    (S_f rows of the direction minus S_dd^{L+D} times the cell's current
+    unknowns, no moments), both against the oracle's block Gauss-Seidel:
+    staged, tiled and per-cell materials, several rows per block, 3D, and
+    in 2D the cell that ends one direction and starts the next."""
+    from paper_2010_04559_gb300 import AMGT_TUNE_GS_FORM, AMGT_TUNE_GS_GRID_BLOCKS
+    prob = _mg_problem(dim, nc, level, "lin", nlev, Nr, sweeps=2, seed=57)
+    if nc == (20, 40):
+        n = 20 * 40
+        prob["sigma_t"] = np.where(np.arange(n) % 7 < 3, 1.0, 4.0)
+        prob["sigma_s"] = np.where(np.arange(n) % 7 < 3, 0.6, 3.7)
+    H = multigrid.Hierarchy(prob)
+    Tc = H.levels[-1]
+    ctx = _ctx(prob)
+    ctx.amgt_set_tuning(1, 6)
+    ctx.amgt_set_tuning(AMGT_TUNE_GS_FORM, form)
+    if blocks:
+        ctx.amgt_set_tuning(AMGT_TUNE_GS_GRID_BLOCKS, blocks)
+    fc = W.random_vector((Tc.nsdof, Tc.nadof), 58)
+    x0 = W.random_vector((Tc.nsdof, Tc.nadof), 59)
+    ref = multigrid.coarse_gs(Tc, fc, x0, 2)
+    for td, tol in ((torch.float64, 1e-12), (torch.float32, 2e-4)):
+        xd = _dev(x0, td)
+        ctx.amgt_op_coarse_gs(2, _dev(fc, td), xd)
+        ctx.amgt_sync()
+        assert _rel(_host(xd), ref) < tol
+    ctx.close()
+
+
 @pytest.mark.parametrize("group", [2, 4, 8], ids=["G2", "G4", "G8"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("nc", [(37, 29), (5, 21), (70, 24)], ids=["37x29", "5x21", "70x24"])
