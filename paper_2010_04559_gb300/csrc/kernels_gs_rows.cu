@@ -212,6 +212,81 @@ struct RowsArgs {
   int* err;
 };
 
+// Per-direction staging of the tables into shared memory (padded, zero
+// filled), by the block's NT threads.  Block inverses of the staged materials:
+// Tin[mt][row][col] over the padded unknowns (l Jv + j).
+template <class T>
+__device__ void stage_tinv(const RowsArgs<T>& p, T* Tin, int d, int J, int Jv, int Ev, int Evp,
+                           int tid, int NT) {
+  for (int mt = 0; mt < p.nmat_s; ++mt) {
+    const T* src = p.TinvT + ((size_t)mt * p.ndir + d) * p.Emax * p.Emax;  // [col][row]
+    T* dst = Tin + (size_t)mt * Ev * Evp;
+    for (int i = tid; i < Ev * Ev; i += NT) {
+      const int cp = i / Ev, rp = i - cp * Ev;  // padded column, row
+      const int lc = cp / Jv, jc = cp - lc * Jv, lr = rp / Jv, jr = rp - lr * Jv;
+      dst[(size_t)rp * Evp + cp] =
+          (jc < J && jr < J) ? src[(size_t)(lc * J + jc) * p.Emax + lr * J + jr] : T(0);
+    }
+  }
+}
+// M_d = S_f[d rows] - S_dd^{L+D} in the direction's own columns: [Jv][NMp]
+template <class T>
+__device__ void stage_md(const RowsArgs<T>& p, T* Md, int d, int q0, int J, int Jv, int NMp,
+                         int nadof, int tid, int NT) {
+  for (int i = tid; i < Jv * NMp; i += NT) {
+    const int j = i / NMp, kk = i - j * NMp;
+    T v = T(0);
+    if (j < J && kk < nadof) {
+      v = p.Sf[(long long)(q0 + j) * nadof + kk];
+      const int j2 = kk - q0;
+      if (j2 >= 0 && j2 < J) v -= p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2];
+    }
+    Md[i] = v;
+  }
+}
+// A^xi of the direction's patches: Ad[patch][axis][A][A]
+template <class T, int DIM, int A>
+__device__ void stage_ad(const RowsArgs<T>& p, T* Ad, int qb, int J, int tid, int NT) {
+  for (int i = tid; i < (J / A) * DIM * A * A; i += NT) {
+    const int jq = i / (DIM * A * A), rem = i - jq * DIM * A * A;
+    const int xi = rem / (A * A), e = rem - xi * A * A;
+    Ad[i] = p.t.Aax[((size_t)(qb + jq) * 3 + xi) * A * A + e];
+  }
+}
+// W[(lr, jr)][(axis, jn, jq A + dd)] = sum over the inflow-face nodes l and m
+// of Tinv[(lr, jr)][(l, jq A + m)] U, with U the coupling of the rhs of
+// (l, jq A + m) to the upwind face value (jn, jq A + dd) as in the rhs
+// assembly; reads the staged Tin and Ad (a barrier after their staging)
+template <class T, int DIM, int A>
+__device__ void stage_w(const RowsArgs<T>& p, const T* Tin, const T* Ad, T* Wl, const int* lj_d,
+                        int J, int Jv, int Ev, int Evp, int Eyl, int Wp, int n1, int n2, int tid,
+                        int NT) {
+  constexpr int S = 1 << DIM, HS = S / 2;
+  for (int i = tid; i < p.nmat_s * Ev * Eyl; i += NT) {
+    const int mt = i / (Ev * Eyl);
+    const int rem = i - mt * Ev * Eyl;
+    const int pe = rem / Eyl, ey = rem - pe * Eyl;
+    const int xi = 1 + ey / (HS * Jv);
+    const int jn = (ey / Jv) % HS, jc = ey % Jv;
+    T w = T(0);
+    if (lj_d[pe] >= 0 && jc < J) {
+      const int own = xi == 1 ? n1 : n2;
+      const int jq = jc / A, dd = jc - jq * A;
+      const T sg = own ? T(-1) : T(1);
+      const T* trow = Tin + ((size_t)mt * Ev + pe) * Evp;
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        if (((l >> xi) & 1) != own) continue;
+        const T fm = sg * T(p.g.facemass[xi][fcompress(l, xi)][jn]);
+#pragma unroll
+        for (int m = 0; m < A; ++m)
+          w += trow[l * Jv + jq * A + m] * fm * Ad[((size_t)jq * DIM + xi) * A * A + m * A + dd];
+      }
+    }
+    Wl[((size_t)mt * Ev + pe) * Wp + ey] = w;
+  }
+}
+
 template <class T, int DIM, int A, int UM, int MM>
 __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(RowsArgs<T> p) {
   constexpr int S = 1 << DIM;
@@ -396,28 +471,9 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
       pend = false;
       __syncthreads();
       // stage this direction's tables (padded, zero filled)
-      for (int mt = 0; mt < p.nmat_s; ++mt) {
-        const T* src = p.TinvT + ((size_t)mt * ndir + d) * p.Emax * p.Emax;  // [col][row]
-        T* dst = Tin + (size_t)mt * Ev * Evp;
-        for (int i = tid; i < Ev * Ev; i += NT) {
-          const int cp = i / Ev, rp = i - cp * Ev;  // padded column, row
-          const int lc = cp / Jv, jc = cp - lc * Jv, lr = rp / Jv, jr = rp - lr * Jv;
-          dst[(size_t)rp * Evp + cp] =
-              (jc < J && jr < J) ? src[(size_t)(lc * J + jc) * p.Emax + lr * J + jr] : T(0);
-        }
-      }
+      stage_tinv(p, Tin, d, J, Jv, Ev, Evp, tid, NT);
       if (dense) {
-        // M_d = S_f[d rows] - S_dd^{L+D} in the direction's own columns
-        for (int i = tid; i < Jv * NMp; i += NT) {
-          const int j = i / NMp, kk = i - j * NMp;
-          T v = T(0);
-          if (j < J && kk < nm) {
-            v = p.Sf[(long long)(qb * A + j) * nadof + kk];
-            const int j2 = kk - qb * A;
-            if (j2 >= 0 && j2 < J) v -= p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2];
-          }
-          XFr[i] = v;
-        }
+        stage_md(p, XFr, d, qb * A, J, Jv, NMp, nadof, tid, NT);
       } else {
         for (int i = tid; i < Jv * NMp; i += NT) {
           const int j = i / NMp, kk = i - j * NMp;
@@ -432,11 +488,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
           SLr[i] = (j < J && j2 < J) ? p.SLD[((size_t)d * p.Jmax + j) * p.Jmax + j2] : T(0);
         }
       }
-      for (int i = tid; i < (J / A) * DIM * A * A; i += NT) {
-        const int jq = i / (DIM * A * A), rem = i - jq * DIM * A * A;
-        const int xi = rem / (A * A), e = rem - xi * A * A;
-        Ad[i] = p.t.Aax[((size_t)(qb + jq) * 3 + xi) * A * A + e];
-      }
+      stage_ad<T, DIM, A>(p, Ad, qb, J, tid, NT);
       // this thread's face word (axis, face node, unknown), if it polls one
       const int npoll = NF * HS * J;
       int pa = 0, pjn = 0, pj = 0;
@@ -447,33 +499,7 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
         pj = rem - pjn * J;
       }
       __syncthreads();
-      // W[(lr, jr)][(axis, jn, jq A + dd)] = sum over the inflow-face nodes l
-      // and m of Tinv[(lr, jr)][(l, jq A + m)] U, with U the coupling of the
-      // rhs of (l, jq A + m) to the upwind face value (jn, jq A + dd) as in
-      // the rhs assembly below
-      for (int i = tid; i < p.nmat_s * Ev * Eyl; i += NT) {
-        const int mt = i / (Ev * Eyl);
-        const int rem = i - mt * Ev * Eyl;
-        const int pe = rem / Eyl, ey = rem - pe * Eyl;
-        const int xi = 1 + ey / (HS * Jv);
-        const int jn = (ey / Jv) % HS, jc = ey % Jv;
-        T w = T(0);
-        if (lj_d[pe] >= 0 && jc < J) {
-          const int own = xi == 1 ? n1 : n2;
-          const int jq = jc / A, dd = jc - jq * A;
-          const T sg = own ? T(-1) : T(1);
-          const T* trow = Tin + ((size_t)mt * Ev + pe) * Evp;
-#pragma unroll
-          for (int l = 0; l < S; ++l) {
-            if (((l >> xi) & 1) != own) continue;
-            const T fm = sg * T(g.facemass[xi][fcompress(l, xi)][jn]);
-#pragma unroll
-            for (int m = 0; m < A; ++m)
-              w += trow[l * Jv + jq * A + m] * fm * Ad[((size_t)jq * DIM + xi) * A * A + m * A + dd];
-          }
-        }
-        Wl[((size_t)mt * Ev + pe) * Wp + ey] = w;
-      }
+      stage_w<T, DIM, A>(p, Tin, Ad, Wl, lj_d, J, Jv, Ev, Evp, Eyl, Wp, n1, n2, tid, NT);
       __syncthreads();
       for (int ri = 0;; ++ri) {
         const int R = row_of(d, ri);
@@ -726,6 +752,340 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
   cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Register form of the row-pipelined Gauss-Seidel: the dense form in FP32 on
+// 2D Lin meshes with every material staged (at most two), at most 24
+// unknowns per node and direction and at most 96 angular unknowns.  The
+// per-cell work of the kernel above is a few short products with the
+// direction's fixed matrices, so here each thread keeps its share of them in
+// registers for the whole direction pass: M_d (warp w: rows j = w, w + 16;
+// lane: columns 3 lane .. 3 lane + 2), each material's block inverse (warp w:
+// rows 6 w .. 6 w + 5, the same columns) and its late-inflow table W (half
+// warp h: rows 6 w + 3 h .. 6 w + 3 h + 2; columns 3 (lane mod 16) ..).  The
+// vectors are read from shared memory by consecutive lanes (no bank
+// conflicts), the partial sums reduced across the warp with the result
+// spread over lane groups, and a cell takes four block barriers:
+//   1  the cell's x_c and f into shared memory, the next cell's prefetch;
+//   2  buf = M_d x_c, rhs0 = f - x-upwind + sigma_s N buf (N mixes the nodes
+//      held by one warp: shuffles);
+//   3  y0 = Tinv rhs0; the face words of the upwind row;
+//   4  x = y0 + W yup, stores (psi, the x- and y-outflow faces).
+// Schedule, face words, tags and waits are those of the kernel above.
+constexpr int kFastThreads = 512;
+
+// sum over the warp of v[0..7]; lane L receives the sum of v[(L >> 2) & 7]
+// (the index halves at each of the first three exchange levels)
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane) {
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  float a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    a[i] = (b4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 4], 16);
+  float c[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    c[i] = (b3 ? a[i + 2] : a[i]) + __shfl_xor_sync(0xffffffffu, b3 ? a[i] : a[i + 2], 8);
+  float e = (b2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b2 ? c[0] : c[1], 4);
+  e += __shfl_xor_sync(0xffffffffu, e, 2);
+  e += __shfl_xor_sync(0xffffffffu, e, 1);
+  return e;
+}
+// sum over a half warp of v[0..3]; lane L receives the sum of v[(L >> 2) & 3]
+__device__ __forceinline__ float half_sum4(const float (&v)[4], int lane) {
+  const bool b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  float c[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    c[i] = (b3 ? v[i + 2] : v[i]) + __shfl_xor_sync(0xffffffffu, b3 ? v[i] : v[i + 2], 8);
+  float e = (b2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b2 ? c[0] : c[1], 4);
+  e += __shfl_xor_sync(0xffffffffu, e, 2);
+  e += __shfl_xor_sync(0xffffffffu, e, 1);
+  return e;
+}
+
+// the fast form applies: FP32 dense form, 2D Lin patches, every material
+// staged (at most two), J <= 24 and nadof <= 96
+__host__ __device__ inline bool rows_fast_applies(int dim, int a, int nadof, int Jmax, int nmat,
+                                                  int nmat_s) {
+  return dim == 2 && a == 3 && nadof <= 96 && Jmax <= 24 && nmat <= 2 && nmat_s == nmat;
+}
+
+template <int NMAT>
+__global__ void __launch_bounds__(kFastThreads, 1) coarse_gs_rows_fast_kernel(RowsArgs<float> p) {
+  using T = float;
+  constexpr int DIM = 2, S = 4, HS = 2, A = 3;
+  constexpr int W = FaceWords<T>::W;
+  const Geom& g = p.g;
+  const int nadof = g.nadof, nx = g.nx, ndir = p.ndir;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
+  const int nb = gridDim.x, b = blockIdx.x;
+  const RowsLayout<T> Ly(p.nmat_s, p.Jmax, nadof, S, DIM, A, ndir, 0, true);
+  const int Jv = Ly.Jv, Ev = Ly.Ev, Evp = Ly.Evp, NMp = Ly.NMp, Eyl = Ly.Eyl, Wp = Ly.Wp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Tin = reinterpret_cast<T*>(smem_raw + Ly.o_Tin);    // [nmat_s][Ev][Evp]
+  T* Md = reinterpret_cast<T*>(smem_raw + Ly.o_XFr);     // [Jv][NMp]
+  T* Ns = reinterpret_cast<T*>(smem_raw + Ly.o_Ns);      // [S][S]
+  T* Ad = reinterpret_cast<T*>(smem_raw + Ly.o_Ad);      // [patch][axis][A][A]
+  int* slj = reinterpret_cast<int*>(smem_raw + Ly.o_lj); // [ndir][Ev] l<<16|j, -1 past J
+  T* rhs = reinterpret_cast<T*>(smem_raw + Ly.o_rhs);    // [S][Jv] rhs0
+  T* fb = reinterpret_cast<T*>(smem_raw + Ly.o_xold);    // [S][Jv] f of the direction block
+  T* xc = reinterpret_cast<T*>(smem_raw + Ly.o_phs);     // [S][NMp] the cell's unknowns
+  T* xfc = reinterpret_cast<T*>(smem_raw + Ly.o_xfc);    // [HS][Jv] x-outflow of the last cell
+  T* yup = reinterpret_cast<T*>(smem_raw + Ly.o_yup);    // [HS][Jv] y inflow
+  T* Wl = reinterpret_cast<T*>(smem_raw + Ly.o_W);       // [nmat_s][Ev][Wp]
+  __shared__ int sdb[8], sde[8];
+  if (tid < ndir) {
+    sdb[tid] = p.dir_begin[tid];
+    sde[tid] = p.dir_end[tid];
+  }
+  for (int i = tid; i < S * S; i += NT) Ns[i] = (T)g.Nmass[i];
+  for (int i = tid; i < Eyl; i += NT) yup[i] = T(0);
+  for (int i = tid; i < HS * Jv; i += NT) xfc[i] = T(0);
+  for (int i = tid; i < ndir * Ev; i += NT) {
+    const int d = i / Ev, pe = i - d * Ev;
+    const int J = (p.dir_end[d] - p.dir_begin[d]) * A;
+    const int l = pe / Jv, j = pe - l * Jv;
+    slj[i] = j < J ? (l << 16) | j : -1;
+  }
+  const int* myrows = p.rows + (size_t)b * p.rpb;
+  auto row_of = [&](int d, int ri) -> int {
+    return ri < p.rpb ? myrows[(size_t)d * nb * p.rpb + ri] : -1;
+  };
+  const T fm00 = T(g.facemass[0][0][0]), fm01 = T(g.facemass[0][0][1]);
+  const T fm10 = T(g.facemass[0][1][0]), fm11 = T(g.facemass[0][1][1]);
+  __syncthreads();
+  // prefetch registers: one value of x_c (threads < S nadof) or of f (the
+  // next Ev threads), the material and sigma_s
+  T xpf = T(0), fpf = T(0);
+  int pmat = 0;
+  T psig = T(0);
+  long long c_next = -1;
+  const int nxc = S * nadof;
+  auto prefetch = [&](int d, int R, int k) {
+    const int n0 = (d >> 1) & 1;
+    const long long c = (n0 ? nx - 1 - k : k) + (long long)nx * R;
+    c_next = c;
+    if (tid < nxc) {
+      xpf = __ldcg(p.psi + c * nxc + tid);
+    } else if (tid < nxc + Ev) {
+      const int e = tid - nxc, l = e / Jv, j = e - (e / Jv) * Jv;
+      const int J = (sde[d] - sdb[d]) * A;
+      fpf = j < J ? p.f[(c * S + l) * nadof + sdb[d] * A + j] : T(0);
+    }
+    pmat = p.cd.mat[c];
+    psig = p.cd.sigma_s32[c];
+  };
+  if (p.sweeps > 0) prefetch(0, row_of(0, 0), 0);
+  float Mr[2][3], Tr[NMAT][6][3], Wr[NMAT][3][3];
+  const int h = lane >> 4;
+  long long last = -1;
+  for (int sw = 0; sw < p.sweeps; ++sw) {
+    const unsigned tag = p.tag0 + (unsigned)sw + 1u;
+    for (int d = 0; d < ndir; ++d) {
+      const int n0 = (d >> 1) & 1, n1 = d & 1;
+      const int qb = sdb[d];
+      const int J = (sde[d] - qb) * A;
+      __syncthreads();  // the last direction's cells are done with the tables
+      stage_tinv(p, Tin, d, J, Jv, Ev, Evp, tid, NT);
+      stage_md(p, Md, d, qb * A, J, Jv, NMp, nadof, tid, NT);
+      stage_ad<T, DIM, A>(p, Ad, qb, J, tid, NT);
+      __syncthreads();
+      stage_w<T, DIM, A>(p, Tin, Ad, Wl, slj + d * Ev, J, Jv, Ev, Evp, Eyl, Wp, n1, 0, tid, NT);
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const int j = warp + 16 * r, k = 3 * lane + t;
+          Mr[r][t] = (j < Jv && k < NMp) ? Md[j * NMp + k] : T(0);
+        }
+#pragma unroll
+      for (int mt = 0; mt < NMAT; ++mt) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int e = 6 * warp + i, cc = 3 * lane + t;
+            Tr[mt][i][t] = (mt < p.nmat_s && e < Ev && cc < Ev) ? Tin[((size_t)mt * Ev + e) * Evp + cc]
+                                                                : T(0);
+          }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int e = 6 * warp + 3 * h + i, cc = 3 * (lane & 15) + t;
+            Wr[mt][i][t] = (mt < p.nmat_s && e < Ev && cc < Eyl) ? Wl[((size_t)mt * Ev + e) * Wp + cc]
+                                                                 : T(0);
+          }
+      }
+      // this thread's face word (face node, unknown), if it polls one
+      const int npoll = HS * J;
+      const int pjn = tid < npoll ? tid / J : 0, pj = tid < npoll ? tid - (tid / J) * J : 0;
+      for (int ri = 0;; ++ri) {
+        const int R = row_of(d, ri);
+        if (R < 0) break;
+        const int jy = n1 ? g.ny - 1 - R : R;
+        for (int k = 0; k < nx; ++k) {
+          const long long c = c_next;
+          const int mat = pmat;
+          const T sig_s = psig;
+          // ---- 1: the cell's vectors; first look at the face words; prefetch
+          if (c != last) {
+            if (tid < nxc) xc[(tid / nadof) * NMp + (tid - (tid / nadof) * nadof)] = xpf;
+          }
+          if (tid >= nxc && tid < nxc + Ev) fb[tid - nxc] = fpf;
+          const unsigned long long* wp = nullptr;
+          unsigned long long fw[W];
+          const bool need = tid < npoll && jy > 0;
+          if (need) {
+            const long long cn = c + (n1 ? (long long)nx : -(long long)nx);
+            wp = p.faces + ((((size_t)0 * ndir + d) * g.C + cn) * HS * p.Jmax + (size_t)pjn * J + pj) * W;
+            FaceWords<T>::load(wp, fw);
+          }
+          {
+            int d2 = d, ri2 = ri, k2 = k + 1, sw2 = sw, R2 = R;
+            bool more = true;
+            if (k2 >= nx) {
+              k2 = 0;
+              ++ri2;
+              R2 = row_of(d2, ri2);
+              if (R2 < 0) {
+                ri2 = 0;
+                if (++d2 >= ndir) {
+                  d2 = 0;
+                  more = ++sw2 < p.sweeps;
+                }
+                if (more) R2 = row_of(d2, ri2);
+              }
+            }
+            if (more) prefetch(d2, R2, k2);
+            else c_next = -2;
+          }
+          __syncthreads();
+          // ---- 2: buf = M_d x_c; rhs0 = f - x-upwind + sigma_s N buf
+          {
+            float v[8];
+            float xv[4][3];
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+              for (int t = 0; t < 3; ++t) {
+                const int kk = 3 * lane + t;
+                xv[l][t] = kk < NMp ? xc[l * NMp + kk] : T(0);
+              }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+              for (int l = 0; l < 4; ++l)
+                v[r * 4 + l] = Mr[r][0] * xv[l][0] + Mr[r][1] * xv[l][1] + Mr[r][2] * xv[l][2];
+            const float tot = warp_sum8(v, lane);
+            const int grp = (lane >> 2) & 7, r = grp >> 2, l = grp & 3;
+            float bi[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) bi[i] = __shfl_sync(0xffffffffu, tot, ((r << 2) | i) << 2);
+            const int j = warp + 16 * r;
+            if ((lane & 3) == 0 && j < Jv) {
+              T val = T(0);
+              if (j < J) {
+                const T mix = Ns[l * S + 0] * bi[0] + Ns[l * S + 1] * bi[1] + Ns[l * S + 2] * bi[2] +
+                              Ns[l * S + 3] * bi[3];
+                val = fb[l * Jv + j] + sig_s * mix;
+                if (k > 0 && (l & 1) == n0) {
+                  const int jq = j / A, m = j - jq * A, jp = l >> 1;
+                  const T* An = Ad + ((size_t)jq * DIM + 0) * A * A + m * A;
+                  const T* u0 = xfc + jq * A;
+                  const T* u1 = xfc + Jv + jq * A;
+                  const T s0 = An[0] * u0[0] + An[1] * u0[1] + An[2] * u0[2];
+                  const T s1 = An[0] * u1[0] + An[1] * u1[1] + An[2] * u1[2];
+                  const T acc = jp ? fm10 * s0 + fm11 * s1 : fm00 * s0 + fm01 * s1;
+                  val -= (n0 ? T(1) : T(-1)) * acc;
+                }
+              }
+              rhs[l * Jv + j] = val;
+            }
+          }
+          __syncthreads();
+          // ---- 3: y0 = Tinv rhs0; the upwind row's face values
+          float y0;
+          {
+            float rv[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) rv[t] = 3 * lane + t < Ev ? rhs[3 * lane + t] : T(0);
+            float v[8];
+            v[6] = v[7] = 0.f;
+            if (NMAT == 1 || mat == 0) {
+#pragma unroll
+              for (int i = 0; i < 6; ++i) v[i] = Tr[0][i][0] * rv[0] + Tr[0][i][1] * rv[1] + Tr[0][i][2] * rv[2];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 6; ++i)
+                v[i] = Tr[NMAT - 1][i][0] * rv[0] + Tr[NMAT - 1][i][1] * rv[1] + Tr[NMAT - 1][i][2] * rv[2];
+            }
+            y0 = warp_sum8(v, lane);
+          }
+          if (need) {
+            if (!FaceWords<T>::ready(fw, tag)) {
+              const unsigned long long t0 = gsx::now_ns();
+              unsigned it = 0;
+              do {
+                FaceWords<T>::load(wp, fw);
+                if ((++it & 63u) == 0) {
+                  // after any block gave up, the others stop waiting too
+                  if (gsx::now_ns() - t0 > kRowsWaitNs) atomicExch(p.err, 5);
+                  if (*reinterpret_cast<volatile int*>(p.err) != 0) break;
+                }
+              } while (!FaceWords<T>::ready(fw, tag));
+            }
+            yup[pjn * Jv + pj] = FaceWords<T>::value(fw);
+          }
+          __syncthreads();
+          // ---- 4: x = y0 + W yup; outputs
+          {
+            float wy = 0.f;
+            if (jy > 0) {
+              float yv[3];
+#pragma unroll
+              for (int t = 0; t < 3; ++t) {
+                const int cc = 3 * (lane & 15) + t;
+                yv[t] = cc < Eyl ? yup[cc] : T(0);
+              }
+              float v[4];
+              v[3] = 0.f;
+              if (NMAT == 1 || mat == 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) v[i] = Wr[0][i][0] * yv[0] + Wr[0][i][1] * yv[1] + Wr[0][i][2] * yv[2];
+              } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                  v[i] = Wr[NMAT - 1][i][0] * yv[0] + Wr[NMAT - 1][i][1] * yv[1] + Wr[NMAT - 1][i][2] * yv[2];
+              }
+              wy = half_sum4(v, lane);
+            }
+            const int ip = (lane >> 2) & 3;
+            const float y0v = __shfl_sync(0xffffffffu, y0, (4 * (3 * h + ip)) & 31);
+            const int e = 6 * warp + 3 * h + ip;
+            if ((lane & 3) == 0 && ip < 3 && e < Ev) {
+              const int l = e / Jv, j = e - (e / Jv) * Jv;
+              if (j < J) {
+                const T x = y0v + wy;
+                p.psi[(c * S + l) * nadof + qb * A + j] = x;
+                if (c_next == c) xc[l * NMp + qb * A + j] = x;  // the next cell is this one
+                if ((l & 1) != n0) xfc[(l >> 1) * Jv + j] = x;
+                if (((l >> 1) & 1) != n1 && jy < g.ny - 1)
+                  FaceWords<T>::put(p.faces + ((((size_t)0 * ndir + d) * g.C + c) * HS * p.Jmax +
+                                               (size_t)(l & 1) * J + j) * W,
+                                    x, tag);
+              }
+            }
+          }
+          __syncthreads();
+          last = c;
+        }
+      }
+    }
+  }
+}
+
 template <class T, int DIM, int A, class F>
 auto with_rows_kernel(int shape, F f) {
   if (shape == 0) return f(coarse_gs_rows_kernel<T, DIM, A, 1, 1>);
@@ -794,6 +1154,26 @@ int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, b
   *gbuf = ns < nmat ? gb : 0;
   const int shape = rows_shape(l0.Ev, S * nmom, nt);
   int nb;
+  if constexpr (sizeof(T) == 4) {
+    if (dense && rows_fast_applies(g.dim, g.a, g.nadof, Jmax, nmat, ns)) {
+      // the register form: 512 threads, one launch shape per material count
+      int per_sm = 0;
+      auto kern = nmat == 1 ? coarse_gs_rows_fast_kernel<1> : coarse_gs_rows_fast_kernel<2>;
+      if (allow_max_smem(kern) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFastThreads, bytes) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+      }
+      int dev = 0, nsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      *nmat_s = ns;
+      *threads = kFastThreads;
+      *smem = bytes;
+      return std::min(per_sm * nsm, g.ny * g.nz);
+    }
+  }
   if (g.dim == 2)
     nb = g.a == 3 ? rows_max_blocks<T, 2, 3>(shape, nt, bytes)
                   : rows_max_blocks<T, 2, 1>(shape, nt, bytes);
@@ -821,7 +1201,21 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
   const RowsLayout<T> l0(0, Jmax, nm, g.s, g.dim, g.a, ndir, 0, dense != 0);
   const int shape = rows_shape(l0.Ev, g.s * nm, threads);
   cudaError_t e;
-  if (g.dim == 2)
+  bool fast = false;
+  if constexpr (sizeof(T) == 4) {
+    fast = dense && threads == kFastThreads && rows_fast_applies(g.dim, g.a, g.nadof, Jmax, nmat,
+                                                                 nmat_s);
+    if (fast) {
+      auto kern = nmat == 1 ? coarse_gs_rows_fast_kernel<1> : coarse_gs_rows_fast_kernel<2>;
+      e = allow_max_smem(kern);
+      if (e == cudaSuccess) {
+        void* args[] = {(void*)&a};
+        e = cudaLaunchCooperativeKernel((void*)kern, dim3(nblocks), dim3(threads), args, smem, st);
+      }
+    }
+  }
+  if (fast) {
+  } else if (g.dim == 2)
     e = g.a == 3 ? rows_launch<T, 2, 3>(a, shape, nblocks, threads, smem, st)
                  : rows_launch<T, 2, 1>(a, shape, nblocks, threads, smem, st);
   else
