@@ -287,11 +287,13 @@ int amgt_set_boundary(amgt_ctx* ctx, int face, int kind, const double* params);
  *                         (default), 1 in FP64 (the right-hand side converted
  *                         to FP64, the FP64 sweeps, the result rounded back)
  *   AMGT_TUNE_GS_FORM     the row-pipelined coarse Gauss-Seidel's scattering
- *                         source: 0 auto (the dense form where the angular
- *                         unknowns are fewer than twice the moments plus a
- *                         direction's unknowns and one moment shape is in
- *                         use), 1 the moment form (flux moments kept per
- *                         cell), 2 the dense form S_f x_c where it applies;
+ *                         source: 0 auto (with one moment shape in use, the
+ *                         dense form where the angular unknowns are fewer
+ *                         than twice the moments plus a direction's unknowns,
+ *                         and in FP32 also where its register kernel applies:
+ *                         2D Lin patches, at most 96 angular unknowns and two
+ *                         materials), 1 the moment form (flux moments kept
+ *                         per cell), 2 the dense form S_f x_c where it applies;
  *                         takes effect at the next set-up (the context is
  *                         rebuilt before its next use)
  *   AMGT_TUNE_TEST_SWEEP_HOLD for tests of the failure path only: 1 makes

@@ -47,7 +47,7 @@ struct Level {
   // materials whose block inverses fit in shared memory and the shared bytes,
   // per precision (blocks 0: not available)
   int rows_nb = 0, rows_rpb = 0;
-  int rows_dense = 0;  // dense form M_d x_c (S_f of the level built)
+  int rows_dense[2] = {0, 0};  // per precision: dense form M_d x_c (S_f built)
   int rows_nmat_s[2] = {0, 0}, rows_threads[2] = {0, 0}, rows_gbuf[2] = {0, 0};
   size_t rows_smem[2] = {0, 0};
   int* d_rows = nullptr;                      // [ndir][rows_nb][rows_rpb]

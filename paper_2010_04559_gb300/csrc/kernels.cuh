@@ -188,6 +188,8 @@ int launch_coarse_gs_tc(const Geom& g, const LevelDev<float>& t, const CellData&
 template <class T>
 int coarse_gs_rows_plan(const Geom& g, int ndir, int nmat, int Jmax, int nmom, bool dense,
                         int* nmat_s, int* threads, size_t* smem, int* gbuf);
+// the register form of the FP32 dense-form kernel serves this plan
+bool coarse_gs_rows_fast(const Geom& g, int Jmax, int nmat, int nmat_s, int threads);
 template <class T>
 int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& cd, int ndir,
                           const int* dir_begin, const int* dir_end, int sweeps, const T* f,

@@ -3,8 +3,12 @@
 // precision conversions.  Reductions are deterministic: each block writes its
 // partial sums to `partials[block][v]` and one block sums them in a fixed
 // order.  Arithmetic runs in the vectors' precision; partial sums of FP32
-// vectors are FP32 per thread and FP64 across threads.
+// vectors are FP32 per thread and FP64 across threads.  Every kernel streams
+// its vectors four elements at a time with 16-byte accesses (one float4, two
+// double2) where all its pointers are 16-byte aligned, and the last n mod 4
+// elements (or everything, for unaligned pointers) one at a time.
 #include <atomic>
+#include <cstdint>
 
 #include "kernels.cuh"
 
@@ -23,6 +27,27 @@ template <>
 struct Acc<float> {
   using type = float;
 };
+
+// four consecutive elements at p (16-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ bool al16(const void* p) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
 
 template <int NV>
 __device__ void block_reduce_store(double (&v)[NV], int nvec, double* __restrict__ partials) {
@@ -52,14 +77,37 @@ __global__ void __launch_bounds__(kThreads) multidot_kernel(long long n, int nve
                                                             double* __restrict__ partials) {
   using A = typename Acc<T>::type;
   A acc[NV];
+  const T* Vk[NV];
+  bool vec = al16(w);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = A(0);
-  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
+  for (int k = 0; k < NV; ++k) {
+    acc[k] = A(0);
+    Vk[k] = k < nvec ? V[k] : w;
+    vec = vec && al16(Vk[k]);
+  }
+  const long long start = blockIdx.x * (long long)kThreads + threadIdx.x;
+  const long long stride = (long long)gridDim.x * kThreads;
+  long long i0 = 0;
+  if (vec) {
+    for (long long i = start; i < (n >> 2); i += stride) {
+      T wv[4];
+      ld4(w + 4 * i, wv);
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k < nvec) {
+          T vv[4];
+          ld4(Vk[k] + 4 * i, vv);
+          acc[k] += ((A)vv[0] * (A)wv[0] + (A)vv[1] * (A)wv[1]) +
+                    ((A)vv[2] * (A)wv[2] + (A)vv[3] * (A)wv[3]);
+        }
+    }
+    i0 = (n >> 2) << 2;
+  }
+  for (long long i = i0 + start; i < n; i += stride) {
     const A wi = (A)w[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      if (k < nvec) acc[k] += (A)V[k][i] * wi;
+      if (k < nvec) acc[k] += (A)Vk[k][i] * wi;
   }
   double d[NV];
 #pragma unroll
@@ -81,16 +129,56 @@ __global__ void __launch_bounds__(kThreads) update_multidot_kernel(
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = A(0);
   A hA[NV];
+  // the 16-byte form keeps 4 NV values of V in registers: up to 8 vectors
+  constexpr int KV = NV <= 8 ? NV : 1;
+  const T* Vk[KV];
+  bool vec = NV <= 8 && al16(w);
 #pragma unroll
   for (int k = 0; k < NV; ++k) hA[k] = k < nvec ? (A)hs[k] : A(0);
-  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
+#pragma unroll
+  for (int k = 0; k < KV; ++k) {
+    Vk[k] = k < nvec ? V[k] : w;
+    vec = vec && al16(Vk[k]);
+  }
+  const long long start = blockIdx.x * (long long)kThreads + threadIdx.x;
+  const long long stride = (long long)gridDim.x * kThreads;
+  long long i0 = 0;
+  if (vec) {
+    for (long long i = start; i < (n >> 2); i += stride) {
+      T vk[KV][4], wv[4];
+      ld4(w + 4 * i, wv);
+      A wa[4] = {(A)wv[0], (A)wv[1], (A)wv[2], (A)wv[3]};
+#pragma unroll
+      for (int k = 0; k < KV; ++k)
+        if (k < nvec) {
+          ld4(Vk[k] + 4 * i, vk[k]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) wa[u] -= hA[k] * (A)vk[k][u];
+        }
+      T wn[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) wn[u] = (T)wa[u];
+      st4(w + 4 * i, wn);
+      if (do_dot == 1) {
+#pragma unroll
+        for (int k = 0; k < KV; ++k)
+          if (k < nvec)
+            acc[k] += ((A)vk[k][0] * (A)wn[0] + (A)vk[k][1] * (A)wn[1]) +
+                      ((A)vk[k][2] * (A)wn[2] + (A)vk[k][3] * (A)wn[3]);
+      } else if (do_dot == 2) {
+        acc[0] += ((A)wn[0] * (A)wn[0] + (A)wn[1] * (A)wn[1]) +
+                  ((A)wn[2] * (A)wn[2] + (A)wn[3] * (A)wn[3]);
+      }
+    }
+    i0 = (n >> 2) << 2;
+  }
+  for (long long i = i0 + start; i < n; i += stride) {
     T vk[NV];
     A wi = (A)w[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
       if (k < nvec) {
-        vk[k] = V[k][i];
+        vk[k] = (NV <= 8 ? Vk[k < KV ? k : 0] : V[k])[i];
         wi -= hA[k] * (A)vk[k];
       }
     const T wn = (T)wi;
@@ -128,8 +216,21 @@ template <class T>
 __global__ void axpby_kernel(long long n, double alpha, const T* __restrict__ x, double beta,
                              T* __restrict__ y) {
   const T a = (T)alpha, bb = (T)beta;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = 0;
+  if (al16(x) && al16(y)) {
+    for (long long i = start; i < (n >> 2); i += stride) {
+      T xv[4], yv[4];
+      ld4(x + 4 * i, xv);
+      if (beta != 0.0) ld4(y + 4 * i, yv);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) yv[u] = beta != 0.0 ? a * xv[u] + bb * yv[u] : a * xv[u];
+      st4(y + 4 * i, yv);
+    }
+    i0 = (n >> 2) << 2;
+  }
+  for (long long i = i0 + start; i < n; i += stride) {
     T v = a * x[i];
     if (beta != 0.0) v += bb * y[i];
     y[i] = v;
@@ -140,16 +241,41 @@ template <class T>
 __global__ void scale_copy_kernel(long long n, double alpha, const T* __restrict__ x,
                                   T* __restrict__ y) {
   const T a = (T)alpha;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = 0;
+  if (al16(x) && al16(y)) {
+    for (long long i = start; i < (n >> 2); i += stride) {
+      T v[4];
+      ld4(x + 4 * i, v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] *= a;
+      st4(y + 4 * i, v);
+    }
+    i0 = (n >> 2) << 2;
+  }
+  for (long long i = i0 + start; i < n; i += stride) y[i] = a * x[i];
 }
 
 template <class Tin, class Tout>
 __global__ void convert_kernel(long long n, const Tin* __restrict__ x, Tout* __restrict__ y) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = (Tout)x[i];
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = 0;
+  if constexpr (sizeof(Tout) >= 4) {
+    if (al16(x) && al16(y)) {
+      for (long long i = start; i < (n >> 2); i += stride) {
+        Tin v[4];
+        ld4(x + 4 * i, v);
+        Tout o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = (Tout)v[u];
+        st4(y + 4 * i, o);
+      }
+      i0 = (n >> 2) << 2;
+    }
+  }
+  for (long long i = i0 + start; i < n; i += stride) y[i] = (Tout)x[i];
 }
 
 template <>
@@ -169,12 +295,37 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(long long n, int nvec
   __shared__ T ys[kMaxVec];
   if (threadIdx.x < nvec) ys[threadIdx.x] = (T)y[threadIdx.x];
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n;
-       i += (long long)gridDim.x * kThreads) {
+  const T* Zk[NV];
+  bool vec = al16(x);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    Zk[k] = k < nvec ? Z[k] : x;
+    vec = vec && al16(Zk[k]);
+  }
+  const long long start = blockIdx.x * (long long)kThreads + threadIdx.x;
+  const long long stride = (long long)gridDim.x * kThreads;
+  long long i0 = 0;
+  if (vec) {
+    for (long long i = start; i < (n >> 2); i += stride) {
+      T v[4];
+      ld4(x + 4 * i, v);
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k < nvec) {
+          T z[4];
+          ld4(Zk[k] + 4 * i, z);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] += ys[k] * z[u];
+        }
+      st4(x + 4 * i, v);
+    }
+    i0 = (n >> 2) << 2;
+  }
+  for (long long i = i0 + start; i < n; i += stride) {
     T v = x[i];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
-      if (k < nvec) v += ys[k] * Z[k][i];
+      if (k < nvec) v += ys[k] * Zk[k][i];
     x[i] = v;
   }
 }

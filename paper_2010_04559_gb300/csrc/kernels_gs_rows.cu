@@ -764,12 +764,15 @@ __global__ void __launch_bounds__(kRowsMaxThreads, 1) coarse_gs_rows_kernel(Rows
 // warp h: rows 6 w + 3 h .. 6 w + 3 h + 2; columns 3 (lane mod 16) ..).  The
 // vectors are read from shared memory by consecutive lanes (no bank
 // conflicts), the partial sums reduced across the warp with the result
-// spread over lane groups, and a cell takes four block barriers:
-//   1  the cell's x_c and f into shared memory, the next cell's prefetch;
-//   2  buf = M_d x_c, rhs0 = f - x-upwind + sigma_s N buf (N mixes the nodes
-//      held by one warp: shuffles);
-//   3  y0 = Tinv rhs0; the face words of the upwind row;
-//   4  x = y0 + W yup, stores (psi, the x- and y-outflow faces).
+// spread over lane groups, and a cell takes three block barriers:
+//   1  buf = M_d x_c, rhs0 = f - x-upwind + sigma_s N buf (N mixes the nodes
+//      held by one warp: shuffles); the next cell's vectors start loading
+//      into registers;
+//   2  y0 = Tinv rhs0; the face words of the upwind row;
+//   3  x = y0 + W yup, stores (psi, the x- and y-outflow faces), then the
+//      next cell's vectors into shared memory (measured against a separate
+//      staging phase: 45.3 against 47.8 ms per 10 sweeps on the 256^2 beam
+//      workload; a three-cell cp.async ring was slower still).
 // Schedule, face words, tags and waits are those of the kernel above.
 constexpr int kFastThreads = 512;
 
@@ -875,10 +878,29 @@ __global__ void __launch_bounds__(kFastThreads, 1) coarse_gs_rows_fast_kernel(Ro
     pmat = p.cd.mat[c];
     psig = p.cd.sigma_s32[c];
   };
-  if (p.sweeps > 0) prefetch(0, row_of(0, 0), 0);
+  // the cell whose vectors are in shared memory, and the prefetched one's
+  // commit into it (x_c stays when the next cell is this one: its direction
+  // block was updated in place)
+  long long c_cur = -1;
+  int mat_cur = 0;
+  T sig_cur = T(0);
+  auto commit = [&](bool same) {
+    if (!same && tid < nxc) xc[(tid / nadof) * NMp + (tid - (tid / nadof) * nadof)] = xpf;
+    if (tid >= nxc && tid < nxc + Ev) fb[tid - nxc] = fpf;
+    c_cur = c_next;
+    mat_cur = pmat;
+    sig_cur = psig;
+  };
+  if (p.sweeps > 0) {
+    prefetch(0, row_of(0, 0), 0);
+    commit(false);
+  }
   float Mr[2][3], Tr[NMAT][6][3], Wr[NMAT][3][3];
   const int h = lane >> 4;
-  long long last = -1;
+  // face word of the upwind row: looked at once when the previous cell ends
+  const unsigned long long* wp = nullptr;
+  unsigned long long fw[W];
+  bool looked = false;
   for (int sw = 0; sw < p.sweeps; ++sw) {
     const unsigned tag = p.tag0 + (unsigned)sw + 1u;
     for (int d = 0; d < ndir; ++d) {
@@ -926,42 +948,35 @@ __global__ void __launch_bounds__(kFastThreads, 1) coarse_gs_rows_fast_kernel(Ro
         if (R < 0) break;
         const int jy = n1 ? g.ny - 1 - R : R;
         for (int k = 0; k < nx; ++k) {
-          const long long c = c_next;
-          const int mat = pmat;
-          const T sig_s = psig;
-          // ---- 1: the cell's vectors; first look at the face words; prefetch
-          if (c != last) {
-            if (tid < nxc) xc[(tid / nadof) * NMp + (tid - (tid / nadof) * nadof)] = xpf;
+          const long long c = c_cur;
+          const int mat = mat_cur;
+          const T sig_s = sig_cur;
+          // the next cell of this block's sequence: its vectors start loading
+          // now and are committed when this cell ends
+          int d2 = d, ri2 = ri, k2 = k + 1, sw2 = sw, R2 = R;
+          bool more = true;
+          if (k2 >= nx) {
+            k2 = 0;
+            ++ri2;
+            R2 = row_of(d2, ri2);
+            if (R2 < 0) {
+              ri2 = 0;
+              if (++d2 >= ndir) {
+                d2 = 0;
+                more = ++sw2 < p.sweeps;
+              }
+              if (more) R2 = row_of(d2, ri2);
+            }
           }
-          if (tid >= nxc && tid < nxc + Ev) fb[tid - nxc] = fpf;
-          const unsigned long long* wp = nullptr;
-          unsigned long long fw[W];
+          if (more) prefetch(d2, R2, k2);
+          else c_next = -2;
           const bool need = tid < npoll && jy > 0;
-          if (need) {
+          if (need && !looked) {
             const long long cn = c + (n1 ? (long long)nx : -(long long)nx);
             wp = p.faces + ((((size_t)0 * ndir + d) * g.C + cn) * HS * p.Jmax + (size_t)pjn * J + pj) * W;
             FaceWords<T>::load(wp, fw);
           }
-          {
-            int d2 = d, ri2 = ri, k2 = k + 1, sw2 = sw, R2 = R;
-            bool more = true;
-            if (k2 >= nx) {
-              k2 = 0;
-              ++ri2;
-              R2 = row_of(d2, ri2);
-              if (R2 < 0) {
-                ri2 = 0;
-                if (++d2 >= ndir) {
-                  d2 = 0;
-                  more = ++sw2 < p.sweeps;
-                }
-                if (more) R2 = row_of(d2, ri2);
-              }
-            }
-            if (more) prefetch(d2, R2, k2);
-            else c_next = -2;
-          }
-          __syncthreads();
+          looked = false;
           // ---- 2: buf = M_d x_c; rhs0 = f - x-upwind + sigma_s N buf
           {
             float v[8];
@@ -971,7 +986,7 @@ __global__ void __launch_bounds__(kFastThreads, 1) coarse_gs_rows_fast_kernel(Ro
 #pragma unroll
               for (int t = 0; t < 3; ++t) {
                 const int kk = 3 * lane + t;
-                xv[l][t] = kk < NMp ? xc[l * NMp + kk] : T(0);
+                xv[l][t] = kk < nadof ? xc[l * NMp + kk] : T(0);  // (padding unset)
               }
 #pragma unroll
             for (int r = 0; r < 2; ++r)
@@ -1078,8 +1093,18 @@ __global__ void __launch_bounds__(kFastThreads, 1) coarse_gs_rows_fast_kernel(Ro
               }
             }
           }
+          // the next cell's vectors; a first look at its face word when it is
+          // in this row
+          if (more) {
+            commit(c_next == c);
+            if (d2 == d && R2 == R && tid < npoll && jy > 0) {
+              const long long cn = c_next + (n1 ? (long long)nx : -(long long)nx);
+              wp = p.faces + ((((size_t)0 * ndir + d) * g.C + cn) * HS * p.Jmax + (size_t)pjn * J + pj) * W;
+              FaceWords<T>::load(wp, fw);
+              looked = true;
+            }
+          }
           __syncthreads();
-          last = c;
         }
       }
     }
@@ -1227,6 +1252,10 @@ int launch_coarse_gs_rows(const Geom& g, const LevelDev<T>& t, const CellData& c
   }
   note_launch();
   return 0;
+}
+
+bool coarse_gs_rows_fast(const Geom& g, int Jmax, int nmat, int nmat_s, int threads) {
+  return threads == kFastThreads && rows_fast_applies(g.dim, g.a, g.nadof, Jmax, nmat, nmat_s);
 }
 
 template int coarse_gs_rows_plan<float>(const Geom&, int, int, int, int, bool, int*, int*, size_t*,
