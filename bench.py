@@ -61,7 +61,7 @@ CLASSES = {
     "scatter_tc": ("tc_gemm_kernel<bf16> (tcgen05, V-cycle scatter)", "tensor", "flop"),
     "scatter_f32": ("gemm_kernel<float> (SIMT)", "alu", "flop"),
     "scatter_f64": ("gemm_kernel<double> (SIMT)", "alu64", "flop"),
-    "coarse_gs": ("coarse_gs_rows_kernel", "alu", "flop"),
+    "coarse_gs": ("coarse_gs_rows_fast_kernel (register form, dense S_f source)", "alu", "flop"),
     "split_tc": ("tc_gemm_kernel<bf16> (tcgen05, slice products of the split FP64 scatter)",
                  "tensor", "flop"),
     "split_aux": ("split_rows_kernel + split_flush_kernel", "hbm", "B"),
@@ -73,9 +73,10 @@ CLASSES = {
 TRAFFIC = {
     # split_tc, tc3: captured at 16384 rows (profiles/ncu_split_gemm_config5shape.md,
     # ncu_tc3_gemm_config5shape.md), scaled to the mean launch's rows (52428 and
-    # 87381); coarse_gs: one 10-sweep launch (profiles/ncu_coarse_gs_rows_config5.md)
-    "config5": {"split_tc": 3.72e9, "tc3": 21.1e9, "coarse_gs": 19.76e9},
-    "config2": {},
+    # 87381); coarse_gs: one 10-sweep launch (profiles/ncu_coarse_gs_rows_config5.md,
+    # ncu_coarse_gs_rows_config2.md)
+    "config5": {"split_tc": 3.72e9, "tc3": 21.1e9, "coarse_gs": 6.60e9},
+    "config2": {"coarse_gs": 0.118e9},
 }
 FP64_PEAK = 1.25          # TFLOP/s, nominal GB300 FP64 rate
 ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
