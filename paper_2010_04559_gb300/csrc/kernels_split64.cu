@@ -18,6 +18,8 @@
 // the tensor cores in FP32 by Horner's rule (each diagonal's first product
 // adds 2^(-b) times the sum of the less significant ones) and accumulated in
 // FP64 once.
+#include <climits>
+
 #include "kernels.cuh"
 
 namespace amgt {
@@ -49,6 +51,26 @@ __device__ __forceinline__ void row_values(const double* __restrict__ x, long lo
   }
 }
 
+// rint(z 2^s) (round half to even) from the FP64 bit pattern of z by integer
+// operations, for |z 2^s| < 2^62; subnormal z by the FP64 route
+__device__ __forceinline__ long long scaled_rint(double z, int s) {
+  const long long b = __double_as_longlong(z);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return (b << 1) == 0 ? 0 : __double2ll_rn(ldexp(z, s));
+  const long long m = (b & 0xfffffffffffffll) | (1ll << 52);
+  const int sh = 1075 - ex - s;  // z 2^s = m 2^(-sh)
+  long long t;
+  if (sh <= 0) {
+    t = m << (-sh);
+  } else if (sh >= 54) {
+    t = 0;  // |z 2^s| < 1/2
+  } else {
+    const long long q = m >> sh, rem = m & ((1ll << sh) - 1), half = 1ll << (sh - 1);
+    t = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  }
+  return b < 0 ? -t : t;
+}
+
 // One block per group of S rows.  mu[r] receives the row scale 2^e,
 // out[i * slice_stride + r K + k] the digit of slice i.
 //
@@ -62,16 +84,18 @@ __device__ __forceinline__ void row_values(const double* __restrict__ x, long lo
 // digit and (T - r) / 2^bits (an exact shift) carries on; what is left after
 // nsl - 1 digits is the leading digit, |d_0| <= 2^bits.  GB300's FP64 rate
 // makes the FP64 form of this (three FP64 operations per digit) the slowest
-// step of the split scatter; here each unknown costs the mixing, two FP64
-// multiplications and one conversion.  A row whose bound is not finite gets
-// mu = NaN, so the product carries it.
+// step of the split scatter; here each unknown costs only the mixing in FP64:
+// the power-of-two scaling and the rounding to T work on the FP64 bit
+// pattern in integer arithmetic, and the digits convert to BF16 through
+// 32-bit integers.  A row whose bound is not finite gets mu = NaN, so the
+// product carries it.
 template <int S, bool MIX>
 __global__ void __launch_bounds__(kSplitThreads) split_rows_kernel(
     long long rows, int K, const double* __restrict__ x, const double* __restrict__ sig,
     NmassArg nm, int nsl, int bits, double* __restrict__ mu, __nv_bfloat16* __restrict__ out,
     long long slice_stride) {
   __shared__ unsigned long long red[kSplitThreads / 32][S];
-  __shared__ double inv_s[S];
+  __shared__ int sh_s[S];  // bits nsl - e, or INT_MIN for a row that is not finite
   __shared__ double Nm[S * S];
   const long long r0 = (long long)blockIdx.x * S;
   if (r0 >= rows) return;
@@ -117,13 +141,12 @@ __global__ void __launch_bounds__(kSplitThreads) split_rows_kernel(
     int e = 0;
     if (bound > 0.0) frexp(bound, &e);  // bound = f 2^e, f in [0.5, 1)
     if (l < nrow) mu[r0 + l] = isfinite(bound) ? ldexp(1.0, e) : __longlong_as_double(0x7ff8000000000000ll);
-    inv_s[l] = isfinite(bound) ? ldexp(1.0, -e) : 0.0;
+    sh_s[l] = isfinite(bound) ? bits * nsl - e : INT_MIN;
   }
   __syncthreads();
-  double inv[S];
+  int shl[S];
 #pragma unroll
-  for (int l = 0; l < S; ++l) inv[l] = inv_s[l];
-  const double p2 = ldexp(1.0, bits * nsl);
+  for (int l = 0; l < S; ++l) shl[l] = sh_s[l];
   const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
   // two adjacent columns per thread, stored as BF16 pairs (K and the slice
   // stride are even)
@@ -135,28 +158,83 @@ __global__ void __launch_bounds__(kSplitThreads) split_rows_kernel(
 #pragma unroll
     for (int l = 0; l < S; ++l) {
       if (l >= nrow) break;
-      long long T0 = __double2ll_rn((z0[l] * inv[l]) * p2);
-      long long T1 = __double2ll_rn((z1[l] * inv[l]) * p2);
+      // T = rint(z 2^(bits nsl - e)), exact (the scale is a power of two)
+      long long T0 = shl[l] == INT_MIN ? 0 : scaled_rint(z0[l], shl[l]);
+      long long T1 = shl[l] == INT_MIN ? 0 : scaled_rint(z1[l], shl[l]);
       __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + (r0 + l) * (long long)K + k);
       for (int i = nsl - 1; i > 0; --i) {
         const long long d0 = ((T0 + half) & mask) - half;
         const long long d1 = ((T1 + half) & mask) - half;
         T0 = (T0 - d0) >> bits;
         T1 = (T1 - d1) >> bits;
-        o[i * ss2] = __floats2bfloat162_rn((float)d0, (float)d1);
+        // digits of at most 8 bits: 32-bit integer to float conversions
+        o[i * ss2] = __floats2bfloat162_rn((float)(int)d0, (float)(int)d1);
       }
-      o[0] = __floats2bfloat162_rn((float)T0, (float)T1);
+      o[0] = __floats2bfloat162_rn((float)(int)T0, (float)(int)T1);
     }
   }
 }
 
+// p 2^k as FP64, exactly, by integer operations on the FP32 bit pattern
+// (zero and normal results; the rest by the FP64 route)
+__device__ __forceinline__ double scaled_f2d(float p, int k) {
+  const unsigned u = __float_as_uint(p);
+  if ((u & 0x7fffffffu) == 0u) return 0.0;
+  const int ex = (int)((u >> 23) & 0xffu);
+  const int e = ex - 127 + 1023 + k;
+  if (ex == 0 || ex == 255 || e <= 0 || e >= 2047) return ldexp((double)p, k);
+  return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                          ((unsigned long long)e << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// the exponent of a finite power of two, or INT_MIN for anything else
+__device__ __forceinline__ int pow2_exp(double v) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  return ((b & 0xfffffffffffffll) == 0 && ex != 0 && ex != 0x7ff) ? ex - 1023 : INT_MIN;
+}
+
 // y[r][c] += sc mu[r] nu[c] P[r][c]  (sc mu nu is a power of two times sc,
 // so each product is exact and only the sum rounds).  A block per row at a
-// time: no index division, one row scale per row.
+// time: no index division, one row scale per row.  Where sc mu[r] and nu[c]
+// are powers of two (the split form's scales; sc = +-2^-k for alpha = +-1)
+// the product is formed by integer operations on the bit patterns, so each
+// element costs one FP64 addition instead of a multiplication, a conversion
+// and a fused multiply-add at GB300's FP64 rate.
 __global__ void split_flush_kernel(long long M, int N, const float* __restrict__ P,
                                    const double* __restrict__ mu, const double* __restrict__ nu,
                                    double sc, double* __restrict__ y) {
-  if ((N & 3) == 0) {
+  if ((N & 3) == 0 && pow2_exp(fabs(sc)) != INT_MIN) {
+    const int n4 = N >> 2;
+    const double2* nu2 = reinterpret_cast<const double2*>(nu);
+    for (long long r = blockIdx.x; r < M; r += gridDim.x) {
+      const double s = sc * mu[r];
+      const int kr = pow2_exp(fabs(s));
+      const float4* pr = reinterpret_cast<const float4*>(P + r * N);
+      double2* yr = reinterpret_cast<double2*>(y + r * N);
+      for (int c4 = threadIdx.x; c4 < n4; c4 += blockDim.x) {
+        const float4 p = __ldcs(pr + c4);
+        const double2 na = nu2[2 * c4], nb = nu2[2 * c4 + 1];
+        double2 a = yr[2 * c4], b = yr[2 * c4 + 1];
+        const int k0 = pow2_exp(na.x), k1 = pow2_exp(na.y), k2 = pow2_exp(nb.x),
+                  k3 = pow2_exp(nb.y);
+        if (kr != INT_MIN && k0 != INT_MIN && k1 != INT_MIN && k2 != INT_MIN && k3 != INT_MIN) {
+          const float sg = s < 0.0 ? -1.f : 1.f;
+          a.x += scaled_f2d(sg * p.x, kr + k0);
+          a.y += scaled_f2d(sg * p.y, kr + k1);
+          b.x += scaled_f2d(sg * p.z, kr + k2);
+          b.y += scaled_f2d(sg * p.w, kr + k3);
+        } else {
+          a.x = fma(s * na.x, (double)p.x, a.x);
+          a.y = fma(s * na.y, (double)p.y, a.y);
+          b.x = fma(s * nb.x, (double)p.z, b.x);
+          b.y = fma(s * nb.y, (double)p.w, b.y);
+        }
+        yr[2 * c4] = a;
+        yr[2 * c4 + 1] = b;
+      }
+    }
+  } else if ((N & 3) == 0) {
     const int n4 = N >> 2;
     const double2* nu2 = reinterpret_cast<const double2*>(nu);
     for (long long r = blockIdx.x; r < M; r += gridDim.x) {
