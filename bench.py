@@ -694,7 +694,7 @@ def run_profile(args):
                                         context_from_problem)
     from paper_2010_04559_gb300 import build as _b
     _b.build()
-    if args.profile in ("gemm5", "tc3_5", "split5"):
+    if args.profile in ("gemm5", "tc3_5", "split5", "ops5"):
         # the headline's contraction shape on a 64x64-cell slab of its rows:
         # K = N = 6144, 65536 rows (a few GB on the device, larger than L2)
         prob = W.config5_beam(n=64)
@@ -751,6 +751,15 @@ def run_profile(args):
         for _ in range(2):
             ctx.amgt_op_scatter(0, x, y, tc=True if args.profile == "gemm5" else "tc3")
         print("kernels: scatter contraction at K = N = 6144 (x2)")
+    elif args.profile == "ops5":
+        # the finest level's FP32 L apply and sweep on the 64x64-cell slab
+        # (6144 angular DOF, 403 MB per vector)
+        x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            ctx.amgt_op_apply_L(0, x, y)
+            ctx.amgt_op_sweep(0, x, y)
+        print("kernels: FP32 L apply and sweep on level 0 (x2)")
     elif args.profile == "split5":
         x = torch.randn((ns, na), device="cuda", dtype=torch.float64)
         y = torch.empty_like(x)
@@ -783,7 +792,7 @@ def main():
                     help="problems of the uneven 2D batch, solved in concurrent waves (0: skip)")
     ap.add_argument("--n", type=int, default=128, help="cells per axis of --profile's workload")
     ap.add_argument("--profile", choices=["solve", "solve5", "sweeps", "gs", "gs5", "gemm5",
-                                          "tc3_5", "split5", "sweep3d"],
+                                          "tc3_5", "split5", "sweep3d", "ops5"],
                     default=None, help="one launch of a hot kernel, and exit (for ncu)")
     ap.add_argument("--table1", action="store_true",
                     help="context run of the paper's Table 1 set-up (iteration counts), and exit")

@@ -865,6 +865,13 @@ int build(amgt_ctx* ctx) {
     }
     const Transfer& t = ctx->tr.back();
     TRY(upload(ctx, t.parent, &F.d_parent));
+    {
+      const int Pc = (int)t.child_begin.size();
+      bool u4 = Pc > 0 && (int)t.parent.size() == 4 * Pc;
+      for (int c = 0; u4 && c < Pc; ++c)
+        u4 = t.child_begin[c] == 4 * c && t.child_end[c] == 4 * c + 4;
+      F.children4 = u4;
+    }
     TRY(upload(ctx, t.child_begin, &F.d_cbeg));
     TRY(upload(ctx, t.child_end, &F.d_cend));
     TRY(upload(ctx, t.blk, &F.d64.tblk));
@@ -1374,7 +1381,7 @@ int restrict_impl(amgt_ctx* ctx, int k, const T* rf, T* rc) {
   const Level& F = ctx->lv[k];
   const Level& Cc = ctx->lv[k + 1];
   launch_restrict<T>(F.nsdof, Cc.mesh.P, F.mesh.a, F.nadof(), Cc.nadof(), F.d_cbeg, F.d_cend,
-                     store<T>(F).tblk, rf, rc, ctx->stream);
+                     store<T>(F).tblk, rf, rc, F.children4, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }
@@ -1384,7 +1391,7 @@ int prolong_impl(amgt_ctx* ctx, int k, const T* xc, T* xf) {
   const Level& F = ctx->lv[k];
   const Level& Cc = ctx->lv[k + 1];
   launch_prolong<T>(F.nsdof, F.mesh.P, F.mesh.a, F.nadof(), Cc.nadof(), F.d_parent,
-                    store<T>(F).tblk, xc, xf, ctx->stream);
+                    store<T>(F).tblk, xc, xf, F.children4, ctx->stream);
   CK(cudaGetLastError());
   return AMGT_OK;
 }

@@ -72,6 +72,7 @@ struct Level {
   double* d_beam = nullptr;
   // transfer to the next coarser level
   int *d_parent = nullptr, *d_cbeg = nullptr, *d_cend = nullptr;
+  bool children4 = false;  // coarse patch c has the children 4c..4c+3 on this level
   std::vector<int> task_dir, task_q0, task_nq;
   int *d_task_dir = nullptr, *d_task_q0 = nullptr, *d_task_nq = nullptr;
   long long nsdof = 0;

@@ -140,11 +140,14 @@ cudaError_t launch_invert_blocks(const Geom& g, int kind, int nmat, int P, int s
                                  int* singular, cudaStream_t st);
 
 template <class T>
+// uniform4: every coarse patch c has the children 4c..4c+3 (a thread per
+// coarse patch with its coefficients in registers, 16-byte fine-side access)
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
-                     const int* cend, const T* blk, const T* rf, T* rc, cudaStream_t st);
+                     const int* cend, const T* blk, const T* rf, T* rc, bool uniform4,
+                     cudaStream_t st);
 template <class T>
 void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, const int* parent,
-                    const T* blk, const T* xc, T* xf, cudaStream_t st);
+                    const T* blk, const T* xc, T* xf, bool uniform4, cudaStream_t st);
 template <class T>
 void launch_source(const Geom& g, const T* w, const T* Aw, const int* octant,
                    const double* q, const double* bnd_val, const int* bnd_kind,

@@ -9,6 +9,7 @@
 // and an inflow face f couples to the upwind neighbour through
 // kron(Fnb_f, A_{f,q}) with A_{f,q} = n_xi A^xi_q.  Fnb_f only links the face
 // nodes of the two cells, with the Q1 face mass `facemass[xi]`.
+#include <cstdint>
 #include <type_traits>
 
 #include "gs_common.cuh"
@@ -625,6 +626,9 @@ __device__ __forceinline__ bool wait_at_least(const int* p, int target, int* err
   const unsigned long long t0 = gsx::now_ns();
   unsigned it = 0;
   while (ld_acquire_cta(p) < target) {
+    // after a few polls, back off: a spinning warp takes issue slots from the
+    // warps it waits for
+    if (it >= 4) __nanosleep(32);
     if ((++it & 63u) == 0) {
       if (*reinterpret_cast<volatile int*>(err) != 0) return false;
       if (gsx::now_ns() - t0 > wait_ns) {
@@ -1365,6 +1369,92 @@ __global__ void restrict_kernel(long long nsdof, int Pc, int a, int nadof_f, int
   }
 }
 
+// Uniform refinement with Lin patches (coarse patch c has the children
+// 4c..4c+3, 3 functions each): a thread per coarse patch over a band of
+// rows, its children's 4 x 3 x 3 coefficients in registers for the whole
+// band, the 12 fine values of a row moved as 16-byte vectors (48 c bytes from
+// a 16-byte aligned row start).
+__device__ __forceinline__ void ld12(const float* p, float (&v)[12]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 q = reinterpret_cast<const float4*>(p)[i];
+    v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+  }
+}
+__device__ __forceinline__ void ld12(const double* p, double (&v)[12]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double2 q = reinterpret_cast<const double2*>(p)[i];
+    v[2 * i] = q.x; v[2 * i + 1] = q.y;
+  }
+}
+__device__ __forceinline__ void st12(float* p, const float (&v)[12]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    reinterpret_cast<float4*>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+__device__ __forceinline__ void st12(double* p, const double (&v)[12]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) reinterpret_cast<double2*>(p)[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+// rc[r][(c,d)] = sum over the children f = 4c + j and k of blk[f][k][d] rf[r][(f,k)]
+template <class T>
+__global__ void __launch_bounds__(256) restrict4_kernel(long long nsdof, int Pc, int rows_per_block,
+                                                       const T* __restrict__ blk,
+                                                       const T* __restrict__ rf,
+                                                       T* __restrict__ rc) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Pc) return;
+  T b[36];
+#pragma unroll
+  for (int i = 0; i < 36; ++i) b[i] = blk[(size_t)c * 36 + i];
+  const long long r0 = (long long)blockIdx.y * rows_per_block;
+  const long long r1 = r0 + rows_per_block < nsdof ? r0 + rows_per_block : nsdof;
+  const long long nf = 12LL * Pc, nc = 3LL * Pc;
+#pragma unroll 4
+  for (long long r = r0; r < r1; ++r) {
+    T v[12];
+    ld12(rf + r * nf + 12LL * c, v);
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int fk = 0; fk < 12; ++fk)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) acc[d] += b[fk * 3 + d] * v[fk];
+    T* o = rc + r * nc + 3LL * c;
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2];
+  }
+}
+
+// xf[r][(f,k)] += sum_d blk[f][k][d] xc[r][(c,d)] for the children f = 4c + j
+template <class T>
+__global__ void __launch_bounds__(256) prolong4_kernel(long long nsdof, int Pc, int rows_per_block,
+                                                      const T* __restrict__ blk,
+                                                      const T* __restrict__ xc,
+                                                      T* __restrict__ xf) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= Pc) return;
+  T b[36];
+#pragma unroll
+  for (int i = 0; i < 36; ++i) b[i] = blk[(size_t)c * 36 + i];
+  const long long r0 = (long long)blockIdx.y * rows_per_block;
+  const long long r1 = r0 + rows_per_block < nsdof ? r0 + rows_per_block : nsdof;
+  const long long nf = 12LL * Pc, nc = 3LL * Pc;
+#pragma unroll 2
+  for (long long r = r0; r < r1; ++r) {
+    const T* xr = xc + r * nc + 3LL * c;
+    const T x0 = xr[0], x1 = xr[1], x2 = xr[2];
+    T v[12];
+    T* o = xf + r * nf + 12LL * c;
+    ld12(o, v);
+#pragma unroll
+    for (int fk = 0; fk < 12; ++fk) v[fk] += b[fk * 3] * x0 + b[fk * 3 + 1] * x1 + b[fk * 3 + 2] * x2;
+    st12(o, v);
+  }
+}
+
 // xf[r][(f,k)] += sum_d blk[f][k][d] xc[r][(parent(f),d)]
 template <class T>
 __global__ void prolong_kernel(long long nsdof, int Pf, int a, int nadof_f, int nadof_c,
@@ -1564,10 +1654,33 @@ void launch_scalar_flux(long long nsdof, int nadof, const T* w, const T* psi, T*
   scalar_flux_kernel<T><<<grid, 256, 0, st>>>(nsdof, nadof, w, psi, phi);
 }
 
+// launch shape of the uniform-refinement transfers: threads over the coarse
+// patches, blocks over bands of rows (about 8 blocks per SM in all)
+static void transfer4_shape(long long nsdof, int Pc, dim3& grid, dim3& block, int& rpb) {
+  const int threads = Pc >= 256 ? 256 : ((Pc + 31) / 32) * 32;
+  const int gx = (Pc + threads - 1) / threads;
+  long long gy = (152LL * 8 + gx - 1) / gx;
+  if (gy > nsdof) gy = nsdof;
+  if (gy < 1) gy = 1;
+  rpb = (int)((nsdof + gy - 1) / gy);
+  gy = (nsdof + rpb - 1) / rpb;
+  grid = dim3((unsigned)gx, (unsigned)gy);
+  block = dim3((unsigned)threads);
+}
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 template <class T>
 void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, const int* cbeg,
-                     const int* cend, const T* blk, const T* rf, T* rc, cudaStream_t st) {
+                     const int* cend, const T* blk, const T* rf, T* rc, bool uniform4,
+                     cudaStream_t st) {
   note_launch();
+  if (uniform4 && a == 3 && aligned16(rf)) {
+    dim3 grid, block;
+    int rpb;
+    transfer4_shape(nsdof, Pc, grid, block, rpb);
+    restrict4_kernel<T><<<grid, block, 0, st>>>(nsdof, Pc, rpb, blk, rf, rc);
+    return;
+  }
   const int grid = grid_for(nsdof * Pc, 256);
   restrict_kernel<T><<<grid, 256, 0, st>>>(nsdof, Pc, a, nadof_f, nadof_c, cbeg, cend, blk, rf,
                                            rc);
@@ -1575,8 +1688,15 @@ void launch_restrict(long long nsdof, int Pc, int a, int nadof_f, int nadof_c, c
 
 template <class T>
 void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, const int* parent,
-                    const T* blk, const T* xc, T* xf, cudaStream_t st) {
+                    const T* blk, const T* xc, T* xf, bool uniform4, cudaStream_t st) {
   note_launch();
+  if (uniform4 && a == 3 && aligned16(xf) && Pf % 4 == 0) {
+    dim3 grid, block;
+    int rpb;
+    transfer4_shape(nsdof, Pf / 4, grid, block, rpb);
+    prolong4_kernel<T><<<grid, block, 0, st>>>(nsdof, Pf / 4, rpb, blk, xc, xf);
+    return;
+  }
   const int grid = grid_for(nsdof * Pf, 256);
   prolong_kernel<T><<<grid, 256, 0, st>>>(nsdof, Pf, a, nadof_f, nadof_c, parent, blk, xc, xf);
 }
@@ -1592,9 +1712,9 @@ void launch_prolong(long long nsdof, int Pf, int a, int nadof_f, int nadof_c, co
                                  const double*, const double*, T*, cudaStream_t);             \
   template void launch_scalar_flux<T>(long long, int, const T*, const T*, T*, cudaStream_t);  \
   template void launch_restrict<T>(long long, int, int, int, int, const int*, const int*,     \
-                                   const T*, const T*, T*, cudaStream_t);                     \
+                                   const T*, const T*, T*, bool, cudaStream_t);               \
   template void launch_prolong<T>(long long, int, int, int, int, const int*, const T*,        \
-                                  const T*, T*, cudaStream_t);
+                                  const T*, T*, bool, cudaStream_t);
 AMGT_INST(double)
 AMGT_INST(float)
 #undef AMGT_INST
