@@ -577,13 +577,15 @@ def adjoint_extra(local, torch):
 def batch_extra(local, torch, nprob, wave=16):
     """The 256-problem batch of uneven 2D problems (n = 16..96 cells per axis,
     levels 1..3, per-cell lognormal sigma_t, own g and order), in waves of
-    `wave` problems: each wave's contexts are set up (block inverses on the
-    GPU), solved concurrently by amgt_solve_batch (each problem on its own
+    `wave` problems: each wave's contexts are set up concurrently by
+    amgt_setup_batch (block inverses on the GPU), solved concurrently by
+    amgt_solve_batch (each problem on its own
     stream, V-cycles replayed from captured graphs; a first solve captures
     them), then solved one after another for comparison.  Times are sums over
     the waves of the timed solves only."""
     from paper_2010_04559_gb300 import (AMGT_MODE_MIXED, AMGT_PREC_MG, AMGT_TUNE_GRAPHS,
-                                        amgt_solve_batch, context_from_problem)
+                                        amgt_setup_batch, amgt_solve_batch,
+                                        context_from_problem)
     probs = W.config4_batch()[:nprob]
     t_conc = t_seq = t_setup = 0.0
     dof_its = 0
@@ -595,6 +597,7 @@ def batch_extra(local, torch, nprob, wave=16):
         t0 = time.perf_counter()
         bctx = [context_from_problem(p, device=local, stream=s.cuda_stream)
                 for p, s in zip(part, bstreams)]
+        amgt_setup_batch(bctx)                          # the wave's set-up, concurrently
         bdof = [int(np.prod(c.amgt_query_sizes(0))) for c in bctx]
         torch.cuda.synchronize()
         t_setup += time.perf_counter() - t0

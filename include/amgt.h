@@ -347,6 +347,15 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
 int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
                      double* const* phi, amgt_stats* stats, int nthreads);
 
+/* Builds the n contexts' set-up tables (what the first use of a context
+ * would build: angular tables, block inverses, transfer and Gauss-Seidel
+ * tables, workspaces of the operators' plans) concurrently on nthreads host
+ * threads (0: min(n, 16)), each context on its own stream; a batch of many
+ * small problems spends most of its set-up in host work and small
+ * synchronous copies, which overlap across contexts this way.  Contexts must
+ * be distinct.  Returns the first non-OK status (all are attempted). */
+int amgt_setup_batch(amgt_ctx* const* ctxs, int n, int nthreads);
+
 /* ---- operators of the hot path on device buffers -------------------------- */
 /* All buffers are contiguous [Nsdof][Nadof(level)] of element type `dtype`
  * unless stated; they must not alias unless stated. */

@@ -17,12 +17,14 @@ from ._capi import (AMGT_OK, AMGT_ERR_ARG, AMGT_ERR_CUDA, AMGT_ERR_NOMEM, AMGT_E
                     AMGT_KT_SCATTER_F32, AMGT_KT_SCATTER_F64, AMGT_KT_SCATTER_TC, AMGT_KT_SWEEP, AMGT_PREC_MG,
                     AMGT_PREC_NONE, AMGT_PREC_SWEEP, AMGT_TUNE_GRAPHS, AMGT_TUNE_KERNEL_TIMERS, AmgtError,
                     Context,
-                    EXPORTS, amgt_query_launches, amgt_solve_batch, context_from_problem)
+                    EXPORTS, amgt_query_launches, amgt_setup_batch, amgt_solve_batch,
+                    context_from_problem)
 
 __all__ = ["Context", "context_from_problem", "AmgtError", "EXPORTS", "AMGT_F64", "AMGT_F32",
            "AMGT_F32_BF16TC", "AMGT_PREC_NONE", "AMGT_PREC_SWEEP", "AMGT_PREC_MG",
            "AMGT_MODE_F64", "AMGT_MODE_MIXED", "amgt_query_launches", "AMGT_TUNE_KERNEL_TIMERS",
-           "AMGT_TUNE_GRAPHS", "amgt_solve_batch", "AMGT_KRYLOV_GMRES", "AMGT_KRYLOV_BICGSTAB",
+           "AMGT_TUNE_GRAPHS", "amgt_solve_batch", "amgt_setup_batch", "AMGT_KRYLOV_GMRES",
+           "AMGT_KRYLOV_BICGSTAB",
            "AMGT_KT_SWEEP", "AMGT_KT_APPLY_L", "AMGT_KT_SCATTER_PREP", "AMGT_KT_SCATTER_TC",
            "AMGT_KT_SCATTER_F32", "AMGT_KT_SCATTER_F64", "AMGT_KT_COARSE_GS",
            "AMGT_F64_SPLIT", "AMGT_F32_TC3", "AMGT_KT_TC3", "AMGT_KT_TC3_PREP",

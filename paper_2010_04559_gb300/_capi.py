@@ -70,7 +70,7 @@ EXPORTS = [
     "amgt_op_coarse_gs_noalloc",
     "amgt_op_vcycle", "amgt_op_scalar_flux",
     "amgt_set_adjoint", "amgt_response", "amgt_response_gradients",
-    "amgt_autotune", "amgt_solve_batch",
+    "amgt_autotune", "amgt_solve_batch", "amgt_setup_batch",
 ]
 
 
@@ -133,6 +133,7 @@ _SIGS = {
     "amgt_solve_batch": ([ctypes.POINTER(_P), _I, ctypes.POINTER(amgt_options),
                           ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(amgt_stats), _I],
                          _I),
+    "amgt_setup_batch": ([ctypes.POINTER(_P), _I, _I], _I),
 }
 
 
@@ -459,6 +460,17 @@ def amgt_solve_batch(contexts, psis, phis=None, tol=1e-8, restart=20, maxit=1000
         raise AmgtError(rc, "amgt_solve_batch failed: " +
                         "; ".join(c.lib.amgt_last_error(c.h).decode() for c in contexts[:3]))
     return list(st)
+
+
+def amgt_setup_batch(contexts, nthreads=0):
+    """Build the set-up tables of `contexts` concurrently (host threads, one
+    stream per context), instead of at each context's first use."""
+    n = len(contexts)
+    hs = (_P * n)(*[c.h for c in contexts])
+    rc = lib().amgt_setup_batch(hs, n, int(nthreads))
+    if rc != AMGT_OK:
+        raise AmgtError(rc, "amgt_setup_batch failed: " +
+                        "; ".join(c.lib.amgt_last_error(c.h).decode() for c in contexts[:3]))
 
 
 def context_from_problem(prob, device=0, stream=None, aniso=None):

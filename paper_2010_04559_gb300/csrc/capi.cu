@@ -2279,6 +2279,32 @@ int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, doub
 }
 
 
+int amgt_setup_batch(amgt_ctx* const* ctxs, int n, int nthreads) {
+  if (!ctxs || n < 0) return AMGT_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return AMGT_ERR_ARG;
+  int nt = nthreads > 0 ? nthreads : std::min(n, 16);
+  nt = std::max(1, std::min(nt, std::max(1, n)));
+  std::vector<int> rc(n, AMGT_OK);
+  std::atomic<int> next{0};
+  auto work = [&] {
+    for (int i; (i = next.fetch_add(1)) < n;) {
+      cudaSetDevice(ctxs[i]->device);
+      rc[i] = build(ctxs[i]);
+      if (rc[i] == AMGT_OK && cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc[i] = fail(ctxs[i], AMGT_ERR_CUDA, "set-up did not complete");
+      }
+    }
+  };
+  std::vector<std::thread> ts;
+  for (int t = 0; t < nt; ++t) ts.emplace_back(work);
+  for (auto& t : ts) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != AMGT_OK) return rc[i];
+  return AMGT_OK;
+}
+
 int amgt_autotune(amgt_ctx* ctx, int what, int* choice) {
   if (!ctx) return AMGT_ERR_ARG;
   TRY(build(ctx));

@@ -50,6 +50,27 @@ def test_batch_matches_individual_solves():
         c.close()
 
 
+def test_concurrent_setup_matches_lazy_setup():
+    """amgt_setup_batch builds the contexts' tables on host threads at once;
+    the solves that follow equal those of contexts set up one by one at
+    their first use (same tables, same kernels)."""
+    from paper_2010_04559_gb300 import amgt_setup_batch, context_from_problem
+    probs = W.config4_batch(nprob=6, nmin=8, nmax=20, seed_k=43)
+    streams = [torch.cuda.Stream() for _ in probs]
+    lazy = [context_from_problem(p, device=0, stream=s.cuda_stream) for p, s in zip(probs, streams)]
+    refs = [_solve(c)[0] for c in lazy]
+    for c in lazy:
+        c.close()
+    ctxs = [context_from_problem(p, device=0, stream=s.cuda_stream) for p, s in zip(probs, streams)]
+    amgt_setup_batch(ctxs, nthreads=4)
+    for c, r in zip(ctxs, refs):
+        psi, st = _solve(c)
+        assert st.relres < 1e-11
+        assert _rel(psi, r) < 1e-12
+    for c in ctxs:
+        c.close()
+
+
 def test_graph_replayed_vcycle_gives_the_same_solve():
     from paper_2010_04559_gb300 import AMGT_TUNE_GRAPHS, context_from_problem
     prob = W.config4_batch(nprob=1, nmin=24, nmax=24, seed_k=42)[0]
