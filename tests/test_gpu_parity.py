@@ -67,6 +67,26 @@ CASES = [
 IDS = [f"{d}d-{'x'.join(map(str, n))}-l{l}-{b}" for d, n, l, b in CASES]
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_L_apply_with_many_patches(dtype):
+    """L x and (L - S) x at angular level 3 (512 Lin patches: grid-stride
+    items over many patch blocks per cell), per-cell cross sections and
+    inflow, against the oracle."""
+    prob = W.random_problem(2, (6, 5), 3, 4, 33, inflow=0.4)
+    T = _oracle(prob)
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-12 if dtype == "f64" else 2e-5
+    x = W.random_vector((T.nsdof, T.nadof), 34)
+    xd = _dev(x, td)
+    y = torch.empty_like(xd)
+    ctx.amgt_op_apply_L(0, xd, y)
+    assert _rel(_host(y), T.apply_L(x)) < tol
+    ctx.amgt_op_apply_A(0, xd, y)
+    assert _rel(_host(y), T.apply_A(x)) < tol
+    ctx.close()
+
+
 @pytest.mark.parametrize("dim,nc,level,basis", CASES, ids=IDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_transport_operators(dim, nc, level, basis, dtype):
