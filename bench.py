@@ -755,14 +755,19 @@ def run_profile(args):
             ctx.amgt_op_scatter(0, x, y, tc=True if args.profile == "gemm5" else "tc3")
         print("kernels: scatter contraction at K = N = 6144 (x2)")
     elif args.profile == "ops5":
-        # the finest level's FP32 L apply and sweep on the 64x64-cell slab
-        # (6144 angular DOF, 403 MB per vector)
+        # the finest level's FP32 L apply and sweep and the double-float L
+        # apply on the 64x64-cell slab (6144 angular DOF, 403 MB per FP32 vector)
         x = torch.randn((ns, na), device="cuda", dtype=torch.float32)
         y = torch.empty_like(x)
         for _ in range(2):
             ctx.amgt_op_apply_L(0, x, y)
             ctx.amgt_op_sweep(0, x, y)
-        print("kernels: FP32 L apply and sweep on level 0 (x2)")
+        del x, y
+        x = torch.randn((ns, na), device="cuda", dtype=torch.float64)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            ctx.amgt_op_apply_L(0, x, y, tc=True)
+        print("kernels: FP32 L apply and sweep, double-float L apply, on level 0 (x2)")
     elif args.profile == "split5":
         x = torch.randn((ns, na), device="cuda", dtype=torch.float64)
         y = torch.empty_like(x)
