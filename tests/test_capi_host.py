@@ -47,6 +47,19 @@ def test_null_context_is_rejected(lib):
     assert lib.amgt_create(None, 0, None) == -1
 
 
+def test_batch_calls_reject_bad_arguments(lib):
+    """The batch entry points refuse a null list, a negative count and null
+    members before any thread or device work; an empty batch succeeds."""
+    P = ctypes.c_void_p
+    lib.amgt_setup_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int]
+    lib.amgt_setup_batch.restype = ctypes.c_int
+    assert lib.amgt_setup_batch(None, 1, 0) == -1
+    empty = (P * 1)(None)
+    assert lib.amgt_setup_batch(empty, -1, 0) == -1
+    assert lib.amgt_setup_batch(empty, 1, 0) == -1        # a null context in the list
+    assert lib.amgt_setup_batch(empty, 0, 0) == 0
+
+
 def _header_constants():
     src = open(os.path.join(ROOT, "include", "amgt.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
