@@ -1553,9 +1553,24 @@ int vcycle_impl(amgt_ctx* ctx, int k, bool tc, const T* f, T* phi) {
   TRY(wsvec<T>(ctx, k, 0, &r));
   TRY(wsvec<T>(ctx, k + 1, 1, &fc));
   TRY(wsvec<T>(ctx, k + 1, 2, &phic));
-  // r = f - (L - S) phi = (S phi + f) - L phi
-  TRY(scatter_impl<T>(ctx, k, tc, phi, r, 1.0, 0.0, f));
-  TRY(applyL_impl<T>(ctx, k, T(-1), T(1), phi, r));
+  if (ctx->nu_pre >= 1) {
+    // the last pre-smoothing sweep solved L phi = t exactly (the sweep
+    // inverts L): t = f after one sweep from zero, else S phi_prev + f in
+    // workspace 3; so r = f - (L - S) phi = S phi + f - t, with no L apply
+    if (ctx->nu_pre == 1) {
+      TRY(scatter_impl<T>(ctx, k, tc, phi, r, 1.0, 0.0, nullptr));
+    } else {
+      T* t;
+      TRY(wsvec<T>(ctx, k, 3, &t));
+      TRY(scatter_impl<T>(ctx, k, tc, phi, r, 1.0, 0.0, f));
+      launch_axpby<T>(L.nsdof * L.nadof(), -1.0, t, 1.0, r, ctx->stream);
+      CK(cudaGetLastError());
+    }
+  } else {
+    // r = f - (L - S) phi = (S phi + f) - L phi
+    TRY(scatter_impl<T>(ctx, k, tc, phi, r, 1.0, 0.0, f));
+    TRY(applyL_impl<T>(ctx, k, T(-1), T(1), phi, r));
+  }
   TRY(restrict_impl<T>(ctx, k, r, fc));
   TRY(vcycle_impl<T>(ctx, k + 1, tc, fc, phic));
   TRY(prolong_impl<T>(ctx, k, phic, phi));

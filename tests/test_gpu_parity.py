@@ -188,6 +188,27 @@ def test_multigrid_operators(dim, nc, level, basis, nlev, Nr, dtype, gs_kernel):
     ctx.close()
 
 
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1), (3, 0)], ids=["V11", "V21", "V30"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_vcycle_smoothing_counts(nu, dtype):
+    """One V-cycle against the oracle with one, two and three pre-smoothing
+    sweeps: the residual after pre-smoothing is formed as S phi + f - t with
+    t the last sweep's right-hand side (the sweep inverts L), which must
+    equal the oracle's f - A phi."""
+    prob = _mg_problem(2, (6, 5), 2, "lin", 3, [8, 4, 3])
+    prob["mg"]["nu_pre"], prob["mg"]["nu_post"] = nu
+    H = multigrid.Hierarchy(prob)
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-11 if dtype == "f64" else 2e-4
+    T0 = H.levels[0]
+    f = W.random_vector((T0.nsdof, T0.nadof), 48)
+    out = torch.empty((T0.nsdof, T0.nadof), device="cuda", dtype=td)
+    ctx.amgt_op_vcycle(_dev(f, td), out)
+    assert _rel(_host(out), H.vcycle(f)) < tol
+    ctx.close()
+
+
 @pytest.mark.parametrize("precond", ["sweep", "mg"])
 def test_fp64_solve_matches_oracle(precond):
     from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_MG, AMGT_PREC_SWEEP
