@@ -2690,11 +2690,39 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     // inner solve can go): the FP16 three-product tensor-core form, or the SIMT
     // FP32 contraction; the preconditioner's scatters use BF16 tensor cores
     const int a32_path = ctx->f32_scatter == 1 ? 0 : 2;
-    auto A32 = [&](const float* xx, float* yy) { return applyA_impl<float>(ctx, 0, a32_path, xx, yy); };
+    // The Krylov method applies A to the preconditioner's output z, and z
+    // left a sweep: L z = t exactly (the sweep inverts L), with t the sweep's
+    // input (the sweep preconditioner) or the last post-smoothing sweep's
+    // right-hand side S z' + f (workspace 3 of level 0, the V-cycle).  Then
+    // A z = t - S z: one scatter and no L apply.
+    const float* mz = nullptr;
+    const float* mt = nullptr;
+    auto A32 = [&](const float* xx, float* yy) -> int {
+      if (xx == mz && mt) {
+        mz = nullptr;
+        return scatter_impl<float>(ctx, 0, a32_path, xx, yy, -1.0, 0.0, mt);
+      }
+      mz = nullptr;
+      return applyA_impl<float>(ctx, 0, a32_path, xx, yy);
+    };
     auto M32 = [&](const float* v, float* z) -> int {
-      if (prec == AMGT_PREC_SWEEP) return sweep_impl<float>(ctx, 0, v, z);
-      if (prec == AMGT_PREC_MG)
-        return graphs ? vcycle_graph<float>(ctx, tc, v, z) : vcycle_impl<float>(ctx, 0, tc, v, z);
+      mz = nullptr;
+      if (prec == AMGT_PREC_SWEEP) {
+        TRY(sweep_impl<float>(ctx, 0, v, z));
+        mz = z;
+        mt = v;
+        return AMGT_OK;
+      }
+      if (prec == AMGT_PREC_MG) {
+        TRY(graphs ? vcycle_graph<float>(ctx, tc, v, z) : vcycle_impl<float>(ctx, 0, tc, v, z));
+        if (ctx->lv.size() > 1 && ctx->nu_post >= 1) {
+          float* t;
+          TRY(wsvec<float>(ctx, 0, 3, &t));
+          mz = z;
+          mt = t;
+        }
+        return AMGT_OK;
+      }
       CK(cudaMemcpyAsync(z, v, (size_t)n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
       return AMGT_OK;
     };
