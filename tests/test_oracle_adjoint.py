@@ -36,6 +36,20 @@ def test_reversed_direction_operator_is_the_transpose(dim, nc, level, basis):
 
 
 @pytest.mark.parametrize("dim,nc,level,basis", CASES)
+def test_reversed_direction_sweep_inverts_the_transpose(dim, nc, level, basis):
+    """The sweep of the reversed-direction operators (every direction swept
+    in its own upwind order) is the exact inverse of L^T, checked against
+    LAPACK on the assembled transpose of the forward L."""
+    prob, am = _setup(dim, nc, level, basis)
+    T = transport.Transport(prob, am)
+    Ta = transport.Transport(prob, adjoint.ReversedMesh(am))
+    b = W.random_vector((T.nsdof, T.nadof), 5)
+    x = Ta.sweep(b)
+    xr = np.linalg.solve(T.dense_L().T, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-12
+
+
+@pytest.mark.parametrize("dim,nc,level,basis", CASES)
 def test_adjoint_identity(dim, nc, level, basis):
     prob, am = _setup(dim, nc, level, basis)
     T = transport.Transport(prob, am)
