@@ -342,8 +342,9 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
  * (may be NULL) receives n entries.  Each solve is followed by amgt_sync, so
  * a bounded device-side wait that gave up is reported as that problem's
  * status (the cooperative coarse solvers rely on the co-residency that a
- * cooperative launch guarantees its blocks).  Returns the first non-OK status
- * of the n solves (all of them run). */
+ * cooperative launch guarantees its blocks).  The contexts must be non-null
+ * and distinct (AMGT_ERR_ARG before any work otherwise).  Returns the first
+ * non-OK status of the n solves (all of them run). */
 int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
                      double* const* phi, amgt_stats* stats, int nthreads);
 
@@ -352,8 +353,9 @@ int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, doub
  * tables, workspaces of the operators' plans) concurrently on nthreads host
  * threads (0: min(n, 16)), each context on its own stream; a batch of many
  * small problems spends most of its set-up in host work and small
- * synchronous copies, which overlap across contexts this way.  Contexts must
- * be distinct.  Returns the first non-OK status (all are attempted). */
+ * synchronous copies, which overlap across contexts this way.  The contexts
+ * must be non-null and distinct (AMGT_ERR_ARG before any work otherwise).
+ * Returns the first non-OK status (all are attempted). */
 int amgt_setup_batch(amgt_ctx* const* ctxs, int n, int nthreads);
 
 /* ---- operators of the hot path on device buffers -------------------------- */

@@ -2266,11 +2266,20 @@ int amgt_response_gradients(amgt_ctx* ctx, int device, const double* psi, const 
 
 // ---- batched solves and autotuning
 
+// A batch's contexts are non-null and distinct: two host threads driving one
+// context would race on its workspaces and stream.
+static bool batch_contexts_ok(amgt_ctx* const* ctxs, int n) {
+  std::vector<amgt_ctx*> v(ctxs, ctxs + n);
+  if (std::find(v.begin(), v.end(), nullptr) != v.end()) return false;
+  std::sort(v.begin(), v.end());
+  return std::adjacent_find(v.begin(), v.end()) == v.end();
+}
+
 int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, double* const* psi,
                      double* const* phi, amgt_stats* stats, int nthreads) {
-  if (!ctxs || n < 0 || !opt || !psi) return AMGT_ERR_ARG;
+  if (!ctxs || n < 0 || !opt || !psi || !batch_contexts_ok(ctxs, n)) return AMGT_ERR_ARG;
   for (int i = 0; i < n; ++i)
-    if (!ctxs[i] || !psi[i]) return AMGT_ERR_ARG;
+    if (!psi[i]) return AMGT_ERR_ARG;
   int nt = nthreads > 0 ? nthreads : std::min(n, 16);
   nt = std::max(1, std::min(nt, std::max(1, n)));
   std::vector<int> rc(n, AMGT_OK);
@@ -2293,11 +2302,8 @@ int amgt_solve_batch(amgt_ctx* const* ctxs, int n, const amgt_options* opt, doub
   return AMGT_OK;
 }
 
-
 int amgt_setup_batch(amgt_ctx* const* ctxs, int n, int nthreads) {
-  if (!ctxs || n < 0) return AMGT_ERR_ARG;
-  for (int i = 0; i < n; ++i)
-    if (!ctxs[i]) return AMGT_ERR_ARG;
+  if (!ctxs || n < 0 || !batch_contexts_ok(ctxs, n)) return AMGT_ERR_ARG;
   int nt = nthreads > 0 ? nthreads : std::min(n, 16);
   nt = std::max(1, std::min(nt, std::max(1, n)));
   std::vector<int> rc(n, AMGT_OK);

@@ -48,8 +48,10 @@ def test_null_context_is_rejected(lib):
 
 
 def test_batch_calls_reject_bad_arguments(lib):
-    """The batch entry points refuse a null list, a negative count and null
-    members before any thread or device work; an empty batch succeeds."""
+    """The batch entry points refuse a null list, a negative count, null
+    members and a context listed twice before any thread or device work (no
+    member is dereferenced: the repeated one below is a zeroed host buffer,
+    not a context); an empty batch succeeds."""
     P = ctypes.c_void_p
     lib.amgt_setup_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_int]
     lib.amgt_setup_batch.restype = ctypes.c_int
@@ -58,6 +60,17 @@ def test_batch_calls_reject_bad_arguments(lib):
     assert lib.amgt_setup_batch(empty, -1, 0) == -1
     assert lib.amgt_setup_batch(empty, 1, 0) == -1        # a null context in the list
     assert lib.amgt_setup_batch(empty, 0, 0) == 0
+    fake = ctypes.create_string_buffer(1 << 16)
+    twice = (P * 2)(ctypes.addressof(fake), ctypes.addressof(fake))
+    assert lib.amgt_setup_batch(twice, 2, 0) == -1
+    lib.amgt_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, ctypes.POINTER(P),
+                                     ctypes.POINTER(P), P, ctypes.c_int]
+    lib.amgt_solve_batch.restype = ctypes.c_int
+    opts = ctypes.create_string_buffer(256)
+    bufs = (P * 2)(ctypes.addressof(fake), ctypes.addressof(fake))
+    assert lib.amgt_solve_batch(twice, 2, ctypes.addressof(opts), bufs, None, None, 0) == -1
+    assert lib.amgt_solve_batch(empty, 1, ctypes.addressof(opts), bufs, None, None, 0) == -1
+    assert lib.amgt_solve_batch(empty, 0, ctypes.addressof(opts), bufs, None, None, 0) == 0
 
 
 def _header_constants():
