@@ -1815,11 +1815,11 @@ int bicgstab(amgt_ctx* ctx, int k, OpA apply_A, OpM apply_M, const T* b, T* x, b
   double bnorm = bnorm_in;
   if (bnorm < 0) TRY(norm2<T>(ctx, b, n, &bnorm));
   res = KrylovResult();
-  res.cycles = 1;
   if (bnorm == 0.0) {
     CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
     return AMGT_OK;
   }
+  res.cycles = 1;
   if (!std::isfinite(bnorm)) return fail(ctx, AMGT_ERR_NAN, "right-hand side is not finite");
   auto residual = [&]() -> int {  // r = b - A x
     if (x_zero) {
@@ -2689,7 +2689,9 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
     TRY(wsvec<float>(ctx, 0, 2, &e32));
     double bnorm;
     TRY(norm2<double>(ctx, b, n, &bnorm));
+    if (!std::isfinite(bnorm)) return fail(ctx, AMGT_ERR_NAN, "right-hand side is not finite");
     if (bnorm == 0.0) {
+      // b = 0: psi = 0 solves it exactly (relres 0, no iteration)
       CK(cudaMemsetAsync(x, 0, bytes, ctx->stream));
     }
     // the inner operator keeps FP32 accuracy (its rounding sets how far each
@@ -2733,7 +2735,7 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
       return AMGT_OK;
     };
     int total_its = 0, outer = 0;
-    double relres = 1.0;
+    double relres = bnorm > 0.0 ? 1.0 : 0.0;
     // inner tolerance: fixed, or aimed at the outer tolerance from the current
     // residual (the FP32 operator's rounding bounds how far one solve can go)
     auto inner_tol_for = [&](double rr) {
