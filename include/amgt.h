@@ -193,7 +193,8 @@ int amgt_set_angular_aniso(amgt_ctx* ctx, int basis, const double axis[3], int l
 /* k-level V(nu_pre, nu_post) cycle on T_L..T_{L-k+1} (Fig. lmg).  Nr[j] is
  * the scatter order used on level j (Sec. 4.3; Nr[0] normally N).  The
  * coarsest level is solved by coarse_sweeps block Gauss-Seidel sweeps
- * (Sec. 4.2).  nlevels = 1 keeps only the finest mesh. */
+ * (Sec. 4.2; 0: no coarse correction).  nlevels = 1 keeps only the finest
+ * mesh, and the cycle is then the Gauss-Seidel sweeps alone. */
 int amgt_set_multigrid(amgt_ctx* ctx, int nlevels, const int* Nr, int nu_pre,
                        int nu_post, int coarse_sweeps);
 /* Isotropic volumetric source: q[C] scalar emission density, Q = q/(4 pi). */
@@ -391,7 +392,8 @@ int amgt_op_prolong(amgt_ctx* ctx, int level, int dtype, const void* xc, void* x
  * phi is read and overwritten. */
 int amgt_op_smooth(amgt_ctx* ctx, int level, int dtype, int nu, const void* f, void* phi);
 /* `sweeps` block Gauss-Seidel sweeps on the coarsest level with self-scatter
- * in each block solve (Sec. 4.2); phi is read and overwritten. */
+ * in each block solve (Sec. 4.2); phi is read and overwritten (left as it
+ * is, with no launch, for sweeps = 0). */
 int amgt_op_coarse_gs(amgt_ctx* ctx, int dtype, int sweeps, const void* f, void* phi);
 /* Same as amgt_op_coarse_gs, but allocates nothing: no cudaMalloc, cudaFree or
  * allocating library call.  Meant for callers that cannot let a library

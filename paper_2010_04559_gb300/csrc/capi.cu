@@ -1440,6 +1440,7 @@ int coarse_gs_noalloc_impl(amgt_ctx* ctx, int sweeps, const T* f, T* phi) {
 
 template <class T>
 int coarse_gs_run(amgt_ctx* ctx, int sweeps, const T* f, T* phi, T* mom, bool timed) {
+  if (sweeps == 0) return AMGT_OK;  // no sweep: phi is left as it is
   const int k = (int)ctx->lv.size() - 1;
   const Level& L = ctx->lv[k];
   const bool rows = store<T>(L).TinvT && (ctx->gs_kernel == 0 || ctx->gs_kernel == 6) &&

@@ -187,3 +187,81 @@ def test_one_cell_wide_solve(dim, nc):
                                    inner_tol=1e-4)
     assert st.relres < 1e-12 and _rel(psi, xo) < 1e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("krylov", [0, 1], ids=["gmres", "bicgstab"])
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_converged_initial_guess_returns_at_once(mode, krylov):
+    """An initial guess that already meets the tolerance (the oracle's
+    solution to 1e-13) is returned unchanged after one residual, with no
+    iteration."""
+    prob = _mg(W.random_problem(2, (6, 5), 1, 4, 85, inflow=0.3), [4, 2], sweeps=10)
+    T = multigrid.Hierarchy(prob).levels[0]
+    xo, _, _, rel = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+    assert rel < 1e-13
+    ctx = _ctx(prob)
+    md, pc = _modes(mode, "mg")
+    psi, _, st, rc = ctx.amgt_solve(tol=1e-9, precond=pc, mode=md, krylov=krylov, x0=xo)
+    assert rc == 0 and st.iterations == 0 and st.relres < 1e-9
+    assert np.array_equal(psi, xo)
+    ctx.close()
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_short_gmres_restarts(m):
+    """GMRES(m) with m = 1, 2, 3 (one- to three-column Hessenberg systems,
+    a restart after every few directions) reaches the oracle's solution."""
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_SWEEP
+    prob = W.random_problem(2, (5, 4), 1, 4, 86, inflow=0.2)
+    T = multigrid.Hierarchy(_mg(dict(prob), [4])).levels[0]
+    xo, _, _, rel = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+    ctx = _ctx(prob)
+    psi, _, st, rc = ctx.amgt_solve(tol=1e-12, restart=m, maxit=5000, precond=AMGT_PREC_SWEEP,
+                                    mode=AMGT_MODE_F64)
+    assert st.relres < 1e-12 and _rel(psi, xo) < 1e-10
+    assert st.outer_iterations >= st.iterations // m
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_one_level_hierarchy(dtype):
+    """nlevels = 1: the cycle is the coarse Gauss-Seidel on the finest mesh
+    at the full order, from zero (Fig. lmg at its coarsest level); the
+    multigrid-preconditioned FP64 solve reaches the oracle's solution."""
+    from paper_2010_04559_gb300 import AMGT_MODE_F64, AMGT_PREC_MG
+    prob = _mg(W.random_problem(2, (6, 5), 1, 4, 87, inflow=0.2), [4], sweeps=3)
+    H = multigrid.Hierarchy(prob)
+    T = H.levels[0]
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-11 if dtype == "f64" else 2e-4
+    f = W.random_vector((T.nsdof, T.nadof), 88)
+    out = torch.empty((T.nsdof, T.nadof), device="cuda", dtype=td)
+    ctx.amgt_op_vcycle(_dev(f, td), out)
+    assert _rel(_host(out), H.vcycle(f)) < tol
+    if dtype == "f64":
+        xo, _, _, rel = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+        psi, _, st, _ = ctx.amgt_solve(tol=1e-12, precond=AMGT_PREC_MG, mode=AMGT_MODE_F64)
+        assert st.relres < 1e-12 and _rel(psi, xo) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_zero_coarse_sweeps(dtype):
+    """coarse_sweeps = 0: the coarse Gauss-Seidel leaves phi as it is and the
+    cycle has no coarse correction (smoothing only), as in the oracle."""
+    prob = _mg(W.random_problem(2, (6, 5), 2, 6, 89), [6, 3], sweeps=0)
+    H = multigrid.Hierarchy(prob)
+    T0, Tc = H.levels[0], H.levels[-1]
+    ctx = _ctx(prob)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    tol = 1e-11 if dtype == "f64" else 2e-4
+    pc0 = W.random_vector((Tc.nsdof, Tc.nadof), 90)
+    pc = _dev(pc0, td)
+    ctx.amgt_op_coarse_gs(0, _dev(W.random_vector((Tc.nsdof, Tc.nadof), 91), td), pc)
+    assert np.array_equal(_host(pc), _host(_dev(pc0, td)))
+    f = W.random_vector((T0.nsdof, T0.nadof), 92)
+    out = torch.empty((T0.nsdof, T0.nadof), device="cuda", dtype=td)
+    ctx.amgt_op_vcycle(_dev(f, td), out)
+    assert _rel(_host(out), H.vcycle(f)) < tol
+    ctx.close()
