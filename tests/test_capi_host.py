@@ -95,3 +95,22 @@ def test_binding_constants_match_the_header():
         if name.startswith(("AMGT_TUNE_", "AMGT_KT_", "AMGT_F", "AMGT_MODE_", "AMGT_PREC_",
                             "AMGT_KRYLOV_")) and name != "AMGT_KT_COUNT":
             assert getattr(pkg, name) == val, name
+
+
+def test_without_a_gpu_the_library_fails_loudly(lib):
+    """No CUDA device (this CPU host): context creation returns
+    AMGT_ERR_CUDA and leaves no handle, and the Python binding raises
+    instead of computing anything on the CPU (there is no CPU fallback)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is visible")
+    from paper_2010_04559_gb300 import AMGT_ERR_CUDA, AmgtError, context_from_problem
+    h = ctypes.c_void_p(1)
+    lib.amgt_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p]
+    lib.amgt_create.restype = ctypes.c_int
+    assert lib.amgt_create(ctypes.byref(h), 0, None) == AMGT_ERR_CUDA
+    assert not h.value
+    import workloads as W
+    with pytest.raises(AmgtError) as e:
+        context_from_problem(W.random_problem(2, (3, 3), 1, 4, 1), device=0)
+    assert e.value.code == AMGT_ERR_CUDA
