@@ -32,7 +32,7 @@ def test_sweep_preconditioned_matches_dense_lu(dim, nc, level, basis):
 
 
 def test_multigrid_preconditioned_matches_dense_lu():
-    prob = W.random_problem(2, (4, 3), 2, 6, 14, g=0.85)
+    prob = W.random_problem(2, (3, 2), 2, 6, 14, g=0.85)
     prob["mg"] = dict(nlevels=3, Nr=[6, 4, 3], nu_pre=1, nu_post=1, coarse_sweeps=4)
     H = multigrid.Hierarchy(prob)
     T = H.levels[0]
