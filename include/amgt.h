@@ -89,8 +89,9 @@ typedef enum {
 
 typedef struct amgt_options {
   double tol;          /* stop when ||b - A x||_2 / ||b||_2 < tol (Sec. 5.1)   */
-  int restart;         /* GMRES restart length m (20)                          */
-  int maxit;           /* cap on Krylov iterations (all cycles)                */
+  int restart;         /* GMRES restart length m (<= 0: 20; at most 30, the
+                          Krylov workspace; larger values run GMRES(30))    */
+  int maxit;           /* cap on Krylov iterations (all cycles; <= 0: 1000)    */
   int precond;         /* AMGT_PREC_*                                          */
   int mode;            /* AMGT_MODE_*                                          */
   int device_ptrs;     /* 1: x0/psi/phi of amgt_solve are device pointers      */
@@ -98,7 +99,7 @@ typedef struct amgt_options {
                           0: adaptive, each inner solve aims at the outer tol:
                           0.3 tol / (current relres), within [3e-5, 1e-2],
                           and stops after 2 restart cycles at most          */
-  int inner_maxit;     /* mixed mode: cap per inner solve                      */
+  int inner_maxit;     /* mixed mode: cap per inner solve (<= 0: 200)          */
   int krylov;          /* AMGT_KRYLOV_GMRES (restarted GMRES(restart)) or
                           AMGT_KRYLOV_BICGSTAB (the paper's method, Sec. 3);
                           in mixed mode it is the inner FP32 solver          */
