@@ -6,9 +6,12 @@ term, a wrong sign, index, operand or order in each oracle function is caught
 by a pin fixed by the paper or the mathematics (dense LU, closed forms,
 LAPACK, scipy, the paper's printed mesh sizes, finite differences).
 
-The Krylov oracles (GMRES, BiCGStab) are not mutated here: their pins compare
-the returned solution with LAPACK's, so any mistake that changes the answer
-fails them by construction.
+The Krylov oracles (GMRES, BiCGStab) are pinned on their returned solution
+against LAPACK; the cases below show that an update along the wrong
+directions or a dropped stabilisation step fails those pins.  (A mistake that
+only slows the iteration -- a Givens rotation of the wrong sign, say, which
+each restart's true residual corrects -- leaves the answer, and the pins,
+unchanged.)
 """
 import numpy as np
 import pytest
@@ -20,7 +23,8 @@ import test_oracle_harmonics_spatial as PH
 import test_oracle_materials as PM
 import test_oracle_transport as PT
 import test_oracle_vcycle as PV
-from oracle import adjoint, angular, harmonics, multigrid, spatial, transport
+import test_oracle_bicgstab as PK
+from oracle import adjoint, angular, bicgstab, gmres, harmonics, multigrid, spatial, transport
 
 
 # --------------------------------------------------------------- V-cycle
@@ -412,7 +416,112 @@ BEAM_ADJOINT = {
 }
 
 
-ALL = {**VCYCLE, **GS, **TRANSPORT, **ANGULAR, **LOCAL, **BEAM_ADJOINT}
+# ------------------------------------------------------------------ Krylov
+def _gmres(update_with_V=False):
+    """Right-preconditioned restarted GMRES(m) with CGS2 and Givens rotations
+    (the oracle's method) with one step changed."""
+    def run(apply_A, b, apply_M, tol, restart=20, maxit=1000, x0=None):
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+        bnorm = np.linalg.norm(b)
+        its = 0
+        m = restart
+        while True:
+            r = b - apply_A(x)
+            beta = np.linalg.norm(r)
+            rel = beta / bnorm
+            if rel < tol or its >= maxit:
+                return x, its, [], rel
+            V, Z = [r / beta], []
+            H = np.zeros((m + 1, m))
+            cs, sn, g = np.zeros(m), np.zeros(m), np.zeros(m + 1)
+            g[0] = beta
+            k = 0
+            for j in range(m):
+                z = apply_M(V[j])
+                w = apply_A(z).reshape(-1)
+                Vm = np.stack([v.reshape(-1) for v in V])
+                h = Vm @ w
+                w = w - Vm.T @ h
+                h2 = Vm @ w
+                w = w - Vm.T @ h2
+                hn = np.linalg.norm(w)
+                H[:j + 1, j] = h + h2
+                H[j + 1, j] = hn
+                Z.append(z)
+                for i in range(j):
+                    t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                    H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                    H[i, j] = t
+                den = np.hypot(H[j, j], H[j + 1, j])
+                cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+                H[j, j], H[j + 1, j] = den, 0.0
+                g[j + 1] = -sn[j] * g[j]
+                g[j] = cs[j] * g[j]
+                its += 1
+                k = j + 1
+                if abs(g[j + 1]) / bnorm < tol or its >= maxit or hn == 0.0:
+                    break
+                V.append((w / hn).reshape(b.shape))
+            y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+            for i in range(k):
+                x = x + y[i] * (V[i] if update_with_V else Z[i])
+    return run
+
+
+def _bicgstab_without_stabilisation_update(apply_A, b, apply_M, tol, maxit=1000, x0=None):
+    """BiCGStab whose iterate misses the minimal-residual step omega M^-1 s
+    (the residual recursion keeps it)."""
+    x = np.zeros_like(b)
+    bnorm = np.linalg.norm(b)
+    r = b - apply_A(x)
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    its = 0
+    while its < maxit and np.linalg.norm(r) / bnorm >= tol:
+        its += 1
+        rho = np.vdot(rhat, r)
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = apply_M(p)
+        v = apply_A(ph)
+        alpha = rho / np.vdot(rhat, v)
+        s = r - alpha * v
+        sh = apply_M(s)
+        t = apply_A(sh)
+        omega = np.vdot(t, s) / np.vdot(t, t)
+        x = x + alpha * ph
+        r = s - omega * t
+        rho_old = rho
+    return x, its, [], np.linalg.norm(b - apply_A(x)) / bnorm
+
+
+def _gmres_pin():
+    PT.test_gmres_matches_dense_lu(*PT.CASES[0])
+
+
+def _bicgstab_pin():
+    PK.test_sweep_preconditioned_matches_dense_lu(2, (3, 2), 1, "lin")
+
+
+KRYLOV = {
+    "GMRES update along the unpreconditioned directions": (
+        lambda mp: mp.setattr(gmres, "gmres", _gmres(update_with_V=True)), _gmres_pin),
+    "BiCGStab iterate without the stabilisation step": (
+        lambda mp: mp.setattr(bicgstab, "bicgstab", _bicgstab_without_stabilisation_update),
+        _bicgstab_pin),
+}
+
+
+def test_the_krylov_mutant_without_a_mistake_passes_the_pins(monkeypatch):
+    """The GMRES copy above, with no step changed, passes the pin: the
+    failures above come from the planted mistakes alone."""
+    monkeypatch.setattr(gmres, "gmres", _gmres())
+    _gmres_pin()
+
+
+ALL = {**VCYCLE, **GS, **TRANSPORT, **ANGULAR, **LOCAL, **BEAM_ADJOINT, **KRYLOV}
 
 
 @pytest.mark.parametrize("name", list(ALL))
