@@ -331,8 +331,9 @@ int amgt_query_sizes(const amgt_ctx* ctx, int level, int64_t* nsdof, int64_t* na
 
 /* Solves (L - S) psi = f to opt->tol (Sec. 3, Sec. 5.1).  psi [Nsdof][Nadof]
  * and phi [Nsdof] (scalar flux, may be NULL) receive the result; x0 may be
- * NULL (zero initial guess).  Pointers are host memory unless
- * opt->device_ptrs.  st may be NULL. */
+ * NULL (zero initial guess) and may equal psi (a warm start in place, e.g.
+ * to resume a solve).  Pointers are host memory unless opt->device_ptrs.
+ * st may be NULL. */
 int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0,
                double* psi, double* phi, amgt_stats* st);
 

@@ -2650,8 +2650,10 @@ int amgt_solve(amgt_ctx* ctx, const amgt_options* opt, const double* x0, double*
   TRY(source_impl<double>(ctx, 0, b));
   bool x_zero = true;
   if (x0) {
-    CK(cudaMemcpyAsync(x, x0, bytes, opt->device_ptrs ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyHostToDevice, ctx->stream));
+    // x0 == psi on the device is a warm start in place: psi already holds it
+    if (x0 != x)
+      CK(cudaMemcpyAsync(x, x0, bytes, opt->device_ptrs ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyHostToDevice, ctx->stream));
     x_zero = false;
   }
   KrylovResult kr;

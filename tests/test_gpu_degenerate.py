@@ -265,3 +265,27 @@ def test_zero_coarse_sweeps(dtype):
     ctx.amgt_op_vcycle(_dev(f, td), out)
     assert _rel(_host(out), H.vcycle(f)) < tol
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_warm_start_in_place(mode):
+    """x0 = psi on the device (resuming a solve in place): a solved psi is
+    kept as it is with no iteration, and a solve to a tighter tolerance from
+    it reaches the oracle's solution."""
+    prob = _mg(W.random_problem(2, (6, 5), 1, 4, 93, inflow=0.3), [4, 2], sweeps=10)
+    T = multigrid.Hierarchy(prob).levels[0]
+    xo, _, _, _ = gmres.gmres(T.apply_A, T.source(), T.sweep, 1e-13, 20, 1000)
+    ctx = _ctx(prob)
+    md, pc = _modes(mode, "mg")
+    ns, na = ctx.amgt_query_sizes(0)
+    psi = torch.empty((ns, na), device="cuda", dtype=torch.float64)
+    _, _, st, _ = ctx.amgt_solve(tol=1e-6, precond=pc, mode=md, psi=psi, device_ptrs=True)
+    first = _host(psi).copy()
+    _, _, st, rc = ctx.amgt_solve(tol=1e-6, precond=pc, mode=md, x0=psi, psi=psi,
+                                  device_ptrs=True)
+    assert rc == 0 and st.iterations == 0 and np.array_equal(_host(psi), first)
+    _, _, st, _ = ctx.amgt_solve(tol=1e-12, precond=pc, mode=md, x0=psi, psi=psi,
+                                 device_ptrs=True, inner_tol=1e-4)
+    assert st.relres < 1e-12
+    assert _rel(_host(psi), xo) < (1e-10 if mode == "f64" else 1e-6)
+    ctx.close()
