@@ -220,6 +220,17 @@ def _degree_shift(mp):
                lambda N: np.minimum(orig(N) + 1, N))
 
 
+def _with_fid0(method):
+    def run(self, *a, **k):
+        saved = self.fid
+        self.fid = np.zeros_like(saved)
+        try:
+            return method(self, *a, **k)
+        finally:
+            self.fid = saved
+    return run
+
+
 def _infinite_medium():
     PT.test_infinite_medium_closed_form(2, (3, 2), "lin")
 
@@ -251,18 +262,6 @@ TRANSPORT = {
                               _with_fid0(transport.Transport.scatter)),
         lambda: PM.test_two_shape_solution_matches_dense_lu(2, (3, 3), 1)),
 }
-
-
-def _with_fid0(method):
-    def run(self, *a, **k):
-        saved = self.fid
-        self.fid = np.zeros_like(saved)
-        try:
-            return method(self, *a, **k)
-        finally:
-            self.fid = saved
-    return run
-
 
 
 # ---------------------------------------------------------------- angular
