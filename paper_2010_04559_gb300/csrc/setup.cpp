@@ -277,32 +277,63 @@ AngMesh build_mesh(const std::vector<std::vector<uint8_t>>& paths, int basis) {
   return m;
 }
 
-void real_harmonics(int N, const double om[3], double* out) {
+namespace {
+// Coefficients of the normalised associated Legendre recurrence, which depend
+// on (n, m) only: the sectoral step sqrt((2m+1)/(2m)), the first off-sectoral
+// factor sqrt(2m+3), and the three-term factors aa(n, m), bb(n, m) for
+// n >= m + 2 (index m (N+1) + n).  Tabulated once per order instead of at
+// every quadrature node; the values are the same expressions.
+struct LegendreCoef {
+  int N = 0;
+  std::vector<double> step, first, aa, bb;
+};
+
+LegendreCoef legendre_coef(int N) {
+  LegendreCoef c;
+  c.N = N;
+  c.step.assign(N + 1, 0.0);
+  c.first.assign(N + 1, 0.0);
+  c.aa.assign((size_t)(N + 1) * (N + 1), 0.0);
+  c.bb.assign((size_t)(N + 1) * (N + 1), 0.0);
+  for (int m = 0; m <= N; ++m) {
+    if (m > 0) c.step[m] = std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+    c.first[m] = std::sqrt(2.0 * m + 3.0);
+    for (int n = m + 2; n <= N; ++n) {
+      c.aa[(size_t)m * (N + 1) + n] =
+          std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+      c.bb[(size_t)m * (N + 1) + n] =
+          std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+    }
+  }
+  return c;
+}
+
+void real_harmonics(const LegendreCoef& c, const double om[3], double* out) {
   // polar axis e_x: t = om_x, azimuthal plane (om_y, om_z)
+  const int N = c.N;
   const double t = om[0];
   const double u = om[1], v = om[2];
   double cm = 1.0 / std::sqrt(4.0 * M_PI);  // Q_m^m (normalised, divided by sin^m)
   double re = 1.0, im = 0.0;                // (u + i v)^m
   for (int m = 0; m <= N; ++m) {
     if (m > 0) {
-      cm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+      cm *= c.step[m];
       double r2 = re * u - im * v;
       double i2 = re * v + im * u;
       re = r2;
       im = i2;
     }
+    const double* aa = &c.aa[(size_t)m * (N + 1)];
+    const double* bb = &c.bb[(size_t)m * (N + 1)];
     double qnm2 = 0.0, qnm1 = cm;
     for (int n = m; n <= N; ++n) {
       double q;
       if (n == m) {
         q = cm;
       } else if (n == m + 1) {
-        q = std::sqrt(2.0 * m + 3.0) * t * cm;
+        q = c.first[m] * t * cm;
       } else {
-        double aa = std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
-        double bb = std::sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) /
-                              (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
-        q = aa * (t * qnm1 - bb * qnm2);
+        q = aa[n] * (t * qnm1 - bb[n] * qnm2);
       }
       if (n > m) {
         qnm2 = qnm1;
@@ -318,26 +349,79 @@ void real_harmonics(int N, const double om[3], double* out) {
     }
   }
 }
+}  // namespace
+
+void real_harmonics(int N, const double om[3], double* out) {
+  real_harmonics(legendre_coef(N), om, out);
+}
 
 std::vector<double> x_table(const AngMesh& m, int N) {
   const int nm = (N + 1) * (N + 1);
   const int a = m.a;
   std::vector<double> X((size_t)m.P * a * nm, 0.0);
-  // patches are independent: spread them over the host's cores
+  const LegendreCoef c = legendre_coef(N);
+  // Patches are independent: spread them over the host's cores.  Inside a
+  // patch the harmonics are generated azimuthal order by azimuthal order for
+  // all quadrature nodes at once (each node keeps its running sectoral value
+  // and (u + i v)^m), so the entries of X that one order touches stay in the
+  // first-level cache while the nodes stream past; every entry still sums its
+  // node terms w_k Psi_i Y_j in node order, as the node-by-node loop did.
   std::atomic<int> next{0};
   auto work = [&] {
-    std::vector<double> nodes, wts, Y(nm);
+    std::vector<double> nodes, wts, T, U, V, CM, RE, IM, WP;
     double psi[3];
     for (int p; (p = next.fetch_add(1)) < m.P;) {
       patch_quadrature(m.patch[p], quadrature_order(m.patch[p].level, N), nodes, wts);
-      for (size_t k = 0; k < wts.size(); ++k) {
+      const size_t K = wts.size();
+      T.resize(K), U.resize(K), V.resize(K), CM.assign(K, 1.0 / std::sqrt(4.0 * M_PI));
+      RE.assign(K, 1.0), IM.assign(K, 0.0), WP.resize(K * a);
+      for (size_t k = 0; k < K; ++k) {
         const double* om = &nodes[3 * k];
+        // polar axis e_x: t = om_x, azimuthal plane (om_y, om_z)
+        T[k] = om[0], U[k] = om[1], V[k] = om[2];
         basis_values(m, p, om, psi);
-        real_harmonics(N, om, Y.data());
-        for (int i = 0; i < a; ++i) {
-          double wp = wts[k] * psi[i];
-          double* row = &X[((size_t)p * a + i) * nm];
-          for (int j = 0; j < nm; ++j) row[j] += wp * Y[j];
+        for (int i = 0; i < a; ++i) WP[k * a + i] = wts[k] * psi[i];
+      }
+      double* Xp = &X[(size_t)p * a * nm];
+      for (int mo = 0; mo <= N; ++mo) {
+        const double* aa = &c.aa[(size_t)mo * (N + 1)];
+        const double* bb = &c.bb[(size_t)mo * (N + 1)];
+        for (size_t k = 0; k < K; ++k) {
+          if (mo > 0) {
+            CM[k] *= c.step[mo];
+            const double r2 = RE[k] * U[k] - IM[k] * V[k];
+            const double i2 = RE[k] * V[k] + IM[k] * U[k];
+            RE[k] = r2;
+            IM[k] = i2;
+          }
+          const double t = T[k], cm = CM[k], re = RE[k], im = IM[k];
+          const double* wp = &WP[k * a];
+          double qnm2 = 0.0, qnm1 = cm;
+          for (int n = mo; n <= N; ++n) {
+            double q;
+            if (n == mo) {
+              q = cm;
+            } else if (n == mo + 1) {
+              q = c.first[mo] * t * cm;
+            } else {
+              q = aa[n] * (t * qnm1 - bb[n] * qnm2);
+            }
+            if (n > mo) {
+              qnm2 = qnm1;
+              qnm1 = q;
+            }
+            const int base = n * n + n;
+            if (mo == 0) {
+              for (int i = 0; i < a; ++i) Xp[(size_t)i * nm + base] += wp[i] * q;
+            } else {
+              const double yr = M_SQRT2 * q * re;
+              const double yi = M_SQRT2 * q * im;
+              for (int i = 0; i < a; ++i) {
+                Xp[(size_t)i * nm + base + mo] += wp[i] * yr;
+                Xp[(size_t)i * nm + base - mo] += wp[i] * yi;
+              }
+            }
+          }
         }
       }
     }
