@@ -5,10 +5,19 @@ term), the balanced integer digits, exact FP32 sums of the slice products,
 and the FP64 result against the FP64 product.  The same rules are what the
 library's host planner and kernels implement for the tensor cores (Ozaki,
 Ogita, Oishi and Rump 2012, error-free splitting); here an FP32 matrix
-product stands in for the tensor-core MMAs with FP32 accumulation."""
+product stands in for the tensor-core MMAs with FP32 accumulation.  The
+last test compiles the library's planner (csrc/split_plan.hpp) and checks
+that it produces exactly the plan checked here."""
+
+import ctypes
+import os
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def plan(K):
@@ -126,3 +135,43 @@ def test_split_product_matches_fp64(K):
     err = np.abs(y - ref) / (np.abs(A).max(axis=1)[:, None] * np.abs(Bt).max(axis=1)[None, :] * K)
     assert err.max() < 1e-14
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def library_plan(tmp_path_factory):
+    """split_plan of the library (csrc/split_plan.hpp), compiled on the host."""
+    if shutil.which("g++") is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("plan") / "libplan.so")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", "-I",
+                    os.path.join(ROOT, "paper_2010_04559_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "split_plan_shim.cpp"), "-o", out],
+                   check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    lib.shim_split_plan.restype = ctypes.c_int
+
+    def get(K):
+        cap = 512
+        I = (ctypes.c_int * cap)
+        bits, nsl = ctypes.c_int(), ctypes.c_int()
+        d, start, gi, gj = I(), I(), I(), I()
+        beta = (ctypes.c_float * cap)()
+        n = lib.shim_split_plan(K, ctypes.byref(bits), ctypes.byref(nsl), d, start, gi, gj,
+                                beta, cap)
+        assert n >= 0
+        passes = [(d[p], [(gi[g], gj[g], float(beta[g])) for g in range(start[p], start[p + 1])])
+                  for p in range(n)]
+        return bits.value, nsl.value, passes
+    return get
+
+
+@pytest.mark.parametrize("K", [64, 96, 384, 1000, 1536, 4096, 6144, 8192, 16384, 65536, 2 ** 21])
+def test_the_library_runs_the_plan_checked_here(library_plan, K):
+    """The library's plan is, pass for pass and product for product, the plan
+    whose bounds and exactness the tests above check (or none where the digit
+    width would drop below 2 bits)."""
+    b, nsl, passes = library_plan(K)
+    if b == 0:
+        assert K * 2.0 ** 4 > 2.0 ** 24 and passes == []
+        return
+    assert (b, nsl, passes) == plan(K)
