@@ -538,26 +538,18 @@ int build_gs_rows(amgt_ctx* ctx) {
   return AMGT_OK;
 }
 
-// Pencil beam on face f (kind 2, Sec. 5.4): psi_b = S delta(Omega - Omega_b)
-// with Omega_b = -n the inward normal, taken in the DG weak form.  Its inflow
-// term on a boundary cell is -S int_face Phi_l (Omega_b.n) Psi_m(Omega_b) =
-// S mf_l Psi_m(Omega_b) on a patch holding Omega_b.  Omega_b is an octahedron
-// vertex, hence a vertex of one patch in each of the 4 octants around it at
-// every refinement level; the Dirac mass is split equally among those k
-// patches.  Table: beam[f][q a + m] = S Psi_[q]m(Omega_b) / k.  Adjoint
-// contexts hold reversed directions, so their patch q covers -D_q: the table
-// is built from the forward mesh (before the reversal) at -Omega_b.
-// Pencil-beam inflow weights per beam face (kinds 2 and 3): the Dirac mass
-// at the beam direction goes to the patches whose closed spherical triangle
-// holds it, each with the fraction of an infinitesimal cap around it that
-// lies in the patch (1 inside, 1/2 on an edge, interior angle / 2 pi at a
-// vertex: 1/4 at an octahedron vertex), times Psi_m there; kind 3 also
-// carries the incidence factor |Omega_b . n|.
+// Pencil-beam inflow tables per beam face (kinds 2 and 3, Sec. 5.4, the
+// Dirac boundary data taken in the DG weak form): beam[f][q a + m] =
+// S |Omega_b . n| share_q Psi_[q]m(Omega_b) from beam_weights (setup.cpp).  A
+// normally incident beam (kind 2) points along the inward normal, an
+// octahedron vertex, where four patches take 1/4 each at every level.
+// Adjoint contexts hold reversed directions (patch q covers -D_q), so their
+// table is built from the forward mesh at -Omega_b.
 int build_beam(amgt_ctx* ctx, Level& Lv, int dim) {
   bool any = false;
   for (int f = 0; f < 2 * dim; ++f) any |= ctx->bkind[f] >= 2;
   if (!any) return AMGT_OK;
-  const int a = Lv.mesh.a, nadof = Lv.mesh.nadof();
+  const int nadof = Lv.mesh.nadof();
   // on an adjoint context patch q stands for -D_q: the same physical beam is
   // found at -Omega_b among the forward patches
   const double sg = ctx->adjoint ? -1.0 : 1.0;
@@ -572,50 +564,7 @@ int build_beam(amgt_ctx* ctx, Level& Lv, int dim) {
       fac *= std::fabs(ob[f / 2]);  // |Omega_b . n|
     }
     const double om[3] = {sg * ob[0], sg * ob[1], sg * ob[2]};
-    double total = 0.0;
-    for (int q = 0; q < Lv.mesh.P; ++q) {
-      const auto& V = Lv.mesh.patch[q].v;
-      // om = sum_i lam_i V_i (Cramer's rule)
-      auto det = [](const double* c0, const double* c1, const double* c2) {
-        return c0[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (c0[1] * c2[2] - c0[2] * c2[1]) +
-               c2[0] * (c0[1] * c1[2] - c0[2] * c1[1]);
-      };
-      const double D = det(V[0], V[1], V[2]);
-      const double lam[3] = {det(om, V[1], V[2]) / D, det(V[0], om, V[2]) / D,
-                             det(V[0], V[1], om) / D};
-      const double lmax = std::max({std::fabs(lam[0]), std::fabs(lam[1]), std::fabs(lam[2])});
-      if (std::min({lam[0], lam[1], lam[2]}) < -1e-12 * lmax) continue;
-      int nz = 0, vi = -1;
-      for (int i = 0; i < 3; ++i) {
-        if (std::fabs(lam[i]) <= 1e-12 * lmax) ++nz;
-        else vi = i;
-      }
-      double share = 1.0;
-      if (nz == 1) {
-        share = 0.5;
-      } else if (nz == 2) {
-        // interior angle at vertex vi between the great circles to the others
-        const double* A = V[vi];
-        const double* B = V[(vi + 1) % 3];
-        const double* C = V[(vi + 2) % 3];
-        double tb[3], tc[3];
-        const double ab = A[0] * B[0] + A[1] * B[1] + A[2] * B[2];
-        const double ac = A[0] * C[0] + A[1] * C[1] + A[2] * C[2];
-        for (int e = 0; e < 3; ++e) {
-          tb[e] = B[e] - ab * A[e];
-          tc[e] = C[e] - ac * A[e];
-        }
-        const double cr[3] = {tb[1] * tc[2] - tb[2] * tc[1], tb[2] * tc[0] - tb[0] * tc[2],
-                              tb[0] * tc[1] - tb[1] * tc[0]};
-        const double dt = tb[0] * tc[0] + tb[1] * tc[1] + tb[2] * tc[2];
-        share = std::atan2(std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), dt) /
-                (2.0 * M_PI);
-      }
-      double psi[3];
-      basis_values(Lv.mesh, q, om, psi);
-      for (int m = 0; m < a; ++m) beam[(size_t)f * nadof + q * a + m] = fac * share * psi[m];
-      total += share;
-    }
+    const double total = beam_weights(Lv.mesh, om, fac, &beam[(size_t)f * nadof]);
     if (std::fabs(total - 1.0) > 1e-9)
       return fail(ctx, AMGT_ERR_UNSUPPORTED,
                   "beam direction: the patch shares around it do not sum to 1");

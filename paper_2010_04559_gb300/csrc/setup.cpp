@@ -440,6 +440,55 @@ std::vector<double> x_table(const AngMesh& m, int N) {
   return X;
 }
 
+double beam_weights(const AngMesh& m, const double om[3], double fac, double* out) {
+  const int a = m.a;
+  double total = 0.0;
+  for (int q = 0; q < m.P; ++q) {
+    const auto& V = m.patch[q].v;
+    // om = sum_i lam_i V_i (Cramer's rule)
+    auto det = [](const double* c0, const double* c1, const double* c2) {
+      return c0[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - c1[0] * (c0[1] * c2[2] - c0[2] * c2[1]) +
+             c2[0] * (c0[1] * c1[2] - c0[2] * c1[1]);
+    };
+    const double D = det(V[0], V[1], V[2]);
+    const double lam[3] = {det(om, V[1], V[2]) / D, det(V[0], om, V[2]) / D,
+                           det(V[0], V[1], om) / D};
+    const double lmax = std::max({std::fabs(lam[0]), std::fabs(lam[1]), std::fabs(lam[2])});
+    if (std::min({lam[0], lam[1], lam[2]}) < -1e-12 * lmax) continue;
+    int nz = 0, vi = -1;
+    for (int i = 0; i < 3; ++i) {
+      if (std::fabs(lam[i]) <= 1e-12 * lmax) ++nz;
+      else vi = i;
+    }
+    double share = 1.0;
+    if (nz == 1) {
+      share = 0.5;
+    } else if (nz == 2) {
+      // interior angle at vertex vi between the great circles to the others
+      const double* A = V[vi];
+      const double* B = V[(vi + 1) % 3];
+      const double* C = V[(vi + 2) % 3];
+      double tb[3], tc[3];
+      const double ab = A[0] * B[0] + A[1] * B[1] + A[2] * B[2];
+      const double ac = A[0] * C[0] + A[1] * C[1] + A[2] * C[2];
+      for (int e = 0; e < 3; ++e) {
+        tb[e] = B[e] - ab * A[e];
+        tc[e] = C[e] - ac * A[e];
+      }
+      const double cr[3] = {tb[1] * tc[2] - tb[2] * tc[1], tb[2] * tc[0] - tb[0] * tc[2],
+                            tb[0] * tc[1] - tb[1] * tc[0]};
+      const double dt = tb[0] * tc[0] + tb[1] * tc[1] + tb[2] * tc[2];
+      share = std::atan2(std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), dt) /
+              (2.0 * M_PI);
+    }
+    double psi[3];
+    basis_values(m, q, om, psi);
+    for (int i = 0; i < a; ++i) out[q * a + i] = fac * share * psi[i];
+    total += share;
+  }
+  return total;
+}
+
 Transfer build_transfer(const AngMesh& fine, const AngMesh& coarse) {
   Transfer t;
   const int a = fine.a;

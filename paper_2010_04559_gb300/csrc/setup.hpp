@@ -53,6 +53,14 @@ void real_harmonics(int N, const double om[3], double* out);
 // X[P*a][(N+1)^2] = int Psi Y (Sec. 4.2)
 std::vector<double> x_table(const AngMesh& m, int N);
 
+// Pencil-beam inflow weights at the beam direction om (Sec. 5.4): the Dirac
+// mass goes to the patches whose closed spherical triangle holds om, each
+// with the fraction of an infinitesimal cap around om that lies in it (1
+// inside, 1/2 on an edge, the interior angle / 2 pi at a vertex); writes
+// out[q a + m] = fac share_q Psi_[q]m(om) for those patches only and returns
+// the sum of the shares (1 when the mesh covers om).
+double beam_weights(const AngMesh& m, const double om[3], double fac, double* out);
+
 // prolongation between nested meshes: parent[f], Pblk[f][a][a] with
 // Pblk[f][k][d] = Psi_{parent,d}(vertex k of f); child ranges per coarse patch
 struct Transfer {

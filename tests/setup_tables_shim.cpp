@@ -77,3 +77,16 @@ void shim_q1(int dim, const double* h, double* N, double* V, double* Fown, doubl
 int shim_invert(int n, const double* A, double* Ainv) { return invert(n, A, Ainv) ? 1 : 0; }
 
 }  // extern "C"
+
+extern "C" {
+
+// Pencil-beam weights at direction om (fac = 1): out [P a] (zero outside the
+// patches holding om); returns the sum of the shares.
+double shim_beam(int level, int aniso, const double* axis, int basis, const double* om,
+                 double* out) {
+  const AngMesh m = build_mesh(mesh_paths(level, aniso, axis), basis);
+  std::memset(out, 0, sizeof(double) * (size_t)m.nadof());
+  return beam_weights(m, om, 1.0, out);
+}
+
+}  // extern "C"

@@ -3,8 +3,9 @@ set-up source (csrc/setup.cpp) is compiled with a test-only shim
 (tests/setup_tables_shim.cpp) and its angular meshes (uniform and
 band-refined), angular matrices, harmonics moments (through the scatter
 matrix S_f = X diag(f_n) X^T, which does not depend on the harmonics' axis
-convention), prolongations, Q1 element matrices and block inverse are
-compared with the oracle's independent construction of the same objects."""
+convention), prolongations, Q1 element matrices, block inverse and
+pencil-beam weights are compared with the oracle's independent construction
+of the same objects."""
 import ctypes
 import os
 import shutil
@@ -144,3 +145,32 @@ def test_block_inverse_is_lapacks(shim):
         assert np.abs(Ai - np.linalg.inv(A)).max() < 1e-13 * np.abs(np.linalg.inv(A)).max()
     Z = np.zeros((4, 4))
     assert shim.shim_invert(4, _p(Z), _p(np.zeros((4, 4)))) == 0     # singular: refused
+
+
+def _beam_directions():
+    import test_oracle_beam as PB
+    out = [("normal+x", np.array([1.0, 0.0, 0.0])), ("normal-z", np.array([0.0, 0.0, -1.0]))]
+    for name, e in PB._general_directions():
+        out.append((name, e / np.linalg.norm(e)))
+    out.append(("inside-other-octant", np.array([-0.3, 0.5, -0.8]) / np.linalg.norm([0.3, 0.5, 0.8])))
+    return out
+
+
+@pytest.mark.parametrize("basis", ["lin", "const"])
+@pytest.mark.parametrize("level,aniso,axis", [(2, 0, None), (3, 1, (1.0, 0.0, 0.0))],
+                         ids=["uniform2", "aniso3x"])
+def test_beam_weights_are_the_oracles(shim, level, aniso, axis, basis):
+    """The library's pencil-beam weights (shares of the Dirac mass times
+    Psi at the beam direction) against the oracle's, for directions at an
+    octahedron vertex, inside a patch, on an edge and at vertices of unequal
+    angles (Sec. 5.4 reading)."""
+    from oracle import transport
+    am = angular.AngularMesh(_oracle_paths(level, aniso, axis), basis)
+    shim.shim_beam.restype = ctypes.c_double
+    for name, e in _beam_directions():
+        out = np.zeros(am.nadof)
+        total = shim.shim_beam(level, aniso, _axis(axis or (0.0, 0.0, 1.0)),
+                               1 if basis == "lin" else 0, _p(np.ascontiguousarray(e)), _p(out))
+        ref = transport.beam_weights(am, e).reshape(-1)
+        assert abs(total - 1.0) < 1e-12, name
+        assert np.abs(out - ref).max() < 1e-13, name
