@@ -90,3 +90,13 @@ double shim_beam(int level, int aniso, const double* axis, int basis, const doub
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// Q1 face mass on the faces normal to each axis: facemass [dim][s/2][s/2].
+void shim_q1_facemass(int dim, const double* h, double* out) {
+  const Q1 q = build_q1(dim, h);
+  std::memcpy(out, q.facemass.data(), q.facemass.size() * sizeof(double));
+}
+
+}  // extern "C"

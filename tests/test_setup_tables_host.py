@@ -136,6 +136,34 @@ def test_q1_matrices_are_the_oracles(shim, dim, h):
         assert np.abs(lib - orc).max() < 1e-15
 
 
+@pytest.mark.parametrize("dim,h", [(2, (0.3, 0.7)), (3, (0.2, 0.5, 0.9))])
+def test_q1_face_mass_is_the_oracles_face_integral(shim, dim, h):
+    """facemass[xi][j'][j]: the integral over a face normal to xi of the
+    products of the face's nodal functions (j', j: nodes of the face, the bit
+    of axis xi inserted), which the kernels use for the upwind coupling."""
+    c = Q1Cell(list(h))
+    hs = 2 ** (dim - 1)
+    fm = np.zeros((dim, hs, hs))
+    shim.shim_q1_facemass(dim, (ctypes.c_double * 3)(*(list(h) + [1.0] * (3 - dim))), _p(fm))
+
+    def face_node(j, axis, bit):
+        lo = j & ((1 << axis) - 1)
+        return lo | (bit << axis) | ((j >> axis) << (axis + 1))
+    for xi in range(dim):
+        for jp in range(hs):
+            for j in range(hs):
+                own = c.Fown[2 * xi][face_node(jp, xi, 0), face_node(j, xi, 0)]
+                nb = c.Fnb[2 * xi][face_node(jp, xi, 0), face_node(j, xi, 1)]
+                assert abs(fm[xi, jp, j] - own) < 1e-15 and abs(fm[xi, jp, j] - nb) < 1e-15
+
+
+@pytest.mark.parametrize("lmax", [4, 5, 6])
+def test_band_refined_hierarchies_up_to_the_papers_largest(shim, lmax):
+    """The library's band-refined meshes about z for l_max = 4, 5, 6 (the
+    paper's 128, 440 and 1388 patches) equal the oracle's path for path."""
+    assert _lib_paths(shim, lmax, 1, (0.0, 0.0, 1.0)) == angular.aniso_paths(lmax)
+
+
 def test_block_inverse_is_lapacks(shim):
     rng = np.random.default_rng(7)
     for n in (1, 3, 12, 24, 48):
